@@ -1,0 +1,624 @@
+/*
+ * oracle.c -- plain, slow FP64 reference for the differentiable Gaussian rasterizer.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path (the CUDA library and its
+ * Python binding) may link, import or call this file; only the tests, the smoke check
+ * and the CPU-baseline leg of the benchmark use it.  It shares no code, header, table
+ * or constant generator with the CUDA path.
+ *
+ * What it computes (the plain definition, no tiling, no sort of keys, no atomics):
+ *   Sec. 3.1 of the paper: each Gaussian has a mean mu, covariance Sigma = (RS)(RS)^T
+ *   with R a rotation (from a quaternion) and S a diagonal scale, a colour c (degree-0
+ *   spherical harmonics: the colour itself) and an opacity o; the Gaussians are
+ *   projected onto the image plane and rasterized, and a reconstruction loss drives
+ *   the parameters.  Sec. 3.2 (Eq. 3): colour and opacity are constant over time; the
+ *   mean is a function of t (here the linear drift mu_t = mu_0 + t v).  Sec. 3.4: the
+ *   camera has constant pinhole intrinsics (focal length, principal point) and per-frame
+ *   extrinsics (R, t).  The paper defers the rasterizer itself to prior 3DGS work, so
+ *   the following readings are fixed here (each is a parameter with a default):
+ *     - quaternion (w,x,y,z), normalised before use; scale = exp(log_scale);
+ *       opacity = sigmoid(logit); colour used raw (no SH constant, no clamp);
+ *     - world->camera x_c = R x_w + t; u = fx x/z + cx, v = fy y/z + cy; pixel (i,j)
+ *       is sampled at its centre (i+0.5, j+0.5); near cull z <= znear (0.2);
+ *     - EWA: Sigma2 = J W Sigma3 W^T J^T + eps2d I (eps2d = 0.3), J the pinhole
+ *       Jacobian at x_c, no guard band; conic = Sigma2^{-1};
+ *     - alpha = min(alpha_max, o exp(-power)), power = 1/2 d^T conic d; Gaussians with
+ *       alpha < alpha_min (1/255) are skipped;
+ *     - front to back in depth order (ties by Gaussian index); a Gaussian is composited
+ *       and then compositing stops if T < T_stop (1e-4); output C + T bg;
+ *     - binning extent of a Gaussian: half-widths k sqrt(Sigma2_xx), k sqrt(Sigma2_yy)
+ *       with k = sqrt(2 ln 255), the exact axis-aligned bound of the alpha >= 1/255
+ *       region, so the image does not depend on the tile shape.
+ *   The backward pass is the analytic adjoint of exactly this function.  A "smooth
+ *   mode" (alpha_min = 0, T_stop = 0, alpha_max = inf) makes the image a smooth
+ *   function of the parameters so central finite differences apply.
+ *
+ * Ambiguity flags: where the CUDA path (FP32) may legitimately take the other side of a
+ * hard threshold, the pixel is flagged: bit 0 an alpha within amb_alpha_rel of
+ * alpha_min, bit 1 a transmittance within amb_T_rel of T_stop, bit 2 two consecutive
+ * contributors whose depths differ by less than amb_depth_rel (relative).
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int32_t W, H;
+    double fx, fy, cx, cy;
+    double R[9]; /* row-major, world -> camera */
+    double t[3];
+    double time;
+} orc_camera;
+
+typedef struct {
+    double alpha_min, alpha_max, T_stop, eps2d, znear, ext_k;
+    double bg[3];
+    double amb_alpha_rel, amb_T_rel, amb_depth_rel;
+} orc_params;
+
+typedef struct {
+    int64_t N;
+    const double *mean, *vel, *log_scale, *quat, *logit, *rgb; /* SoA [k][N]; vel may be NULL */
+} orc_gaussians;
+
+/* number of per-Gaussian parameter gradients: mean 3, vel 3, log_scale 3, quat 4, logit 1, rgb 3 */
+#define ORC_NGRAD 17
+/* screen-space gradient record: du, dv, dA, dB, dC, do, dr, dg, db */
+#define ORC_N2D 9
+/* projection output record stride */
+#define ORC_PROJ 20
+
+/* Per-Gaussian projection with every intermediate the adjoint needs. */
+typedef struct {
+    int valid;
+    double mu[3];        /* world mean at the camera's time */
+    double xc[3];        /* camera-space mean */
+    double s[3];         /* scales */
+    double qn[4];        /* normalised quaternion */
+    double qnorm;
+    double Rq[9];        /* rotation of the Gaussian */
+    double M[9];         /* Rq diag(s) */
+    double S3[9];        /* world covariance */
+    double J[6];         /* 2x3 */
+    double T[6];         /* J W, 2x3 */
+    double S2[3];        /* a, b, c of Sigma2 (with eps2d) */
+    double Q[3];         /* conic A, B, C */
+    double u, v, ex, ey, o;
+    double c[3];
+} orc_proj;
+
+static void quat_to_rot(const double q[4], double R[9]) {
+    double w = q[0], x = q[1], y = q[2], z = q[3];
+    R[0] = 1 - 2 * (y * y + z * z); R[1] = 2 * (x * y - w * z);     R[2] = 2 * (x * z + w * y);
+    R[3] = 2 * (x * y + w * z);     R[4] = 1 - 2 * (x * x + z * z); R[5] = 2 * (y * z - w * x);
+    R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
+}
+
+/* Projection of Gaussian i under the camera (Sec. 3.1 parameterisation, EWA splatting). */
+static void project_one(const orc_gaussians *g, int64_t i, const orc_camera *cam,
+                        const orc_params *p, orc_proj *pr) {
+    int64_t N = g->N;
+    memset(pr, 0, sizeof(*pr));
+    for (int k = 0; k < 3; k++) {
+        pr->mu[k] = g->mean[k * N + i] + (g->vel ? cam->time * g->vel[k * N + i] : 0.0);
+        pr->s[k] = exp(g->log_scale[k * N + i]);
+        pr->c[k] = g->rgb[k * N + i];
+    }
+    double qq = 0;
+    for (int k = 0; k < 4; k++) qq += g->quat[k * N + i] * g->quat[k * N + i];
+    pr->qnorm = sqrt(qq);
+    for (int k = 0; k < 4; k++) pr->qn[k] = g->quat[k * N + i] / pr->qnorm;
+    pr->o = 1.0 / (1.0 + exp(-g->logit[i]));
+    quat_to_rot(pr->qn, pr->Rq);
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) pr->M[r * 3 + c] = pr->Rq[r * 3 + c] * pr->s[c];
+    for (int r = 0; r < 3; r++)
+        for (int c = 0; c < 3; c++) {
+            double acc = 0;
+            for (int k = 0; k < 3; k++) acc += pr->M[r * 3 + k] * pr->M[c * 3 + k];
+            pr->S3[r * 3 + c] = acc;
+        }
+    const double *W = cam->R;
+    for (int r = 0; r < 3; r++)
+        pr->xc[r] = W[r * 3 + 0] * pr->mu[0] + W[r * 3 + 1] * pr->mu[1] + W[r * 3 + 2] * pr->mu[2] + cam->t[r];
+    double x = pr->xc[0], y = pr->xc[1], z = pr->xc[2];
+    if (!(z > p->znear)) { pr->valid = 0; return; }
+    pr->J[0] = cam->fx / z; pr->J[1] = 0;            pr->J[2] = -cam->fx * x / (z * z);
+    pr->J[3] = 0;           pr->J[4] = cam->fy / z;  pr->J[5] = -cam->fy * y / (z * z);
+    for (int r = 0; r < 2; r++)
+        for (int c = 0; c < 3; c++) {
+            double acc = 0;
+            for (int k = 0; k < 3; k++) acc += pr->J[r * 3 + k] * W[k * 3 + c];
+            pr->T[r * 3 + c] = acc;
+        }
+    double S2[4];
+    for (int r = 0; r < 2; r++)
+        for (int c = 0; c < 2; c++) {
+            double acc = 0;
+            for (int k = 0; k < 3; k++)
+                for (int l = 0; l < 3; l++) acc += pr->T[r * 3 + k] * pr->S3[k * 3 + l] * pr->T[c * 3 + l];
+            S2[r * 2 + c] = acc;
+        }
+    double a = S2[0] + p->eps2d, b = 0.5 * (S2[1] + S2[2]), c = S2[3] + p->eps2d;
+    pr->S2[0] = a; pr->S2[1] = b; pr->S2[2] = c;
+    double det = a * c - b * b;
+    if (!(det > 0)) { pr->valid = 0; return; }
+    pr->Q[0] = c / det; pr->Q[1] = -b / det; pr->Q[2] = a / det;
+    pr->u = cam->fx * x / z + cam->cx;
+    pr->v = cam->fy * y / z + cam->cy;
+    pr->ex = p->ext_k * sqrt(a);
+    pr->ey = p->ext_k * sqrt(c);
+    pr->valid = 1;
+}
+
+/* Exported: projection records, ORC_PROJ doubles per Gaussian:
+ * valid, depth, u, v, a, b, c, A, B, C, ex, ey, o, xc0, xc1, xc2, r, g, b, 0 */
+int orc_project(const orc_gaussians *g, const orc_camera *cam, const orc_params *p, double *out) {
+    for (int64_t i = 0; i < g->N; i++) {
+        orc_proj pr;
+        project_one(g, i, cam, p, &pr);
+        double *o = out + i * ORC_PROJ;
+        o[0] = pr.valid; o[1] = pr.xc[2]; o[2] = pr.u; o[3] = pr.v;
+        o[4] = pr.S2[0]; o[5] = pr.S2[1]; o[6] = pr.S2[2];
+        o[7] = pr.Q[0]; o[8] = pr.Q[1]; o[9] = pr.Q[2];
+        o[10] = pr.ex; o[11] = pr.ey; o[12] = pr.o;
+        o[13] = pr.xc[0]; o[14] = pr.xc[1]; o[15] = pr.xc[2];
+        o[16] = pr.c[0]; o[17] = pr.c[1]; o[18] = pr.c[2]; o[19] = 0;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Per-pixel front-to-back compositing over all Gaussians.                              */
+/* ------------------------------------------------------------------------------------ */
+
+typedef struct {
+    double depth;
+    int64_t idx;
+    double alpha, araw, power, dx, dy;
+} orc_cand;
+
+static int cand_cmp(const void *pa, const void *pb) {
+    const orc_cand *a = (const orc_cand *)pa, *b = (const orc_cand *)pb;
+    if (a->depth < b->depth) return -1;
+    if (a->depth > b->depth) return 1;
+    return (a->idx < b->idx) ? -1 : (a->idx > b->idx);
+}
+
+/* Contributor of a pixel, in front-to-back order, with the transmittance in front of it. */
+typedef struct {
+    int64_t idx;
+    double alpha, araw, power, dx, dy, Tin;
+} orc_contrib;
+
+typedef struct {
+    double C[3];
+    double T;
+    int64_t last;
+    int32_t amb;
+    int32_t n;        /* number of contributors */
+} orc_pixel_result;
+
+/* Walk one pixel.  cand/contrib are caller scratch of capacity N. */
+static void render_pixel(const orc_proj *pr, int64_t N, const orc_params *p, double px, double py,
+                         orc_cand *cand, orc_contrib *contrib, orc_pixel_result *res) {
+    int64_t nc = 0;
+    double a_lo = p->alpha_min * (1.0 - p->amb_alpha_rel);
+    for (int64_t i = 0; i < N; i++) {
+        const orc_proj *q = &pr[i];
+        if (!q->valid) continue;
+        double dx = q->u - px, dy = q->v - py;
+        double power = 0.5 * (q->Q[0] * dx * dx + q->Q[2] * dy * dy) + q->Q[1] * dx * dy;
+        double araw = q->o * exp(-power);
+        double alpha = araw < p->alpha_max ? araw : p->alpha_max;
+        if (!(alpha >= a_lo)) continue;
+        orc_cand *c = &cand[nc++];
+        c->depth = q->xc[2]; c->idx = i; c->alpha = alpha; c->araw = araw;
+        c->power = power; c->dx = dx; c->dy = dy;
+    }
+    qsort(cand, (size_t)nc, sizeof(orc_cand), cand_cmp);
+    double T = 1.0, C[3] = {0, 0, 0};
+    int64_t last = -1;
+    int32_t amb = 0, n = 0;
+    double prev_depth = -1.0;
+    for (int64_t k = 0; k < nc; k++) {
+        const orc_cand *c = &cand[k];
+        if (p->alpha_min > 0 && fabs(c->alpha - p->alpha_min) <= p->amb_alpha_rel * p->alpha_min) amb |= 1;
+        if (c->alpha < p->alpha_min) continue;
+        if (n > 0 && fabs(c->depth - prev_depth) <= p->amb_depth_rel * fabs(c->depth)) amb |= 4;
+        prev_depth = c->depth;
+        const orc_proj *q = &pr[c->idx];
+        if (contrib) {
+            orc_contrib *o = &contrib[n];
+            o->idx = c->idx; o->alpha = c->alpha; o->araw = c->araw; o->power = c->power;
+            o->dx = c->dx; o->dy = c->dy; o->Tin = T;
+        }
+        n++;
+        for (int ch = 0; ch < 3; ch++) C[ch] += q->c[ch] * c->alpha * T;
+        T *= (1.0 - c->alpha);
+        last = c->idx;
+        if (p->T_stop > 0 && fabs(T - p->T_stop) <= p->amb_T_rel * p->T_stop) amb |= 2;
+        if (T < p->T_stop) break;
+    }
+    for (int ch = 0; ch < 3; ch++) res->C[ch] = C[ch] + T * p->bg[ch];
+    res->T = T; res->last = last; res->amb = amb; res->n = n;
+}
+
+typedef struct {
+    const orc_proj *pr;
+    int64_t N;
+    const orc_params *p;
+    int64_t npix;
+    const int32_t *px, *py;
+    double *out_rgb, *out_T;
+    int64_t *out_last;
+    int32_t *out_amb, *out_n;
+    int tid, nthreads;
+    int err;
+} render_job;
+
+static void *render_worker(void *arg) {
+    render_job *j = (render_job *)arg;
+    orc_cand *cand = (orc_cand *)malloc(sizeof(orc_cand) * (size_t)(j->N > 0 ? j->N : 1));
+    if (!cand) { j->err = 1; return NULL; }
+    for (int64_t k = j->tid; k < j->npix; k += j->nthreads) {
+        orc_pixel_result r;
+        render_pixel(j->pr, j->N, j->p, j->px[k] + 0.5, j->py[k] + 0.5, cand, NULL, &r);
+        for (int ch = 0; ch < 3; ch++) j->out_rgb[k * 3 + ch] = r.C[ch];
+        j->out_T[k] = r.T;
+        j->out_last[k] = r.last;
+        if (j->out_amb) j->out_amb[k] = r.amb;
+        if (j->out_n) j->out_n[k] = r.n;
+    }
+    free(cand);
+    return NULL;
+}
+
+static orc_proj *project_all(const orc_gaussians *g, const orc_camera *cam, const orc_params *p) {
+    orc_proj *pr = (orc_proj *)malloc(sizeof(orc_proj) * (size_t)(g->N > 0 ? g->N : 1));
+    if (!pr) return NULL;
+    for (int64_t i = 0; i < g->N; i++) project_one(g, i, cam, p, &pr[i]);
+    return pr;
+}
+
+/* Exported: render the listed pixels (x = px[k], y = py[k]).
+ * out_rgb [npix][3], out_T [npix], out_last [npix] (Gaussian index, -1 if none),
+ * out_amb [npix] (ambiguity bits, may be NULL), out_n [npix] (contributors, may be NULL). */
+int orc_render(const orc_gaussians *g, const orc_camera *cam, const orc_params *p,
+               int64_t npix, const int32_t *px, const int32_t *py,
+               double *out_rgb, double *out_T, int64_t *out_last, int32_t *out_amb, int32_t *out_n,
+               int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    orc_proj *pr = project_all(g, cam, p);
+    if (!pr) return 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    render_job *jobs = (render_job *)malloc(sizeof(render_job) * (size_t)nthreads);
+    for (int t = 0; t < nthreads; t++) {
+        render_job jb = {pr, g->N, p, npix, px, py, out_rgb, out_T, out_last, out_amb, out_n, t, nthreads, 0};
+        jobs[t] = jb;
+        pthread_create(&th[t], NULL, render_worker, &jobs[t]);
+    }
+    int err = 0;
+    for (int t = 0; t < nthreads; t++) { pthread_join(th[t], NULL); err |= jobs[t].err; }
+    free(th); free(jobs); free(pr);
+    return err;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Analytic adjoint.                                                                     */
+/* ------------------------------------------------------------------------------------ */
+
+/* Chain rule from a screen-space gradient (du, dv, dA, dB, dC, do, dr, dg, db) of one
+ * Gaussian to its 17 raw-parameter gradients (mean, vel, log_scale, quat, logit, rgb). */
+static void chain_rule(const orc_proj *q, const orc_camera *cam, const double d2[ORC_N2D], double out[ORC_NGRAD]) {
+    double gu = d2[0], gv = d2[1], gA = d2[2], gB = d2[3], gC = d2[4], go = d2[5];
+    memset(out, 0, sizeof(double) * ORC_NGRAD);
+    /* colour */
+    out[14] = d2[6]; out[15] = d2[7]; out[16] = d2[8];
+    /* opacity = sigmoid(logit) */
+    out[13] = go * q->o * (1.0 - q->o);
+    /* conic (A,B,C) = inverse of Sigma2 (a,b,c), written out entry by entry */
+    double a = q->S2[0], b = q->S2[1], c = q->S2[2];
+    double D = a * c - b * b, D2 = D * D;
+    double dA_da = -c * c / D2, dA_db = 2 * b * c / D2, dA_dc = -b * b / D2;
+    double dB_da = b * c / D2,  dB_db = -(a * c + b * b) / D2, dB_dc = a * b / D2;
+    double dC_da = -b * b / D2, dC_db = 2 * a * b / D2, dC_dc = -a * a / D2;
+    double ga = gA * dA_da + gB * dB_da + gC * dC_da;
+    double gb = gA * dA_db + gB * dB_db + gC * dC_db;
+    double gc = gA * dA_dc + gB * dB_dc + gC * dC_dc;
+    /* Sigma2 = T S3 T^T (+eps): a = T0 S3 T0^T, b = T0 S3 T1^T, c = T1 S3 T1^T */
+    double G2[4] = {ga, 0.5 * gb, 0.5 * gb, gc};
+    double gS3[9], gT[6];
+    for (int k = 0; k < 3; k++)
+        for (int l = 0; l < 3; l++) {
+            double acc = 0;
+            for (int r = 0; r < 2; r++)
+                for (int s = 0; s < 2; s++) acc += q->T[r * 3 + k] * G2[r * 2 + s] * q->T[s * 3 + l];
+            gS3[k * 3 + l] = acc;
+        }
+    for (int r = 0; r < 2; r++)
+        for (int k = 0; k < 3; k++) {
+            double acc = 0;
+            for (int s = 0; s < 2; s++)
+                for (int l = 0; l < 3; l++) acc += G2[r * 2 + s] * q->T[s * 3 + l] * q->S3[l * 3 + k];
+            gT[r * 3 + k] = 2.0 * acc;
+        }
+    /* T = J W  ->  dJ = dT W^T */
+    const double *W = cam->R;
+    double gJ[6];
+    for (int r = 0; r < 2; r++)
+        for (int k = 0; k < 3; k++) {
+            double acc = 0;
+            for (int l = 0; l < 3; l++) acc += gT[r * 3 + l] * W[k * 3 + l];
+            gJ[r * 3 + k] = acc;
+        }
+    double x = q->xc[0], y = q->xc[1], z = q->xc[2];
+    double fx = cam->fx, fy = cam->fy;
+    double gx = 0, gy = 0, gz = 0;
+    /* u = fx x/z + cx, v = fy y/z + cy */
+    gx += gu * fx / z;
+    gz += -gu * fx * x / (z * z);
+    gy += gv * fy / z;
+    gz += -gv * fy * y / (z * z);
+    /* J00 = fx/z, J02 = -fx x/z^2, J11 = fy/z, J12 = -fy y/z^2 */
+    gz += gJ[0] * (-fx / (z * z));
+    gx += gJ[2] * (-fx / (z * z));
+    gz += gJ[2] * (2.0 * fx * x / (z * z * z));
+    gz += gJ[4] * (-fy / (z * z));
+    gy += gJ[5] * (-fy / (z * z));
+    gz += gJ[5] * (2.0 * fy * y / (z * z * z));
+    /* x_c = W mu + t  ->  dmu = W^T dxc */
+    double gmu[3];
+    for (int k = 0; k < 3; k++) gmu[k] = W[0 * 3 + k] * gx + W[1 * 3 + k] * gy + W[2 * 3 + k] * gz;
+    for (int k = 0; k < 3; k++) { out[k] = gmu[k]; out[3 + k] = cam->time * gmu[k]; }
+    /* S3 = M M^T  ->  dM = (gS3 + gS3^T) M */
+    double gM[9];
+    for (int r = 0; r < 3; r++)
+        for (int c2 = 0; c2 < 3; c2++) {
+            double acc = 0;
+            for (int k = 0; k < 3; k++) acc += (gS3[r * 3 + k] + gS3[k * 3 + r]) * q->M[k * 3 + c2];
+            gM[r * 3 + c2] = acc;
+        }
+    /* M = Rq diag(s) */
+    double gR[9];
+    for (int r = 0; r < 3; r++)
+        for (int c2 = 0; c2 < 3; c2++) gR[r * 3 + c2] = gM[r * 3 + c2] * q->s[c2];
+    for (int c2 = 0; c2 < 3; c2++) {
+        double acc = 0;
+        for (int r = 0; r < 3; r++) acc += gM[r * 3 + c2] * q->Rq[r * 3 + c2];
+        out[6 + c2] = acc * q->s[c2]; /* d/dlog_s = s d/ds */
+    }
+    /* Rq(qn): partial derivatives of each entry w.r.t. w, x, y, z */
+    double w = q->qn[0], qx = q->qn[1], qy = q->qn[2], qz = q->qn[3];
+    double dR[4][9] = {
+        /* d/dw */ {0, -2 * qz, 2 * qy, 2 * qz, 0, -2 * qx, -2 * qy, 2 * qx, 0},
+        /* d/dx */ {0, 2 * qy, 2 * qz, 2 * qy, -4 * qx, -2 * w, 2 * qz, 2 * w, -4 * qx},
+        /* d/dy */ {-4 * qy, 2 * qx, 2 * w, 2 * qx, 0, 2 * qz, -2 * w, 2 * qz, -4 * qy},
+        /* d/dz */ {-4 * qz, -2 * w, 2 * qx, 2 * w, -4 * qz, 2 * qy, 2 * qx, 2 * qy, 0},
+    };
+    double gqn[4];
+    for (int k = 0; k < 4; k++) {
+        double acc = 0;
+        for (int e = 0; e < 9; e++) acc += dR[k][e] * gR[e];
+        gqn[k] = acc;
+    }
+    /* qn = q/|q| */
+    double dot = gqn[0] * q->qn[0] + gqn[1] * q->qn[1] + gqn[2] * q->qn[2] + gqn[3] * q->qn[3];
+    for (int k = 0; k < 4; k++) out[9 + k] = (gqn[k] - q->qn[k] * dot) / q->qnorm;
+}
+
+/* Per-pixel adjoint: fills contribution records (idx, 9-vector) for every contributor. */
+static int64_t pixel_adjoint(const orc_proj *pr, int64_t N, const orc_params *p, double px, double py,
+                             const double g[3], orc_cand *cand, orc_contrib *contrib,
+                             int64_t *out_idx, double *out_d2) {
+    orc_pixel_result res;
+    render_pixel(pr, N, p, px, py, cand, contrib, &res);
+    double S[3];
+    for (int ch = 0; ch < 3; ch++) S[ch] = res.T * p->bg[ch];
+    for (int32_t k = res.n - 1; k >= 0; k--) {
+        const orc_contrib *c = &contrib[k];
+        const orc_proj *q = &pr[c->idx];
+        double w = c->alpha * c->Tin;
+        double *d = out_d2 + (int64_t)k * ORC_N2D;
+        memset(d, 0, sizeof(double) * ORC_N2D);
+        double dalpha = 0;
+        for (int ch = 0; ch < 3; ch++) {
+            d[6 + ch] = w * g[ch];
+            dalpha += g[ch] * (q->c[ch] * c->Tin - S[ch] / (1.0 - c->alpha));
+        }
+        for (int ch = 0; ch < 3; ch++) S[ch] += q->c[ch] * w;
+        if (c->araw < p->alpha_max) {
+            double G = exp(-c->power);
+            d[5] = dalpha * G;                       /* d alpha / d o = exp(-power) */
+            double dpow = -dalpha * c->araw;         /* d alpha / d power = -alpha */
+            d[2] = dpow * 0.5 * c->dx * c->dx;
+            d[3] = dpow * c->dx * c->dy;
+            d[4] = dpow * 0.5 * c->dy * c->dy;
+            d[0] = dpow * (q->Q[0] * c->dx + q->Q[1] * c->dy);
+            d[1] = dpow * (q->Q[1] * c->dx + q->Q[2] * c->dy);
+        }
+        out_idx[k] = c->idx;
+    }
+    return res.n;
+}
+
+typedef struct {
+    int64_t n, cap;
+    int64_t *idx;
+    double *d2;
+} contrib_list;
+
+static int list_push(contrib_list *L, int64_t n_new, const int64_t *idx, const double *d2) {
+    if (L->n + n_new > L->cap) {
+        int64_t nc = L->cap ? L->cap : 1024;
+        while (nc < L->n + n_new) nc *= 2;
+        int64_t *ni = (int64_t *)realloc(L->idx, sizeof(int64_t) * (size_t)nc);
+        if (!ni) return 1;
+        L->idx = ni;
+        double *nd = (double *)realloc(L->d2, sizeof(double) * ORC_N2D * (size_t)nc);
+        if (!nd) return 1;
+        L->d2 = nd;
+        L->cap = nc;
+    }
+    memcpy(L->idx + L->n, idx, sizeof(int64_t) * (size_t)n_new);
+    memcpy(L->d2 + L->n * ORC_N2D, d2, sizeof(double) * ORC_N2D * (size_t)n_new);
+    L->n += n_new;
+    return 0;
+}
+
+typedef struct {
+    const orc_proj *pr;
+    int64_t N;
+    const orc_params *p;
+    const orc_camera *cam;
+    int64_t npix;
+    const int32_t *px, *py;
+    const double *dL_dC;
+    contrib_list *lists; /* one per thread */
+    double *grad, *gabs, *grad2d;
+    int tid, nthreads;
+    int err;
+} bwd_job;
+
+static void *bwd_pixels_worker(void *arg) {
+    bwd_job *j = (bwd_job *)arg;
+    size_t n1 = (size_t)(j->N > 0 ? j->N : 1);
+    orc_cand *cand = (orc_cand *)malloc(sizeof(orc_cand) * n1);
+    orc_contrib *contrib = (orc_contrib *)malloc(sizeof(orc_contrib) * n1);
+    int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * n1);
+    double *d2 = (double *)malloc(sizeof(double) * ORC_N2D * n1);
+    if (!cand || !contrib || !idx || !d2) { j->err = 1; goto done; }
+    for (int64_t k = j->tid; k < j->npix; k += j->nthreads) {
+        const double *g = j->dL_dC + k * 3;
+        if (g[0] == 0 && g[1] == 0 && g[2] == 0) continue;
+        int64_t n = pixel_adjoint(j->pr, j->N, j->p, j->px[k] + 0.5, j->py[k] + 0.5, g, cand, contrib, idx, d2);
+        if (list_push(&j->lists[j->tid], n, idx, d2)) { j->err = 1; break; }
+    }
+done:
+    free(cand); free(contrib); free(idx); free(d2);
+    return NULL;
+}
+
+/* Gaussians are partitioned over threads (i % nthreads == tid); each thread scans every
+ * contribution list and accumulates the chain-ruled contributions of its own Gaussians. */
+static void *bwd_accum_worker(void *arg) {
+    bwd_job *j = (bwd_job *)arg;
+    int64_t N = j->N;
+    for (int t = 0; t < j->nthreads; t++) {
+        const contrib_list *L = &j->lists[t];
+        for (int64_t e = 0; e < L->n; e++) {
+            int64_t i = L->idx[e];
+            if (i % j->nthreads != j->tid) continue;
+            const double *d = L->d2 + e * ORC_N2D;
+            double out[ORC_NGRAD];
+            chain_rule(&j->pr[i], j->cam, d, out);
+            for (int k = 0; k < ORC_NGRAD; k++) {
+                j->grad[k * N + i] += out[k];
+                if (j->gabs) j->gabs[k * N + i] += fabs(out[k]);
+            }
+            if (j->grad2d)
+                for (int k = 0; k < ORC_N2D; k++) j->grad2d[k * N + i] += d[k];
+        }
+    }
+    return NULL;
+}
+
+/* Exported: gradient of L = sum_k dL_dC[k] . C(pixel k) over the listed pixels.
+ * grad [17][N] (overwritten), gabs [17][N] sum of |per-pixel contributions| (may be NULL),
+ * grad2d [9][N] screen-space gradients (may be NULL).  If the Gaussians have no velocity,
+ * the vel rows are still written (time * dmu) and may be ignored. */
+int orc_render_bwd(const orc_gaussians *g, const orc_camera *cam, const orc_params *p,
+                   int64_t npix, const int32_t *px, const int32_t *py, const double *dL_dC,
+                   double *grad, double *gabs, double *grad2d, int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    int64_t N = g->N;
+    memset(grad, 0, sizeof(double) * ORC_NGRAD * (size_t)N);
+    if (gabs) memset(gabs, 0, sizeof(double) * ORC_NGRAD * (size_t)N);
+    if (grad2d) memset(grad2d, 0, sizeof(double) * ORC_N2D * (size_t)N);
+    orc_proj *pr = project_all(g, cam, p);
+    if (!pr) return 1;
+    contrib_list *lists = (contrib_list *)calloc((size_t)nthreads, sizeof(contrib_list));
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    bwd_job *jobs = (bwd_job *)malloc(sizeof(bwd_job) * (size_t)nthreads);
+    for (int t = 0; t < nthreads; t++) {
+        bwd_job jb = {pr, N, p, cam, npix, px, py, dL_dC, lists, grad, gabs, grad2d, t, nthreads, 0};
+        jobs[t] = jb;
+        pthread_create(&th[t], NULL, bwd_pixels_worker, &jobs[t]);
+    }
+    int err = 0;
+    for (int t = 0; t < nthreads; t++) { pthread_join(th[t], NULL); err |= jobs[t].err; }
+    if (!err) {
+        for (int t = 0; t < nthreads; t++) pthread_create(&th[t], NULL, bwd_accum_worker, &jobs[t]);
+        for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
+    }
+    for (int t = 0; t < nthreads; t++) { free(lists[t].idx); free(lists[t].d2); }
+    free(lists); free(th); free(jobs); free(pr);
+    return err;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Tile binning references (the integer stage).                                          */
+/* ------------------------------------------------------------------------------------ */
+
+/* FP32 binning reference: the pixel-centre range [x0, x1] of the extent box
+ * [u - ex, u + ex] is x0 = ceil((u - ex) - 0.5), x1 = floor((u + ex) - 0.5), each
+ * operation rounded to FP32, clipped to the image; the tile range is x0/TW .. x1/TW.
+ * count = number of tiles in the rectangle, 0 if empty or invalid.
+ * rect [n][4] = tx0, ty0, tx1, ty1 (0, 0, -1, -1 when empty). */
+int orc_bin_f32(int64_t n, const float *u, const float *v, const float *ex, const float *ey,
+                const uint8_t *valid, int32_t W, int32_t H, int32_t TW, int32_t TH,
+                int32_t *count, int32_t *rect) {
+    for (int64_t i = 0; i < n; i++) {
+        int32_t *r = rect + i * 4;
+        count[i] = 0; r[0] = 0; r[1] = 0; r[2] = -1; r[3] = -1;
+        if (!valid[i]) continue;
+        /* built with -ffp-contract=off: every operation below rounds to FP32 */
+        float lo_x = u[i] - ex[i], hi_x = u[i] + ex[i];
+        float lo_y = v[i] - ey[i], hi_y = v[i] + ey[i];
+        float sx0 = lo_x - 0.5f, sx1 = hi_x - 0.5f, sy0 = lo_y - 0.5f, sy1 = hi_y - 0.5f;
+        float x0 = ceilf(sx0), x1 = floorf(sx1), y0 = ceilf(sy0), y1 = floorf(sy1);
+        if (x0 < 0.0f) x0 = 0.0f;
+        if (y0 < 0.0f) y0 = 0.0f;
+        if (x1 > (float)(W - 1)) x1 = (float)(W - 1);
+        if (y1 > (float)(H - 1)) y1 = (float)(H - 1);
+        if (!(x0 <= x1) || !(y0 <= y1)) continue;
+        int32_t tx0 = (int32_t)x0 / TW, tx1 = (int32_t)x1 / TW;
+        int32_t ty0 = (int32_t)y0 / TH, ty1 = (int32_t)y1 / TH;
+        r[0] = tx0; r[1] = ty0; r[2] = tx1; r[3] = ty1;
+        count[i] = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+    }
+    return 0;
+}
+
+/* FP64 version of the same rule, for the end-to-end comparison against the FP64
+ * projection (mismatches allowed only within a small margin of a pixel-centre edge). */
+int orc_bin_f64(int64_t n, const double *u, const double *v, const double *ex, const double *ey,
+                const uint8_t *valid, int32_t W, int32_t H, int32_t TW, int32_t TH,
+                int32_t *count, int32_t *rect, double *edge_margin) {
+    for (int64_t i = 0; i < n; i++) {
+        int32_t *r = rect + i * 4;
+        count[i] = 0; r[0] = 0; r[1] = 0; r[2] = -1; r[3] = -1;
+        edge_margin[i] = INFINITY;
+        if (!valid[i]) continue;
+        double s[4] = {u[i] - ex[i] - 0.5, u[i] + ex[i] - 0.5, v[i] - ey[i] - 0.5, v[i] + ey[i] - 0.5};
+        double m = INFINITY;
+        for (int k = 0; k < 4; k++) {
+            double d = fabs(s[k] - nearbyint(s[k]));
+            if (d < m) m = d;
+        }
+        edge_margin[i] = m;
+        double x0 = ceil(s[0]), x1 = floor(s[1]), y0 = ceil(s[2]), y1 = floor(s[3]);
+        if (x0 < 0.0) x0 = 0.0;
+        if (y0 < 0.0) y0 = 0.0;
+        if (x1 > (double)(W - 1)) x1 = (double)(W - 1);
+        if (y1 > (double)(H - 1)) y1 = (double)(H - 1);
+        if (!(x0 <= x1) || !(y0 <= y1)) continue;
+        int32_t tx0 = (int32_t)x0 / TW, tx1 = (int32_t)x1 / TW;
+        int32_t ty0 = (int32_t)y0 / TH, ty1 = (int32_t)y1 / TH;
+        r[0] = tx0; r[1] = ty0; r[2] = tx1; r[3] = ty1;
+        count[i] = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
+    }
+    return 0;
+}
