@@ -1,0 +1,525 @@
+#!/usr/bin/env python
+"""Benchmark of the differentiable Gaussian rasterizer: forward + backward megapixels/s
+on a 960x540 frame with 200,000 Gaussians (the plain per-frame renderer), with the
+batched, CUDA-graph-captured multi-frame form of the same workload reported beside it.
+
+One step = the whole hot path on one synthetic frame: projection -> tile binning ->
+depth and tile radix sorts -> compositing forward -> L2 loss gradient -> compositing
+backward -> projection backward, through the C ABI of libgv on the device-resident
+inputs.  The L2 cache is flushed (512 MB write) between timed steps; each step is timed
+with CUDA events on the launching stream.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gv|reference]
+
+--impl reference times the FP64 CPU oracle on bounded pixel samples of the same frame.
+Under torchrun (N > 1) every rank renders its own frame (replicas; weak scaling) and the
+slowest rank's time counts.  Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd megapixels/s at 960×540, 200k Gaussians (batched vs per-frame)"
+UNIT = "Mpix/s"
+W, H, N_GAUSS = 960, 540, 200_000
+BATCH_FRAMES = 8
+
+# FP32 ALU operations per (pixel, Gaussian) pair, counted from the compositing arithmetic
+# (an FMA counts as one operation; exp counts one MUFU op):
+#   evaluated pair: dx, dy (2), dx^2, dy^2, dx dy (3), quadratic form (4), exp (2),
+#                   o*G (1), clamp (1), cutoff compare (1)                      = 14
+#   composited pair, forward extra: weight, 3 colour FMAs, 1 - alpha, T update,
+#                   stop compare                                                = 7
+#   replayed pair, backward extra: 1 - alpha, reciprocal, T recovery, weight,
+#                   3 colour gradients, dL/dalpha (9), suffix update (3), clamp test,
+#                   dL/do, dL/dpower, conic gradients (6), mean gradients (6)  = 35
+#                   plus the warp reduction of 9 values over 5 levels amortised
+#                   per lane (2 * 9 * 5 / 32 ~ 3)                               = 38
+OPS_EVAL, OPS_COMP_FWD, OPS_COMP_BWD = 14, 7, 38
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gv", choices=["gv", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget (cpu_baseline)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and e2e legs")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------
+# distributed helpers (replicas; barrier and max over ranks only)
+# ------------------------------------------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    """Maximum of a per-rank scalar over all ranks (identity for one rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def aggregate(units_per_rank: float, seconds_per_rank: float, world: int, device=None) -> tuple[float, float]:
+    """Whole-job throughput: all ranks' units over the slowest rank's time."""
+    t = reduce_max(seconds_per_rank, world, device)
+    return units_per_rank * world / t, t
+
+
+# ------------------------------------------------------------------------------------
+# clock sampling during the timed region
+# ------------------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.rows = []
+        self.proc = None
+        self.gpu_id = gpu_id
+
+    def start(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "100"]
+        if self.gpu_id is not None:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=5)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows),
+                "power_w_max": max((float(r[2]) for r in self.rows if _isnum(r[2])), default=None)}
+
+
+def _isnum(s):
+    try:
+        float(s)
+        return True
+    except ValueError:
+        return False
+
+
+# ------------------------------------------------------------------------------------
+# the GPU arm
+# ------------------------------------------------------------------------------------
+
+def run_gv(args):
+    import torch
+    from paper_2501_04782_gb300 import build as gvbuild
+    from paper_2501_04782_gb300 import gv, synth
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    gvbuild.build()
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
+
+    # ---- workload (seeded; each replica its own frame) --------------------------------
+    wl = synth.workload_single_540p(seed_offset=1000 * rank)
+    g = wl["gaussians"]
+    cam = wl["frames"][0][0]
+    params = {k: torch.from_numpy(v).to(dev) for k, v in g.items()}
+    target = torch.from_numpy(wl["targets"][0]).to(dev).reshape(-1)
+    frames = [gv.Frame(cam, 0, N_GAUSS, 0)]
+    P = W * H
+    ctx = gv.Context((16, 16), 256)
+    image = torch.empty(3 * P, device=dev)
+    T = torch.empty(P, device=dev)
+    idx = torch.empty(P, dtype=torch.int32, device=dev)
+    dL = torch.empty(3 * P, device=dev)
+    loss = torch.zeros(1, device=dev)
+    flat = torch.zeros(14 * N_GAUSS, device=dev)
+    grads = {k: flat[a * N_GAUSS:b * N_GAUSS].view(b - a, N_GAUSS) if b - a > 1 else flat[a * N_GAUSS:b * N_GAUSS]
+             for k, (a, b) in dict(mean=(0, 3), log_scale=(3, 6), quat=(6, 10), opacity_logit=(10, 11),
+                                   rgb=(11, 14)).items()}
+    # size the workspace from the keys the frame needs (8x8 tiles need the most)
+    ws = torch.empty(ctx.workspace_size(frames, 0), dtype=torch.uint8, device=dev)
+    ctx.set_options(tile=(8, 8), stage_depth=64)
+    ctx.render_fwd(params, frames, ws, image, T, idx)
+    st, keys88 = ctx.read_status(ws, raise_on_error=False)
+    ws = torch.empty(ctx.workspace_size(frames, int(keys88 * 1.1) + 65536), dtype=torch.uint8, device=dev)
+    ctx.set_options(tile=(16, 16), stage_depth=256)
+    scale = 1.0 / (3 * P)  # mean-squared error over the frame
+
+    def step():
+        ctx.render_fwd(params, frames, ws, image, T, idx)
+        loss.zero_()
+        ctx.l2_loss_grad(image, target, scale, dL, loss)
+        flat.zero_()
+        ctx.render_bwd(params, frames, ws, T, idx, dL, grads)
+
+    # ---- autotune tile shape and stage depth on this workload (untimed) ----------------
+    best, tune_ms = ctx.autotune(params, frames, ws, image, T, idx, dL, grads, reps=3)
+    ctx.read_status(ws)
+
+    flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)  # 512 MB > L2 (129 MB)
+    ctx.profile_enable(True)
+    for _ in range(args.warmup):
+        step()
+    ctx.read_status(ws)
+    torch.cuda.synchronize()
+    stage_ms = {s: [] for s in gv.STAGES}
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    gpu_id = None
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).pci_bus_id)
+    except Exception:
+        gpu_id = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] if world == 1 else str(local)
+    clocks = ClockSampler(gpu_id)
+    launches = None
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    torch.cuda.nvtx.range_push("timed_steps")
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record()
+        step()
+        ev[i][1].record()
+        ms, nl = ctx.profile_read()  # synchronises this step's events
+        for s, v in ms.items():
+            if v >= 0:
+                stage_ms[s].append(v)
+        launches = nl
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    torch.cuda.nvtx.range_pop()
+    barrier(world)
+    clk = clocks.stop()
+    ctx.profile_enable(False)
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_s = sum(step_ms) / 1000.0
+    value, t_max = aggregate(args.steps * P / 1e6, dev_s, world, dev)
+    counters = ctx.read_counters(ws)
+    st, _ = ctx.read_status(ws)
+
+    # ---- roofline of the dominant kernel ----------------------------------------------
+    mean_stage = {s: (sum(v) / len(v) if v else 0.0) for s, v in stage_ms.items()}
+    dom = max(mean_stage, key=mean_stage.get)
+    sm_mhz = clk.get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1485.0)
+    alu_peak_gops = num_sms * 128 * sm_mhz / 1e3  # FP32 lanes x clock
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    o = ctx.options
+    tiles = math.ceil(W / o.tile_w) * math.ceil(H / o.tile_h)
+    tile_passes = math.ceil(max(1, math.ceil(math.log2(tiles))) / 8)
+    work = {
+        "composite_fwd": ("alu", OPS_EVAL * counters["fwd_eval"] + OPS_COMP_FWD * counters["fwd_composited"]),
+        "composite_bwd": ("alu", OPS_EVAL * counters["bwd_eval"] + OPS_COMP_BWD * counters["bwd_replayed"]),
+        "project": ("hbm", 112 * N_GAUSS),
+        "depth_sort": ("hbm", N_GAUSS * (4 + 4 * 16)),
+        "tile_sort": ("hbm", counters["keys"] * tile_passes * 16),
+        "emit": ("hbm", N_GAUSS * 20 + counters["keys"] * 8),
+        "project_bwd": ("hbm", N_GAUSS * (56 + 36 + 56)),
+    }
+    stages = {}
+    for s, (kind, amount) in work.items():
+        t_s = mean_stage.get(s, 0.0) / 1000.0
+        if t_s <= 0:
+            continue
+        if kind == "alu":
+            a = amount / t_s / 1e9
+            stages[s] = {"ms": round(mean_stage[s], 4), "bound": "alu", "achieved": round(a, 1),
+                         "unit": "Gop/s", "frac": round(a / alu_peak_gops, 4)}
+        else:
+            a = amount / t_s / 1e9
+            stages[s] = {"ms": round(mean_stage[s], 4), "bound": "hbm", "achieved": round(a, 1), "unit": "GB/s",
+                         "frac": round(a / hbm_peak, 4), "l2_resident": amount < 100e6}
+    for s in ("setup", "ranges"):
+        stages[s] = {"ms": round(mean_stage[s], 4)}
+    d = stages.get(dom, {"bound": "alu", "achieved": None, "unit": "Gop/s", "frac": None})
+    roofline = {"kernel": dom, "bound": d.get("bound"), "achieved": d.get("achieved"),
+                "peak": round(alu_peak_gops, 1) if d.get("bound") == "alu" else hbm_peak, "unit": d.get("unit"),
+                "frac": d.get("frac"), "traffic": None,
+                "peak_source": ("152 SMs x 128 FP32 lanes x median SM clock sampled during the timed region"
+                                if d.get("bound") == "alu" else "MEASURED_PEAKS.json hbm_gbs (of measured)")}
+
+    per_step_launches = sum(launches.values()) + 1  # + the loss kernel
+    out = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1000 * t_max / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "frame_960x540_200k: one 960x540 frame, 200,000 Gaussians, random pose, "
+                               "per-frame plain renderer, fwd+L2 loss+bwd",
+                   "width": W, "height": H, "gaussians": N_GAUSS, "frames_per_step": 1,
+                   "tile": f"{o.tile_w}x{o.tile_h}", "stage_depth": o.stage_depth, "autotuned": True,
+                   "keys": counters["keys"], "l2": "512 MB write between timed steps (L2 flushed)",
+                   "parallelism": "replicas" if world > 1 else "single"},
+        "roofline": roofline,
+        "stages": stages,
+        "gpu_launches": per_step_launches * args.steps,
+        "wall_s_timed_loop": round(wall, 3),
+        "clocks": clk,
+        "work_counters": counters,
+    }
+    if not args.no_extras:
+        out["batched"] = run_batched(torch, gv, synth, ctx, dev, flush, max(20, args.steps // 4))
+        out["e2e"] = run_e2e(torch, gv, ctx, params, target, frames, ws, dev, flush, max(20, args.steps // 4), scale,
+                             world)
+    else:
+        out["e2e"] = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(g, cam, wl["targets"][0], args.cpu_seconds)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def run_batched(torch, gv, synth, ctx, dev, flush, steps):
+    """The same frame size and Gaussian count, 8 frames with their own poses sharing one
+    200k set: one CUDA graph (forward, L2 loss, backward) per step, against the plain
+    renderer called once per frame on the same frames."""
+    rng = np.random.default_rng(synth.SEED_BASE + 2)
+    g = synth.gaussians(rng, N_GAUSS, box=((-4.0, 4.0), (-4.0, 4.0), (2.0, 12.0)))
+    params = {k: torch.from_numpy(v).to(dev) for k, v in g.items()}
+    cams = []
+    for f in range(BATCH_FRAMES):
+        R, t = synth.random_pose(rng)
+        cams.append(synth.centred_camera(W, H, float(W), R, t))
+    frames, total = gv.layout_frames([(c, 0, N_GAUSS) for c in cams])
+    target = torch.from_numpy(np.concatenate([synth.target_image(rng, W, H).reshape(-1) for _ in cams])).to(dev)
+    image = torch.empty(3 * total, device=dev)
+    T = torch.empty(total, device=dev)
+    idx = torch.empty(total, dtype=torch.int32, device=dev)
+    dL = torch.empty(3 * total, device=dev)
+    loss = torch.zeros(1, device=dev)
+    grads = {k: torch.zeros_like(v) for k, v in params.items()}
+    ws = torch.empty(ctx.workspace_size(frames, 0), dtype=torch.uint8, device=dev)
+    ctx.render_fwd(params, frames, ws, image, T, idx)
+    st, keys = ctx.read_status(ws, raise_on_error=False)
+    ws = torch.empty(ctx.workspace_size(frames, int(keys * 1.1) + 65536), dtype=torch.uint8, device=dev)
+    scale = 1.0 / (3 * total)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        graph = gv.Graph(ctx, params, frames, ws, image, T, idx, dL, grads, stream, target=target,
+                         loss_scale=scale, loss=loss)
+
+    def batched_step():
+        for v in grads.values():
+            v.zero_()
+        graph.launch(stream)
+
+    def per_frame_step():
+        for f, fr in enumerate(frames):
+            fr0 = [gv.Frame(fr.cam, 0, N_GAUSS, 0)]
+            sl = slice(3 * fr.pixel_offset, 3 * (fr.pixel_offset + W * H))
+            pl = slice(fr.pixel_offset, fr.pixel_offset + W * H)
+            ctx.render_fwd(params, fr0, ws1, image[sl], T[pl], idx[pl])
+            ctx.l2_loss_grad(image[sl], target[sl], scale, dL[sl], loss)
+            ctx.render_bwd(params, fr0, ws1, T[pl], idx[pl], dL[sl], grads)
+
+    ws1 = torch.empty(ctx.workspace_size([gv.Frame(cams[0], 0, N_GAUSS, 0)], int(keys * 0.3) + 65536),
+                      dtype=torch.uint8, device=dev)
+    res = {}
+    for name, fn, strm in (("graph", batched_step, stream), ("per_frame", per_frame_step, torch.cuda.current_stream())):
+        with torch.cuda.stream(strm):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            total_ms = 0.0
+            for _ in range(steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fn()
+                b.record()
+                b.synchronize()
+                total_ms += a.elapsed_time(b)
+        res[name] = round(steps * BATCH_FRAMES * W * H / (total_ms / 1000) / 1e6, 2)
+    st, _ = ctx.read_status(ws)
+    graph.close()
+    return {"value": res["graph"], "unit": UNIT, "frames_per_step": BATCH_FRAMES, "steps": steps,
+            "per_frame_same_frames": res["per_frame"],
+            "workload": f"{BATCH_FRAMES} frames 960x540 sharing 200,000 Gaussians, own random poses; one CUDA "
+                        "graph per step (forward, L2 loss, backward) vs the plain renderer once per frame"}
+
+
+def run_e2e(torch, gv, ctx, params, target, frames, ws, dev, flush, steps, scale, world):
+    """Same step through the C ABI with HOST inputs: the parameter planes and the target
+    copied from pinned host memory, gradients and loss copied back, every step."""
+    host_params = {k: v.cpu().pin_memory() for k, v in params.items()}
+    host_target = target.cpu().pin_memory()
+    dparams = {k: torch.empty_like(v) for k, v in params.items()}
+    dtarget = torch.empty_like(target)
+    P = W * H
+    image = torch.empty(3 * P, device=dev)
+    T = torch.empty(P, device=dev)
+    idx = torch.empty(P, dtype=torch.int32, device=dev)
+    dL = torch.empty(3 * P, device=dev)
+    loss = torch.zeros(1, device=dev)
+    grads = {k: torch.zeros_like(v) for k, v in params.items()}
+    host_grads = {k: torch.empty(v.shape, dtype=v.dtype).pin_memory() for k, v in grads.items()}
+    host_loss = torch.empty(1).pin_memory()
+    h2d = sum(v.numel() * 4 for v in host_params.values()) + host_target.numel() * 4
+    d2h = sum(v.numel() * 4 for v in host_grads.values()) + 4
+
+    def step():
+        for k in dparams:
+            dparams[k].copy_(host_params[k], non_blocking=True)
+        dtarget.copy_(host_target, non_blocking=True)
+        ctx.render_fwd(dparams, frames, ws, image, T, idx)
+        loss.zero_()
+        ctx.l2_loss_grad(image, dtarget, scale, dL, loss)
+        for v in grads.values():
+            v.zero_()
+        ctx.render_bwd(dparams, frames, ws, T, idx, dL, grads)
+        for k in grads:
+            host_grads[k].copy_(grads[k], non_blocking=True)
+        host_loss.copy_(loss, non_blocking=True)
+
+    for _ in range(3):
+        step()
+    torch.cuda.synchronize()
+    total_ms = 0.0
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        step()
+        b.record()
+        b.synchronize()
+        total_ms += a.elapsed_time(b)
+    value, _ = aggregate(steps * P / 1e6, total_ms / 1000, world, dev)
+    return {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "api": "gv_render_fwd / gv_l2_loss_grad / gv_render_bwd with pinned host buffers copied in and out"}
+
+
+# ------------------------------------------------------------------------------------
+# the oracle (CPU baseline / reference arm)
+# ------------------------------------------------------------------------------------
+
+def oracle_step(oracle, g, cam, tgt, px, py):
+    r = oracle.render_pixels(g, cam, px, py)
+    dLp = 2.0 * (r["rgb"] - tgt[:, py, px].T) / (3 * W * H)
+    oracle.render_bwd_pixels(g, cam, px, py, dLp, want_abs=False, want_2d=False)
+
+
+def cpu_baseline(g, cam, tgt, seconds: float) -> dict:
+    import oracle
+    from paper_2501_04782_gb300 import synth
+    oracle.lib()
+    px, py = synth.pixel_sample(4242, W, H, 64)
+    t0 = time.perf_counter()
+    oracle_step(oracle, g, cam, tgt, px, py)
+    t64 = time.perf_counter() - t0
+    n = int(min(W * H, max(64, 64 * seconds / max(t64, 1e-3))))
+    px, py = synth.pixel_sample(4243, W, H, n)
+    t0 = time.perf_counter()
+    oracle_step(oracle, g, cam, tgt, px, py)
+    t = time.perf_counter() - t0
+    return {"value": round(n / t / 1e6, 6), "unit": UNIT, "cores": oracle.default_threads(), "kind": "oracle",
+            "sample": f"{n} seeded pixels of the 960x540 / 200k-Gaussian frame, FP64 forward + analytic "
+                      f"backward over all Gaussians per pixel, {t:.1f} s"}
+
+
+def run_reference(args):
+    from paper_2501_04782_gb300 import synth
+    import oracle
+
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    oracle.lib()
+    wl = synth.workload_single_540p()
+    g = wl["gaussians"]
+    cam = wl["frames"][0][0]
+    tgt = wl["targets"][0]
+    n_pix = 256
+    for i in range(args.warmup):
+        px, py = synth.pixel_sample(10 + i, W, H, n_pix)
+        oracle_step(oracle, g, cam, tgt, px, py)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        px, py = synth.pixel_sample(100 + i, W, H, n_pix)
+        oracle_step(oracle, g, cam, tgt, px, py)
+    t = time.perf_counter() - t0
+    value = args.steps * n_pix / t / 1e6
+    cores = oracle.default_threads()
+    sample = f"{n_pix} seeded pixels of the 960x540 / 200k-Gaussian frame per step (FP64 forward + backward)"
+    print(json.dumps({
+        "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(1000 * t / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": "frame_960x540_200k sampled pixels", "width": W, "height": H,
+                   "gaussians": N_GAUSS, "pixels_per_step": n_pix},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gv(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -73,8 +73,12 @@ class Params:
     znear: float = ZNEAR
     ext_k: float = EXT_K
     bg: tuple = (0.0, 0.0, 0.0)
-    amb_alpha_rel: float = 2e-3
-    amb_T_rel: float = 5e-2
+    # ambiguity windows (decisions within FP32 reach of a threshold): alpha within 1e-5
+    # (relative) of 1/255; T within 1e-3 (relative) of the stop value -- a flipped stop
+    # changes a pixel by at most T_stop * max colour, inside the pixel tolerance anyway;
+    # consecutive contributor depths within 1e-6 (relative, ~8 FP32 ulps)
+    amb_alpha_rel: float = 1e-5
+    amb_T_rel: float = 1e-3
     amb_depth_rel: float = 1e-6
 
     @staticmethod

@@ -1,0 +1,247 @@
+// binning.cu -- per-call setup, tile-count prefix scan, key emission and tile ranges.
+//
+// Binning is two-level.  The pairs are first sorted by camera depth (one 32-bit radix
+// sort over the P pairs), then each pair, in depth order, emits one key per tile its
+// extent rectangle covers (row-major), and the keys are sorted stably by tile id only.
+// The result is the unique list a stable sort of (tile << 32 | depth bits) keys emitted in
+// pair order would give -- ordered by tile, then depth, then pair index -- but the
+// expensive per-key sort touches only the live tile-id bits (one or two 8-bit passes
+// instead of five or six).
+#include "gv_internal.cuh"
+
+namespace gvk {
+
+namespace {
+
+__global__ void setup_kernel(Work w, FrameChunk chunk, int first, int count, int zero_all,
+                             long long spin_limit, int drop_signal) {
+    int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    int stride = gridDim.x * blockDim.x;
+    for (int i = tid; i < count; i += stride) w.frames[first + i] = chunk.f[i];
+    if (!zero_all) return;
+    if (tid == 0) {
+        DevHeader h = {};
+        h.spin_limit = spin_limit;
+        h.drop_signal = drop_signal;
+        h.n_pairs = w.L.P;
+        *w.hdr = h;
+    }
+    for (int i = tid; i < 8 * kRadix; i += stride) w.hist[i] = 0u;
+    for (unsigned i = tid; i < w.L.tiles; i += stride) w.ranges[i] = make_uint2(0u, 0u);
+}
+
+// Sum of the tile counts of each block of kEmitBlock pairs taken in depth order.
+__global__ void __launch_bounds__(kEmitThreads) count_reduce_kernel(Work w, const unsigned *order) {
+    __shared__ unsigned s_w[8];
+    unsigned b = blockIdx.x;
+    unsigned base = b * kEmitBlock;
+    unsigned sum = 0;
+    for (int i = 0; i < kEmitItems; i++) {
+        unsigned idx = base + i * kEmitThreads + threadIdx.x;
+        if (idx < w.L.P) {
+            unsigned p = order[idx];
+            if (p < w.L.P) sum += w.rect[p].z;  // ids are in range unless a bounded wait gave up
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned tot = 0;
+        for (int i = 0; i < kEmitThreads / 32; i++) tot += s_w[i];
+        w.blocksum[b] = tot;
+    }
+}
+
+// Exclusive scan of the block sums (single block), total key count and capacity check.
+__global__ void __launch_bounds__(1024) count_scan_kernel(Work w) {
+    __shared__ unsigned long long s_w[32];
+    __shared__ unsigned long long s_carry;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    const unsigned nb = w.L.emit_blocks;
+    for (unsigned base = 0; base < nb; base += 1024) {
+        unsigned i = base + threadIdx.x;
+        unsigned long long x = i < nb ? w.blocksum[i] : 0ull;
+        unsigned long long inc = x;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) s_w[wid] = inc;
+        __syncthreads();
+        if (wid == 0) {
+            unsigned long long t = s_w[lane], ti = t;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned long long y = __shfl_up_sync(0xffffffffu, ti, o);
+                if (lane >= o) ti += y;
+            }
+            s_w[lane] = ti - t;
+        }
+        __syncthreads();
+        unsigned long long ex = s_carry + s_w[wid] + inc - x;
+        // prefixes beyond the capacity are clamped: those blocks emit nothing
+        if (i < nb) w.blockprefix[i] = (unsigned)min(ex, (unsigned long long)w.L.key_cap);
+        __syncthreads();
+        if (threadIdx.x == 1023) s_carry = ex + x;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        unsigned long long K = s_carry;
+        w.hdr->keys_total = K;
+        w.hdr->keys_used = (unsigned)min(K, (unsigned long long)w.L.key_cap);
+        if (K > w.L.key_cap) atomicOr(&w.hdr->err, ERR_CAPACITY);
+    }
+}
+
+// Load-balanced emission: block b owns kEmitBlock pairs in depth order; its keys are
+// spread evenly over the threads (each key finds its pair by binary search over the
+// block's exclusive count offsets).  Also counts the tile-sort digit histograms.
+__global__ void __launch_bounds__(kEmitThreads) emit_kernel(Work w, const unsigned *order, int tile_passes,
+                                                            unsigned *tile_hist) {
+    __shared__ unsigned s_off[kEmitBlock + 1];
+    __shared__ unsigned s_pair[kEmitBlock];
+    __shared__ unsigned s_hist[4][kRadix];
+    __shared__ unsigned s_w[8];
+    const unsigned b = blockIdx.x, base = b * kEmitBlock;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    for (int i = t; i < 4 * kRadix; i += kEmitThreads) (&s_hist[0][0])[i] = 0u;
+    // blocked: thread t owns pairs base + t*8 .. +7
+    unsigned c[kEmitItems], sum = 0;
+#pragma unroll
+    for (int i = 0; i < kEmitItems; i++) {
+        unsigned idx = base + t * kEmitItems + i;
+        unsigned p = idx < w.L.P ? order[idx] : 0u;
+        if (p >= w.L.P) p = 0u;  // ids are in range unless a bounded wait gave up
+        c[i] = idx < w.L.P ? w.rect[p].z : 0u;
+        s_pair[t * kEmitItems + i] = p;
+        sum += c[i];
+    }
+    unsigned inc = sum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_w[wid] = inc;
+    __syncthreads();
+    unsigned wex = 0;
+    for (int q = 0; q < wid; q++) wex += s_w[q];
+    unsigned run = wex + inc - sum;
+#pragma unroll
+    for (int i = 0; i < kEmitItems; i++) {
+        s_off[t * kEmitItems + i] = run;
+        run += c[i];
+    }
+    if (t == kEmitThreads - 1) s_off[kEmitBlock] = run;
+    __syncthreads();
+    const unsigned total = s_off[kEmitBlock];
+    const unsigned gbase = w.blockprefix[b];
+    const unsigned cap = w.L.key_cap;
+    // every thread runs the same number of rounds, so warp votes see the full warp
+    for (unsigned e0 = 0; e0 < total; e0 += kEmitThreads) {
+        const unsigned e = e0 + t;
+        bool ok = e < total;
+        unsigned tile = 0;
+        if (ok) {
+            // largest i with s_off[i] <= e (pairs with zero count share offsets)
+            int lo = 0, hi = kEmitBlock - 1;
+            while (lo < hi) {
+                int mid = (lo + hi + 1) >> 1;
+                if (s_off[mid] <= e) lo = mid; else hi = mid - 1;
+            }
+            unsigned p = s_pair[lo];
+            unsigned j = e - s_off[lo];
+            uint4 r = w.rect[p];
+            unsigned tx0 = r.x & 0xFFFFu, ty0 = r.x >> 16, tx1 = r.y & 0xFFFFu;
+            unsigned wr = tx1 - tx0 + 1u;
+            unsigned ty = ty0 + j / wr, tx = tx0 + j % wr;
+            const DevFrame &fr = w.frames[r.w];
+            tile = fr.tile_offset + ty * fr.tiles_x + tx;
+            unsigned gk = gbase + e;
+            ok = gk < cap;
+            if (ok) {
+                w.tkey[0][gk] = tile;
+                w.tval[0][gk] = p;
+            }
+        }
+        unsigned active = __ballot_sync(0xffffffffu, ok);
+        if (ok) {
+            for (int ps = 0; ps < tile_passes; ps++) {
+                unsigned d = (tile >> (8 * ps)) & 255u;
+                unsigned peers = __match_any_sync(active, d);
+                if (lane == __ffs(peers) - 1) atomicAdd(&s_hist[ps][d], (unsigned)__popc(peers));
+            }
+        }
+    }
+    __syncthreads();
+    for (int i = t; i < tile_passes * kRadix; i += kEmitThreads) {
+        unsigned v = (&s_hist[0][0])[i];
+        if (v) atomicAdd(tile_hist + i, v);
+    }
+}
+
+__global__ void ranges_kernel(Work w, const unsigned *keys) {
+    const unsigned n = w.hdr->keys_used;
+    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
+        unsigned t = keys[k];
+        if (t >= w.L.tiles) continue;  // only after a bounded wait gave up
+        if (k == 0 || keys[k - 1] != t) w.ranges[t].x = k;
+        if (k == n - 1 || keys[k + 1] != t) w.ranges[t].y = k + 1;
+    }
+}
+
+__global__ void gather_debug_kernel(Work w, float *mean2d, float *conic, float *opacity, float *depth,
+                                    int32_t *counts, int depth_buf) {
+    unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned P = w.L.P;
+    if (p >= P) return;
+    float4 a = w.feat0[p], b = w.feat1[p];
+    if (mean2d) { mean2d[p] = a.x; mean2d[P + p] = a.y; }
+    if (conic) { conic[p] = a.z; conic[P + p] = a.w; conic[2 * P + p] = b.x; }
+    if (opacity) opacity[p] = b.y;
+    if (counts) counts[p] = (int32_t)w.rect[p].z;
+    // position p of the depth-sorted list holds (depth key, pair id); culled pairs: NaN
+    if (depth) depth[w.dval[depth_buf][p]] = __uint_as_float(w.dkey[depth_buf][p]);
+}
+
+}  // namespace
+
+const void *setup_kernel_ptr() { return (const void *)setup_kernel; }
+
+cudaError_t launch_setup(const Work &w, const FrameChunk &chunk, int first, int count, bool zero_all,
+                         long long spin_limit, int drop_signal, cudaStream_t s) {
+    unsigned work = zero_all ? max(w.L.tiles, (unsigned)(8 * kRadix)) : (unsigned)count;
+    unsigned blocks = min((work + 255u) / 256u, 1024u);
+    if (blocks == 0) blocks = 1;
+    setup_kernel<<<blocks, 256, 0, s>>>(w, chunk, first, count, zero_all ? 1 : 0, spin_limit, drop_signal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_emit(const Work &w, int depth_buf, int tile_bits, int tile_hist_slot, cudaStream_t s) {
+    if (w.L.P == 0) return cudaSuccess;
+    const unsigned *order = w.dval[depth_buf];
+    count_reduce_kernel<<<w.L.emit_blocks, kEmitThreads, 0, s>>>(w, order);
+    count_scan_kernel<<<1, 1024, 0, s>>>(w);
+    int passes = tile_bits <= 0 ? 0 : (tile_bits + 7) / 8;
+    emit_kernel<<<w.L.emit_blocks, kEmitThreads, 0, s>>>(w, order, passes, w.hist + (size_t)tile_hist_slot * kRadix);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ranges(const Work &w, int tile_buf, int num_sms, cudaStream_t s) {
+    ranges_kernel<<<num_sms * 4, 256, 0, s>>>(w, w.tkey[tile_buf]);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_debug(const Work &w, float *mean2d, float *conic, float *opacity, float *depth,
+                                int32_t *counts, int depth_buf, cudaStream_t s) {
+    if (w.L.P == 0) return cudaSuccess;
+    gather_debug_kernel<<<(w.L.P + 255) / 256, 256, 0, s>>>(w, mean2d, conic, opacity, depth, counts, depth_buf);
+    return cudaGetLastError();
+}
+
+}  // namespace gvk

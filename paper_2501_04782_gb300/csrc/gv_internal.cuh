@@ -1,0 +1,193 @@
+// gv_internal.cuh -- definitions shared by the libgv kernels and the host ABI layer.
+//
+// Device data layout of one render call (all in the caller's workspace, see plan_layout):
+//   header      DevHeader: error word, key count, work-queue and sort counters
+//   frames      DevFrame[F]: camera and offsets of each frame
+//   per pair    (frame, Gaussian) pairs, P = sum of per-frame Gaussian counts:
+//               feat0 float4 (u, v, conic A, conic B), feat1 float4 (conic C, opacity, r, g),
+//               feat2 float (b), rect uint4 (tile rect + frame tile base), depth keys and
+//               pair ids (double-buffered for the depth sort), grad2d (two float4 + float)
+//   per key     tile ids and pair ids, double-buffered for the tile sort
+//   per tile    [start, end) ranges into the sorted key list
+//   sort        digit histograms and decoupled look-back status words
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "gv.h"
+
+namespace gvk {
+
+// Rendering constants (Sec. 3.1 conventions; see include/gv.h).
+constexpr float kAlphaMin = 0.003921568859368563f;  // 1/255
+constexpr float kAlphaMax = 0.99f;
+constexpr float kTStop = 1e-4f;
+constexpr float kEps2d = 0.3f;
+constexpr float kZNear = 0.2f;
+constexpr float kExtK = 3.329042911529541f;          // sqrt(2 ln 255), rounded to FP32
+
+// Device error bits (DevHeader::err).
+enum : unsigned { ERR_CAPACITY = 1u, ERR_TIMEOUT = 2u };
+
+constexpr int kMaxFramesPerSetup = 96;  // frames per setup launch (kernel parameter space)
+
+struct DevFrame {
+    int W, H;
+    float fx, fy, cx, cy;
+    float R[9];
+    float t[3];
+    float time;
+    long long gauss_offset;
+    long long pixel_offset;
+    unsigned pair_offset, gauss_count;
+    unsigned tile_offset, tiles_x, tiles_y, pad;
+};
+
+struct DevHeader {
+    unsigned err;
+    unsigned keys_used;             // min(keys_total, capacity)
+    unsigned long long keys_total;  // keys the call needed
+    unsigned n_pairs;               // P, read by the depth sort
+    unsigned pad0;
+    unsigned sort_ctr[16];          // tile-acquisition counters of the sort passes
+    unsigned queue[4];              // persistent work-queue counters
+    long long spin_limit;           // iteration limit of every device-side wait
+    int drop_signal;                // test hook: first look-back block never publishes
+    int pad;
+    unsigned long long work[4];     // pairs evaluated / composited: fwd 0-1, bwd 2-3
+};
+
+// Radix sort geometry (one onesweep pass = one 8-bit digit).
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 15;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 3840 keys per block tile
+constexpr int kRadix = 256;
+
+// Emission block geometry (count scan + load-balanced key emission).
+constexpr int kEmitThreads = 256;
+constexpr int kEmitItems = 8;
+constexpr int kEmitBlock = kEmitThreads * kEmitItems;  // 2048 pairs per block
+
+// Workspace layout (byte offsets), computed on the host.
+struct Layout {
+    size_t hdr, frames;
+    size_t feat0, feat1, feat2, rect, dkey[2], dval[2];
+    size_t blocksum, blockprefix;
+    size_t g0, g1, g2;
+    size_t ranges;
+    size_t tkey[2], tval[2];
+    size_t hist, look;
+    size_t total;
+    unsigned P, tiles, F;
+    unsigned tiles_alloc;  // ranges capacity (tile count of the finest tiling, 8x8)
+    unsigned key_cap;
+    unsigned look_tiles;   // look-back tiles per buffer
+    unsigned emit_blocks;
+    int tile_bits;         // live bits of the global tile id
+};
+
+// Pointers into one workspace.
+struct Work {
+    DevHeader *hdr;
+    DevFrame *frames;
+    float4 *feat0, *feat1;
+    float *feat2;
+    uint4 *rect;
+    unsigned *dkey[2], *dval[2];
+    unsigned *blocksum, *blockprefix;
+    float4 *g0, *g1;
+    float *g2;
+    uint2 *ranges;
+    unsigned *tkey[2], *tval[2];
+    unsigned *hist;   // [8][256]: depth-sort passes 0-3, tile-sort passes 4-7
+    unsigned *look;   // [2][look_tiles][256]
+    Layout L;
+};
+
+struct GaussPtrs {
+    const float *mean, *vel, *log_scale, *quat, *logit, *rgb;
+    long long N;
+};
+
+struct GradPtrs {
+    float *mean, *vel, *log_scale, *quat, *logit, *rgb;
+};
+
+struct FrameChunk {
+    DevFrame f[kMaxFramesPerSetup];
+};
+
+// ---- host launchers (stream-ordered, no allocation) --------------------------------
+
+// setup.cu
+cudaError_t launch_setup(const Work &w, const FrameChunk &chunk, int first, int count, bool zero_all,
+                         long long spin_limit, int drop_signal, cudaStream_t s);
+const void *setup_kernel_ptr();
+// project.cu
+cudaError_t launch_project_fwd(const Work &w, const GaussPtrs &g, int tile_w, int tile_h, cudaStream_t s);
+cudaError_t launch_bin_from_screen(const Work &w, long long n, const float *u, const float *v,
+                                   const float *ex, const float *ey, const float *depth,
+                                   const uint8_t *valid, int tile_w, int tile_h, int32_t *counts,
+                                   cudaStream_t s);
+cudaError_t launch_project_bwd(const Work &w, const GaussPtrs &g, const GradPtrs &gr, int mode, cudaStream_t s);
+// sort.cu
+int sort_passes(int bits);
+cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2], const unsigned *n_dev,
+                              unsigned n_cap, int bits, bool vals_identity, bool hist_counted, int hist_slot,
+                              int ctr_slot, int num_sms, cudaStream_t s, int *result_buf);
+// binning.cu
+cudaError_t launch_emit(const Work &w, int depth_buf, int tile_bits, int tile_hist_slot, cudaStream_t s);
+cudaError_t launch_ranges(const Work &w, int tile_buf, int num_sms, cudaStream_t s);
+// composite.cu
+cudaError_t launch_composite_fwd(const Work &w, int tile_w, int tile_h, int depth, int tile_buf,
+                                 float bg0, float bg1, float bg2, float *image, float *final_T,
+                                 int32_t *last_idx, int num_sms, cudaStream_t s);
+cudaError_t launch_composite_bwd(const Work &w, int tile_w, int tile_h, int depth, int tile_buf,
+                                 float bg0, float bg1, float bg2, const float *final_T,
+                                 const int32_t *last_idx, const float *dL_dimage, int num_sms,
+                                 cudaStream_t s);
+// optim.cu
+cudaError_t launch_l2_loss(const float *image, const float *target, long long n, float scale,
+                           float *dL, float *loss, cudaStream_t s);
+cudaError_t launch_adam(float *p, float *g, float *m, float *v, long long n, float lr, float b1,
+                        float b2, float eps, float bc1, float bc2, int zero_grad, cudaStream_t s);
+cudaError_t launch_gather_debug(const Work &w, float *mean2d, float *conic, float *opacity,
+                                float *depth, int32_t *counts, int depth_buf, cudaStream_t s);
+cudaError_t launch_grad2d_debug(const Work &w, float *out, cudaStream_t s);
+
+// ---- small device helpers ----------------------------------------------------------
+
+__device__ __forceinline__ int find_frame_by_pair(const DevFrame *fr, int F, unsigned p) {
+    int lo = 0, hi = F - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (fr[mid].pair_offset <= p) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int find_frame_by_tile(const DevFrame *fr, int F, unsigned t) {
+    int lo = 0, hi = F - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (fr[mid].tile_offset <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Alpha of a staged Gaussian at a pixel centre.  Written with explicit round-to-nearest
+// intrinsics so that the forward and the backward kernels compute bit-identical values
+// (the backward replays the forward's decisions and divides its transmittance back).
+// power = 1/2 (A dx^2 + C dy^2) + B dx dy;  G = exp(-power);  alpha = min(0.99, o G).
+__device__ __forceinline__ float splat_alpha(float mx, float my, float A, float B, float C, float o,
+                                             float px, float py, float &dx, float &dy, float &G) {
+    dx = __fsub_rn(mx, px);
+    dy = __fsub_rn(my, py);
+    float q = __fmaf_rn(A, __fmul_rn(dx, dx), __fmul_rn(C, __fmul_rn(dy, dy)));
+    float power = __fmaf_rn(0.5f, q, __fmul_rn(B, __fmul_rn(dx, dy)));
+    G = __expf(-power);
+    return fminf(kAlphaMax, __fmul_rn(o, G));
+}
+
+}  // namespace gvk

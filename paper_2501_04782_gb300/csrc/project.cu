@@ -1,0 +1,328 @@
+// project.cu -- projection of (frame, Gaussian) pairs to screen space (forward) and the
+// chain rule from screen-space gradients back to the raw parameters (backward).
+//
+// Sec. 3.1: Sigma = (R S)(R S)^T from a quaternion and log-scales; the Gaussian is
+// projected onto the image plane of the frame's pinhole camera (Sec. 3.4: intrinsics
+// fx, fy, cx, cy; extrinsics R, t).  The 2D covariance is the local-affine (EWA)
+// approximation J W Sigma W^T J^T plus a 0.3 px^2 low-pass, its inverse the conic.
+// Sec. 3.2 / Eq. 3: the mean moves with time (mu_t = mu_0 + t vel), colour and opacity
+// do not.  Both kernels are HBM-bound: one thread per pair, coalesced SoA plane reads.
+#include "gv_internal.cuh"
+
+namespace gvk {
+
+namespace {
+
+struct PairState {
+    float mx, my, mz;        // world mean at the frame's time
+    float xc, yc, zc;        // camera-space mean
+    float s0, s1, s2;        // scales
+    float qw, qx, qy, qz;    // normalised quaternion
+    float inv_qn;            // 1 / |q|
+    float R[9];              // Gaussian rotation
+    float S3[6];             // world covariance xx, xy, xz, yy, yz, zz
+    float T0[3], T1[3];      // rows of J W
+    float a, b, c;           // Sigma2 (with low-pass)
+    float A, B, C;           // conic
+    float u, v;
+    float o;
+    bool valid;
+};
+
+__device__ __forceinline__ void load_and_project(const GaussPtrs &g, long long gi, const DevFrame &fr,
+                                                 PairState &st) {
+    const long long N = g.N;
+    st.mx = g.mean[gi];
+    st.my = g.mean[N + gi];
+    st.mz = g.mean[2 * N + gi];
+    if (g.vel) {
+        st.mx = fmaf(fr.time, g.vel[gi], st.mx);
+        st.my = fmaf(fr.time, g.vel[N + gi], st.my);
+        st.mz = fmaf(fr.time, g.vel[2 * N + gi], st.mz);
+    }
+    st.s0 = expf(g.log_scale[gi]);
+    st.s1 = expf(g.log_scale[N + gi]);
+    st.s2 = expf(g.log_scale[2 * N + gi]);
+    float qw = g.quat[gi], qx = g.quat[N + gi], qy = g.quat[2 * N + gi], qz = g.quat[3 * N + gi];
+    float inv = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    st.inv_qn = inv;
+    qw *= inv; qx *= inv; qy *= inv; qz *= inv;
+    st.qw = qw; st.qx = qx; st.qy = qy; st.qz = qz;
+    float *R = st.R;
+    R[0] = 1.f - 2.f * (qy * qy + qz * qz); R[1] = 2.f * (qx * qy - qw * qz); R[2] = 2.f * (qx * qz + qw * qy);
+    R[3] = 2.f * (qx * qy + qw * qz); R[4] = 1.f - 2.f * (qx * qx + qz * qz); R[5] = 2.f * (qy * qz - qw * qx);
+    R[6] = 2.f * (qx * qz - qw * qy); R[7] = 2.f * (qy * qz + qw * qx); R[8] = 1.f - 2.f * (qx * qx + qy * qy);
+    float s0q = st.s0 * st.s0, s1q = st.s1 * st.s1, s2q = st.s2 * st.s2;
+    // Sigma3_ij = sum_k R_ik R_jk s_k^2
+    st.S3[0] = R[0] * R[0] * s0q + R[1] * R[1] * s1q + R[2] * R[2] * s2q;
+    st.S3[1] = R[0] * R[3] * s0q + R[1] * R[4] * s1q + R[2] * R[5] * s2q;
+    st.S3[2] = R[0] * R[6] * s0q + R[1] * R[7] * s1q + R[2] * R[8] * s2q;
+    st.S3[3] = R[3] * R[3] * s0q + R[4] * R[4] * s1q + R[5] * R[5] * s2q;
+    st.S3[4] = R[3] * R[6] * s0q + R[4] * R[7] * s1q + R[5] * R[8] * s2q;
+    st.S3[5] = R[6] * R[6] * s0q + R[7] * R[7] * s1q + R[8] * R[8] * s2q;
+    const float *W = fr.R;
+    st.xc = W[0] * st.mx + W[1] * st.my + W[2] * st.mz + fr.t[0];
+    st.yc = W[3] * st.mx + W[4] * st.my + W[5] * st.mz + fr.t[1];
+    st.zc = W[6] * st.mx + W[7] * st.my + W[8] * st.mz + fr.t[2];
+    st.o = 1.f / (1.f + expf(-g.logit[gi]));
+    st.valid = st.zc > kZNear;
+    if (!st.valid) return;
+    float iz = 1.f / st.zc;
+    float rx = st.xc * iz, ry = st.yc * iz;
+    float jx = fr.fx * iz, jy = fr.fy * iz;
+    // rows of T = J W with J = [[fx/z, 0, -fx x/z^2], [0, fy/z, -fy y/z^2]]
+    for (int j = 0; j < 3; j++) {
+        st.T0[j] = jx * (W[j] - rx * W[6 + j]);
+        st.T1[j] = jy * (W[3 + j] - ry * W[6 + j]);
+    }
+    const float *S = st.S3;
+    float v0x = S[0] * st.T0[0] + S[1] * st.T0[1] + S[2] * st.T0[2];
+    float v0y = S[1] * st.T0[0] + S[3] * st.T0[1] + S[4] * st.T0[2];
+    float v0z = S[2] * st.T0[0] + S[4] * st.T0[1] + S[5] * st.T0[2];
+    float v1x = S[0] * st.T1[0] + S[1] * st.T1[1] + S[2] * st.T1[2];
+    float v1y = S[1] * st.T1[0] + S[3] * st.T1[1] + S[4] * st.T1[2];
+    float v1z = S[2] * st.T1[0] + S[4] * st.T1[1] + S[5] * st.T1[2];
+    st.a = st.T0[0] * v0x + st.T0[1] * v0y + st.T0[2] * v0z + kEps2d;
+    st.b = st.T0[0] * v1x + st.T0[1] * v1y + st.T0[2] * v1z;
+    st.c = st.T1[0] * v1x + st.T1[1] * v1y + st.T1[2] * v1z + kEps2d;
+    float det = st.a * st.c - st.b * st.b;
+    if (!(det > 0.f)) { st.valid = false; return; }
+    float idet = 1.f / det;
+    st.A = st.c * idet;
+    st.B = -st.b * idet;
+    st.C = st.a * idet;
+    st.u = fmaf(fr.fx, rx, fr.cx);
+    st.v = fmaf(fr.fy, ry, fr.cy);
+    if (!(isfinite(st.u) && isfinite(st.v) && isfinite(st.A) && isfinite(st.B) && isfinite(st.C)))
+        st.valid = false;
+}
+
+// Tile rectangle of the extent box [u - ex, u + ex] x [v - ey, v + ey]: pixel centres
+// x + 0.5 inside it, x0 = ceil((u - ex) - 0.5), x1 = floor((u + ex) - 0.5), clipped to the
+// image, then divided by the (power-of-two) tile size.  Every operation is rounded to FP32
+// explicitly so the integer result is reproducible.  Returns the tile count (0: empty).
+__device__ __forceinline__ unsigned tile_rect(float u, float v, float ex, float ey, int W, int H,
+                                              int lw, int lh, unsigned &lo, unsigned &hi) {
+    float x0 = ceilf(__fsub_rn(__fsub_rn(u, ex), 0.5f));
+    float x1 = floorf(__fsub_rn(__fadd_rn(u, ex), 0.5f));
+    float y0 = ceilf(__fsub_rn(__fsub_rn(v, ey), 0.5f));
+    float y1 = floorf(__fsub_rn(__fadd_rn(v, ey), 0.5f));
+    if (x0 < 0.f) x0 = 0.f;
+    if (y0 < 0.f) y0 = 0.f;
+    if (x1 > (float)(W - 1)) x1 = (float)(W - 1);
+    if (y1 > (float)(H - 1)) y1 = (float)(H - 1);
+    lo = hi = 0;
+    if (!(x0 <= x1) || !(y0 <= y1)) return 0u;
+    unsigned tx0 = (unsigned)(int)x0 >> lw, tx1 = (unsigned)(int)x1 >> lw;
+    unsigned ty0 = (unsigned)(int)y0 >> lh, ty1 = (unsigned)(int)y1 >> lh;
+    lo = tx0 | (ty0 << 16);
+    hi = tx1 | (ty1 << 16);
+    return (tx1 - tx0 + 1u) * (ty1 - ty0 + 1u);
+}
+
+__global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, int lw, int lh) {
+    unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= w.L.P) return;
+    int f = find_frame_by_pair(w.frames, (int)w.L.F, p);
+    const DevFrame &fr = w.frames[f];
+    long long gi = fr.gauss_offset + (long long)(p - fr.pair_offset);
+    PairState st;
+    load_and_project(g, gi, fr, st);
+    unsigned cnt = 0, lo = 0, hi = 0;
+    float ex = 0.f, ey = 0.f;
+    if (st.valid) {
+        ex = kExtK * sqrtf(st.a);
+        ey = kExtK * sqrtf(st.c);
+        cnt = tile_rect(st.u, st.v, ex, ey, fr.W, fr.H, lw, lh, lo, hi);
+    }
+    const long long N = g.N;
+    w.feat0[p] = make_float4(st.u, st.v, st.A, st.B);
+    w.feat1[p] = make_float4(st.C, st.o, g.rgb[gi], g.rgb[N + gi]);
+    w.feat2[p] = g.rgb[2 * N + gi];
+    w.rect[p] = make_uint4(lo, hi, cnt, (unsigned)f);
+    w.dkey[0][p] = cnt ? __float_as_uint(st.zc) : 0xFFFFFFFFu;
+}
+
+// Stage-isolated binning: screen-space inputs of one frame given by the caller.
+__global__ void __launch_bounds__(256) bin_from_screen_kernel(Work w, long long n, const float *u,
+                                                              const float *v, const float *ex,
+                                                              const float *ey, const float *depth,
+                                                              const uint8_t *valid, int lw, int lh,
+                                                              int32_t *counts) {
+    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const DevFrame &fr = w.frames[0];
+    unsigned lo = 0, hi = 0, cnt = 0;
+    if (valid[p]) cnt = tile_rect(u[p], v[p], ex[p], ey[p], fr.W, fr.H, lw, lh, lo, hi);
+    w.rect[p] = make_uint4(lo, hi, cnt, 0u);
+    w.dkey[0][p] = cnt ? __float_as_uint(depth[p]) : 0xFFFFFFFFu;
+    if (counts) counts[p] = (int32_t)cnt;
+}
+
+// Chain rule of one pair: screen-space gradient (du, dv, dA, dB, dC, do, dr, dg, db) to
+// the raw-parameter gradients, added into acc[17] (mean 3, vel 3, log_scale 3, quat 4,
+// logit 1, rgb 3).
+__device__ __forceinline__ void pair_backward(const PairState &st, const DevFrame &fr, float4 g0,
+                                              float4 g1, float g2, float acc[17]) {
+    acc[14] += g1.z;
+    acc[15] += g1.w;
+    acc[16] += g2;
+    acc[13] += g1.y * st.o * (1.f - st.o);
+    if (!st.valid) return;
+    float dA = g0.z, dB = g0.w, dC = g1.x;
+    // conic Q = Sigma2^{-1}: dL/dSigma2 = -Q G Q with G = [[dA, dB/2], [dB/2, dC]]
+    float X00 = st.A * dA + 0.5f * st.B * dB, X01 = 0.5f * st.A * dB + st.B * dC;
+    float X10 = st.B * dA + 0.5f * st.C * dB, X11 = 0.5f * st.B * dB + st.C * dC;
+    float ga = -(X00 * st.A + X01 * st.B);
+    float gb = -(X00 * st.B + X01 * st.C);
+    float gc = -(X10 * st.B + X11 * st.C);
+    // Sigma2 = T Sigma3 T^T: dSigma3 = T^T G T, dT = 2 G T Sigma3
+    const float *S = st.S3;
+    float v0[3], v1[3];
+    v0[0] = S[0] * st.T0[0] + S[1] * st.T0[1] + S[2] * st.T0[2];
+    v0[1] = S[1] * st.T0[0] + S[3] * st.T0[1] + S[4] * st.T0[2];
+    v0[2] = S[2] * st.T0[0] + S[4] * st.T0[1] + S[5] * st.T0[2];
+    v1[0] = S[0] * st.T1[0] + S[1] * st.T1[1] + S[2] * st.T1[2];
+    v1[1] = S[1] * st.T1[0] + S[3] * st.T1[1] + S[4] * st.T1[2];
+    v1[2] = S[2] * st.T1[0] + S[4] * st.T1[1] + S[5] * st.T1[2];
+    float dT0[3], dT1[3];
+    for (int j = 0; j < 3; j++) {
+        dT0[j] = 2.f * (ga * v0[j] + gb * v1[j]);
+        dT1[j] = 2.f * (gb * v0[j] + gc * v1[j]);
+    }
+    float dS[3][3];
+    for (int k = 0; k < 3; k++)
+        for (int l = 0; l < 3; l++)
+            dS[k][l] = ga * st.T0[k] * st.T0[l] + gb * (st.T0[k] * st.T1[l] + st.T1[k] * st.T0[l]) +
+                       gc * st.T1[k] * st.T1[l];
+    // T = J W
+    const float *W = fr.R;
+    float dJ00 = dT0[0] * W[0] + dT0[1] * W[1] + dT0[2] * W[2];
+    float dJ02 = dT0[0] * W[6] + dT0[1] * W[7] + dT0[2] * W[8];
+    float dJ11 = dT1[0] * W[3] + dT1[1] * W[4] + dT1[2] * W[5];
+    float dJ12 = dT1[0] * W[6] + dT1[1] * W[7] + dT1[2] * W[8];
+    float iz = 1.f / st.zc, iz2 = iz * iz, iz3 = iz2 * iz;
+    float fx = fr.fx, fy = fr.fy;
+    float du = g0.x, dv = g0.y;
+    float dxc = du * fx * iz - dJ02 * fx * iz2;
+    float dyc = dv * fy * iz - dJ12 * fy * iz2;
+    float dzc = -du * fx * st.xc * iz2 - dv * fy * st.yc * iz2 - dJ00 * fx * iz2 - dJ11 * fy * iz2 +
+                2.f * (dJ02 * fx * st.xc + dJ12 * fy * st.yc) * iz3;
+    // x_c = W mu + t
+    float dmx = W[0] * dxc + W[3] * dyc + W[6] * dzc;
+    float dmy = W[1] * dxc + W[4] * dyc + W[7] * dzc;
+    float dmz = W[2] * dxc + W[5] * dyc + W[8] * dzc;
+    acc[0] += dmx; acc[1] += dmy; acc[2] += dmz;
+    acc[3] += fr.time * dmx; acc[4] += fr.time * dmy; acc[5] += fr.time * dmz;
+    // Sigma3 = M M^T, M = R diag(s): dM = 2 dSigma3 M
+    const float *R = st.R;
+    float s[3] = {st.s0, st.s1, st.s2};
+    float G[9];
+    for (int j = 0; j < 3; j++) {
+        float dsj = 0.f;
+        for (int k = 0; k < 3; k++) {
+            float dMkj = 2.f * s[j] * (dS[k][0] * R[j] + dS[k][1] * R[3 + j] + dS[k][2] * R[6 + j]);
+            G[k * 3 + j] = dMkj * s[j];
+            dsj += dMkj * R[k * 3 + j];
+        }
+        acc[6 + j] += dsj * s[j];
+    }
+    // R(q): gradient w.r.t. the normalised quaternion, then through the normalisation
+    float w = st.qw, x = st.qx, y = st.qy, z = st.qz;
+    float S01 = G[1] + G[3], S02 = G[2] + G[6], S12 = G[5] + G[7];
+    float A10 = G[3] - G[1], A02 = G[2] - G[6], A21 = G[7] - G[5];
+    float dw = 2.f * (z * A10 + y * A02 + x * A21);
+    float dx = 2.f * (y * S01 + z * S02 + w * A21 - 2.f * x * (G[4] + G[8]));
+    float dy = 2.f * (x * S01 + z * S12 + w * A02 - 2.f * y * (G[0] + G[8]));
+    float dz = 2.f * (x * S02 + y * S12 + w * A10 - 2.f * z * (G[0] + G[4]));
+    float dot = dw * w + dx * x + dy * y + dz * z;
+    acc[9] += (dw - w * dot) * st.inv_qn;
+    acc[10] += (dx - x * dot) * st.inv_qn;
+    acc[11] += (dy - y * dot) * st.inv_qn;
+    acc[12] += (dz - z * dot) * st.inv_qn;
+}
+
+__device__ __forceinline__ void store_grad(const GradPtrs &gr, long long N, long long gi, const float acc[17],
+                                           bool atomic) {
+    float *rows[17] = {gr.mean, gr.mean + N, gr.mean + 2 * N,
+                       gr.vel, gr.vel ? gr.vel + N : nullptr, gr.vel ? gr.vel + 2 * N : nullptr,
+                       gr.log_scale, gr.log_scale + N, gr.log_scale + 2 * N,
+                       gr.quat, gr.quat + N, gr.quat + 2 * N, gr.quat + 3 * N,
+                       gr.logit, gr.rgb, gr.rgb + N, gr.rgb + 2 * N};
+#pragma unroll
+    for (int k = 0; k < 17; k++) {
+        if (!rows[k]) continue;
+        if (atomic) atomicAdd(rows[k] + gi, acc[k]);
+        else rows[k][gi] += acc[k];
+    }
+}
+
+// mode 0: one thread per pair, each Gaussian in at most one frame (plain +=)
+// mode 2: one thread per pair, overlapping sets (atomicAdd)
+__global__ void __launch_bounds__(128) project_bwd_pairs_kernel(Work w, GaussPtrs g, GradPtrs gr, int atomic) {
+    unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= w.L.P) return;
+    int f = find_frame_by_pair(w.frames, (int)w.L.F, p);
+    const DevFrame &fr = w.frames[f];
+    long long gi = fr.gauss_offset + (long long)(p - fr.pair_offset);
+    PairState st;
+    load_and_project(g, gi, fr, st);
+    float acc[17];
+#pragma unroll
+    for (int k = 0; k < 17; k++) acc[k] = 0.f;
+    pair_backward(st, fr, w.g0[p], w.g1[p], w.g2[p], acc);
+    store_grad(gr, g.N, gi, acc, atomic != 0);
+}
+
+// mode 1: one shared Gaussian set; one thread per Gaussian sums over all frames.
+__global__ void __launch_bounds__(128) project_bwd_shared_kernel(Work w, GaussPtrs g, GradPtrs gr) {
+    const DevFrame &f0 = w.frames[0];
+    unsigned j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= f0.gauss_count) return;
+    long long gi = f0.gauss_offset + j;
+    float acc[17];
+#pragma unroll
+    for (int k = 0; k < 17; k++) acc[k] = 0.f;
+    for (int f = 0; f < (int)w.L.F; f++) {
+        const DevFrame &fr = w.frames[f];
+        unsigned p = fr.pair_offset + j;
+        PairState st;
+        load_and_project(g, gi, fr, st);
+        pair_backward(st, fr, w.g0[p], w.g1[p], w.g2[p], acc);
+    }
+    store_grad(gr, g.N, gi, acc, false);
+}
+
+}  // namespace
+
+cudaError_t launch_project_fwd(const Work &w, const GaussPtrs &g, int tile_w, int tile_h, cudaStream_t s) {
+    if (w.L.P == 0) return cudaSuccess;
+    int lw = __builtin_ctz(tile_w), lh = __builtin_ctz(tile_h);
+    project_fwd_kernel<<<(w.L.P + 255) / 256, 256, 0, s>>>(w, g, lw, lh);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bin_from_screen(const Work &w, long long n, const float *u, const float *v,
+                                   const float *ex, const float *ey, const float *depth,
+                                   const uint8_t *valid, int tile_w, int tile_h, int32_t *counts,
+                                   cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    int lw = __builtin_ctz(tile_w), lh = __builtin_ctz(tile_h);
+    bin_from_screen_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w, n, u, v, ex, ey, depth, valid,
+                                                                        lw, lh, counts);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_bwd(const Work &w, const GaussPtrs &g, const GradPtrs &gr, int mode, cudaStream_t s) {
+    if (w.L.P == 0) return cudaSuccess;
+    if (mode == 1) {
+        // all frames share one set; its size is the first frame's count
+        unsigned n = w.L.P / w.L.F;
+        project_bwd_shared_kernel<<<(n + 127) / 128, 128, 0, s>>>(w, g, gr);
+    } else {
+        project_bwd_pairs_kernel<<<(w.L.P + 127) / 128, 128, 0, s>>>(w, g, gr, mode == 2 ? 1 : 0);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gvk

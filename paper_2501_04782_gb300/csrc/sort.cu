@@ -1,0 +1,271 @@
+// sort.cu -- stable LSD radix sort of (32-bit key, 32-bit value) pairs, 8 bits per pass.
+//
+// One pass is a single "onesweep" kernel: each block takes the next 3840-key tile from an
+// atomic counter, ranks its keys stably per digit (warp match + per-warp histograms),
+// publishes its per-digit counts, obtains the exclusive prefix of all earlier tiles by
+// decoupled look-back, and scatters.  The per-digit global offsets come from one
+// histogram kernel that counts every pass's digits up front.  Keys and values are read
+// once and written once per pass (the HBM roofline of the sort).
+//
+// Bounded waits: a look-back spin gives up after DevHeader::spin_limit polls, sets
+// ERR_TIMEOUT and publishes anyway; a block that gave up writes nothing (its output is
+// undefined but every write stays in bounds).
+#include <algorithm>
+#include <cstddef>
+
+#include "gv_internal.cuh"
+
+namespace gvk {
+
+namespace {
+
+constexpr unsigned kFlagAgg = 1u << 30;
+constexpr unsigned kFlagInc = 2u << 30;
+constexpr unsigned kValMask = (1u << 30) - 1u;
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Exclusive scan of one value per thread over a 256-thread block; returns the total.
+__device__ __forceinline__ unsigned block_excl_scan_256(unsigned x, unsigned *s_warp, unsigned &excl) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned t = lane < 8 ? s_warp[lane] : 0u;
+        unsigned ti = t;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            unsigned y = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= o) ti += y;
+        }
+        if (lane < 8) s_warp[8 + lane] = ti - t;
+        if (lane == 7) s_warp[16] = ti;
+    }
+    __syncthreads();
+    excl = s_warp[8 + wid] + inc - x;
+    unsigned total = s_warp[16];
+    __syncthreads();
+    return total;
+}
+
+// Per-pass digit histograms of n keys (passes of 8 bits starting at bit 0); also clears
+// look-back buffer 0 for the tiles this sort will use.
+// passes == 0: the histograms were counted by the producer of the keys; only clear.
+__global__ void __launch_bounds__(256) sort_hist_kernel(const unsigned *keys, const unsigned *n_dev, unsigned n_cap,
+                                                        int passes, unsigned *hist, unsigned *look0) {
+    __shared__ unsigned s_h[4][kRadix];
+    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0u;
+    __syncthreads();
+    unsigned n = min(*n_dev, n_cap);
+    unsigned stride = gridDim.x * blockDim.x;
+    for (unsigned base = blockIdx.x * blockDim.x; base < n; base += stride) {
+        unsigned i = base + threadIdx.x;
+        bool ok = i < n;
+        unsigned k = ok ? keys[i] : 0u;
+        unsigned active = __ballot_sync(0xffffffffu, ok);
+        if (!ok) continue;
+        for (int ps = 0; ps < passes; ps++) {
+            unsigned d = (k >> (8 * ps)) & 255u;
+            unsigned peers = __match_any_sync(active, d);
+            if ((threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) atomicAdd(&s_h[ps][d], (unsigned)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) {
+        unsigned c = (&s_h[0][0])[i];
+        if (c) atomicAdd(hist + i, c);
+    }
+    unsigned ntiles = (n + kSortTile - 1) / kSortTile;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < ntiles * kRadix; i += stride) look0[i] = 0u;
+}
+
+struct PassArgs {
+    const unsigned *keys_in, *vals_in;  // vals_in == nullptr: value = input position
+    unsigned *keys_out, *vals_out;
+    const unsigned *n_dev;
+    unsigned n_cap;
+    int shift;
+    const unsigned *hist;   // this pass's 256 digit counts
+    unsigned *look_cur;     // [tiles][256] status words of this pass
+    unsigned *look_next;    // cleared for the next pass
+    unsigned *ctr;          // tile counter of this pass
+    DevHeader *hdr;
+};
+
+__global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(PassArgs a) {
+    __shared__ unsigned s_keys[kSortTile];
+    __shared__ unsigned s_vals[kSortTile];
+    __shared__ unsigned s_whist[8][kRadix];
+    __shared__ unsigned s_gexcl[kRadix];    // exclusive global digit offsets
+    __shared__ unsigned s_dstart[kRadix];   // exclusive digit offsets inside the tile
+    __shared__ unsigned s_gbase[kRadix];    // global position of this tile's first key of a digit
+    __shared__ unsigned s_scan[24];
+    __shared__ unsigned s_tile;
+    __shared__ int s_abort;
+
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const unsigned n = min(*a.n_dev, a.n_cap);
+    const unsigned ntiles = (n + kSortTile - 1) / kSortTile;
+    const long long limit = a.hdr->spin_limit;
+    const bool drop = a.hdr->drop_signal != 0;
+    {
+        unsigned ex;
+        block_excl_scan_256(a.hist[t], s_scan, ex);
+        s_gexcl[t] = ex;
+    }
+    for (;;) {
+        if (t == 0) { s_tile = atomicAdd(a.ctr, 1u); s_abort = 0; }
+        for (int i = t; i < 8 * kRadix; i += kSortThreads) (&s_whist[0][0])[i] = 0u;
+        __syncthreads();
+        const unsigned tile = s_tile;
+        if (tile >= ntiles) break;
+        const unsigned base = tile * kSortTile;
+        unsigned k[kSortItems], v[kSortItems], r[kSortItems];
+#pragma unroll
+        for (int i = 0; i < kSortItems; i++) {
+            unsigned idx = base + wid * (32 * kSortItems) + i * 32 + lane;
+            if (idx < n) {
+                k[i] = a.keys_in[idx];
+                v[i] = a.vals_in ? a.vals_in[idx] : idx;
+            } else {
+                k[i] = 0xFFFFFFFFu;  // tail sentinel: ranks after every real key of digit 255
+                v[i] = 0u;
+            }
+        }
+        // stable rank inside the warp: by item, then by lane
+#pragma unroll
+        for (int i = 0; i < kSortItems; i++) {
+            unsigned d = (k[i] >> a.shift) & 255u;
+            unsigned peers = __match_any_sync(0xffffffffu, d);
+            unsigned before = s_whist[wid][d];
+            r[i] = before + __popc(peers & lanemask_lt());
+            __syncwarp();
+            if (lane == __ffs(peers) - 1) s_whist[wid][d] = before + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        // thread t owns digit t: exclusive offsets over warps, tile total
+        unsigned total = 0;
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            unsigned c = s_whist[q][t];
+            s_whist[q][t] = total;
+            total += c;
+        }
+        unsigned tail = 0;  // sentinels counted in digit 255 of the last tile
+        if (t == 255 && base + kSortTile > n) tail = base + kSortTile - n;
+        const unsigned mine = total - tail;
+        // decoupled look-back for digit t
+        unsigned excl = 0;
+        if (tile == 0) {
+            if (!drop) atomicExch(a.look_cur + t, kFlagInc | mine);
+        } else {
+            atomicExch(a.look_cur + (size_t)tile * kRadix + t, kFlagAgg | mine);
+            long long spins = 0;
+            int j = (int)tile - 1;
+            bool gave_up = false;
+            while (j >= 0) {
+                unsigned st = *((volatile unsigned *)(a.look_cur + (size_t)j * kRadix + t));
+                unsigned fl = st & ~kValMask;
+                if (fl == kFlagInc) { excl += st & kValMask; break; }
+                if (fl == kFlagAgg) { excl += st & kValMask; j--; spins = 0; continue; }
+                if (++spins > limit || (*((volatile unsigned *)&a.hdr->err) & ERR_TIMEOUT)) {
+                    gave_up = true;
+                    break;
+                }
+                __nanosleep(32);
+            }
+            if (gave_up) {
+                atomicOr(&a.hdr->err, ERR_TIMEOUT);
+                s_abort = 1;
+            }
+            atomicExch(a.look_cur + (size_t)tile * kRadix + t, kFlagInc | ((excl + mine) & kValMask));
+        }
+        unsigned dex;
+        block_excl_scan_256(total, s_scan, dex);
+        s_dstart[t] = dex;
+        s_gbase[t] = s_gexcl[t] + excl;
+        a.look_next[(size_t)tile * kRadix + t] = 0u;
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kSortItems; i++) {
+            unsigned d = (k[i] >> a.shift) & 255u;
+            unsigned pos = s_dstart[d] + s_whist[wid][d] + r[i];
+            s_keys[pos] = k[i];
+            s_vals[pos] = v[i];
+        }
+        __syncthreads();
+        if (!s_abort) {
+            for (int pos = t; pos < kSortTile; pos += kSortThreads) {
+                unsigned key = s_keys[pos];
+                unsigned d = (key >> a.shift) & 255u;
+                unsigned gpos = s_gbase[d] + (unsigned)pos - s_dstart[d];
+                if (gpos < n) {
+                    a.keys_out[gpos] = key;
+                    a.vals_out[gpos] = s_vals[pos];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+int sort_passes(int bits) { return bits <= 0 ? 0 : (bits + 7) / 8; }
+
+// Sorts keys[0]/vals[0] by their low `bits` bits.  *result_buf receives the buffer index
+// (0 or 1) that holds the sorted output.  hist_slot selects 4 histogram rows of the
+// workspace (0 or 4), ctr_slot 4 tile counters.  Histogram rows and counters must be
+// zero on entry (the setup kernel clears them), unless hist_counted says the producer
+// of the keys already counted every pass's digits into those rows.
+cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2], const unsigned *n_dev,
+                              unsigned n_cap, int bits, bool vals_identity, bool hist_counted, int hist_slot,
+                              int ctr_slot, int num_sms, cudaStream_t s, int *result_buf) {
+    int passes = sort_passes(bits);
+    *result_buf = 0;
+    if (passes == 0 || n_cap == 0) return cudaSuccess;
+    unsigned *hist = w.hist + (size_t)hist_slot * kRadix;
+    unsigned max_tiles = (n_cap + kSortTile - 1) / kSortTile;
+    unsigned *look[2] = {w.look, w.look + (size_t)w.L.look_tiles * kRadix};
+    int hist_blocks = (int)std::min<unsigned>((n_cap + 255) / 256, (unsigned)num_sms * 4u);
+    sort_hist_kernel<<<hist_blocks, 256, 0, s>>>(keys[0], n_dev, n_cap, hist_counted ? 0 : passes, hist, look[0]);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    int grid = (int)std::min<unsigned>(max_tiles, (unsigned)num_sms * 3u);
+    int cur = 0;
+    for (int ps = 0; ps < passes; ps++) {
+        PassArgs a;
+        a.keys_in = keys[cur];
+        a.vals_in = (ps == 0 && vals_identity) ? nullptr : vals[cur];
+        a.keys_out = keys[cur ^ 1];
+        a.vals_out = vals[cur ^ 1];
+        a.n_dev = n_dev;
+        a.n_cap = n_cap;
+        a.shift = 8 * ps;
+        a.hist = hist + (size_t)ps * kRadix;
+        a.look_cur = look[ps & 1];
+        a.look_next = look[(ps & 1) ^ 1];
+        a.ctr = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(w.hdr) + offsetof(DevHeader, sort_ctr)) +
+                ctr_slot + ps;
+        a.hdr = w.hdr;
+        sort_pass_kernel<<<grid, kSortThreads, 0, s>>>(a);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        cur ^= 1;
+    }
+    *result_buf = cur;
+    return cudaSuccess;
+}
+
+}  // namespace gvk

@@ -1,0 +1,134 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the C ABI, run the
+FP64 oracle on the same seeded inputs, and compare with the stated tolerances.
+
+Tolerances (from the task's accuracy bar): tile counts and sorted key lists bit-exact;
+pixel values within max-abs 1e-4; gradients within 1e-3 relative or 1e-6 absolute.
+Pixels the oracle flags as ambiguous (a decision within FP32 reach of a threshold)
+are compared at 1e-2 and counted; their upstream gradient is set to zero on both sides.
+A gradient element failing both bounds but within 1e-5 of the sum of absolute per-pixel
+contributions is counted as cancellation-limited (FP32 summation order), not hidden."""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+import oracle
+from paper_2501_04782_gb300 import gv, synth
+
+PIX_TOL = 1e-4
+AMB_TOL = 1e-2
+GRAD_REL = 1e-3
+GRAD_ABS = 1e-6
+CANCEL_REL = 1e-5
+
+
+def dev_params(g: dict) -> dict:
+    return {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).cuda() for k, v in g.items()}
+
+
+class GpuRun:
+    """Forward (and optionally backward) of a batch of frames through the C ABI."""
+
+    def __init__(self, ctx: gv.Context, g: dict, frames, key_capacity: int = 0):
+        self.ctx = ctx
+        self.g = g
+        self.params = dev_params(g)
+        self.frames, self.total = gv.layout_frames(frames)
+        self.ws = torch.empty(ctx.workspace_size(self.frames, key_capacity), dtype=torch.uint8, device="cuda")
+        self.image = torch.full((3 * self.total,), float("nan"), device="cuda")
+        self.T = torch.full((self.total,), float("nan"), device="cuda")
+        self.idx = torch.full((self.total,), -7, dtype=torch.int32, device="cuda")
+
+    def forward(self, grow: bool = True):
+        self.ctx.render_fwd(self.params, self.frames, self.ws, self.image, self.T, self.idx)
+        st, self.K = self.ctx.read_status(self.ws, raise_on_error=not grow)
+        if st == gv.GV_ERR_CAPACITY:
+            self.ws = torch.empty(self.ctx.workspace_size(self.frames, self.K + 1024), dtype=torch.uint8,
+                                  device="cuda")
+            self.ctx.render_fwd(self.params, self.frames, self.ws, self.image, self.T, self.idx)
+            st, self.K = self.ctx.read_status(self.ws)
+        elif st != gv.GV_OK:
+            self.ctx.check(st)
+        return self
+
+    def backward(self, dL_flat: np.ndarray) -> dict:
+        dL = torch.from_numpy(np.ascontiguousarray(dL_flat, np.float32)).cuda()
+        grads = {k: torch.zeros_like(v) for k, v in self.params.items()}
+        self.ctx.render_bwd(self.params, self.frames, self.ws, self.T, self.idx, dL, grads)
+        torch.cuda.synchronize()
+        return {k: v.cpu().numpy() for k, v in grads.items()}
+
+    def frame_image(self, f: int) -> np.ndarray:
+        fr = self.frames[f]
+        W, H = fr.cam.W, fr.cam.H
+        s = 3 * fr.pixel_offset
+        return self.image[s:s + 3 * W * H].view(3, H, W).cpu().numpy()
+
+    def frame_T(self, f: int) -> np.ndarray:
+        fr = self.frames[f]
+        return self.T[fr.pixel_offset:fr.pixel_offset + fr.cam.W * fr.cam.H].view(fr.cam.H, fr.cam.W).cpu().numpy()
+
+    def frame_idx(self, f: int) -> np.ndarray:
+        fr = self.frames[f]
+        return self.idx[fr.pixel_offset:fr.pixel_offset + fr.cam.W * fr.cam.H].view(fr.cam.H, fr.cam.W).cpu().numpy()
+
+    def debug(self) -> dict:
+        P = sum(f.gauss_count for f in self.frames)
+        tiles = sum(((f.cam.W + 7) // 8) * ((f.cam.H + 7) // 8) for f in self.frames)
+        return self.ctx.debug_read(self.frames, self.ws, P, max(self.K, 1), tiles)
+
+
+def frame_gaussians(g: dict, off: int, cnt: int) -> dict:
+    return {k: v[..., off:off + cnt] for k, v in g.items()}
+
+
+def compare_pixels(gpu_rgb: np.ndarray, ref_rgb: np.ndarray, amb: np.ndarray, label: str = "") -> dict:
+    """gpu_rgb, ref_rgb: [n,3]; amb: [n] ambiguity bits."""
+    err = np.abs(gpu_rgb.astype(np.float64) - ref_rgb).max(axis=1)
+    clean = amb == 0
+    st = dict(n=len(err), n_amb=int((~clean).sum()), max_clean=float(err[clean].max()) if clean.any() else 0.0,
+              max_amb=float(err[~clean].max()) if (~clean).any() else 0.0)
+    assert st["max_clean"] <= PIX_TOL, f"{label} max-abs {st['max_clean']:.3e} > {PIX_TOL} ({st})"
+    assert st["max_amb"] <= AMB_TOL, f"{label} ambiguous pixel error {st['max_amb']:.3e} > {AMB_TOL}"
+    assert st["n_amb"] <= max(3, 0.01 * st["n"]), f"{label} too many ambiguous pixels {st}"
+    print(f"[pixels {label}] {st}")
+    return st
+
+
+def compare_grads(gpu: dict, ref: np.ndarray, gabs: np.ndarray, label: str = "", keys=None,
+                  max_cancel_frac: float = 0.002) -> dict:
+    """gpu: dict of parameter arrays; ref, gabs: [17, N] from the oracle."""
+    refs = oracle.split_grad(ref)
+    abss = oracle.split_grad(gabs)
+    stats = {}
+    total_fail, total_cancel, total = 0, 0, 0
+    for k in keys or ("mean", "log_scale", "quat", "opacity_logit", "rgb", "vel"):
+        if k not in gpu:
+            continue
+        a = gpu[k].astype(np.float64).reshape(refs[k].shape)
+        b = refs[k]
+        d = np.abs(a - b)
+        ok = (d <= GRAD_REL * np.abs(b)) | (d <= GRAD_ABS)
+        cancel = ~ok & (d <= CANCEL_REL * abss[k])
+        fail = ~ok & ~cancel
+        stats[k] = dict(n=int(a.size), cancel=int(cancel.sum()), fail=int(fail.sum()),
+                        worst_rel=float(np.max(d / np.maximum(np.abs(b), GRAD_ABS / GRAD_REL))))
+        if fail.any():
+            i = np.argwhere(fail)[0]
+            stats[k]["example"] = (tuple(int(x) for x in i), float(a[tuple(i)]), float(b[tuple(i)]),
+                                   float(abss[k][tuple(i)]))
+        total_fail += int(fail.sum())
+        total_cancel += int(cancel.sum())
+        total += a.size
+    print(f"[grads {label}] {stats}")
+    assert total_fail == 0, f"{label} gradient mismatches: {stats}"
+    assert total_cancel <= max(2, max_cancel_frac * total), f"{label} too many cancellation-limited: {stats}"
+    return stats
+
+
+def oracle_pixels_for_frame(g, cam, px, py, params=None):
+    return oracle.render_pixels(g, cam, px, py, params)
+
+
+def sample_pixels(seed: int, W: int, H: int, n: int):
+    return synth.pixel_sample(seed, W, H, n)

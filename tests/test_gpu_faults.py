@@ -1,0 +1,60 @@
+"""Failure reporting without a GPU fault: capacity overflow is detected and reported with
+the key count needed (nothing is written out of bounds), a bounded device wait that runs
+out (a look-back flag that nothing sets) returns GV_ERR_TIMEOUT, and the context stays
+usable afterwards; invalid arguments are rejected on the host."""
+import numpy as np
+import pytest
+import torch
+
+from gvtest import GpuRun
+from paper_2501_04782_gb300 import gv, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def test_capacity_overflow_is_reported_and_retry_succeeds():
+    w = synth.workload_single_128()
+    ctx = gv.Context((8, 8), 64)
+    small = GpuRun(ctx, w["gaussians"], w["frames"], key_capacity=500)
+    guard = torch.full((1 << 16,), 7, dtype=torch.uint8, device="cuda")
+    ws = torch.cat([small.ws, guard])  # bytes after the workspace must stay untouched
+    small.ws = ws[:small.ws.numel()]
+    ctx.render_fwd(small.params, small.frames, small.ws, small.image, small.T, small.idx)
+    st, needed = ctx.read_status(small.ws, raise_on_error=False)
+    assert st == gv.GV_ERR_CAPACITY
+    assert needed > 500
+    assert torch.all(ws[small.ws.numel():] == 7)
+    big = GpuRun(ctx, w["gaussians"], w["frames"], key_capacity=needed).forward()
+    assert big.K == needed
+
+
+def test_bounded_wait_times_out_and_context_recovers():
+    w = synth.workload_single_540p(N=40000)
+    ctx = gv.Context((16, 16), 128)
+    ref = GpuRun(ctx, w["gaussians"], w["frames"]).forward()
+    ctx.debug_set_wait(spin_limit=64, drop_signal=True)
+    run = GpuRun(ctx, w["gaussians"], w["frames"])
+    ctx.render_fwd(run.params, run.frames, run.ws, run.image, run.T, run.idx)
+    st, _ = ctx.read_status(run.ws, raise_on_error=False)
+    assert st == gv.GV_ERR_TIMEOUT
+    ctx.debug_set_wait(0, False)
+    again = GpuRun(ctx, w["gaussians"], w["frames"]).forward()
+    assert torch.equal(again.image, ref.image)
+
+
+def test_invalid_arguments_are_rejected():
+    with pytest.raises(gv.GVError):
+        gv.Context((12, 12), 64)
+    with pytest.raises(gv.GVError):
+        gv.Context((16, 16), 100)
+    ctx = gv.Context((16, 16), 64)
+    w = synth.workload_single_128(N=10)
+    run = GpuRun(ctx, w["gaussians"], w["frames"])
+    bad = [gv.Frame(w["frames"][0][0], 5, 10, 0)]  # range beyond N
+    with pytest.raises(gv.GVError):
+        ctx.render_fwd(run.params, bad, run.ws, run.image, run.T, run.idx)
+    with pytest.raises(gv.GVError):
+        ctx.render_fwd(run.params, run.frames, run.ws[:64], run.image, run.T, run.idx)
+    zero = [gv.Frame(synth.Camera(0, 10, 1, 1, 0, 0), 0, 10, 0)]
+    with pytest.raises(gv.GVError):
+        ctx.workspace_size(zero)
