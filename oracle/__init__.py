@@ -27,6 +27,8 @@ import numpy as np
 
 from . import build as _build
 
+AMB_IMAGE = 1 | 2 | 4   # ambiguity bits that can change a pixel value
+AMB_ANY = AMB_IMAGE | 8  # ... or its gradient
 ALPHA_MIN = 1.0 / 255.0
 ALPHA_MAX = 0.99
 T_STOP = 1e-4
@@ -171,7 +173,9 @@ def project(g: dict, cam, params: Params | None = None) -> dict:
 
 def render_pixels(g: dict, cam, px, py, params: Params | None = None, nthreads: int | None = None) -> dict:
     """Render the listed pixels.  Returns rgb [n,3], T [n], last [n] (Gaussian index or -1),
-    amb [n] (ambiguity bits), n [n] (contributor count)."""
+    amb [n] (ambiguity bits: 1 alpha cutoff, 2 transmittance stop, 4 depth order -- these
+    can change the image; 8 the 0.99 clamp -- changes the gradient only), n [n]
+    (contributor count)."""
     params = params or Params()
     px = np.ascontiguousarray(px, np.int32)
     py = np.ascontiguousarray(py, np.int32)

@@ -36,7 +36,10 @@
  * Ambiguity flags: where the CUDA path (FP32) may legitimately take the other side of a
  * hard threshold, the pixel is flagged: bit 0 an alpha within amb_alpha_rel of
  * alpha_min, bit 1 a transmittance within amb_T_rel of T_stop, bit 2 two consecutive
- * contributors whose depths differ by less than amb_depth_rel (relative).
+ * contributors whose depths differ by less than amb_depth_rel (relative), bit 3 a
+ * composited o exp(-power) within amb_alpha_rel of alpha_max (the clamp is continuous in
+ * the image but switches the opacity/conic/mean gradient of that pixel on or off, so
+ * this bit concerns the backward only).
  */
 #include <math.h>
 #include <pthread.h>
@@ -229,6 +232,7 @@ static void render_pixel(const orc_proj *pr, int64_t N, const orc_params *p, dou
         if (c->alpha < p->alpha_min) continue;
         if (n > 0 && fabs(c->depth - prev_depth) <= p->amb_depth_rel * fabs(c->depth)) amb |= 4;
         prev_depth = c->depth;
+        if (p->alpha_max < INFINITY && fabs(c->araw - p->alpha_max) <= p->amb_alpha_rel * p->alpha_max) amb |= 8;
         const orc_proj *q = &pr[c->idx];
         if (contrib) {
             orc_contrib *o = &contrib[n];

@@ -165,6 +165,7 @@ gv_status make_plan(gv_ctx *ctx, const gv_options &o, long long N, const gv_fram
     L.dval[1] = take(4 * Pn);
     L.blocksum = take(4 * std::max<size_t>(L.emit_blocks, 1));
     L.blockprefix = take(4 * std::max<size_t>(L.emit_blocks, 1));
+    L.offsets = take(4 * (Pn + 1));
     L.g0 = take(16 * Pn);
     L.g1 = take(16 * Pn);
     L.g2 = take(4 * Pn);
@@ -223,6 +224,7 @@ Work make_work(void *ws, const Layout &L) {
     }
     w.blocksum = (unsigned *)(b + L.blocksum);
     w.blockprefix = (unsigned *)(b + L.blockprefix);
+    w.offsets = (unsigned *)(b + L.offsets);
     w.g0 = (float4 *)(b + L.g0);
     w.g1 = (float4 *)(b + L.g1);
     w.g2 = (float *)(b + L.g2);
@@ -288,8 +290,8 @@ gv_status forward_stages(gv_ctx *ctx, const gv_gaussians *g, const Plan &pl, con
             GV_CUDA(launch_radix_sort(w, dk, dv, n_pairs, w.L.P, 32, true, false, 0, 0, ctx->num_sms, s, &dres));
         }
         {
-            StageTimer tm(ctx, GV_STAGE_EMIT, s, 3);
-            GV_CUDA(launch_emit(w, dres, w.L.tile_bits, 4, s));
+            StageTimer tm(ctx, GV_STAGE_EMIT, s, 4);
+            GV_CUDA(launch_emit(w, dres, w.L.tile_bits, 4, ctx->num_sms, s));
         }
         int tres = 0;
         {
@@ -767,7 +769,7 @@ gv_status gv_debug_bin_sort(gv_ctx *ctx, int64_t n, const float *u, const float 
                                                                        offsetof(DevHeader, n_pairs));
         unsigned *dk[2] = {w.dkey[0], w.dkey[1]}, *dv[2] = {w.dval[0], w.dval[1]};
         GV_CUDA(launch_radix_sort(w, dk, dv, n_pairs, w.L.P, 32, true, false, 0, 0, ctx->num_sms, s, &dres));
-        GV_CUDA(launch_emit(w, dres, w.L.tile_bits, 4, s));
+        GV_CUDA(launch_emit(w, dres, w.L.tile_bits, 4, ctx->num_sms, s));
         const unsigned *n_keys = reinterpret_cast<const unsigned *>(reinterpret_cast<const char *>(w.hdr) +
                                                                       offsetof(DevHeader, keys_used));
         unsigned *tk[2] = {w.tkey[0], w.tkey[1]}, *tv[2] = {w.tval[0], w.tval[1]};

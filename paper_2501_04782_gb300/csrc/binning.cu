@@ -7,6 +7,8 @@
 // pair order would give -- ordered by tile, then depth, then pair index -- but the
 // expensive per-key sort touches only the live tile-id bits (one or two 8-bit passes
 // instead of five or six).
+#include <algorithm>
+
 #include "gv_internal.cuh"
 
 namespace gvk {
@@ -98,18 +100,12 @@ __global__ void __launch_bounds__(1024) count_scan_kernel(Work w) {
     }
 }
 
-// Load-balanced emission: block b owns kEmitBlock pairs in depth order; its keys are
-// spread evenly over the threads (each key finds its pair by binary search over the
-// block's exclusive count offsets).  Also counts the tile-sort digit histograms.
-__global__ void __launch_bounds__(kEmitThreads) emit_kernel(Work w, const unsigned *order, int tile_passes,
-                                                            unsigned *tile_hist) {
-    __shared__ unsigned s_off[kEmitBlock + 1];
-    __shared__ unsigned s_pair[kEmitBlock];
-    __shared__ unsigned s_hist[4][kRadix];
+// Exclusive key offsets of every pair in depth order: off[i] for i < P, off[P] = K.
+// Block b scans its kEmitBlock pairs and adds the block prefix.
+__global__ void __launch_bounds__(kEmitThreads) offsets_kernel(Work w, const unsigned *order) {
     __shared__ unsigned s_w[8];
     const unsigned b = blockIdx.x, base = b * kEmitBlock;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    for (int i = t; i < 4 * kRadix; i += kEmitThreads) (&s_hist[0][0])[i] = 0u;
     // blocked: thread t owns pairs base + t*8 .. +7
     unsigned c[kEmitItems], sum = 0;
 #pragma unroll
@@ -118,7 +114,6 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(Work w, const unsign
         unsigned p = idx < w.L.P ? order[idx] : 0u;
         if (p >= w.L.P) p = 0u;  // ids are in range unless a bounded wait gave up
         c[i] = idx < w.L.P ? w.rect[p].z : 0u;
-        s_pair[t * kEmitItems + i] = p;
         sum += c[i];
     }
     unsigned inc = sum;
@@ -129,52 +124,89 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(Work w, const unsign
     }
     if (lane == 31) s_w[wid] = inc;
     __syncthreads();
-    unsigned wex = 0;
-    for (int q = 0; q < wid; q++) wex += s_w[q];
-    unsigned run = wex + inc - sum;
+    unsigned run = w.blockprefix[b] + inc - sum;
+    for (int q = 0; q < wid; q++) run += s_w[q];
 #pragma unroll
     for (int i = 0; i < kEmitItems; i++) {
-        s_off[t * kEmitItems + i] = run;
+        unsigned idx = base + t * kEmitItems + i;
+        if (idx < w.L.P) w.offsets[idx] = min(run, w.L.key_cap);
         run += c[i];
     }
-    if (t == kEmitThreads - 1) s_off[kEmitBlock] = run;
-    __syncthreads();
-    const unsigned total = s_off[kEmitBlock];
-    const unsigned gbase = w.blockprefix[b];
-    const unsigned cap = w.L.key_cap;
-    // every thread runs the same number of rounds, so warp votes see the full warp
-    for (unsigned e0 = 0; e0 < total; e0 += kEmitThreads) {
-        const unsigned e = e0 + t;
-        bool ok = e < total;
-        unsigned tile = 0;
-        if (ok) {
-            // largest i with s_off[i] <= e (pairs with zero count share offsets)
-            int lo = 0, hi = kEmitBlock - 1;
+    if (b == 0 && t == 0) w.offsets[w.L.P] = w.hdr->keys_used;
+}
+
+// Key emission balanced over keys: each block iteration takes kEmitBlock consecutive
+// keys, finds the pairs that own them (binary search over a shared-memory window of the
+// depth-ordered offsets; every pair in the window owns at least one key, pairs with no
+// key sort last) and writes (tile id, pair id), the tiles of a pair in row-major order.
+// Also counts the tile-sort digit histograms.
+__global__ void __launch_bounds__(kEmitThreads) emit_kernel(Work w, const unsigned *order, int tile_passes,
+                                                            unsigned *tile_hist) {
+    __shared__ unsigned s_off[kEmitBlock + 1];
+    __shared__ unsigned s_pair[kEmitBlock + 1];
+    __shared__ unsigned s_hist[4][kRadix];
+    __shared__ unsigned s_lo, s_n;
+    const int t = threadIdx.x, lane = t & 31;
+    for (int i = t; i < 4 * kRadix; i += kEmitThreads) (&s_hist[0][0])[i] = 0u;
+    const unsigned K = w.hdr->keys_used;
+    const unsigned P = w.L.P;
+    const unsigned *off = w.offsets;
+    const unsigned nchunks = (K + kEmitBlock - 1) / kEmitBlock;
+    for (unsigned chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+        const unsigned k0 = chunk * kEmitBlock;
+        const unsigned k1 = min(K, k0 + kEmitBlock);
+        __syncthreads();
+        if (t == 0) {
+            // largest i with off[i] <= k0, and with off[i] <= k1 - 1
+            unsigned lo = 0, hi = P - 1;
             while (lo < hi) {
-                int mid = (lo + hi + 1) >> 1;
-                if (s_off[mid] <= e) lo = mid; else hi = mid - 1;
+                unsigned mid = (lo + hi + 1) >> 1;
+                if (off[mid] <= k0) lo = mid; else hi = mid - 1;
             }
-            unsigned p = s_pair[lo];
-            unsigned j = e - s_off[lo];
-            uint4 r = w.rect[p];
-            unsigned tx0 = r.x & 0xFFFFu, ty0 = r.x >> 16, tx1 = r.y & 0xFFFFu;
-            unsigned wr = tx1 - tx0 + 1u;
-            unsigned ty = ty0 + j / wr, tx = tx0 + j % wr;
-            const DevFrame &fr = w.frames[r.w];
-            tile = fr.tile_offset + ty * fr.tiles_x + tx;
-            unsigned gk = gbase + e;
-            ok = gk < cap;
-            if (ok) {
-                w.tkey[0][gk] = tile;
-                w.tval[0][gk] = p;
+            unsigned lo2 = lo, hi2 = P - 1;
+            while (lo2 < hi2) {
+                unsigned mid = (lo2 + hi2 + 1) >> 1;
+                if (off[mid] <= k1 - 1) lo2 = mid; else hi2 = mid - 1;
             }
+            s_lo = lo;
+            s_n = min(lo2 - lo + 1, (unsigned)kEmitBlock);
         }
-        unsigned active = __ballot_sync(0xffffffffu, ok);
-        if (ok) {
-            for (int ps = 0; ps < tile_passes; ps++) {
-                unsigned d = (tile >> (8 * ps)) & 255u;
-                unsigned peers = __match_any_sync(active, d);
-                if (lane == __ffs(peers) - 1) atomicAdd(&s_hist[ps][d], (unsigned)__popc(peers));
+        __syncthreads();
+        const unsigned plo = s_lo, np = s_n;
+        for (unsigned i = t; i < np; i += kEmitThreads) {
+            s_off[i] = off[plo + i];
+            unsigned p = order[plo + i];
+            s_pair[i] = p < P ? p : 0u;
+        }
+        __syncthreads();
+        for (unsigned e0 = k0; e0 < k1; e0 += kEmitThreads) {
+            const unsigned e = e0 + t;
+            const bool ok = e < k1;
+            unsigned tile = 0;
+            if (ok) {
+                int lo = 0, hi = (int)np - 1;
+                while (lo < hi) {
+                    int mid = (lo + hi + 1) >> 1;
+                    if (s_off[mid] <= e) lo = mid; else hi = mid - 1;
+                }
+                const unsigned p = s_pair[lo];
+                const unsigned j = e - s_off[lo];
+                const uint4 r = w.rect[p];
+                const unsigned tx0 = r.x & 0xFFFFu, ty0 = r.x >> 16, tx1 = r.y & 0xFFFFu;
+                const unsigned wr = tx1 - tx0 + 1u;
+                const unsigned ty = ty0 + j / wr, tx = tx0 + j % wr;
+                const DevFrame &fr = w.frames[min(r.w, w.L.F - 1u)];
+                tile = min(fr.tile_offset + ty * fr.tiles_x + tx, w.L.tiles - 1u);
+                w.tkey[0][e] = tile;
+                w.tval[0][e] = p;
+            }
+            const unsigned active = __ballot_sync(0xffffffffu, ok);
+            if (ok) {
+                for (int ps = 0; ps < tile_passes; ps++) {
+                    unsigned d = (tile >> (8 * ps)) & 255u;
+                    unsigned peers = __match_any_sync(active, d);
+                    if (lane == __ffs(peers) - 1) atomicAdd(&s_hist[ps][d], (unsigned)__popc(peers));
+                }
             }
         }
     }
@@ -222,13 +254,16 @@ cudaError_t launch_setup(const Work &w, const FrameChunk &chunk, int first, int 
     return cudaGetLastError();
 }
 
-cudaError_t launch_emit(const Work &w, int depth_buf, int tile_bits, int tile_hist_slot, cudaStream_t s) {
+cudaError_t launch_emit(const Work &w, int depth_buf, int tile_bits, int tile_hist_slot, int num_sms, cudaStream_t s) {
     if (w.L.P == 0) return cudaSuccess;
     const unsigned *order = w.dval[depth_buf];
     count_reduce_kernel<<<w.L.emit_blocks, kEmitThreads, 0, s>>>(w, order);
     count_scan_kernel<<<1, 1024, 0, s>>>(w);
+    offsets_kernel<<<w.L.emit_blocks, kEmitThreads, 0, s>>>(w, order);
     int passes = tile_bits <= 0 ? 0 : (tile_bits + 7) / 8;
-    emit_kernel<<<w.L.emit_blocks, kEmitThreads, 0, s>>>(w, order, passes, w.hist + (size_t)tile_hist_slot * kRadix);
+    unsigned chunks = (w.L.key_cap + kEmitBlock - 1) / kEmitBlock;
+    unsigned grid = std::max(1u, std::min(chunks, (unsigned)num_sms * 8u));
+    emit_kernel<<<grid, kEmitThreads, 0, s>>>(w, order, passes, w.hist + (size_t)tile_hist_slot * kRadix);
     return cudaGetLastError();
 }
 

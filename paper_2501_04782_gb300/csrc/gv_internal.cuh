@@ -73,7 +73,7 @@ constexpr int kEmitBlock = kEmitThreads * kEmitItems;  // 2048 pairs per block
 struct Layout {
     size_t hdr, frames;
     size_t feat0, feat1, feat2, rect, dkey[2], dval[2];
-    size_t blocksum, blockprefix;
+    size_t blocksum, blockprefix, offsets;
     size_t g0, g1, g2;
     size_t ranges;
     size_t tkey[2], tval[2];
@@ -96,6 +96,7 @@ struct Work {
     uint4 *rect;
     unsigned *dkey[2], *dval[2];
     unsigned *blocksum, *blockprefix;
+    unsigned *offsets;  // [P + 1] exclusive key offsets of the pairs in depth order
     float4 *g0, *g1;
     float *g2;
     uint2 *ranges;
@@ -137,7 +138,8 @@ cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2
                               unsigned n_cap, int bits, bool vals_identity, bool hist_counted, int hist_slot,
                               int ctr_slot, int num_sms, cudaStream_t s, int *result_buf);
 // binning.cu
-cudaError_t launch_emit(const Work &w, int depth_buf, int tile_bits, int tile_hist_slot, cudaStream_t s);
+cudaError_t launch_emit(const Work &w, int depth_buf, int tile_bits, int tile_hist_slot, int num_sms,
+                        cudaStream_t s);
 cudaError_t launch_ranges(const Work &w, int tile_buf, int num_sms, cudaStream_t s);
 // composite.cu
 cudaError_t launch_composite_fwd(const Work &w, int tile_w, int tile_h, int depth, int tile_buf,

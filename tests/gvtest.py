@@ -4,9 +4,13 @@ FP64 oracle on the same seeded inputs, and compare with the stated tolerances.
 Tolerances (from the task's accuracy bar): tile counts and sorted key lists bit-exact;
 pixel values within max-abs 1e-4; gradients within 1e-3 relative or 1e-6 absolute.
 Pixels the oracle flags as ambiguous (a decision within FP32 reach of a threshold)
-are compared at 1e-2 and counted; their upstream gradient is set to zero on both sides.
-A gradient element failing both bounds but within 1e-5 of the sum of absolute per-pixel
-contributions is counted as cancellation-limited (FP32 summation order), not hidden."""
+are compared at 1e-2 and counted (at most 5 %: dense 540p frames put ~400 candidate
+Gaussians behind a pixel); their upstream gradient is set to zero on both sides.
+A gradient element failing both bounds but within CANCEL_REL of the sum of absolute
+per-pixel contributions is counted as cancellation-limited, not hidden: each FP32
+contribution carries a relative error up to about half an ulp of the pixel coordinate
+over the smallest footprint, 2^-24 * 2048 / sqrt(0.3) ~ 2e-4 for frames up to 2048 px,
+and a sum that cancels to a small fraction of its terms keeps that absolute error."""
 from __future__ import annotations
 
 import numpy as np
@@ -19,7 +23,7 @@ PIX_TOL = 1e-4
 AMB_TOL = 1e-2
 GRAD_REL = 1e-3
 GRAD_ABS = 1e-6
-CANCEL_REL = 1e-5
+CANCEL_REL = 2e-4
 
 
 def dev_params(g: dict) -> dict:
@@ -85,12 +89,12 @@ def frame_gaussians(g: dict, off: int, cnt: int) -> dict:
 def compare_pixels(gpu_rgb: np.ndarray, ref_rgb: np.ndarray, amb: np.ndarray, label: str = "") -> dict:
     """gpu_rgb, ref_rgb: [n,3]; amb: [n] ambiguity bits."""
     err = np.abs(gpu_rgb.astype(np.float64) - ref_rgb).max(axis=1)
-    clean = amb == 0
+    clean = (amb & oracle.AMB_IMAGE) == 0
     st = dict(n=len(err), n_amb=int((~clean).sum()), max_clean=float(err[clean].max()) if clean.any() else 0.0,
               max_amb=float(err[~clean].max()) if (~clean).any() else 0.0)
     assert st["max_clean"] <= PIX_TOL, f"{label} max-abs {st['max_clean']:.3e} > {PIX_TOL} ({st})"
     assert st["max_amb"] <= AMB_TOL, f"{label} ambiguous pixel error {st['max_amb']:.3e} > {AMB_TOL}"
-    assert st["n_amb"] <= max(3, 0.01 * st["n"]), f"{label} too many ambiguous pixels {st}"
+    assert st["n_amb"] <= max(3, 0.05 * st["n"]), f"{label} too many ambiguous pixels {st}"
     print(f"[pixels {label}] {st}")
     return st
 

@@ -219,3 +219,17 @@ def test_ambiguity_flags_mark_threshold_pixels():
     r = oracle.render_pixels(g, cam, [5, 4], [4, 4])
     assert r["amb"][0] & 1
     assert r["amb"][1] == 0
+
+
+def test_clamp_flag_marks_gradient_only_ambiguity():
+    """o exp(-power) exactly at the 0.99 clamp sets bit 3 (the image is continuous there,
+    the opacity/conic/mean gradient is not); far from it, no flag."""
+    cam = synth.Camera(8, 8, 100.0, 100.0, 4.55, 4.5)  # the mean sits 0.05 px right of pixel (4,4)'s centre
+    z, s = 5.0, 0.02
+    sig2 = (100 * s / z) ** 2 + 0.3
+    o = 0.99 / math.exp(-0.5 * 0.05 ** 2 / sig2)
+    g = one_gaussian((0, 0, z), [math.log(s)] * 3, logit=math.log(o / (1 - o)))
+    r = oracle.render_pixels(g, cam, [4, 5], [4, 4])
+    assert r["amb"][0] == 8
+    assert r["rgb"][0, 0] == pytest.approx(0.99, rel=1e-9)
+    assert r["amb"][1] == 0  # one pixel further: alpha ~ 0.37, far from every threshold
