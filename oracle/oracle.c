@@ -413,10 +413,13 @@ static void chain_rule(const orc_proj *q, const orc_camera *cam, const double d2
     for (int k = 0; k < 4; k++) out[9 + k] = (gqn[k] - q->qn[k] * dot) / q->qnorm;
 }
 
-/* Per-pixel adjoint: fills contribution records (idx, 9-vector) for every contributor. */
+/* Per-pixel adjoint: fills contribution records (idx, 9-vector) for every contributor,
+ * and in out_abs (may be NULL) the same 9-vector with every elementary term replaced by
+ * its absolute value (a running error bound: the FP32 error of a result is at most a few
+ * ulps of the sum of the absolute values of the terms that formed it). */
 static int64_t pixel_adjoint(const orc_proj *pr, int64_t N, const orc_params *p, double px, double py,
                              const double g[3], orc_cand *cand, orc_contrib *contrib,
-                             int64_t *out_idx, double *out_d2) {
+                             int64_t *out_idx, double *out_d2, double *out_abs) {
     orc_pixel_result res;
     render_pixel(pr, N, p, px, py, cand, contrib, &res);
     double S[3];
@@ -427,12 +430,18 @@ static int64_t pixel_adjoint(const orc_proj *pr, int64_t N, const orc_params *p,
         double w = c->alpha * c->Tin;
         double *d = out_d2 + (int64_t)k * ORC_N2D;
         memset(d, 0, sizeof(double) * ORC_N2D);
-        double dalpha = 0;
+        double dalpha = 0, dalpha_abs = 0;
         for (int ch = 0; ch < 3; ch++) {
             d[6 + ch] = w * g[ch];
             dalpha += g[ch] * (q->c[ch] * c->Tin - S[ch] / (1.0 - c->alpha));
+            dalpha_abs += fabs(g[ch]) * (fabs(q->c[ch] * c->Tin) + fabs(S[ch]) / (1.0 - c->alpha));
         }
         for (int ch = 0; ch < 3; ch++) S[ch] += q->c[ch] * w;
+        double *da = out_abs ? out_abs + (int64_t)k * ORC_N2D : NULL;
+        if (da) {
+            memset(da, 0, sizeof(double) * ORC_N2D);
+            for (int ch = 0; ch < 3; ch++) da[6 + ch] = fabs(d[6 + ch]);
+        }
         if (c->araw < p->alpha_max) {
             double G = exp(-c->power);
             d[5] = dalpha * G;                       /* d alpha / d o = exp(-power) */
@@ -442,6 +451,15 @@ static int64_t pixel_adjoint(const orc_proj *pr, int64_t N, const orc_params *p,
             d[4] = dpow * 0.5 * c->dy * c->dy;
             d[0] = dpow * (q->Q[0] * c->dx + q->Q[1] * c->dy);
             d[1] = dpow * (q->Q[1] * c->dx + q->Q[2] * c->dy);
+            if (da) {
+                double pa = dalpha_abs * c->araw;
+                da[5] = dalpha_abs * G;
+                da[2] = pa * 0.5 * c->dx * c->dx;
+                da[3] = pa * fabs(c->dx * c->dy);
+                da[4] = pa * 0.5 * c->dy * c->dy;
+                da[0] = pa * (fabs(q->Q[0] * c->dx) + fabs(q->Q[1] * c->dy));
+                da[1] = pa * (fabs(q->Q[1] * c->dx) + fabs(q->Q[2] * c->dy));
+            }
         }
         out_idx[k] = c->idx;
     }
@@ -451,10 +469,10 @@ static int64_t pixel_adjoint(const orc_proj *pr, int64_t N, const orc_params *p,
 typedef struct {
     int64_t n, cap;
     int64_t *idx;
-    double *d2;
+    double *d2, *da;
 } contrib_list;
 
-static int list_push(contrib_list *L, int64_t n_new, const int64_t *idx, const double *d2) {
+static int list_push(contrib_list *L, int64_t n_new, const int64_t *idx, const double *d2, const double *da) {
     if (L->n + n_new > L->cap) {
         int64_t nc = L->cap ? L->cap : 1024;
         while (nc < L->n + n_new) nc *= 2;
@@ -464,10 +482,14 @@ static int list_push(contrib_list *L, int64_t n_new, const int64_t *idx, const d
         double *nd = (double *)realloc(L->d2, sizeof(double) * ORC_N2D * (size_t)nc);
         if (!nd) return 1;
         L->d2 = nd;
+        double *na = (double *)realloc(L->da, sizeof(double) * ORC_N2D * (size_t)nc);
+        if (!na) return 1;
+        L->da = na;
         L->cap = nc;
     }
     memcpy(L->idx + L->n, idx, sizeof(int64_t) * (size_t)n_new);
     memcpy(L->d2 + L->n * ORC_N2D, d2, sizeof(double) * ORC_N2D * (size_t)n_new);
+    memcpy(L->da + L->n * ORC_N2D, da, sizeof(double) * ORC_N2D * (size_t)n_new);
     L->n += n_new;
     return 0;
 }
@@ -493,23 +515,28 @@ static void *bwd_pixels_worker(void *arg) {
     orc_contrib *contrib = (orc_contrib *)malloc(sizeof(orc_contrib) * n1);
     int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * n1);
     double *d2 = (double *)malloc(sizeof(double) * ORC_N2D * n1);
-    if (!cand || !contrib || !idx || !d2) { j->err = 1; goto done; }
+    double *da = (double *)malloc(sizeof(double) * ORC_N2D * n1);
+    if (!cand || !contrib || !idx || !d2 || !da) { j->err = 1; goto done; }
     for (int64_t k = j->tid; k < j->npix; k += j->nthreads) {
         const double *g = j->dL_dC + k * 3;
         if (g[0] == 0 && g[1] == 0 && g[2] == 0) continue;
-        int64_t n = pixel_adjoint(j->pr, j->N, j->p, j->px[k] + 0.5, j->py[k] + 0.5, g, cand, contrib, idx, d2);
-        if (list_push(&j->lists[j->tid], n, idx, d2)) { j->err = 1; break; }
+        int64_t n = pixel_adjoint(j->pr, j->N, j->p, j->px[k] + 0.5, j->py[k] + 0.5, g, cand, contrib, idx, d2, da);
+        if (list_push(&j->lists[j->tid], n, idx, d2, da)) { j->err = 1; break; }
     }
 done:
-    free(cand); free(contrib); free(idx); free(d2);
+    free(cand); free(contrib); free(idx); free(d2); free(da);
     return NULL;
 }
 
 /* Gaussians are partitioned over threads (i % nthreads == tid); each thread scans every
- * contribution list and accumulates the chain-ruled contributions of its own Gaussians. */
+ * contribution list and accumulates the chain-ruled contributions of its own Gaussians.
+ * gabs (an error scale for every gradient element): |J| applied to the per-Gaussian sum of
+ * the absolute-term vectors, J the (linear) chain rule of that Gaussian, whose columns are
+ * the chain rule of the nine unit vectors. */
 static void *bwd_accum_worker(void *arg) {
     bwd_job *j = (bwd_job *)arg;
     int64_t N = j->N;
+    double *abs2d = j->gabs ? (double *)calloc((size_t)ORC_N2D * (size_t)(N > 0 ? N : 1), sizeof(double)) : NULL;
     for (int t = 0; t < j->nthreads; t++) {
         const contrib_list *L = &j->lists[t];
         for (int64_t e = 0; e < L->n; e++) {
@@ -518,19 +545,37 @@ static void *bwd_accum_worker(void *arg) {
             const double *d = L->d2 + e * ORC_N2D;
             double out[ORC_NGRAD];
             chain_rule(&j->pr[i], j->cam, d, out);
-            for (int k = 0; k < ORC_NGRAD; k++) {
-                j->grad[k * N + i] += out[k];
-                if (j->gabs) j->gabs[k * N + i] += fabs(out[k]);
-            }
+            for (int k = 0; k < ORC_NGRAD; k++) j->grad[k * N + i] += out[k];
+            if (abs2d)
+                for (int k = 0; k < ORC_N2D; k++) abs2d[k * N + i] += L->da[e * ORC_N2D + k];
             if (j->grad2d)
                 for (int k = 0; k < ORC_N2D; k++) j->grad2d[k * N + i] += d[k];
         }
+    }
+    if (abs2d) {
+        for (int64_t i = j->tid; i < N; i += j->nthreads) {
+            if (!j->pr[i].valid) {
+                for (int k = 0; k < 3; k++) j->gabs[(14 + k) * N + i] = abs2d[(6 + k) * N + i];
+                j->gabs[13 * N + i] = abs2d[5 * N + i] * j->pr[i].o * (1.0 - j->pr[i].o);
+                continue;
+            }
+            for (int c = 0; c < ORC_N2D; c++) {
+                double a = abs2d[c * N + i];
+                if (a == 0) continue;
+                double unit[ORC_N2D] = {0}, col[ORC_NGRAD];
+                unit[c] = 1.0;
+                chain_rule(&j->pr[i], j->cam, unit, col);
+                for (int k = 0; k < ORC_NGRAD; k++) j->gabs[k * N + i] += fabs(col[k]) * a;
+            }
+        }
+        free(abs2d);
     }
     return NULL;
 }
 
 /* Exported: gradient of L = sum_k dL_dC[k] . C(pixel k) over the listed pixels.
- * grad [17][N] (overwritten), gabs [17][N] sum of |per-pixel contributions| (may be NULL),
+ * grad [17][N] (overwritten), gabs [17][N] error scale of each element: |J| times the
+ * summed absolute elementary terms of the screen-space adjoint (may be NULL),
  * grad2d [9][N] screen-space gradients (may be NULL).  If the Gaussians have no velocity,
  * the vel rows are still written (time * dmu) and may be ignored. */
 int orc_render_bwd(const orc_gaussians *g, const orc_camera *cam, const orc_params *p,
@@ -557,7 +602,7 @@ int orc_render_bwd(const orc_gaussians *g, const orc_camera *cam, const orc_para
         for (int t = 0; t < nthreads; t++) pthread_create(&th[t], NULL, bwd_accum_worker, &jobs[t]);
         for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
     }
-    for (int t = 0; t < nthreads; t++) { free(lists[t].idx); free(lists[t].d2); }
+    for (int t = 0; t < nthreads; t++) { free(lists[t].idx); free(lists[t].d2); free(lists[t].da); }
     free(lists); free(th); free(jobs); free(pr);
     return err;
 }
