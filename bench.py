@@ -268,7 +268,8 @@ def run_gv(args):
     tiles = math.ceil(W / o.tile_w) * math.ceil(H / o.tile_h)
     tile_passes = math.ceil(max(1, math.ceil(math.log2(tiles))) / 8)
     work = {
-        "composite_fwd": ("alu", OPS_EVAL * counters["fwd_eval"] + OPS_COMP_FWD * counters["fwd_composited"]),
+        # the backward replays exactly the pairs the forward composited
+        "composite_fwd": ("alu", OPS_EVAL * counters["fwd_eval"] + OPS_COMP_FWD * counters["bwd_replayed"]),
         "composite_bwd": ("alu", OPS_EVAL * counters["bwd_eval"] + OPS_COMP_BWD * counters["bwd_replayed"]),
         "project": ("hbm", 112 * N_GAUSS),
         "depth_sort": ("hbm", N_GAUSS * (4 + 4 * 16)),

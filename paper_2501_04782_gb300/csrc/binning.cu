@@ -234,8 +234,12 @@ __global__ void gather_debug_kernel(Work w, float *mean2d, float *conic, float *
     if (p >= P) return;
     float4 a = w.feat0[p], b = w.feat1[p];
     if (mean2d) { mean2d[p] = a.x; mean2d[P + p] = a.y; }
-    if (conic) { conic[p] = a.z; conic[P + p] = a.w; conic[2 * P + p] = b.x; }
-    if (opacity) opacity[p] = b.y;
+    if (conic) {  // the staged record holds -log2(e) (A/2, B, C/2)
+        conic[p] = -2.f * kLn2 * a.z;
+        conic[P + p] = -kLn2 * a.w;
+        conic[2 * P + p] = -2.f * kLn2 * b.x;
+    }
+    if (opacity) opacity[p] = exp2f(b.y);
     if (counts) counts[p] = (int32_t)w.rect[p].z;
     // position p of the depth-sorted list holds (depth key, pair id); culled pairs: NaN
     if (depth) depth[w.dval[depth_buf][p]] = __uint_as_float(w.dkey[depth_buf][p]);

@@ -78,24 +78,6 @@ __device__ __forceinline__ float warp_reduce9(const float v[9], int lane, int &s
     return d;
 }
 
-// One pixel's front-to-back step over a staged Gaussian (forward).
-__device__ __forceinline__ void fwd_pixel(const float4 &a, const float4 &b, float cb, float px, float py, int pos,
-                                          float &T, float &c0, float &c1, float &c2, int &last, bool &done,
-                                          unsigned &n_comp) {
-    if (done) return;
-    float dx, dy, G;
-    const float alpha = splat_alpha(a.x, a.y, a.z, a.w, b.x, b.y, px, py, dx, dy, G);
-    if (alpha < kAlphaMin) return;
-    n_comp++;
-    const float wgt = __fmul_rn(alpha, T);
-    c0 = fmaf(b.z, wgt, c0);
-    c1 = fmaf(b.w, wgt, c1);
-    c2 = fmaf(cb, wgt, c2);
-    T = __fmul_rn(T, __fsub_rn(1.f, alpha));
-    last = pos;
-    if (T < kTStop) done = true;
-}
-
 template <int TW, int TH, int DEPTH>
 __global__ void __launch_bounds__(TW *TH / 2) composite_fwd_kernel(Work w, const unsigned *ids, float bg0, float bg1,
                                                                    float bg2, float *image, float *final_T,
@@ -120,12 +102,12 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_fwd_kernel(Work w, const
         const int x = (int)(lt % fr.tiles_x) * TW + lx;
         const int y0 = (int)(lt / fr.tiles_x) * TH + ly, y1 = y0 + 4;
         const bool in0 = x < W && y0 < H, in1 = x < W && y1 < H;
-        const float px = (float)x + 0.5f, py0 = (float)y0 + 0.5f, py1 = (float)y1 + 0.5f;
+        const float px = (float)x + 0.5f;
+        const float2 npy = make_float2(-((float)y0 + 0.5f), -((float)y1 + 0.5f));
         const uint2 rg = w.ranges[tile];
-        float T0 = 1.f, r0 = 0.f, g0 = 0.f, b0 = 0.f, T1 = 1.f, r1 = 0.f, g1 = 0.f, b1 = 0.f;
+        float2 T = make_float2(1.f, 1.f), cr = make_float2(0.f, 0.f), cg = cr, cb = cr;
         int last0 = -1, last1 = -1;
         bool done0 = !in0, done1 = !in1;
-        unsigned n_comp = 0;
         for (unsigned start = rg.x; start < rg.y; start += DEPTH) {
             if (__syncthreads_and(done0 && done1)) break;
             const int n = (int)min((unsigned)DEPTH, rg.y - start);
@@ -137,80 +119,51 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_fwd_kernel(Work w, const
             }
             __syncthreads();
             for (int j = 0; j < n && !(done0 && done1); j++) {
-                const float4 a = s_a[j], b = s_b[j];
-                const float cb = s_c[j];
+                const float4 f0 = s_a[j], f1 = s_b[j];
+                float dx;
+                float2 dy;
+                const float2 e = splat_exponent2(f0, f1, px, npy, dx, dy);
+                float a0 = fminf(ex2_approx(e.x), kAlphaMax), a1 = fminf(ex2_approx(e.y), kAlphaMax);
+                // a pixel that is done, or below the cutoff, takes alpha 0: T and colour unchanged
+                a0 = (done0 || a0 < kAlphaMin) ? 0.f : a0;
+                a1 = (done1 || a1 < kAlphaMin) ? 0.f : a1;
+                const float2 wg = __fmul2_rn(make_float2(a0, a1), T);
+                cr = __ffma2_rn(dup2(f1.z), wg, cr);
+                cg = __ffma2_rn(dup2(f1.w), wg, cg);
+                cb = __ffma2_rn(dup2(s_c[j]), wg, cb);
+                T = __fmul2_rn(T, __fadd2_rn(make_float2(1.f, 1.f), make_float2(-a0, -a1)));
                 const int pos = (int)(start + j);
-                fwd_pixel(a, b, cb, px, py0, pos, T0, r0, g0, b0, last0, done0, n_comp);
-                fwd_pixel(a, b, cb, px, py1, pos, T1, r1, g1, b1, last1, done1, n_comp);
+                if (a0 > 0.f) { last0 = pos; done0 = T.x < kTStop; }
+                if (a1 > 0.f) { last1 = pos; done1 = T.y < kTStop; }
             }
         }
-        // evaluated entries: up to the stop, or the whole list
+        // evaluated entries: up to the stop, or the whole list (composited pairs are
+        // counted by the backward, which replays exactly those)
         unsigned n_eval = 0;
-        if (in0) n_eval += (T0 < kTStop) ? (unsigned)(last0 + 1 - (int)rg.x) : rg.y - rg.x;
-        if (in1) n_eval += (T1 < kTStop) ? (unsigned)(last1 + 1 - (int)rg.x) : rg.y - rg.x;
-        add_work(w.hdr->work, n_eval, n_comp);
+        if (in0) n_eval += (T.x < kTStop) ? (unsigned)(last0 + 1 - (int)rg.x) : rg.y - rg.x;
+        if (in1) n_eval += (T.y < kTStop) ? (unsigned)(last1 + 1 - (int)rg.x) : rg.y - rg.x;
+        add_work(w.hdr->work, n_eval, 0u);
         const size_t plane = (size_t)W * H;
         if (in0) {
             const size_t pix = (size_t)fr.pixel_offset + (size_t)y0 * W + x;
             const size_t img = 3 * (size_t)fr.pixel_offset + (size_t)y0 * W + x;
-            image[img] = fmaf(T0, bg0, r0);
-            image[img + plane] = fmaf(T0, bg1, g0);
-            image[img + 2 * plane] = fmaf(T0, bg2, b0);
-            final_T[pix] = T0;
+            image[img] = fmaf(T.x, bg0, cr.x);
+            image[img + plane] = fmaf(T.x, bg1, cg.x);
+            image[img + 2 * plane] = fmaf(T.x, bg2, cb.x);
+            final_T[pix] = T.x;
             last_idx[pix] = last0;
         }
         if (in1) {
             const size_t pix = (size_t)fr.pixel_offset + (size_t)y1 * W + x;
             const size_t img = 3 * (size_t)fr.pixel_offset + (size_t)y1 * W + x;
-            image[img] = fmaf(T1, bg0, r1);
-            image[img + plane] = fmaf(T1, bg1, g1);
-            image[img + 2 * plane] = fmaf(T1, bg2, b1);
-            final_T[pix] = T1;
+            image[img] = fmaf(T.y, bg0, cr.y);
+            image[img + plane] = fmaf(T.y, bg1, cg.y);
+            image[img + 2 * plane] = fmaf(T.y, bg2, cb.y);
+            final_T[pix] = T.y;
             last_idx[pix] = last1;
         }
         __syncthreads();
     }
-}
-
-// Per-pixel replay state of the backward.
-struct BwdPixel {
-    float px, py;
-    float T;               // transmittance behind the current Gaussian
-    float g0, g1, g2;      // dL/dC
-    float S0, S1, S2;      // colour composited behind the current Gaussian (incl. background)
-    int last;
-};
-
-// One pixel's back-to-front step over a staged Gaussian: adds its nine screen-space
-// gradient contributions (du, dv, dA, dB, dC, do, dr, dg, db) to acc.
-__device__ __forceinline__ bool bwd_pixel(const float4 &a, const float4 &b, float cb, int pos, BwdPixel &q,
-                                          float acc[9]) {
-    if (pos > q.last) return false;
-    float dx, dy, G;
-    const float alpha = splat_alpha(a.x, a.y, a.z, a.w, b.x, b.y, q.px, q.py, dx, dy, G);
-    if (alpha < kAlphaMin) return false;
-    const float ra = __frcp_rn(__fsub_rn(1.f, alpha));
-    const float Tin = q.T * ra;
-    const float wgt = alpha * Tin;
-    acc[6] = fmaf(wgt, q.g0, acc[6]);
-    acc[7] = fmaf(wgt, q.g1, acc[7]);
-    acc[8] = fmaf(wgt, q.g2, acc[8]);
-    const float dal = q.g0 * (b.z * Tin - q.S0 * ra) + q.g1 * (b.w * Tin - q.S1 * ra) + q.g2 * (cb * Tin - q.S2 * ra);
-    q.S0 = fmaf(b.z, wgt, q.S0);
-    q.S1 = fmaf(b.w, wgt, q.S1);
-    q.S2 = fmaf(cb, wgt, q.S2);
-    q.T = Tin;
-    if (__fmul_rn(b.y, G) < kAlphaMax) {
-        acc[5] = fmaf(dal, G, acc[5]);
-        const float dpow = -dal * alpha;
-        const float hp = 0.5f * dpow;
-        acc[2] = fmaf(hp * dx, dx, acc[2]);
-        acc[3] = fmaf(dpow * dx, dy, acc[3]);
-        acc[4] = fmaf(hp * dy, dy, acc[4]);
-        acc[0] = fmaf(dpow, a.z * dx + a.w * dy, acc[0]);
-        acc[1] = fmaf(dpow, a.w * dx + b.x * dy, acc[1]);
-    }
-    return true;
 }
 
 template <int TW, int TH, int DEPTH>
@@ -238,41 +191,41 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_bwd_kernel(Work w, const
         const int W = fr.W, H = fr.H;
         const unsigned lt = tile - fr.tile_offset;
         const int x = (int)(lt % fr.tiles_x) * TW + lx;
-        const int ybase = (int)(lt / fr.tiles_x) * TH + ly;
+        const int y0 = (int)(lt / fr.tiles_x) * TH + ly, y1 = y0 + 4;
+        const float px = (float)x + 0.5f;
+        const float2 npy = make_float2(-((float)y0 + 0.5f), -((float)y1 + 0.5f));
         const uint2 rg = w.ranges[tile];
-        BwdPixel q[2];
-#pragma unroll
-        for (int k = 0; k < 2; k++) {
-            const int y = ybase + 4 * k;
-            q[k].px = (float)x + 0.5f;
-            q[k].py = (float)y + 0.5f;
-            q[k].T = 1.f;
-            q[k].g0 = q[k].g1 = q[k].g2 = 0.f;
-            q[k].last = -1;
-            if (x < W && y < H) {
-                const size_t plane = (size_t)W * H;
-                const size_t pix = (size_t)fr.pixel_offset + (size_t)y * W + x;
-                const size_t img = 3 * (size_t)fr.pixel_offset + (size_t)y * W + x;
-                q[k].T = final_T[pix];
-                q[k].last = min(last_idx[pix], (int)rg.y - 1);  // from the forward: in [rg.x, rg.y)
-                q[k].g0 = dL[img];
-                q[k].g1 = dL[img + plane];
-                q[k].g2 = dL[img + 2 * plane];
-            }
-            q[k].S0 = q[k].T * bg0;
-            q[k].S1 = q[k].T * bg1;
-            q[k].S2 = q[k].T * bg2;
+        // per-pixel replay state, packed over the thread's two pixels
+        float2 T = make_float2(1.f, 1.f), g0 = make_float2(0.f, 0.f), g1 = g0, g2 = g0;
+        int last0 = -1, last1 = -1;
+        const size_t plane = (size_t)W * H;
+        if (x < W && y0 < H) {
+            const size_t pix = (size_t)fr.pixel_offset + (size_t)y0 * W + x;
+            const size_t img = 3 * (size_t)fr.pixel_offset + (size_t)y0 * W + x;
+            T.x = final_T[pix];
+            last0 = min(last_idx[pix], (int)rg.y - 1);  // from the forward: in [rg.x, rg.y)
+            g0.x = dL[img];
+            g1.x = dL[img + plane];
+            g2.x = dL[img + 2 * plane];
         }
-        unsigned n_comp = 0;
-        unsigned n_eval = 0;
-#pragma unroll
-        for (int k = 0; k < 2; k++)
-            if (q[k].last >= (int)rg.x) n_eval += (unsigned)(q[k].last + 1 - (int)rg.x);
-        const int wmax = __reduce_max_sync(0xffffffffu, max(q[0].last, q[1].last));
+        if (x < W && y1 < H) {
+            const size_t pix = (size_t)fr.pixel_offset + (size_t)y1 * W + x;
+            const size_t img = 3 * (size_t)fr.pixel_offset + (size_t)y1 * W + x;
+            T.y = final_T[pix];
+            last1 = min(last_idx[pix], (int)rg.y - 1);
+            g0.y = dL[img];
+            g1.y = dL[img + plane];
+            g2.y = dL[img + 2 * plane];
+        }
+        // colour composited behind the current Gaussian, negated: nS = -(sum c w + T bg)
+        float2 nS0 = __fmul2_rn(T, dup2(-bg0)), nS1 = __fmul2_rn(T, dup2(-bg1)), nS2 = __fmul2_rn(T, dup2(-bg2));
+        unsigned n_comp = 0, n_eval = 0;
+        if (last0 >= (int)rg.x) n_eval += (unsigned)(last0 + 1 - (int)rg.x);
+        if (last1 >= (int)rg.x) n_eval += (unsigned)(last1 + 1 - (int)rg.x);
+        const int wmax = __reduce_max_sync(0xffffffffu, max(last0, last1));
         if (lane == 0) atomicMax(&s_max, wmax);
         __syncthreads();
         const int end = min(s_max + 1, (int)rg.y);
-        const int wlast = wmax;  // this warp's last position: earlier entries only
         for (int bend = end; bend > (int)rg.x; bend -= DEPTH) {
             const int bstart = max((int)rg.x, bend - DEPTH);
             const int n = bend - bstart;
@@ -285,20 +238,52 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_bwd_kernel(Work w, const
                 s_c[i] = w.feat2[p];
             }
             __syncthreads();
-            const int jtop = min(n - 1, wlast - bstart);
+            const int jtop = min(n - 1, wmax - bstart);  // this warp's pixels stop before the rest
             for (int j = jtop; j >= 0; j--) {
-                const float4 a = s_a[j], b = s_b[j];
-                const float cb = s_c[j];
+                const float4 f0 = s_a[j], f1 = s_b[j];
                 const int pos = bstart + j;
-                float acc[9];
-#pragma unroll
-                for (int k = 0; k < 9; k++) acc[k] = 0.f;
-                const bool c0 = bwd_pixel(a, b, cb, pos, q[0], acc);
-                const bool c1 = bwd_pixel(a, b, cb, pos, q[1], acc);
-                n_comp += (unsigned)c0 + (unsigned)c1;
-                if (!__any_sync(0xffffffffu, c0 || c1)) continue;
+                float dx;
+                float2 dy;
+                const float2 e = splat_exponent2(f0, f1, px, npy, dx, dy);
+                const float r0 = ex2_approx(e.x), r1 = ex2_approx(e.y);  // o exp(-power), unclamped
+                float a0 = fminf(r0, kAlphaMax), a1 = fminf(r1, kAlphaMax);
+                const bool v0 = pos <= last0 && a0 >= kAlphaMin;
+                const bool v1 = pos <= last1 && a1 >= kAlphaMin;
+                if (!__any_sync(0xffffffffu, v0 || v1)) continue;
+                n_comp += (unsigned)v0 + (unsigned)v1;
+                a0 = v0 ? a0 : 0.f;
+                a1 = v1 ? a1 : 0.f;
+                const float2 al = make_float2(a0, a1);
+                const float2 ra = make_float2(rcp_approx(1.f - a0), rcp_approx(1.f - a1));
+                float2 Tin = __fmul2_rn(T, ra);
+                Tin.x = v0 ? Tin.x : T.x;
+                Tin.y = v1 ? Tin.y : T.y;
+                const float2 wg = __fmul2_rn(al, Tin);
+                const float cb = s_c[j];
+                // dL/dalpha = sum_ch g_ch (c_ch Tin - S_ch / (1 - alpha))
+                const float2 x0 = __ffma2_rn(nS0, ra, __fmul2_rn(dup2(f1.z), Tin));
+                const float2 x1 = __ffma2_rn(nS1, ra, __fmul2_rn(dup2(f1.w), Tin));
+                const float2 x2 = __ffma2_rn(nS2, ra, __fmul2_rn(dup2(cb), Tin));
+                const float2 dal = __ffma2_rn(g2, x2, __ffma2_rn(g1, x1, __fmul2_rn(g0, x0)));
+                nS0 = __ffma2_rn(dup2(-f1.z), wg, nS0);
+                nS1 = __ffma2_rn(dup2(-f1.w), wg, nS1);
+                nS2 = __ffma2_rn(dup2(-cb), wg, nS2);
+                T = Tin;
+                // dL/de for the exponent e (alpha = 2^e unless clamped at 0.99)
+                const float2 k = make_float2((v0 && r0 < kAlphaMax) ? r0 * kLn2 : 0.f,
+                                             (v1 && r1 < kAlphaMax) ? r1 * kLn2 : 0.f);
+                const float2 de = __fmul2_rn(dal, k);
+                const float2 dxy = __fmul2_rn(dup2(dx), dy);
+                const float2 gu = __ffma2_rn(dup2(f0.w), dy, dup2(2.f * f0.z * dx));  // de/du = 2a'dx + b'dy
+                const float2 gv = __ffma2_rn(dup2(2.f * f1.x), dy, dup2(f0.w * dx));  // de/dv = b'dx + 2c'dy
+                const float2 cu = __fmul2_rn(de, gu), cv = __fmul2_rn(de, gv);
+                const float2 ca = __fmul2_rn(de, dup2(dx * dx)), cbb = __fmul2_rn(de, dxy);
+                const float2 cc = __fmul2_rn(de, __fmul2_rn(dy, dy));
+                const float2 dr = __fmul2_rn(wg, g0), dg = __fmul2_rn(wg, g1), db = __fmul2_rn(wg, g2);
+                float v[9] = {cu.x + cu.y, cv.x + cv.y, ca.x + ca.y, cbb.x + cbb.y, cc.x + cc.y,
+                              de.x + de.y, dr.x + dr.y, dg.x + dg.y, db.x + db.y};
                 int slot;
-                const float sum = warp_reduce9(acc, lane, slot);
+                const float sum = warp_reduce9(v, lane, slot);
                 if (slot < 9 && !(lane & 1)) {
                     const unsigned p = s_p[j];
                     float *dst = slot < 4 ? &w.g0[p].x + slot : (slot < 8 ? &w.g1[p].x + (slot - 4) : w.g2 + p);

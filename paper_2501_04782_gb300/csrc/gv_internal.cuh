@@ -178,18 +178,41 @@ __device__ __forceinline__ int find_frame_by_tile(const DevFrame *fr, int F, uns
     return lo;
 }
 
-// Alpha of a staged Gaussian at a pixel centre.  Written with explicit round-to-nearest
-// intrinsics so that the forward and the backward kernels compute bit-identical values
-// (the backward replays the forward's decisions and divides its transmittance back).
-// power = 1/2 (A dx^2 + C dy^2) + B dx dy;  G = exp(-power);  alpha = min(0.99, o G).
-__device__ __forceinline__ float splat_alpha(float mx, float my, float A, float B, float C, float o,
-                                             float px, float py, float &dx, float &dy, float &G) {
-    dx = __fsub_rn(mx, px);
-    dy = __fsub_rn(my, py);
-    float q = __fmaf_rn(A, __fmul_rn(dx, dx), __fmul_rn(C, __fmul_rn(dy, dy)));
-    float power = __fmaf_rn(0.5f, q, __fmul_rn(B, __fmul_rn(dx, dy)));
-    G = __expf(-power);
-    return fminf(kAlphaMax, __fmul_rn(o, G));
+// Staged splat record.  The compositing kernels read, per (frame, Gaussian) pair,
+// feat0 = (u, v, a', b') and feat1 = (c', log2 o, r, g), feat2 = b, where
+//   a' = -log2(e) A / 2,  b' = -log2(e) B,  c' = -log2(e) C / 2
+// for the conic (A, B, C), so that o exp(-1/2 (A dx^2 + 2 B dx dy + C dy^2)) =
+// 2^(a' dx^2 + b' dx dy + c' dy^2 + log2 o): one exponent, no separate opacity product.
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+
+__device__ __forceinline__ float ex2_approx(float x) {  // hardware 2^x (MUFU), flush-to-zero
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {  // hardware 1/x (MUFU), flush-to-zero
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+
+// Exponents of one staged Gaussian at the two pixels (px, py.x) and (px, py.y) a thread
+// owns: e = a' dx^2 + b' dx dy + c' dy^2 + log2 o, with dx shared.  Written with explicit
+// round-to-nearest (packed) operations so the forward and the backward compute
+// bit-identical values (the backward replays the forward's decisions and divides its
+// transmittance back).  Also returns dx, dy (packed) for the gradients.
+__device__ __forceinline__ float2 splat_exponent2(float4 f0, float4 f1, float px, float2 npy, float &dx,
+                                                  float2 &dy) {
+    dx = __fsub_rn(f0.x, px);
+    dy = __fadd2_rn(dup2(f0.y), npy);                       // v - py, both pixels
+    const float s0 = __fmaf_rn(__fmul_rn(f0.z, dx), dx, f1.y);  // a' dx^2 + log2 o
+    const float bdx = __fmul_rn(f0.w, dx);                  // b' dx
+    const float2 t = __ffma2_rn(dup2(bdx), dy, dup2(s0));   // + b' dx dy
+    return __ffma2_rn(__fmul2_rn(dup2(f1.x), dy), dy, t);   // + c' dy^2
 }
 
 }  // namespace gvk

@@ -52,7 +52,10 @@ __global__ void grad2d_debug_kernel(Work w, float *out) {
     unsigned P = w.L.P;
     if (p >= P) return;
     float4 a = w.g0[p], b = w.g1[p];
-    float vals[9] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, w.g2[p]};
+    // staged basis (du, dv, da', db', dc', dlog2o, ...) -> (du, dv, dA, dB, dC, do, ...)
+    const float o = exp2f(w.feat1[p].y);
+    float vals[9] = {a.x, a.y, -0.5f * kLog2e * a.z, -kLog2e * a.w, -0.5f * kLog2e * b.x,
+                     o > 0.f ? b.y * kLog2e / o : 0.f, b.z, b.w, w.g2[p]};
     for (int k = 0; k < 9; k++) out[(size_t)k * P + p] = vals[k];
 }
 

@@ -136,8 +136,8 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, i
         cnt = tile_rect(st.u, st.v, ex, ey, fr.W, fr.H, lw, lh, lo, hi);
     }
     const long long N = g.N;
-    w.feat0[p] = make_float4(st.u, st.v, st.A, st.B);
-    w.feat1[p] = make_float4(st.C, st.o, g.rgb[gi], g.rgb[N + gi]);
+    w.feat0[p] = make_float4(st.u, st.v, -0.5f * kLog2e * st.A, -kLog2e * st.B);
+    w.feat1[p] = make_float4(-0.5f * kLog2e * st.C, log2f(st.o), g.rgb[gi], g.rgb[N + gi]);
     w.feat2[p] = g.rgb[2 * N + gi];
     w.rect[p] = make_uint4(lo, hi, cnt, (unsigned)f);
     w.dkey[0][p] = cnt ? __float_as_uint(st.zc) : 0xFFFFFFFFu;
@@ -159,17 +159,19 @@ __global__ void __launch_bounds__(256) bin_from_screen_kernel(Work w, long long 
     if (counts) counts[p] = (int32_t)cnt;
 }
 
-// Chain rule of one pair: screen-space gradient (du, dv, dA, dB, dC, do, dr, dg, db) to
-// the raw-parameter gradients, added into acc[17] (mean 3, vel 3, log_scale 3, quat 4,
-// logit 1, rgb 3).
+// Chain rule of one pair: screen-space gradient to the raw-parameter gradients, added
+// into acc[17] (mean 3, vel 3, log_scale 3, quat 4, logit 1, rgb 3).  The compositing
+// backward accumulates (du, dv, da', db', dc', dlog2o, dr, dg, db) for the staged record
+// (a', b', c') = -log2(e) (A/2, B, C/2) and log2 o; converted here to the conic and opacity.
 __device__ __forceinline__ void pair_backward(const PairState &st, const DevFrame &fr, float4 g0,
                                               float4 g1, float g2, float acc[17]) {
     acc[14] += g1.z;
     acc[15] += g1.w;
     acc[16] += g2;
-    acc[13] += g1.y * st.o * (1.f - st.o);
+    // d log2(o) / d logit = (1 - o) / ln 2
+    acc[13] += g1.y * (1.f - st.o) * kLog2e;
     if (!st.valid) return;
-    float dA = g0.z, dB = g0.w, dC = g1.x;
+    float dA = -0.5f * kLog2e * g0.z, dB = -kLog2e * g0.w, dC = -0.5f * kLog2e * g1.x;
     // conic Q = Sigma2^{-1}: dL/dSigma2 = -Q G Q with G = [[dA, dB/2], [dB/2, dC]]
     float X00 = st.A * dA + 0.5f * st.B * dB, X01 = 0.5f * st.A * dB + st.B * dC;
     float X10 = st.B * dA + 0.5f * st.C * dB, X11 = 0.5f * st.B * dB + st.C * dC;
