@@ -279,6 +279,33 @@ GV_API gv_status gv_debug_set_wait(gv_ctx *ctx, int64_t spin_limit, int32_t drop
 GV_API gv_status gv_debug_read_grad2d(gv_ctx *ctx, const gv_frame_desc *frames, int32_t F,
                                const void *workspace, size_t ws_bytes, float *out, gv_stream stream);
 
+/* ---- forward without any allocation ------------------------------------------------ */
+
+/* Largest scratch gv_render_fwd_noalloc can use: 32 MiB. */
+#define GV_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* gv_render_fwd without a caller workspace, for callers that cannot call cudaMalloc at
+ * all: a plug-in whose host application owns every device allocation, or a real-time
+ * loop that must never let cudaMalloc / cudaFree synchronise the device.  (The paper has
+ * no counterpart; this is a deployment convenience.)
+ *
+ * The scratch is one file-scope device array of GV_NOALLOC_SCRATCH_BYTES inside the
+ * library, which every GPU that loads the library holds until the process exits.  The
+ * call allocates nothing (no cudaMalloc, no cudaFree, no allocating library routine);
+ * image, final_T and last_idx are the caller's device buffers as for gv_render_fwd, and
+ * the results are the same.
+ *  - The first call on a device looks up that device's address of the array (with the
+ *    device current); make that first call before any stream capture.
+ *  - Every call on a device shares the one array and leaves the last call's contents in
+ *    it; each call clears what must start at zero.  Calls that overlap on the GPU (two
+ *    streams, two threads, two contexts of one process) race on the array: serialise them.
+ *  - A frame whose Gaussian count or key count does not fit returns GV_ERR_INVALID_ARG or
+ *    GV_ERR_CAPACITY with a message naming the limit.  The call synchronises `stream`
+ *    before it returns, to report a key-capacity overflow. */
+GV_API gv_status gv_render_fwd_noalloc(gv_ctx *ctx, const gv_gaussians *g, const gv_camera *cam,
+                                       float *image, float *final_T, int32_t *last_idx,
+                                       gv_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

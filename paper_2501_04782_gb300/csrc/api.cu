@@ -8,6 +8,7 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -367,6 +368,32 @@ gv_frame_desc single_frame(const gv_camera *cam, long long N) {
 
 }  // namespace
 
+// Scratch of gv_render_fwd_noalloc: one device array per GPU that loads the library, held
+// until exit.  Host code needs the array's device address, looked up once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[GV_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+constexpr int kMaxDevices = 256;
+std::mutex g_noalloc_mu;
+void *g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device (looked up on first use).
+cudaError_t noalloc_scratch(int device, void **out) {
+    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[device] = p;
+    }
+    *out = g_noalloc_addr[device];
+    return cudaSuccess;
+}
+
+}  // namespace
+
 struct gv_graph {
     gv_ctx *ctx = nullptr;
     cudaGraph_t graph = nullptr;
@@ -522,6 +549,41 @@ gv_status gv_render_bwd(gv_ctx *ctx, const gv_gaussians *g, const gv_camera *cam
     if (!ctx || !g || !cam) return ctx ? fail(ctx, GV_ERR_INVALID_ARG, "NULL argument") : GV_ERR_INVALID_ARG;
     gv_frame_desc d = single_frame(cam, g->N);
     return gv_render_batch_bwd(ctx, g, &d, 1, workspace, ws_bytes, final_T, last_idx, dL_dimage, grad, stream);
+}
+
+gv_status gv_render_fwd_noalloc(gv_ctx *ctx, const gv_gaussians *g, const gv_camera *cam, float *image,
+                                float *final_T, int32_t *last_idx, gv_stream stream) {
+    if (!ctx) return GV_ERR_INVALID_ARG;
+    if (!cam) return fail(ctx, GV_ERR_INVALID_ARG, "NULL camera");
+    gv_status st = check_gaussians(ctx, g);
+    if (st != GV_OK) return st;
+    if (!image || !final_T || !last_idx) return fail(ctx, GV_ERR_INVALID_ARG, "NULL buffer");
+    int device = 0;
+    GV_CUDA(cudaGetDevice(&device));
+    void *scratch = nullptr;
+    GV_CUDA(noalloc_scratch(device, &scratch));
+    gv_frame_desc d = single_frame(cam, g->N);
+    Plan pl;
+    st = make_plan(ctx, ctx->opt, g->N, &d, 1, 0, GV_NOALLOC_SCRATCH_BYTES, pl);
+    if (st != GV_OK)
+        return fail(ctx, GV_ERR_INVALID_ARG,
+                    "%d Gaussians on a %dx%d frame need more than the %u-byte static scratch (%s)", (int)g->N,
+                    cam->W, cam->H, (unsigned)GV_NOALLOC_SCRATCH_BYTES, ctx->err.c_str());
+    Work w = make_work(scratch, pl.L);
+    cudaStream_t s = (cudaStream_t)stream;
+    // the array keeps the previous call's contents: the forward's own setup kernel clears
+    // the header, counters, histograms and tile ranges, and each sort clears its look-back
+    // words, exactly as for a reused caller workspace
+    st = forward_stages(ctx, g, pl, w, image, final_T, last_idx, s);
+    if (st != GV_OK) return st;
+    DevHeader h;
+    GV_CUDA(cudaMemcpyAsync(&h, scratch, sizeof(h), cudaMemcpyDeviceToHost, s));
+    GV_CUDA(cudaStreamSynchronize(s));
+    if (h.err & ERR_TIMEOUT) return fail(ctx, GV_ERR_TIMEOUT, "a device-side wait exceeded its limit");
+    if (h.err & ERR_CAPACITY)
+        return fail(ctx, GV_ERR_CAPACITY, "the frame needs %llu keys; the %u-byte static scratch holds %u",
+                    (unsigned long long)h.keys_total, (unsigned)GV_NOALLOC_SCRATCH_BYTES, pl.L.key_cap);
+    return GV_OK;
 }
 
 gv_status gv_read_status(gv_ctx *ctx, const void *workspace, size_t ws_bytes, gv_stream stream,

@@ -23,7 +23,7 @@ EXPORTS = [
     "gv_read_status", "gv_l2_loss_grad", "gv_adam_step", "gv_autotune", "gv_graph_capture",
     "gv_graph_set_frames", "gv_graph_launch", "gv_graph_destroy", "gv_debug_bin_sort", "gv_debug_read",
     "gv_debug_set_wait", "gv_debug_read_grad2d", "gv_profile_enable", "gv_profile_read",
-    "gv_read_counters",
+    "gv_read_counters", "gv_render_fwd_noalloc",
 ]
 
 STAGES = ["setup", "project", "depth_sort", "emit", "tile_sort", "ranges", "composite_fwd", "composite_bwd",
@@ -94,6 +94,7 @@ _SIGS = {
                          ctypes.c_size_t, _vp, _vp, _vp, _vp, ctypes.c_float, _vp, _vp,
                          ctypes.POINTER(GaussiansGrad), _vp, ctypes.POINTER(_vp)],
     "gv_read_counters": [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_int64)],
+    "gv_render_fwd_noalloc": [_vp, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), _vp, _vp, _vp, _vp],
     "gv_graph_set_frames": [_vp, ctypes.POINTER(FrameDesc), ctypes.c_int32],
     "gv_graph_launch": [_vp, _vp],
     "gv_graph_destroy": [_vp],
