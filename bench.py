@@ -60,7 +60,9 @@ def parse_args():
     ap.add_argument("--impl", default="gv", choices=["gv", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="oracle sample budget (cpu_baseline)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the batched and e2e legs")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched, e2e and training legs")
+    ap.add_argument("--no-training", action="store_true", help="skip the 1080p / 1M-Gaussian training leg")
+    ap.add_argument("--train-steps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -321,6 +323,9 @@ def run_gv(args):
         out["batched"] = run_batched(torch, gv, synth, ctx, dev, flush, max(20, args.steps // 4))
         out["e2e"] = run_e2e(torch, gv, ctx, params, target, frames, ws, dev, flush, max(20, args.steps // 4), scale,
                              world)
+        if not args.no_training:
+            out["training"], out["large_stages"] = run_training(torch, gv, synth, dev, args.train_steps, hbm_peak,
+                                                                alu_peak_gops)
     else:
         out["e2e"] = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -399,6 +404,108 @@ def run_batched(torch, gv, synth, ctx, dev, flush, steps):
             "per_frame_same_frames": res["per_frame"],
             "workload": f"{BATCH_FRAMES} frames 960x540 sharing 200,000 Gaussians, own random poses; one CUDA "
                         "graph per step (forward, L2 loss, backward) vs the plain renderer once per frame"}
+
+
+def run_training(torch, gv, synth, dev, steps, hbm_peak, alu_peak_gops):
+    """Training-step throughput on the 50-frame 1920x1080 clip: targets rendered from the
+    seeded 1M-Gaussian ground truth, a perturbed 1M-Gaussian model, 8 random frames per step
+    (one CUDA graph of forward + L2 loss + backward, then one fused Adam over all planes).
+    Also the steady-state render rate (forward of one frame) and, with per-stage events on
+    the plain batched calls, the HBM rates of projection and the sorts at this size."""
+    from paper_2501_04782_gb300 import render
+    TW, TH, F, B = 1920, 1080, 50, 8
+    w = synth.workload_training()
+    cams = [c for c, _, _ in w["frames"]]
+    N = w["gaussians"]["opacity_logit"].shape[-1]
+    gctx = gv.Context((16, 16), 128)
+    gt = {k: torch.from_numpy(v).to(dev) for k, v in w["gt"].items()}
+    targets = torch.empty(F, 3 * TW * TH, device=dev)
+    for c0 in range(0, F, 10):
+        fr, total = gv.layout_frames([(c, 0, N) for c in cams[c0:c0 + 10]])
+        rnd = render.Renderer((16, 16), 128)
+        img, _, _, _ = rnd.forward(gt, fr, total)
+        targets[c0:c0 + len(fr)] = img.view(len(fr), -1)
+    del gt
+    params = {k: torch.from_numpy(v).to(dev) for k, v in w["gaussians"].items()}
+    tr = render.Trainer(params, cams, targets, batch=B, lr=0.01, seed=7)
+
+    def clip_psnr(ids):
+        fr, total = gv.layout_frames([(cams[i], 0, N) for i in ids])
+        img, _, _, _ = render.Renderer((16, 16), 128).forward(tr.params, fr, total)
+        return render.psnr(img, targets[ids].reshape(-1))
+
+    probe = [0, 13, 27, 41]
+    psnr0 = clip_psnr(probe)
+    for _ in range(3):
+        tr.step()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(tr.stream)
+    for _ in range(steps):
+        tr.step()
+    b.record(tr.stream)
+    b.synchronize()
+    t = a.elapsed_time(b) / 1000.0
+    st, keys = tr.status()
+    psnr1 = clip_psnr(probe)
+    # steady-state render rate: forward of one 1080p frame of the model
+    one = [gv.Frame(cams[0], 0, N, 0)]
+    rws = torch.empty(gctx.workspace_size(one, int(keys / B * 1.5) + 65536), dtype=torch.uint8, device=dev)
+    im = torch.empty(3 * TW * TH, device=dev)
+    T = torch.empty(TW * TH, device=dev)
+    ix = torch.empty(TW * TH, dtype=torch.int32, device=dev)
+    for _ in range(3):
+        gctx.render_fwd(tr.params, one, rws, im, T, ix)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(20):
+        gctx.render_fwd(tr.params, one, rws, im, T, ix)
+    b.record()
+    b.synchronize()
+    fps = 20 / (a.elapsed_time(b) / 1000.0)
+    # per-stage rates at this size (plain batched calls with per-stage events)
+    pctx = gv.Context((16, 16), 128)
+    pctx.profile_enable(True)
+    fr, total = gv.layout_frames([(cams[i], 0, N) for i in range(B)])
+    pimg = torch.empty(3 * total, device=dev)
+    pT = torch.empty(total, device=dev)
+    pidx = torch.empty(total, dtype=torch.int32, device=dev)
+    pdl = torch.randn(3 * total, device=dev) * 1e-3
+    pws = torch.empty(pctx.workspace_size(fr, int(keys * 1.2) + 65536), dtype=torch.uint8, device=dev)
+    grads = {k: torch.zeros_like(v) for k, v in tr.params.items()}
+    ms_acc = {}
+    for rep in range(4):
+        pctx.render_fwd(tr.params, fr, pws, pimg, pT, pidx)
+        pctx.render_bwd(tr.params, fr, pws, pT, pidx, pdl, grads)
+        ms, _ = pctx.profile_read()
+        if rep:
+            for k, v in ms.items():
+                ms_acc.setdefault(k, []).append(v)
+    cnt = pctx.read_counters(pws)
+    P, K = cnt["pairs"], cnt["keys"]
+    tiles = B * math.ceil(TW / 16) * math.ceil(TH / 16)
+    tpass = math.ceil(math.ceil(math.log2(tiles)) / 8)
+    amounts = {"project": ("hbm", 112 * P), "depth_sort": ("hbm", P * (4 + 4 * 16)),
+               "tile_sort": ("hbm", K * tpass * 16), "emit": ("hbm", P * 20 + K * 8),
+               "project_bwd": ("hbm", N * 56 * 2 + P * (56 + 36)),
+               "composite_fwd": ("alu", OPS_EVAL * cnt["fwd_eval"] + OPS_COMP_FWD * cnt["bwd_replayed"]),
+               "composite_bwd": ("alu", OPS_EVAL * cnt["bwd_eval"] + OPS_COMP_BWD * cnt["bwd_replayed"])}
+    large = {"workload": f"{B} frames 1920x1080 sharing 1M Gaussians (pairs {P}, keys {K})"}
+    for k, (kind, amount) in amounts.items():
+        m = statistics.median(ms_acc.get(k, [0.0]))
+        if m <= 0:
+            continue
+        r = amount / (m / 1000) / 1e9
+        peak = hbm_peak if kind == "hbm" else alu_peak_gops
+        large[k] = {"ms": round(m, 3), "bound": kind, "achieved": round(r, 1),
+                    "unit": "GB/s" if kind == "hbm" else "Gop/s", "frac": round(r / peak, 4)}
+    training = {"frames_per_s": round(steps * B / t, 2), "steps_per_s": round(steps / t, 3), "steps": steps,
+                "frames_per_step": B, "render_fps_1080p": round(fps, 1),
+                "psnr_before": round(psnr0, 2), "psnr_after": round(psnr1, 2),
+                "workload": "50-frame 1920x1080 clip, targets from 1M ground-truth Gaussians drifting linearly, "
+                            "perturbed 1M-Gaussian model; step = 8 random frames fwd + L2 + bwd (one CUDA graph) "
+                            "+ fused Adam over all parameters"}
+    return training, large
 
 
 def run_e2e(torch, gv, ctx, params, target, frames, ws, dev, flush, steps, scale, world):

@@ -14,6 +14,8 @@ torch and passes pointers (no CPU fallback exists: CPU tensors are rejected).
 """
 from __future__ import annotations
 
+import math
+
 import torch
 
 from . import gv
@@ -114,3 +116,91 @@ def split_images(flat: torch.Tensor, frames: list[gv.Frame], channels: int = 3) 
 
 def params_to_device(g: dict, device="cuda") -> dict:
     return {k: torch.as_tensor(v, dtype=torch.float32).contiguous().to(device) for k, v in g.items() if v is not None}
+
+
+class Trainer:
+    """Batched training step (Sec. 4.1: L2 reconstruction loss, optimiser step): each step
+    renders `batch` frames of a clip in one CUDA graph (forward, L2 loss, backward, all
+    libgv kernels), then updates every Gaussian parameter with one fused Adam launch.
+
+    The parameter planes live in one flat buffer (so one Adam launch covers them all) and
+    the graph is captured once; a step replaces the frames' cameras in the instantiated
+    graph, copies their targets into the graph's target buffer, and launches."""
+
+    KEYS = ("mean", "vel", "log_scale", "quat", "opacity_logit", "rgb")
+
+    def __init__(self, params: dict, cams: list, targets: torch.Tensor, batch: int = 8, lr: float = 0.01,
+                 betas=(0.9, 0.999), eps: float = 1e-8, tile=(16, 16), stage_depth: int = 128,
+                 key_capacity: int = 0, seed: int = 0):
+        dev = params["mean"].device
+        self.N = int(params["opacity_logit"].shape[-1])
+        self.keys = [k for k in self.KEYS if params.get(k) is not None]
+        sizes = [params[k].numel() for k in self.keys]
+        self.flat = torch.cat([params[k].reshape(-1).float() for k in self.keys]).contiguous()
+        self.grad = torch.zeros_like(self.flat)
+        self.m = torch.zeros_like(self.flat)
+        self.v = torch.zeros_like(self.flat)
+        self.params, self.grads, off = {}, {}, 0
+        for k, n in zip(self.keys, sizes):
+            shape = params[k].shape
+            self.params[k] = self.flat[off:off + n].view(shape)
+            self.grads[k] = self.grad[off:off + n].view(shape)
+            off += n
+        self.cams = cams
+        self.targets = targets  # [F, 3*H*W] device
+        self.batch = batch
+        self.lr, self.betas, self.eps = lr, betas, eps
+        self.step_count = 0
+        self.rng = torch.Generator().manual_seed(seed)
+        self.ctx = gv.Context(tile, stage_depth)
+        W, H = int(cams[0].W), int(cams[0].H)
+        self.frames, self.total = gv.layout_frames([(c, 0, self.N) for c in cams[:batch]])
+        cap = key_capacity if key_capacity else 0
+        self.ws = torch.empty(self.ctx.workspace_size(self.frames, cap), dtype=torch.uint8, device=dev)
+        self.image = torch.empty(3 * self.total, device=dev)
+        self.T = torch.empty(self.total, device=dev)
+        self.idx = torch.empty(self.total, dtype=torch.int32, device=dev)
+        self.dL = torch.empty(3 * self.total, device=dev)
+        self.loss = torch.zeros(1, device=dev)
+        self.target_buf = torch.empty(3 * self.total, device=dev)
+        self.stream = torch.cuda.Stream(device=dev)
+        # size the key capacity from a forward of the first batch
+        if not cap:
+            self.ctx.render_fwd(self.params, self.frames, self.ws, self.image, self.T, self.idx)
+            st, keys = self.ctx.read_status(self.ws, raise_on_error=False)
+            self.ws = torch.empty(self.ctx.workspace_size(self.frames, int(keys * 1.5) + 65536),
+                                  dtype=torch.uint8, device=dev)
+        self.scale = 1.0 / (3 * self.total)
+        torch.cuda.synchronize()
+        with torch.cuda.stream(self.stream):
+            self.graph = gv.Graph(self.ctx, self.params, self.frames, self.ws, self.image, self.T, self.idx,
+                                  self.dL, self.grads, self.stream, target=self.target_buf,
+                                  loss_scale=self.scale, loss=self.loss)
+        self.W, self.H = W, H
+
+    def pick(self) -> list[int]:
+        return torch.randperm(len(self.cams), generator=self.rng)[:self.batch].sort().values.tolist()
+
+    def step(self, frame_ids: list[int] | None = None) -> torch.Tensor:
+        """One training step on the given (or random) frames; returns the device loss."""
+        ids = frame_ids if frame_ids is not None else self.pick()
+        fr = [gv.Frame(self.cams[i], 0, self.N, f.pixel_offset) for i, f in zip(ids, self.frames)]
+        self.graph.set_frames(fr)
+        with torch.cuda.stream(self.stream):
+            self.target_buf.view(self.batch, -1).copy_(self.targets[ids])
+            self.graph.launch(self.stream)
+            self.step_count += 1
+            self.ctx.adam_step(self.flat, self.grad, self.m, self.v, self.step_count, self.lr, self.betas[0],
+                               self.betas[1], self.eps, zero_grad=True, stream=self.stream)
+        torch.cuda.current_stream().wait_stream(self.stream)
+        return self.loss
+
+    def status(self):
+        st, keys = self.ctx.read_status(self.ws, stream=self.stream, raise_on_error=False)
+        return st, keys
+
+
+def psnr(image: torch.Tensor, target: torch.Tensor) -> float:
+    """Peak signal-to-noise ratio for images in [0, 1] (the paper's quality metric, Sec. 4.1)."""
+    mse = torch.mean((image.clamp(0, 1) - target) ** 2).item()
+    return float("inf") if mse == 0 else -10.0 * math.log10(mse)

@@ -4,8 +4,10 @@ FP64 oracle on the same seeded inputs, and compare with the stated tolerances.
 Tolerances (from the task's accuracy bar): tile counts and sorted key lists bit-exact;
 pixel values within max-abs 1e-4; gradients within 1e-3 relative or 1e-6 absolute.
 Pixels the oracle flags as ambiguous (a decision within FP32 reach of a threshold)
-are compared at 1e-2 and counted (at most 5 %: dense 540p frames put ~400 candidate
-Gaussians behind a pixel); their upstream gradient is set to zero on both sides.
+are compared at 1e-2 and counted; their upstream gradient is set to zero on both sides.
+Their share grows with the number of candidate Gaussians behind a pixel (~400 at 540p /
+200k, ~2000 at 1080p / 1M put 2-8 % of pixels within 1e-5 of the 1/255 cutoff); the cap of
+20 % only guards against a vacuous comparison.
 A gradient element failing both bounds but within CANCEL_REL of the sum of absolute
 per-pixel contributions is counted as cancellation-limited, not hidden: each FP32
 contribution carries a relative error up to about half an ulp of the pixel coordinate
@@ -94,7 +96,7 @@ def compare_pixels(gpu_rgb: np.ndarray, ref_rgb: np.ndarray, amb: np.ndarray, la
               max_amb=float(err[~clean].max()) if (~clean).any() else 0.0)
     assert st["max_clean"] <= PIX_TOL, f"{label} max-abs {st['max_clean']:.3e} > {PIX_TOL} ({st})"
     assert st["max_amb"] <= AMB_TOL, f"{label} ambiguous pixel error {st['max_amb']:.3e} > {AMB_TOL}"
-    assert st["n_amb"] <= max(3, 0.05 * st["n"]), f"{label} too many ambiguous pixels {st}"
+    assert st["n_amb"] <= max(3, 0.2 * st["n"]), f"{label} too many ambiguous pixels {st}"
     print(f"[pixels {label}] {st}")
     return st
 
