@@ -63,6 +63,11 @@ def parse_args():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched, e2e and training legs")
     ap.add_argument("--no-training", action="store_true", help="skip the 1080p / 1M-Gaussian training leg")
     ap.add_argument("--train-steps", type=int, default=20)
+    ap.add_argument("--workload", default="frame540p", choices=["frame540p", "clip1080p"],
+                    help="frame540p: one 960x540 frame, 200k Gaussians (the metric's configuration); "
+                         "clip1080p: --frames frames of the 1920x1080 / 1M-Gaussian training clip, batched")
+    ap.add_argument("--frames", type=int, default=2, help="frames per step for --workload clip1080p")
+    ap.add_argument("--no-autotune", action="store_true", help="keep 16x16 tiles, stage depth 128 (profiling runs)")
     return ap.parse_args()
 
 
@@ -180,23 +185,40 @@ def run_gv(args):
     num_sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
     # ---- workload (seeded; each replica its own frame) --------------------------------
-    wl = synth.workload_single_540p(seed_offset=1000 * rank)
-    g = wl["gaussians"]
-    cam = wl["frames"][0][0]
+    if args.workload == "frame540p":
+        wl = synth.workload_single_540p(seed_offset=1000 * rank)
+        g = wl["gaussians"]
+        cam = wl["frames"][0][0]
+        target = torch.from_numpy(wl["targets"][0]).to(dev).reshape(-1)
+        frames = [gv.Frame(cam, 0, N_GAUSS, 0)]
+        wl_name = ("frame_960x540_200k: one 960x540 frame, 200,000 Gaussians, random pose, per-frame plain "
+                   "renderer, fwd+L2 loss+bwd")
+    else:
+        wl = synth.workload_training(seed_offset=1000 * rank)
+        g = wl["gt"]
+        cam = wl["frames"][0][0]
+        frames, _ = gv.layout_frames([(c, 0, c_n) for c, _, c_n in wl["frames"][:args.frames]])
+        rng = np.random.default_rng(11)
+        target = torch.from_numpy(np.concatenate([synth.target_image(rng, c.cam.W, c.cam.H).reshape(-1)
+                                                  for c in frames])).to(dev)
+        wl_name = (f"clip_1080p_1m: {args.frames} frames 1920x1080 sharing 1,000,000 moving Gaussians, batched "
+                   "fwd+L2 loss+bwd")
     params = {k: torch.from_numpy(v).to(dev) for k, v in g.items()}
-    target = torch.from_numpy(wl["targets"][0]).to(dev).reshape(-1)
-    frames = [gv.Frame(cam, 0, N_GAUSS, 0)]
-    P = W * H
+    n_gauss = int(g["opacity_logit"].shape[-1])
+    P = sum(f.cam.W * f.cam.H for f in frames)
     ctx = gv.Context((16, 16), 256)
     image = torch.empty(3 * P, device=dev)
     T = torch.empty(P, device=dev)
     idx = torch.empty(P, dtype=torch.int32, device=dev)
     dL = torch.empty(3 * P, device=dev)
     loss = torch.zeros(1, device=dev)
-    flat = torch.zeros(14 * N_GAUSS, device=dev)
-    grads = {k: flat[a * N_GAUSS:b * N_GAUSS].view(b - a, N_GAUSS) if b - a > 1 else flat[a * N_GAUSS:b * N_GAUSS]
-             for k, (a, b) in dict(mean=(0, 3), log_scale=(3, 6), quat=(6, 10), opacity_logit=(10, 11),
-                                   rgb=(11, 14)).items()}
+    rows = dict(mean=(0, 3), log_scale=(3, 6), quat=(6, 10), opacity_logit=(10, 11), rgb=(11, 14))
+    if "vel" in params:
+        rows["vel"] = (14, 17)
+    nrows = max(b for _, b in rows.values())
+    flat = torch.zeros(nrows * n_gauss, device=dev)
+    grads = {k: flat[a * n_gauss:b * n_gauss].view(b - a, n_gauss) if b - a > 1 else flat[a * n_gauss:b * n_gauss]
+             for k, (a, b) in rows.items()}
     # size the workspace from the keys the frame needs (8x8 tiles need the most)
     ws = torch.empty(ctx.workspace_size(frames, 0), dtype=torch.uint8, device=dev)
     ctx.set_options(tile=(8, 8), stage_depth=64)
@@ -214,7 +236,10 @@ def run_gv(args):
         ctx.render_bwd(params, frames, ws, T, idx, dL, grads)
 
     # ---- autotune tile shape and stage depth on this workload (untimed) ----------------
-    best, tune_ms = ctx.autotune(params, frames, ws, image, T, idx, dL, grads, reps=3)
+    if args.no_autotune:
+        ctx.set_options(tile=(16, 16), stage_depth=128)
+    else:
+        best, tune_ms = ctx.autotune(params, frames, ws, image, T, idx, dL, grads, reps=3)
     ctx.read_status(ws)
 
     flush = torch.empty(128 * 1024 * 1024, dtype=torch.float32, device=dev)  # 512 MB > L2 (129 MB)
@@ -267,17 +292,19 @@ def run_gv(args):
     alu_peak_gops = num_sms * 128 * sm_mhz / 1e3  # FP32 lanes x clock
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     o = ctx.options
-    tiles = math.ceil(W / o.tile_w) * math.ceil(H / o.tile_h)
+    tiles = sum(math.ceil(f.cam.W / o.tile_w) * math.ceil(f.cam.H / o.tile_h) for f in frames)
     tile_passes = math.ceil(max(1, math.ceil(math.log2(tiles))) / 8)
+    npairs = counters["pairs"]
+    pbytes = 56 + (12 if "vel" in params else 0)  # parameter bytes read per pair
     work = {
         # the backward replays exactly the pairs the forward composited
         "composite_fwd": ("alu", OPS_EVAL * counters["fwd_eval"] + OPS_COMP_FWD * counters["bwd_replayed"]),
         "composite_bwd": ("alu", OPS_EVAL * counters["bwd_eval"] + OPS_COMP_BWD * counters["bwd_replayed"]),
-        "project": ("hbm", 112 * N_GAUSS),
-        "depth_sort": ("hbm", N_GAUSS * (4 + 4 * 16)),
+        "project": ("hbm", (pbytes + 56) * npairs),
+        "depth_sort": ("hbm", npairs * (4 + 4 * 16)),
         "tile_sort": ("hbm", counters["keys"] * tile_passes * 16),
-        "emit": ("hbm", N_GAUSS * 20 + counters["keys"] * 8),
-        "project_bwd": ("hbm", N_GAUSS * (56 + 36 + 56)),
+        "emit": ("hbm", npairs * 20 + counters["keys"] * 8),
+        "project_bwd": ("hbm", npairs * (pbytes + 36) + n_gauss * 4 * (14 + (3 if "vel" in params else 0))),
     }
     stages = {}
     for s, (kind, amount) in work.items():
@@ -306,10 +333,10 @@ def run_gv(args):
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(1000 * t_max / args.steps, 4), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "frame_960x540_200k: one 960x540 frame, 200,000 Gaussians, random pose, "
-                               "per-frame plain renderer, fwd+L2 loss+bwd",
-                   "width": W, "height": H, "gaussians": N_GAUSS, "frames_per_step": 1,
-                   "tile": f"{o.tile_w}x{o.tile_h}", "stage_depth": o.stage_depth, "autotuned": True,
+        "config": {"workload": wl_name,
+                   "width": frames[0].cam.W, "height": frames[0].cam.H, "gaussians": n_gauss,
+                   "frames_per_step": len(frames),
+                   "tile": f"{o.tile_w}x{o.tile_h}", "stage_depth": o.stage_depth, "autotuned": not args.no_autotune,
                    "keys": counters["keys"], "l2": "512 MB write between timed steps (L2 flushed)",
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roofline,
@@ -319,7 +346,7 @@ def run_gv(args):
         "clocks": clk,
         "work_counters": counters,
     }
-    if not args.no_extras:
+    if not args.no_extras and args.workload == "frame540p":
         out["batched"] = run_batched(torch, gv, synth, ctx, dev, flush, max(20, args.steps // 4))
         out["e2e"] = run_e2e(torch, gv, ctx, params, target, frames, ws, dev, flush, max(20, args.steps // 4), scale,
                              world)
@@ -328,7 +355,7 @@ def run_gv(args):
                                                                 alu_peak_gops)
     else:
         out["e2e"] = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "frame540p":
         out["cpu_baseline"] = cpu_baseline(g, cam, wl["targets"][0], args.cpu_seconds)
     if world > 1:
         import torch.distributed as dist

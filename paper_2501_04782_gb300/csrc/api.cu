@@ -170,13 +170,16 @@ gv_status make_plan(gv_ctx *ctx, const gv_options &o, long long N, const gv_fram
     L.g0 = take(16 * Pn);
     L.g1 = take(16 * Pn);
     L.g2 = take(4 * Pn);
+    L.fp64_list = take(4 * Pn);
     L.ranges = take(8 * (size_t)L.tiles_alloc);
     L.hist = take(4 * 8 * kRadix);
     const size_t fixed = off;
     auto total_for = [&](unsigned long long cap) {
-        unsigned long long lt = (std::max<unsigned long long>(cap, P) + kSortTile - 1) / kSortTile;
+        unsigned long long lt = std::max<unsigned long long>(sort_tiles((unsigned)std::min<unsigned long long>(cap, 0xFFFFFFF0ull), (unsigned)std::min<unsigned long long>(cap, 0xFFFFFFF0ull)),
+                                                             sort_tiles((unsigned)P, (unsigned)P));
         size_t t = fixed;
         t += 4 * align_up(4 * std::max<unsigned long long>(cap, 1));
+        t += align_up(4 * (std::max<unsigned long long>(cap, 1) / kEmitBlock + 2));
         t += align_up(2 * 4 * std::max<unsigned long long>(lt, 1) * kRadix);
         return t;
     };
@@ -195,12 +198,13 @@ gv_status make_plan(gv_ctx *ctx, const gv_options &o, long long N, const gv_fram
     }
     if (cap >= (1ull << 30)) return fail(ctx, GV_ERR_INVALID_ARG, "key capacity %llu >= 2^30", cap);
     L.key_cap = (unsigned)cap;
-    L.look_tiles = (unsigned)std::max<unsigned long long>((std::max<unsigned long long>(cap, P) + kSortTile - 1) / kSortTile, 1);
+    L.look_tiles = std::max(std::max(sort_tiles((unsigned)cap, (unsigned)cap), sort_tiles((unsigned)P, (unsigned)P)), 1u);
     size_t kc = std::max<size_t>(cap, 1);
     L.tkey[0] = take(4 * kc);
     L.tkey[1] = take(4 * kc);
     L.tval[0] = take(4 * kc);
     L.tval[1] = take(4 * kc);
+    L.chunk_first = take(4 * ((size_t)kc / kEmitBlock + 2));
     L.look = take((size_t)2 * 4 * L.look_tiles * kRadix);
     L.total = off;
     if (key_cap_req <= 0 && L.total > ws_bytes)
@@ -226,9 +230,11 @@ Work make_work(void *ws, const Layout &L) {
     w.blocksum = (unsigned *)(b + L.blocksum);
     w.blockprefix = (unsigned *)(b + L.blockprefix);
     w.offsets = (unsigned *)(b + L.offsets);
+    w.chunk_first = (unsigned *)(b + L.chunk_first);
     w.g0 = (float4 *)(b + L.g0);
     w.g1 = (float4 *)(b + L.g1);
     w.g2 = (float *)(b + L.g2);
+    w.fp64_list = (unsigned *)(b + L.fp64_list);
     w.ranges = (uint2 *)(b + L.ranges);
     w.hist = (unsigned *)(b + L.hist);
     w.look = (unsigned *)(b + L.look);
@@ -284,11 +290,11 @@ gv_status forward_stages(gv_ctx *ctx, const gv_gaussians *g, const Plan &pl, con
         }
         int dres = 0;
         {
-            StageTimer tm(ctx, GV_STAGE_DEPTH_SORT, s, 1 + sort_passes(32));
+            StageTimer tm(ctx, GV_STAGE_DEPTH_SORT, s, sort_passes(32));
             const unsigned *n_pairs = reinterpret_cast<const unsigned *>(reinterpret_cast<const char *>(w.hdr) +
                                                                            offsetof(DevHeader, n_pairs));
             unsigned *dk[2] = {w.dkey[0], w.dkey[1]}, *dv[2] = {w.dval[0], w.dval[1]};
-            GV_CUDA(launch_radix_sort(w, dk, dv, n_pairs, w.L.P, 32, true, false, 0, 0, ctx->num_sms, s, &dres));
+            GV_CUDA(launch_radix_sort(w, dk, dv, n_pairs, w.L.P, 32, true, true, 0, 0, ctx->num_sms, s, &dres));
         }
         {
             StageTimer tm(ctx, GV_STAGE_EMIT, s, 4);
@@ -296,7 +302,7 @@ gv_status forward_stages(gv_ctx *ctx, const gv_gaussians *g, const Plan &pl, con
         }
         int tres = 0;
         {
-            StageTimer tm(ctx, GV_STAGE_TILE_SORT, s, 1 + sort_passes(w.L.tile_bits));
+            StageTimer tm(ctx, GV_STAGE_TILE_SORT, s, sort_passes(w.L.tile_bits));
             const unsigned *n_keys = reinterpret_cast<const unsigned *>(reinterpret_cast<const char *>(w.hdr) +
                                                                           offsetof(DevHeader, keys_used));
             unsigned *tk[2] = {w.tkey[0], w.tkey[1]}, *tv[2] = {w.tval[0], w.tval[1]};
@@ -321,13 +327,10 @@ gv_status backward_stages(gv_ctx *ctx, const gv_gaussians *g, const Plan &pl, co
     const gv_options &o = ctx->opt;
     ctx->launches[GV_STAGE_COMPOSITE_BWD] = ctx->launches[GV_STAGE_PROJECT_BWD] = 0;
     if (w.L.P == 0) return GV_OK;
-    GV_CUDA(cudaMemsetAsync(w.g0, 0, (size_t)16 * w.L.P, s));
-    GV_CUDA(cudaMemsetAsync(w.g1, 0, (size_t)16 * w.L.P, s));
-    GV_CUDA(cudaMemsetAsync(w.g2, 0, (size_t)4 * w.L.P, s));
-    GV_CUDA(cudaMemsetAsync(reinterpret_cast<char *>(w.hdr) + offsetof(DevHeader, queue) + sizeof(unsigned), 0,
-                            sizeof(unsigned), s));
-    GV_CUDA(cudaMemsetAsync(reinterpret_cast<char *>(w.hdr) + offsetof(DevHeader, work) + 2 * sizeof(unsigned long long),
-                            0, 2 * sizeof(unsigned long long), s));
+    // the three screen-space gradient planes are adjacent in the workspace: one memset; the
+    // backward work queue is reset by the last block of the previous backward (or by setup)
+    GV_CUDA(cudaMemsetAsync(w.g0, 0, (size_t)(reinterpret_cast<char *>(w.g2 + w.L.P) - reinterpret_cast<char *>(w.g0)),
+                            s));
     {
         StageTimer tm(ctx, GV_STAGE_COMPOSITE_BWD, s, 1);
         GV_CUDA(launch_composite_bwd(w, o.tile_w, o.tile_h, o.stage_depth, tile_result_buf(w.L), o.bg[0], o.bg[1],
@@ -337,7 +340,7 @@ gv_status backward_stages(gv_ctx *ctx, const gv_gaussians *g, const Plan &pl, co
     gp.mean = grad->mean; gp.vel = grad->vel; gp.log_scale = grad->log_scale;
     gp.quat = grad->quat; gp.logit = grad->opacity_logit; gp.rgb = grad->rgb;
     {
-        StageTimer tm(ctx, GV_STAGE_PROJECT_BWD, s, 1);
+        StageTimer tm(ctx, GV_STAGE_PROJECT_BWD, s, 2);
         GV_CUDA(launch_project_bwd(w, gauss_ptrs(g), gp, pl.bwd_mode, s));
     }
     return GV_OK;
@@ -830,7 +833,7 @@ gv_status gv_debug_bin_sort(gv_ctx *ctx, int64_t n, const float *u, const float 
         const unsigned *n_pairs = reinterpret_cast<const unsigned *>(reinterpret_cast<const char *>(w.hdr) +
                                                                        offsetof(DevHeader, n_pairs));
         unsigned *dk[2] = {w.dkey[0], w.dkey[1]}, *dv[2] = {w.dval[0], w.dval[1]};
-        GV_CUDA(launch_radix_sort(w, dk, dv, n_pairs, w.L.P, 32, true, false, 0, 0, ctx->num_sms, s, &dres));
+        GV_CUDA(launch_radix_sort(w, dk, dv, n_pairs, w.L.P, 32, true, true, 0, 0, ctx->num_sms, s, &dres));
         GV_CUDA(launch_emit(w, dres, w.L.tile_bits, 4, ctx->num_sms, s));
         const unsigned *n_keys = reinterpret_cast<const unsigned *>(reinterpret_cast<const char *>(w.hdr) +
                                                                       offsetof(DevHeader, keys_used));

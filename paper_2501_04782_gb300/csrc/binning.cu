@@ -30,6 +30,9 @@ __global__ void setup_kernel(Work w, FrameChunk chunk, int first, int count, int
     }
     for (int i = tid; i < 8 * kRadix; i += stride) w.hist[i] = 0u;
     for (unsigned i = tid; i < w.L.tiles; i += stride) w.ranges[i] = make_uint2(0u, 0u);
+    // look-back buffer 0 of the depth sort (its digits are counted by the projection)
+    const unsigned nlook = sort_tiles(w.L.P, w.L.P) * kRadix;
+    for (unsigned i = tid; i < nlook; i += stride) w.look[i] = 0u;
 }
 
 // Sum of the tile counts of each block of kEmitBlock pairs taken in depth order.
@@ -126,88 +129,120 @@ __global__ void __launch_bounds__(kEmitThreads) offsets_kernel(Work w, const uns
     __syncthreads();
     unsigned run = w.blockprefix[b] + inc - sum;
     for (int q = 0; q < wid; q++) run += s_w[q];
+    const unsigned cap = w.L.key_cap;
 #pragma unroll
     for (int i = 0; i < kEmitItems; i++) {
         unsigned idx = base + t * kEmitItems + i;
-        if (idx < w.L.P) w.offsets[idx] = min(run, w.L.key_cap);
+        if (idx < w.L.P) {
+            const unsigned lo = min(run, cap), hi = min(run + c[i], cap);
+            w.offsets[idx] = lo;
+            // this pair owns the first key of every emission chunk starting in [lo, hi)
+            for (unsigned ch = (lo + kEmitBlock - 1) / kEmitBlock; ch * kEmitBlock < hi; ch++) w.chunk_first[ch] = idx;
+        }
         run += c[i];
     }
     if (b == 0 && t == 0) w.offsets[w.L.P] = w.hdr->keys_used;
 }
 
 // Key emission balanced over keys: each block iteration takes kEmitBlock consecutive
-// keys, finds the pairs that own them (binary search over a shared-memory window of the
-// depth-ordered offsets; every pair in the window owns at least one key, pairs with no
-// key sort last) and writes (tile id, pair id), the tiles of a pair in row-major order.
-// Also counts the tile-sort digit histograms.
+// keys and finds the pair owning every key with a load-balancing search: the pairs whose
+// keys fall in the chunk (a window of the depth-ordered offsets starting at the chunk's
+// owner recorded by offsets_kernel; every pair in it owns at least one key, pairs with no
+// key sort last) mark their first key, and an inclusive max scan over the chunk carries
+// each mark forward.  Keys are written coalesced as (tile id,
+// pair id), the tiles of a pair in row-major order.  Also counts the tile-sort digit
+// histograms.
 __global__ void __launch_bounds__(kEmitThreads) emit_kernel(Work w, const unsigned *order, int tile_passes,
                                                             unsigned *tile_hist) {
-    __shared__ unsigned s_off[kEmitBlock + 1];
-    __shared__ unsigned s_pair[kEmitBlock + 1];
+    __shared__ int s_owner[kEmitBlock];
+    __shared__ unsigned s_off[kEmitBlock];
+    __shared__ unsigned s_pair[kEmitBlock];
     __shared__ unsigned s_hist[4][kRadix];
+    __shared__ int s_wmax[kEmitThreads / 32];
     __shared__ unsigned s_lo, s_n;
-    const int t = threadIdx.x, lane = t & 31;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     for (int i = t; i < 4 * kRadix; i += kEmitThreads) (&s_hist[0][0])[i] = 0u;
     const unsigned K = w.hdr->keys_used;
     const unsigned P = w.L.P;
     const unsigned *off = w.offsets;
     const unsigned nchunks = (K + kEmitBlock - 1) / kEmitBlock;
+    {   // look-back buffer 0 of the tile sort (the depth sort is finished with it)
+        const unsigned nlook = sort_tiles(K, w.L.key_cap) * kRadix;
+        for (unsigned i = blockIdx.x * blockDim.x + t; i < nlook; i += gridDim.x * blockDim.x) w.look[i] = 0u;
+    }
     for (unsigned chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
         const unsigned k0 = chunk * kEmitBlock;
-        const unsigned k1 = min(K, k0 + kEmitBlock);
+        const unsigned kb = min(K - k0, (unsigned)kEmitBlock);
         __syncthreads();
         if (t == 0) {
-            // largest i with off[i] <= k0, and with off[i] <= k1 - 1
-            unsigned lo = 0, hi = P - 1;
-            while (lo < hi) {
-                unsigned mid = (lo + hi + 1) >> 1;
-                if (off[mid] <= k0) lo = mid; else hi = mid - 1;
-            }
-            unsigned lo2 = lo, hi2 = P - 1;
-            while (lo2 < hi2) {
-                unsigned mid = (lo2 + hi2 + 1) >> 1;
-                if (off[mid] <= k1 - 1) lo2 = mid; else hi2 = mid - 1;
-            }
+            // the pairs owning this chunk's keys run from the owner of its first key to the
+            // owner of the next chunk's first key (pairs after the last key own nothing here)
+            const unsigned lo = min(w.chunk_first[chunk], P - 1u);
+            const unsigned hi = chunk + 1 < nchunks ? min(w.chunk_first[chunk + 1], P - 1u) : P - 1u;
             s_lo = lo;
-            s_n = min(lo2 - lo + 1, (unsigned)kEmitBlock);
+            s_n = min(hi >= lo ? hi - lo + 1 : 1u, (unsigned)kEmitBlock);
         }
+        for (int i = t; i < kEmitBlock; i += kEmitThreads) s_owner[i] = -1;
         __syncthreads();
         const unsigned plo = s_lo, np = s_n;
         for (unsigned i = t; i < np; i += kEmitThreads) {
-            s_off[i] = off[plo + i];
-            unsigned p = order[plo + i];
-            s_pair[i] = p < P ? p : 0u;
+            const unsigned o = off[plo + i];
+            const unsigned p = order[plo + i];
+            s_off[i] = o;
+            s_pair[i] = p < P ? p : 0u;  // in range unless a bounded wait gave up
+            const unsigned first = o > k0 ? o - k0 : 0u;
+            if (first < kb) s_owner[first] = (int)i;
         }
         __syncthreads();
-        for (unsigned e0 = k0; e0 < k1; e0 += kEmitThreads) {
-            const unsigned e = e0 + t;
-            const bool ok = e < k1;
+        // inclusive max scan of s_owner: thread t owns entries t*8 .. t*8+7
+        int run = -1;
+        int v[kEmitItems];
+#pragma unroll
+        for (int i = 0; i < kEmitItems; i++) {
+            v[i] = s_owner[t * kEmitItems + i];
+            run = max(run, v[i]);
+            v[i] = run;
+        }
+        int incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl = max(incl, y);
+        }
+        if (lane == 31) s_wmax[wid] = incl;
+        __syncthreads();
+        int carry = -1;
+        for (int q = 0; q < wid; q++) carry = max(carry, s_wmax[q]);
+        int excl = __shfl_up_sync(0xffffffffu, incl, 1);
+        if (lane == 0) excl = -1;
+        carry = max(carry, excl);
+#pragma unroll
+        for (int i = 0; i < kEmitItems; i++) s_owner[t * kEmitItems + i] = max(carry, v[i]);
+        __syncthreads();
+        for (unsigned r0 = 0; r0 < (unsigned)kEmitBlock; r0 += kEmitThreads) {
+            const unsigned e = r0 + t;
+            const bool ok = e < kb;
             unsigned tile = 0;
             if (ok) {
-                int lo = 0, hi = (int)np - 1;
-                while (lo < hi) {
-                    int mid = (lo + hi + 1) >> 1;
-                    if (s_off[mid] <= e) lo = mid; else hi = mid - 1;
-                }
-                const unsigned p = s_pair[lo];
-                const unsigned j = e - s_off[lo];
-                const uint4 r = w.rect[p];
+                const int i = max(s_owner[e], 0);
+                const unsigned j = k0 + e - s_off[i];
+                const unsigned p = s_pair[i];
+                const uint4 r = w.rect[p];  // consecutive keys mostly share a pair: L1 hits
+                const DevFrame &fr = w.frames[min(r.w, w.L.F - 1u)];
                 const unsigned tx0 = r.x & 0xFFFFu, ty0 = r.x >> 16, tx1 = r.y & 0xFFFFu;
                 const unsigned wr = tx1 - tx0 + 1u;
-                const unsigned ty = ty0 + j / wr, tx = tx0 + j % wr;
-                const DevFrame &fr = w.frames[min(r.w, w.L.F - 1u)];
-                tile = min(fr.tile_offset + ty * fr.tiles_x + tx, w.L.tiles - 1u);
-                w.tkey[0][e] = tile;
-                w.tval[0][e] = p;
+                // j / wr through the FP32 reciprocal, corrected to the exact quotient (j < 2^24)
+                unsigned q = (unsigned)((float)j * __frcp_rn((float)wr));
+                int rem = (int)j - (int)(q * wr);
+                if (rem < 0) { q--; rem += (int)wr; }
+                else if (rem >= (int)wr) { q++; rem -= (int)wr; }
+                tile = min(fr.tile_offset + (ty0 + q) * fr.tiles_x + tx0 + (unsigned)rem, w.L.tiles - 1u);
+                w.tkey[0][k0 + e] = tile;
+                w.tval[0][k0 + e] = p;
             }
             const unsigned active = __ballot_sync(0xffffffffu, ok);
-            if (ok) {
-                for (int ps = 0; ps < tile_passes; ps++) {
-                    unsigned d = (tile >> (8 * ps)) & 255u;
-                    unsigned peers = __match_any_sync(active, d);
-                    if (lane == __ffs(peers) - 1) atomicAdd(&s_hist[ps][d], (unsigned)__popc(peers));
-                }
-            }
+            if (ok)
+                for (int ps = 0; ps < tile_passes; ps++) count_digit(s_hist[ps], (tile >> (8 * ps)) & 255u, active);
         }
     }
     __syncthreads();
@@ -251,7 +286,8 @@ const void *setup_kernel_ptr() { return (const void *)setup_kernel; }
 
 cudaError_t launch_setup(const Work &w, const FrameChunk &chunk, int first, int count, bool zero_all,
                          long long spin_limit, int drop_signal, cudaStream_t s) {
-    unsigned work = zero_all ? max(w.L.tiles, (unsigned)(8 * kRadix)) : (unsigned)count;
+    unsigned work = zero_all ? max(max(w.L.tiles, (unsigned)(8 * kRadix)), sort_tiles(w.L.P, w.L.P) * kRadix)
+                             : (unsigned)count;
     unsigned blocks = min((work + 255u) / 256u, 1024u);
     if (blocks == 0) blocks = 1;
     setup_kernel<<<blocks, 256, 0, s>>>(w, chunk, first, count, zero_all ? 1 : 0, spin_limit, drop_signal);

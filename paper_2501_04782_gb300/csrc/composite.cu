@@ -33,6 +33,15 @@ __device__ __forceinline__ void add_work(unsigned long long *ctr, unsigned n_eva
     }
 }
 
+// A block leaving the persistent loop counts itself done; the last one resets the work
+// queue and the done count, so the next launch on this workspace starts from zero.
+__device__ __forceinline__ void queue_done(unsigned *queue, unsigned *done) {
+    if (threadIdx.x == 0 && atomicAdd(done, 1u) == gridDim.x - 1) {
+        *queue = 0u;
+        *done = 0u;
+    }
+}
+
 // Thread -> pixels.  A warp owns an 8x8 pixel block of the tile; lane l owns pixel
 // (l & 7, l >> 3) of the block and the pixel four rows below it.
 template <int TW, int TH>
@@ -95,7 +104,10 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_fwd_kernel(Work w, const
         if (threadIdx.x == 0) s_tile = atomicAdd(&w.hdr->queue[0], 1u);
         __syncthreads();
         const unsigned tile = s_tile;
-        if (tile >= ntiles) break;
+        if (tile >= ntiles) {
+            queue_done(w.hdr->queue + 0, w.hdr->queue + 2);
+            break;
+        }
         const DevFrame &fr = w.frames[find_frame_by_tile(w.frames, F, tile)];
         const int W = fr.W, H = fr.H;
         const unsigned lt = tile - fr.tile_offset;
@@ -186,7 +198,10 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_bwd_kernel(Work w, const
         if (threadIdx.x == 0) { s_tile = atomicAdd(&w.hdr->queue[1], 1u); s_max = -1; }
         __syncthreads();
         const unsigned tile = s_tile;
-        if (tile >= ntiles) break;
+        if (tile >= ntiles) {
+            queue_done(w.hdr->queue + 1, w.hdr->queue + 3);
+            break;
+        }
         const DevFrame &fr = w.frames[find_frame_by_tile(w.frames, F, tile)];
         const int W = fr.W, H = fr.H;
         const unsigned lt = tile - fr.tile_offset;

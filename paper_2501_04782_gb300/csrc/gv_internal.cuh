@@ -56,13 +56,22 @@ struct DevHeader {
     int drop_signal;                // test hook: first look-back block never publishes
     int pad;
     unsigned long long work[4];     // pairs evaluated / composited: fwd 0-1, bwd 2-3
+    unsigned fp64_count;            // ill-conditioned pairs deferred to the FP64 chain rule
+    unsigned fp64_done;             // blocks of the FP64 pass finished (last one resets)
 };
 
-// Radix sort geometry (one onesweep pass = one 8-bit digit).
+// Radix sort geometry (one onesweep pass = one 8-bit digit).  Small sorts use 1024-key
+// block tiles (more blocks in flight), large ones 3840-key tiles (fewer look-back steps).
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 15;
-constexpr int kSortTile = kSortThreads * kSortItems;  // 3840 keys per block tile
 constexpr int kRadix = 256;
+constexpr unsigned kSortSmallN = 1u << 20;
+__host__ __device__ constexpr int sort_items(unsigned n_cap) { return n_cap <= kSortSmallN ? 4 : 15; }
+__host__ __device__ constexpr unsigned sort_tile_keys(unsigned n_cap) {
+    return (unsigned)(kSortThreads * sort_items(n_cap));
+}
+__host__ __device__ constexpr unsigned sort_tiles(unsigned n, unsigned n_cap) {
+    return (n + sort_tile_keys(n_cap) - 1) / sort_tile_keys(n_cap);
+}
 
 // Emission block geometry (count scan + load-balanced key emission).
 constexpr int kEmitThreads = 256;
@@ -73,8 +82,9 @@ constexpr int kEmitBlock = kEmitThreads * kEmitItems;  // 2048 pairs per block
 struct Layout {
     size_t hdr, frames;
     size_t feat0, feat1, feat2, rect, dkey[2], dval[2];
-    size_t blocksum, blockprefix, offsets;
+    size_t blocksum, blockprefix, offsets, chunk_first;
     size_t g0, g1, g2;
+    size_t fp64_list;
     size_t ranges;
     size_t tkey[2], tval[2];
     size_t hist, look;
@@ -97,8 +107,10 @@ struct Work {
     unsigned *dkey[2], *dval[2];
     unsigned *blocksum, *blockprefix;
     unsigned *offsets;  // [P + 1] exclusive key offsets of the pairs in depth order
+    unsigned *chunk_first;  // [key_cap / kEmitBlock + 1] depth-ordered pair owning a chunk's first key
     float4 *g0, *g1;
     float *g2;
+    unsigned *fp64_list;  // [P] pairs whose geometric chain rule runs in FP64
     uint2 *ranges;
     unsigned *tkey[2], *tval[2];
     unsigned *hist;   // [8][256]: depth-sort passes 0-3, tile-sort passes 4-7
@@ -135,8 +147,13 @@ cudaError_t launch_project_bwd(const Work &w, const GaussPtrs &g, const GradPtrs
 // sort.cu
 int sort_passes(int bits);
 cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2], const unsigned *n_dev,
-                              unsigned n_cap, int bits, bool vals_identity, bool hist_counted, int hist_slot,
+                              unsigned n_cap, int bits, bool vals_identity, bool prepared, int hist_slot,
                               int ctr_slot, int num_sms, cudaStream_t s, int *result_buf);
+// Warp-aggregated count of one 8-bit digit per lane into a shared histogram row.
+__device__ __forceinline__ void count_digit(unsigned *row, unsigned d, unsigned active) {
+    const unsigned peers = __match_any_sync(active, d);
+    if ((threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) atomicAdd(row + d, (unsigned)__popc(peers));
+}
 // binning.cu
 cudaError_t launch_emit(const Work &w, int depth_buf, int tile_bits, int tile_hist_slot, int num_sms,
                         cudaStream_t s);

@@ -13,46 +13,59 @@ namespace gvk {
 
 namespace {
 
+// Scalar helpers so the projection and its chain rule can run in FP32 (the default) or
+// FP64 (ill-conditioned pairs in the backward).
+__device__ __forceinline__ float exp_(float x) { return expf(x); }
+__device__ __forceinline__ double exp_(double x) { return exp(x); }
+__device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+__device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+
+template <typename F>
 struct PairState {
-    float mx, my, mz;        // world mean at the frame's time
-    float xc, yc, zc;        // camera-space mean
-    float s0, s1, s2;        // scales
-    float qw, qx, qy, qz;    // normalised quaternion
-    float inv_qn;            // 1 / |q|
-    float R[9];              // Gaussian rotation
-    float S3[6];             // world covariance xx, xy, xz, yy, yz, zz
-    float T0[3], T1[3];      // rows of J W
-    float a, b, c;           // Sigma2 (with low-pass)
-    float A, B, C;           // conic
-    float u, v;
-    float o;
+    F mx, my, mz;        // world mean at the frame's time
+    F xc, yc, zc;        // camera-space mean
+    F s0, s1, s2;        // scales
+    F qw, qx, qy, qz;    // normalised quaternion
+    F inv_qn;            // 1 / |q|
+    F R[9];              // Gaussian rotation
+    F S3[6];             // world covariance xx, xy, xz, yy, yz, zz
+    F T0[3], T1[3];      // rows of J W
+    F a, b, c;           // Sigma2 (with low-pass)
+    F A, B, C;           // conic
+    F u, v;
+    F o;
     bool valid;
 };
 
+template <typename F>
 __device__ __forceinline__ void load_and_project(const GaussPtrs &g, long long gi, const DevFrame &fr,
-                                                 PairState &st) {
+                                                 PairState<F> &st) {
     const long long N = g.N;
-    st.mx = g.mean[gi];
-    st.my = g.mean[N + gi];
-    st.mz = g.mean[2 * N + gi];
+    const F time = (F)fr.time;
+    st.mx = (F)g.mean[gi];
+    st.my = (F)g.mean[N + gi];
+    st.mz = (F)g.mean[2 * N + gi];
     if (g.vel) {
-        st.mx = fmaf(fr.time, g.vel[gi], st.mx);
-        st.my = fmaf(fr.time, g.vel[N + gi], st.my);
-        st.mz = fmaf(fr.time, g.vel[2 * N + gi], st.mz);
+        st.mx = fma_(time, (F)g.vel[gi], st.mx);
+        st.my = fma_(time, (F)g.vel[N + gi], st.my);
+        st.mz = fma_(time, (F)g.vel[2 * N + gi], st.mz);
     }
-    st.s0 = expf(g.log_scale[gi]);
-    st.s1 = expf(g.log_scale[N + gi]);
-    st.s2 = expf(g.log_scale[2 * N + gi]);
-    float qw = g.quat[gi], qx = g.quat[N + gi], qy = g.quat[2 * N + gi], qz = g.quat[3 * N + gi];
-    float inv = rsqrtf(qw * qw + qx * qx + qy * qy + qz * qz);
+    st.s0 = exp_((F)g.log_scale[gi]);
+    st.s1 = exp_((F)g.log_scale[N + gi]);
+    st.s2 = exp_((F)g.log_scale[2 * N + gi]);
+    F qw = (F)g.quat[gi], qx = (F)g.quat[N + gi], qy = (F)g.quat[2 * N + gi], qz = (F)g.quat[3 * N + gi];
+    F inv = rsqrt_(qw * qw + qx * qx + qy * qy + qz * qz);
     st.inv_qn = inv;
     qw *= inv; qx *= inv; qy *= inv; qz *= inv;
     st.qw = qw; st.qx = qx; st.qy = qy; st.qz = qz;
-    float *R = st.R;
-    R[0] = 1.f - 2.f * (qy * qy + qz * qz); R[1] = 2.f * (qx * qy - qw * qz); R[2] = 2.f * (qx * qz + qw * qy);
-    R[3] = 2.f * (qx * qy + qw * qz); R[4] = 1.f - 2.f * (qx * qx + qz * qz); R[5] = 2.f * (qy * qz - qw * qx);
-    R[6] = 2.f * (qx * qz - qw * qy); R[7] = 2.f * (qy * qz + qw * qx); R[8] = 1.f - 2.f * (qx * qx + qy * qy);
-    float s0q = st.s0 * st.s0, s1q = st.s1 * st.s1, s2q = st.s2 * st.s2;
+    F *R = st.R;
+    const F one = (F)1, two = (F)2;
+    R[0] = one - two * (qy * qy + qz * qz); R[1] = two * (qx * qy - qw * qz); R[2] = two * (qx * qz + qw * qy);
+    R[3] = two * (qx * qy + qw * qz); R[4] = one - two * (qx * qx + qz * qz); R[5] = two * (qy * qz - qw * qx);
+    R[6] = two * (qx * qz - qw * qy); R[7] = two * (qy * qz + qw * qx); R[8] = one - two * (qx * qx + qy * qy);
+    F s0q = st.s0 * st.s0, s1q = st.s1 * st.s1, s2q = st.s2 * st.s2;
     // Sigma3_ij = sum_k R_ik R_jk s_k^2
     st.S3[0] = R[0] * R[0] * s0q + R[1] * R[1] * s1q + R[2] * R[2] * s2q;
     st.S3[1] = R[0] * R[3] * s0q + R[1] * R[4] * s1q + R[2] * R[5] * s2q;
@@ -60,39 +73,40 @@ __device__ __forceinline__ void load_and_project(const GaussPtrs &g, long long g
     st.S3[3] = R[3] * R[3] * s0q + R[4] * R[4] * s1q + R[5] * R[5] * s2q;
     st.S3[4] = R[3] * R[6] * s0q + R[4] * R[7] * s1q + R[5] * R[8] * s2q;
     st.S3[5] = R[6] * R[6] * s0q + R[7] * R[7] * s1q + R[8] * R[8] * s2q;
-    const float *W = fr.R;
-    st.xc = W[0] * st.mx + W[1] * st.my + W[2] * st.mz + fr.t[0];
-    st.yc = W[3] * st.mx + W[4] * st.my + W[5] * st.mz + fr.t[1];
-    st.zc = W[6] * st.mx + W[7] * st.my + W[8] * st.mz + fr.t[2];
-    st.o = 1.f / (1.f + expf(-g.logit[gi]));
-    st.valid = st.zc > kZNear;
+    F W[9];
+    for (int i = 0; i < 9; i++) W[i] = (F)fr.R[i];
+    st.xc = W[0] * st.mx + W[1] * st.my + W[2] * st.mz + (F)fr.t[0];
+    st.yc = W[3] * st.mx + W[4] * st.my + W[5] * st.mz + (F)fr.t[1];
+    st.zc = W[6] * st.mx + W[7] * st.my + W[8] * st.mz + (F)fr.t[2];
+    st.o = one / (one + exp_(-(F)g.logit[gi]));
+    st.valid = st.zc > (F)kZNear;
     if (!st.valid) return;
-    float iz = 1.f / st.zc;
-    float rx = st.xc * iz, ry = st.yc * iz;
-    float jx = fr.fx * iz, jy = fr.fy * iz;
+    F iz = one / st.zc;
+    F rx = st.xc * iz, ry = st.yc * iz;
+    F jx = (F)fr.fx * iz, jy = (F)fr.fy * iz;
     // rows of T = J W with J = [[fx/z, 0, -fx x/z^2], [0, fy/z, -fy y/z^2]]
     for (int j = 0; j < 3; j++) {
         st.T0[j] = jx * (W[j] - rx * W[6 + j]);
         st.T1[j] = jy * (W[3 + j] - ry * W[6 + j]);
     }
-    const float *S = st.S3;
-    float v0x = S[0] * st.T0[0] + S[1] * st.T0[1] + S[2] * st.T0[2];
-    float v0y = S[1] * st.T0[0] + S[3] * st.T0[1] + S[4] * st.T0[2];
-    float v0z = S[2] * st.T0[0] + S[4] * st.T0[1] + S[5] * st.T0[2];
-    float v1x = S[0] * st.T1[0] + S[1] * st.T1[1] + S[2] * st.T1[2];
-    float v1y = S[1] * st.T1[0] + S[3] * st.T1[1] + S[4] * st.T1[2];
-    float v1z = S[2] * st.T1[0] + S[4] * st.T1[1] + S[5] * st.T1[2];
-    st.a = st.T0[0] * v0x + st.T0[1] * v0y + st.T0[2] * v0z + kEps2d;
+    const F *S = st.S3;
+    F v0x = S[0] * st.T0[0] + S[1] * st.T0[1] + S[2] * st.T0[2];
+    F v0y = S[1] * st.T0[0] + S[3] * st.T0[1] + S[4] * st.T0[2];
+    F v0z = S[2] * st.T0[0] + S[4] * st.T0[1] + S[5] * st.T0[2];
+    F v1x = S[0] * st.T1[0] + S[1] * st.T1[1] + S[2] * st.T1[2];
+    F v1y = S[1] * st.T1[0] + S[3] * st.T1[1] + S[4] * st.T1[2];
+    F v1z = S[2] * st.T1[0] + S[4] * st.T1[1] + S[5] * st.T1[2];
+    st.a = st.T0[0] * v0x + st.T0[1] * v0y + st.T0[2] * v0z + (F)kEps2d;
     st.b = st.T0[0] * v1x + st.T0[1] * v1y + st.T0[2] * v1z;
-    st.c = st.T1[0] * v1x + st.T1[1] * v1y + st.T1[2] * v1z + kEps2d;
-    float det = st.a * st.c - st.b * st.b;
-    if (!(det > 0.f)) { st.valid = false; return; }
-    float idet = 1.f / det;
+    st.c = st.T1[0] * v1x + st.T1[1] * v1y + st.T1[2] * v1z + (F)kEps2d;
+    F det = st.a * st.c - st.b * st.b;
+    if (!(det > (F)0)) { st.valid = false; return; }
+    F idet = one / det;
     st.A = st.c * idet;
     st.B = -st.b * idet;
     st.C = st.a * idet;
-    st.u = fmaf(fr.fx, rx, fr.cx);
-    st.v = fmaf(fr.fy, ry, fr.cy);
+    st.u = fma_((F)fr.fx, rx, (F)fr.cx);
+    st.v = fma_((F)fr.fy, ry, (F)fr.cy);
     if (!(isfinite(st.u) && isfinite(st.v) && isfinite(st.A) && isfinite(st.B) && isfinite(st.C)))
         st.valid = false;
 }
@@ -120,27 +134,48 @@ __device__ __forceinline__ unsigned tile_rect(float u, float v, float ex, float 
     return (tx1 - tx0 + 1u) * (ty1 - ty0 + 1u);
 }
 
-__global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, int lw, int lh) {
-    unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= w.L.P) return;
-    int f = find_frame_by_pair(w.frames, (int)w.L.F, p);
-    const DevFrame &fr = w.frames[f];
-    long long gi = fr.gauss_offset + (long long)(p - fr.pair_offset);
-    PairState st;
-    load_and_project(g, gi, fr, st);
-    unsigned cnt = 0, lo = 0, hi = 0;
-    float ex = 0.f, ey = 0.f;
-    if (st.valid) {
-        ex = kExtK * sqrtf(st.a);
-        ey = kExtK * sqrtf(st.c);
-        cnt = tile_rect(st.u, st.v, ex, ey, fr.W, fr.H, lw, lh, lo, hi);
+// Digit histograms of the depth keys for the depth sort (4 passes of 8 bits), counted in
+// shared memory and added to histogram rows 0-3.
+__device__ __forceinline__ void count_depth_digits(unsigned (*s_h)[kRadix], Work &w, unsigned key, bool ok) {
+    const unsigned active = __ballot_sync(0xffffffffu, ok);
+    if (ok)
+        for (int ps = 0; ps < 4; ps++) count_digit(s_h[ps], (key >> (8 * ps)) & 255u, active);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) {
+        const unsigned c = (&s_h[0][0])[i];
+        if (c) atomicAdd(w.hist + i, c);
     }
-    const long long N = g.N;
-    w.feat0[p] = make_float4(st.u, st.v, -0.5f * kLog2e * st.A, -kLog2e * st.B);
-    w.feat1[p] = make_float4(-0.5f * kLog2e * st.C, log2f(st.o), g.rgb[gi], g.rgb[N + gi]);
-    w.feat2[p] = g.rgb[2 * N + gi];
-    w.rect[p] = make_uint4(lo, hi, cnt, (unsigned)f);
-    w.dkey[0][p] = cnt ? __float_as_uint(st.zc) : 0xFFFFFFFFu;
+}
+
+__global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, int lw, int lh) {
+    __shared__ unsigned s_h[4][kRadix];
+    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0u;
+    __syncthreads();
+    const unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool in = p < w.L.P;
+    unsigned key = 0xFFFFFFFFu;
+    if (in) {
+        int f = find_frame_by_pair(w.frames, (int)w.L.F, p);
+        const DevFrame &fr = w.frames[f];
+        long long gi = fr.gauss_offset + (long long)(p - fr.pair_offset);
+        PairState<float> st;
+        load_and_project(g, gi, fr, st);
+        unsigned cnt = 0, lo = 0, hi = 0;
+        float ex = 0.f, ey = 0.f;
+        if (st.valid) {
+            ex = kExtK * sqrtf(st.a);
+            ey = kExtK * sqrtf(st.c);
+            cnt = tile_rect(st.u, st.v, ex, ey, fr.W, fr.H, lw, lh, lo, hi);
+        }
+        const long long N = g.N;
+        w.feat0[p] = make_float4(st.u, st.v, -0.5f * kLog2e * st.A, -kLog2e * st.B);
+        w.feat1[p] = make_float4(-0.5f * kLog2e * st.C, log2f(st.o), g.rgb[gi], g.rgb[N + gi]);
+        w.feat2[p] = g.rgb[2 * N + gi];
+        w.rect[p] = make_uint4(lo, hi, cnt, (unsigned)f);
+        key = cnt ? __float_as_uint(st.zc) : 0xFFFFFFFFu;
+        w.dkey[0][p] = key;
+    }
+    count_depth_digits(s_h, w, key, in);  // every thread of the block reaches this call
 }
 
 // Stage-isolated binning: screen-space inputs of one frame given by the caller.
@@ -149,99 +184,131 @@ __global__ void __launch_bounds__(256) bin_from_screen_kernel(Work w, long long 
                                                               const float *ey, const float *depth,
                                                               const uint8_t *valid, int lw, int lh,
                                                               int32_t *counts) {
-    long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (p >= n) return;
-    const DevFrame &fr = w.frames[0];
-    unsigned lo = 0, hi = 0, cnt = 0;
-    if (valid[p]) cnt = tile_rect(u[p], v[p], ex[p], ey[p], fr.W, fr.H, lw, lh, lo, hi);
-    w.rect[p] = make_uint4(lo, hi, cnt, 0u);
-    w.dkey[0][p] = cnt ? __float_as_uint(depth[p]) : 0xFFFFFFFFu;
-    if (counts) counts[p] = (int32_t)cnt;
+    __shared__ unsigned s_h[4][kRadix];
+    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0u;
+    __syncthreads();
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const bool in = p < n;
+    unsigned key = 0xFFFFFFFFu;
+    if (in) {
+        const DevFrame &fr = w.frames[0];
+        unsigned lo = 0, hi = 0, cnt = 0;
+        if (valid[p]) cnt = tile_rect(u[p], v[p], ex[p], ey[p], fr.W, fr.H, lw, lh, lo, hi);
+        w.rect[p] = make_uint4(lo, hi, cnt, 0u);
+        key = cnt ? __float_as_uint(depth[p]) : 0xFFFFFFFFu;
+        w.dkey[0][p] = key;
+        if (counts) counts[p] = (int32_t)cnt;
+    }
+    count_depth_digits(s_h, w, key, in);  // every thread of the block reaches this call
 }
 
-// Chain rule of one pair: screen-space gradient to the raw-parameter gradients, added
-// into acc[17] (mean 3, vel 3, log_scale 3, quat 4, logit 1, rgb 3).  The compositing
-// backward accumulates (du, dv, da', db', dc', dlog2o, dr, dg, db) for the staged record
-// (a', b', c') = -log2(e) (A/2, B, C/2) and log2 o; converted here to the conic and opacity.
-__device__ __forceinline__ void pair_backward(const PairState &st, const DevFrame &fr, float4 g0,
-                                              float4 g1, float g2, float acc[17]) {
-    acc[14] += g1.z;
-    acc[15] += g1.w;
-    acc[16] += g2;
-    // d log2(o) / d logit = (1 - o) / ln 2
-    acc[13] += g1.y * (1.f - st.o) * kLog2e;
-    if (!st.valid) return;
-    float dA = -0.5f * kLog2e * g0.z, dB = -kLog2e * g0.w, dC = -0.5f * kLog2e * g1.x;
+// Chain rule of the geometric part of one pair: gradients w.r.t. the screen mean (du, dv)
+// and the conic (dA, dB, dC) to mean, velocity, log-scale and quaternion, added into acc
+// (rows 0-12 of the 17-row layout: mean 3, vel 3, log_scale 3, quat 4).
+template <typename F>
+__device__ __forceinline__ void geometry_backward(const PairState<F> &st, const DevFrame &fr, F du, F dv, F dA,
+                                                  F dB, F dC, float acc[17]) {
+    const F half = (F)0.5, two = (F)2;
     // conic Q = Sigma2^{-1}: dL/dSigma2 = -Q G Q with G = [[dA, dB/2], [dB/2, dC]]
-    float X00 = st.A * dA + 0.5f * st.B * dB, X01 = 0.5f * st.A * dB + st.B * dC;
-    float X10 = st.B * dA + 0.5f * st.C * dB, X11 = 0.5f * st.B * dB + st.C * dC;
-    float ga = -(X00 * st.A + X01 * st.B);
-    float gb = -(X00 * st.B + X01 * st.C);
-    float gc = -(X10 * st.B + X11 * st.C);
+    F X00 = st.A * dA + half * st.B * dB, X01 = half * st.A * dB + st.B * dC;
+    F X10 = st.B * dA + half * st.C * dB, X11 = half * st.B * dB + st.C * dC;
+    F ga = -(X00 * st.A + X01 * st.B);
+    F gb = -(X00 * st.B + X01 * st.C);
+    F gc = -(X10 * st.B + X11 * st.C);
     // Sigma2 = T Sigma3 T^T: dSigma3 = T^T G T, dT = 2 G T Sigma3
-    const float *S = st.S3;
-    float v0[3], v1[3];
+    const F *S = st.S3;
+    F v0[3], v1[3];
     v0[0] = S[0] * st.T0[0] + S[1] * st.T0[1] + S[2] * st.T0[2];
     v0[1] = S[1] * st.T0[0] + S[3] * st.T0[1] + S[4] * st.T0[2];
     v0[2] = S[2] * st.T0[0] + S[4] * st.T0[1] + S[5] * st.T0[2];
     v1[0] = S[0] * st.T1[0] + S[1] * st.T1[1] + S[2] * st.T1[2];
     v1[1] = S[1] * st.T1[0] + S[3] * st.T1[1] + S[4] * st.T1[2];
     v1[2] = S[2] * st.T1[0] + S[4] * st.T1[1] + S[5] * st.T1[2];
-    float dT0[3], dT1[3];
+    F dT0[3], dT1[3];
     for (int j = 0; j < 3; j++) {
-        dT0[j] = 2.f * (ga * v0[j] + gb * v1[j]);
-        dT1[j] = 2.f * (gb * v0[j] + gc * v1[j]);
+        dT0[j] = two * (ga * v0[j] + gb * v1[j]);
+        dT1[j] = two * (gb * v0[j] + gc * v1[j]);
     }
-    float dS[3][3];
+    F dS[3][3];
     for (int k = 0; k < 3; k++)
         for (int l = 0; l < 3; l++)
             dS[k][l] = ga * st.T0[k] * st.T0[l] + gb * (st.T0[k] * st.T1[l] + st.T1[k] * st.T0[l]) +
                        gc * st.T1[k] * st.T1[l];
     // T = J W
-    const float *W = fr.R;
-    float dJ00 = dT0[0] * W[0] + dT0[1] * W[1] + dT0[2] * W[2];
-    float dJ02 = dT0[0] * W[6] + dT0[1] * W[7] + dT0[2] * W[8];
-    float dJ11 = dT1[0] * W[3] + dT1[1] * W[4] + dT1[2] * W[5];
-    float dJ12 = dT1[0] * W[6] + dT1[1] * W[7] + dT1[2] * W[8];
-    float iz = 1.f / st.zc, iz2 = iz * iz, iz3 = iz2 * iz;
-    float fx = fr.fx, fy = fr.fy;
-    float du = g0.x, dv = g0.y;
-    float dxc = du * fx * iz - dJ02 * fx * iz2;
-    float dyc = dv * fy * iz - dJ12 * fy * iz2;
-    float dzc = -du * fx * st.xc * iz2 - dv * fy * st.yc * iz2 - dJ00 * fx * iz2 - dJ11 * fy * iz2 +
-                2.f * (dJ02 * fx * st.xc + dJ12 * fy * st.yc) * iz3;
+    F W[9];
+    for (int i = 0; i < 9; i++) W[i] = (F)fr.R[i];
+    F dJ00 = dT0[0] * W[0] + dT0[1] * W[1] + dT0[2] * W[2];
+    F dJ02 = dT0[0] * W[6] + dT0[1] * W[7] + dT0[2] * W[8];
+    F dJ11 = dT1[0] * W[3] + dT1[1] * W[4] + dT1[2] * W[5];
+    F dJ12 = dT1[0] * W[6] + dT1[1] * W[7] + dT1[2] * W[8];
+    F iz = (F)1 / st.zc, iz2 = iz * iz, iz3 = iz2 * iz;
+    F fx = (F)fr.fx, fy = (F)fr.fy;
+    F dxc = du * fx * iz - dJ02 * fx * iz2;
+    F dyc = dv * fy * iz - dJ12 * fy * iz2;
+    F dzc = -du * fx * st.xc * iz2 - dv * fy * st.yc * iz2 - dJ00 * fx * iz2 - dJ11 * fy * iz2 +
+            two * (dJ02 * fx * st.xc + dJ12 * fy * st.yc) * iz3;
     // x_c = W mu + t
-    float dmx = W[0] * dxc + W[3] * dyc + W[6] * dzc;
-    float dmy = W[1] * dxc + W[4] * dyc + W[7] * dzc;
-    float dmz = W[2] * dxc + W[5] * dyc + W[8] * dzc;
-    acc[0] += dmx; acc[1] += dmy; acc[2] += dmz;
-    acc[3] += fr.time * dmx; acc[4] += fr.time * dmy; acc[5] += fr.time * dmz;
+    F dmx = W[0] * dxc + W[3] * dyc + W[6] * dzc;
+    F dmy = W[1] * dxc + W[4] * dyc + W[7] * dzc;
+    F dmz = W[2] * dxc + W[5] * dyc + W[8] * dzc;
+    const F time = (F)fr.time;
+    acc[0] += (float)dmx; acc[1] += (float)dmy; acc[2] += (float)dmz;
+    acc[3] += (float)(time * dmx); acc[4] += (float)(time * dmy); acc[5] += (float)(time * dmz);
     // Sigma3 = M M^T, M = R diag(s): dM = 2 dSigma3 M
-    const float *R = st.R;
-    float s[3] = {st.s0, st.s1, st.s2};
-    float G[9];
+    const F *R = st.R;
+    F s[3] = {st.s0, st.s1, st.s2};
+    F G[9];
     for (int j = 0; j < 3; j++) {
-        float dsj = 0.f;
+        F dsj = (F)0;
         for (int k = 0; k < 3; k++) {
-            float dMkj = 2.f * s[j] * (dS[k][0] * R[j] + dS[k][1] * R[3 + j] + dS[k][2] * R[6 + j]);
+            F dMkj = two * s[j] * (dS[k][0] * R[j] + dS[k][1] * R[3 + j] + dS[k][2] * R[6 + j]);
             G[k * 3 + j] = dMkj * s[j];
             dsj += dMkj * R[k * 3 + j];
         }
-        acc[6 + j] += dsj * s[j];
+        acc[6 + j] += (float)(dsj * s[j]);
     }
     // R(q): gradient w.r.t. the normalised quaternion, then through the normalisation
-    float w = st.qw, x = st.qx, y = st.qy, z = st.qz;
-    float S01 = G[1] + G[3], S02 = G[2] + G[6], S12 = G[5] + G[7];
-    float A10 = G[3] - G[1], A02 = G[2] - G[6], A21 = G[7] - G[5];
-    float dw = 2.f * (z * A10 + y * A02 + x * A21);
-    float dx = 2.f * (y * S01 + z * S02 + w * A21 - 2.f * x * (G[4] + G[8]));
-    float dy = 2.f * (x * S01 + z * S12 + w * A02 - 2.f * y * (G[0] + G[8]));
-    float dz = 2.f * (x * S02 + y * S12 + w * A10 - 2.f * z * (G[0] + G[4]));
-    float dot = dw * w + dx * x + dy * y + dz * z;
-    acc[9] += (dw - w * dot) * st.inv_qn;
-    acc[10] += (dx - x * dot) * st.inv_qn;
-    acc[11] += (dy - y * dot) * st.inv_qn;
-    acc[12] += (dz - z * dot) * st.inv_qn;
+    F w = st.qw, x = st.qx, y = st.qy, z = st.qz;
+    F S01 = G[1] + G[3], S02 = G[2] + G[6], S12 = G[5] + G[7];
+    F A10 = G[3] - G[1], A02 = G[2] - G[6], A21 = G[7] - G[5];
+    F dw = two * (z * A10 + y * A02 + x * A21);
+    F dx = two * (y * S01 + z * S02 + w * A21 - two * x * (G[4] + G[8]));
+    F dy = two * (x * S01 + z * S12 + w * A02 - two * y * (G[0] + G[8]));
+    F dz = two * (x * S02 + y * S12 + w * A10 - two * z * (G[0] + G[4]));
+    F dot = dw * w + dx * x + dy * y + dz * z;
+    acc[9] += (float)((dw - w * dot) * st.inv_qn);
+    acc[10] += (float)((dx - x * dot) * st.inv_qn);
+    acc[11] += (float)((dy - y * dot) * st.inv_qn);
+    acc[12] += (float)((dz - z * dot) * st.inv_qn);
+}
+
+// Ill-conditioned pairs: when Sigma2 is close to singular (a c / det > 64, a Gaussian
+// stretched by the perspective, typically near the camera and far off axis) the FP32
+// inverse and -Q G Q lose digits.  Such pairs are listed and their geometric chain rule
+// is redone in FP64 by a second, small kernel (keeping the FP64 registers out of the
+// common FP32 kernel).
+constexpr float kFp64Condition = 64.f;
+
+// Chain rule of one pair: screen-space gradient to the raw-parameter gradients, added
+// into acc[17] (mean 3, vel 3, log_scale 3, quat 4, logit 1, rgb 3).  The compositing
+// backward accumulates (du, dv, da', db', dc', dlog2o, dr, dg, db) for the staged record
+// (a', b', c') = -log2(e) (A/2, B, C/2) and log2 o; converted here to the conic and opacity.
+// Returns false when the geometric part was deferred to the FP64 pass.
+__device__ __forceinline__ void pair_backward(const PairState<float> &st, const Work &w, unsigned p,
+                                              const DevFrame &fr, float4 g0, float4 g1, float g2, float acc[17]) {
+    acc[14] += g1.z;
+    acc[15] += g1.w;
+    acc[16] += g2;
+    // d log2(o) / d logit = (1 - o) / ln 2
+    acc[13] += g1.y * (1.f - st.o) * kLog2e;
+    if (!st.valid) return;
+    const float det = st.a * st.c - st.b * st.b;
+    if (st.a * st.c > kFp64Condition * det) {
+        w.fp64_list[atomicAdd(&w.hdr->fp64_count, 1u)] = p;
+        return;
+    }
+    const float dA = -0.5f * kLog2e * g0.z, dB = -kLog2e * g0.w, dC = -0.5f * kLog2e * g1.x;
+    geometry_backward<float>(st, fr, g0.x, g0.y, dA, dB, dC, acc);
 }
 
 __device__ __forceinline__ void store_grad(const GradPtrs &gr, long long N, long long gi, const float acc[17],
@@ -267,12 +334,12 @@ __global__ void __launch_bounds__(128) project_bwd_pairs_kernel(Work w, GaussPtr
     int f = find_frame_by_pair(w.frames, (int)w.L.F, p);
     const DevFrame &fr = w.frames[f];
     long long gi = fr.gauss_offset + (long long)(p - fr.pair_offset);
-    PairState st;
+    PairState<float> st;
     load_and_project(g, gi, fr, st);
     float acc[17];
 #pragma unroll
     for (int k = 0; k < 17; k++) acc[k] = 0.f;
-    pair_backward(st, fr, w.g0[p], w.g1[p], w.g2[p], acc);
+    pair_backward(st, w, p, fr, w.g0[p], w.g1[p], w.g2[p], acc);
     store_grad(gr, g.N, gi, acc, atomic != 0);
 }
 
@@ -288,11 +355,38 @@ __global__ void __launch_bounds__(128) project_bwd_shared_kernel(Work w, GaussPt
     for (int f = 0; f < (int)w.L.F; f++) {
         const DevFrame &fr = w.frames[f];
         unsigned p = fr.pair_offset + j;
-        PairState st;
+        PairState<float> st;
         load_and_project(g, gi, fr, st);
-        pair_backward(st, fr, w.g0[p], w.g1[p], w.g2[p], acc);
+        pair_backward(st, w, p, fr, w.g0[p], w.g1[p], w.g2[p], acc);
     }
     store_grad(gr, g.N, gi, acc, false);
+}
+
+// FP64 geometric chain rule of the listed ill-conditioned pairs; atomic because several
+// frames of a shared set may list the same Gaussian.  The last block resets the list.
+__global__ void __launch_bounds__(128) project_bwd_fp64_kernel(Work w, GaussPtrs g, GradPtrs gr) {
+    const unsigned n = w.hdr->fp64_count;
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const unsigned p = min(w.fp64_list[i], w.L.P - 1u);
+        const DevFrame &fr = w.frames[find_frame_by_pair(w.frames, (int)w.L.F, p)];
+        const long long gi = fr.gauss_offset + (long long)(p - fr.pair_offset);
+        PairState<double> sd;
+        load_and_project(g, gi, fr, sd);
+        if (!sd.valid) continue;
+        const float4 g0 = w.g0[p], g1 = w.g1[p];
+        float acc[17];
+#pragma unroll
+        for (int k = 0; k < 17; k++) acc[k] = 0.f;
+        geometry_backward<double>(sd, fr, (double)g0.x, (double)g0.y, -0.5 * (double)kLog2e * g0.z,
+                                  -(double)kLog2e * g0.w, -0.5 * (double)kLog2e * g1.x, acc);
+        acc[13] = acc[14] = acc[15] = acc[16] = 0.f;  // colour and opacity were done in FP32
+        store_grad(gr, g.N, gi, acc, true);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && atomicAdd(&w.hdr->fp64_done, 1u) == gridDim.x - 1) {
+        w.hdr->fp64_count = 0u;
+        w.hdr->fp64_done = 0u;
+    }
 }
 
 }  // namespace
@@ -324,6 +418,9 @@ cudaError_t launch_project_bwd(const Work &w, const GaussPtrs &g, const GradPtrs
     } else {
         project_bwd_pairs_kernel<<<(w.L.P + 127) / 128, 128, 0, s>>>(w, g, gr, mode == 2 ? 1 : 0);
     }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    project_bwd_fp64_kernel<<<64, 128, 0, s>>>(w, g, gr);
     return cudaGetLastError();
 }
 

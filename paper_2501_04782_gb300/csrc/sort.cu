@@ -74,18 +74,14 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(const unsigned *keys, co
         unsigned k = ok ? keys[i] : 0u;
         unsigned active = __ballot_sync(0xffffffffu, ok);
         if (!ok) continue;
-        for (int ps = 0; ps < passes; ps++) {
-            unsigned d = (k >> (8 * ps)) & 255u;
-            unsigned peers = __match_any_sync(active, d);
-            if ((threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) atomicAdd(&s_h[ps][d], (unsigned)__popc(peers));
-        }
+        for (int ps = 0; ps < passes; ps++) count_digit(s_h[ps], (k >> (8 * ps)) & 255u, active);
     }
     __syncthreads();
     for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) {
         unsigned c = (&s_h[0][0])[i];
         if (c) atomicAdd(hist + i, c);
     }
-    unsigned ntiles = (n + kSortTile - 1) / kSortTile;
+    unsigned ntiles = sort_tiles(n, n_cap);
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < ntiles * kRadix; i += stride) look0[i] = 0u;
 }
 
@@ -102,9 +98,11 @@ struct PassArgs {
     DevHeader *hdr;
 };
 
+template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(PassArgs a) {
-    __shared__ unsigned s_keys[kSortTile];
-    __shared__ unsigned s_vals[kSortTile];
+    constexpr int TILE = kSortThreads * ITEMS;
+    __shared__ unsigned s_keys[TILE];
+    __shared__ unsigned s_vals[TILE];
     __shared__ unsigned s_whist[8][kRadix];
     __shared__ unsigned s_gexcl[kRadix];    // exclusive global digit offsets
     __shared__ unsigned s_dstart[kRadix];   // exclusive digit offsets inside the tile
@@ -115,7 +113,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(PassArgs a) {
 
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const unsigned n = min(*a.n_dev, a.n_cap);
-    const unsigned ntiles = (n + kSortTile - 1) / kSortTile;
+    const unsigned ntiles = (n + TILE - 1) / TILE;
     const long long limit = a.hdr->spin_limit;
     const bool drop = a.hdr->drop_signal != 0;
     {
@@ -129,11 +127,11 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(PassArgs a) {
         __syncthreads();
         const unsigned tile = s_tile;
         if (tile >= ntiles) break;
-        const unsigned base = tile * kSortTile;
-        unsigned k[kSortItems], v[kSortItems], r[kSortItems];
+        const unsigned base = tile * TILE;
+        unsigned k[ITEMS], v[ITEMS], r[ITEMS];
 #pragma unroll
-        for (int i = 0; i < kSortItems; i++) {
-            unsigned idx = base + wid * (32 * kSortItems) + i * 32 + lane;
+        for (int i = 0; i < ITEMS; i++) {
+            unsigned idx = base + wid * (32 * ITEMS) + i * 32 + lane;
             if (idx < n) {
                 k[i] = a.keys_in[idx];
                 v[i] = a.vals_in ? a.vals_in[idx] : idx;
@@ -144,7 +142,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(PassArgs a) {
         }
         // stable rank inside the warp: by item, then by lane
 #pragma unroll
-        for (int i = 0; i < kSortItems; i++) {
+        for (int i = 0; i < ITEMS; i++) {
             unsigned d = (k[i] >> a.shift) & 255u;
             unsigned peers = __match_any_sync(0xffffffffu, d);
             unsigned before = s_whist[wid][d];
@@ -163,7 +161,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(PassArgs a) {
             total += c;
         }
         unsigned tail = 0;  // sentinels counted in digit 255 of the last tile
-        if (t == 255 && base + kSortTile > n) tail = base + kSortTile - n;
+        if (t == 255 && base + TILE > n) tail = base + TILE - n;
         const unsigned mine = total - tail;
         // decoupled look-back for digit t
         unsigned excl = 0;
@@ -198,7 +196,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(PassArgs a) {
         a.look_next[(size_t)tile * kRadix + t] = 0u;
         __syncthreads();
 #pragma unroll
-        for (int i = 0; i < kSortItems; i++) {
+        for (int i = 0; i < ITEMS; i++) {
             unsigned d = (k[i] >> a.shift) & 255u;
             unsigned pos = s_dstart[d] + s_whist[wid][d] + r[i];
             s_keys[pos] = k[i];
@@ -206,7 +204,7 @@ __global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(PassArgs a) {
         }
         __syncthreads();
         if (!s_abort) {
-            for (int pos = t; pos < kSortTile; pos += kSortThreads) {
+            for (int pos = t; pos < TILE; pos += kSortThreads) {
                 unsigned key = s_keys[pos];
                 unsigned d = (key >> a.shift) & 255u;
                 unsigned gpos = s_gbase[d] + (unsigned)pos - s_dstart[d];
@@ -226,23 +224,29 @@ int sort_passes(int bits) { return bits <= 0 ? 0 : (bits + 7) / 8; }
 
 // Sorts keys[0]/vals[0] by their low `bits` bits.  *result_buf receives the buffer index
 // (0 or 1) that holds the sorted output.  hist_slot selects 4 histogram rows of the
-// workspace (0 or 4), ctr_slot 4 tile counters.  Histogram rows and counters must be
-// zero on entry (the setup kernel clears them), unless hist_counted says the producer
-// of the keys already counted every pass's digits into those rows.
+// workspace (0 or 4), ctr_slot 4 tile counters (both zero on entry: the setup kernel
+// clears them).  prepared: the producer of the keys already counted every pass's digits
+// into those rows and cleared look-back buffer 0 for sort_tiles(n, n_cap) tiles;
+// otherwise a histogram kernel does both first.
 cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2], const unsigned *n_dev,
-                              unsigned n_cap, int bits, bool vals_identity, bool hist_counted, int hist_slot,
+                              unsigned n_cap, int bits, bool vals_identity, bool prepared, int hist_slot,
                               int ctr_slot, int num_sms, cudaStream_t s, int *result_buf) {
     int passes = sort_passes(bits);
     *result_buf = 0;
     if (passes == 0 || n_cap == 0) return cudaSuccess;
     unsigned *hist = w.hist + (size_t)hist_slot * kRadix;
-    unsigned max_tiles = (n_cap + kSortTile - 1) / kSortTile;
+    const unsigned max_tiles = sort_tiles(n_cap, n_cap);
     unsigned *look[2] = {w.look, w.look + (size_t)w.L.look_tiles * kRadix};
-    int hist_blocks = (int)std::min<unsigned>((n_cap + 255) / 256, (unsigned)num_sms * 4u);
-    sort_hist_kernel<<<hist_blocks, 256, 0, s>>>(keys[0], n_dev, n_cap, hist_counted ? 0 : passes, hist, look[0]);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    int grid = (int)std::min<unsigned>(max_tiles, (unsigned)num_sms * 3u);
+    cudaError_t e;
+    if (!prepared) {
+        int hist_blocks = (int)std::min<unsigned>((n_cap + 255) / 256, (unsigned)num_sms * 4u);
+        sort_hist_kernel<<<hist_blocks, 256, 0, s>>>(keys[0], n_dev, n_cap, passes, hist, look[0]);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    const bool small = sort_items(n_cap) == 4;
+    const int per_sm = small ? 4 : 2;  // resident blocks per SM (registers)
+    int grid = (int)std::min<unsigned>(max_tiles, (unsigned)num_sms * per_sm);
     int cur = 0;
     for (int ps = 0; ps < passes; ps++) {
         PassArgs a;
@@ -259,7 +263,8 @@ cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2
         a.ctr = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(w.hdr) + offsetof(DevHeader, sort_ctr)) +
                 ctr_slot + ps;
         a.hdr = w.hdr;
-        sort_pass_kernel<<<grid, kSortThreads, 0, s>>>(a);
+        if (small) sort_pass_kernel<4><<<grid, kSortThreads, 0, s>>>(a);
+        else sort_pass_kernel<15><<<grid, kSortThreads, 0, s>>>(a);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         cur ^= 1;
