@@ -24,8 +24,9 @@
  *   by camera depth (ties by Gaussian index); a Gaussian is composited and then the pixel
  *   stops if T < 1e-4.  image = sum_i c_i alpha_i T_i + T_final * bg.
  *   A Gaussian is binned into every tile holding a pixel centre inside
- *   [u - k sqrt(Sigma2_xx), u + k sqrt(Sigma2_xx)] x [v - k sqrt(Sigma2_yy), ...],
- *   k = sqrt(2 ln 255), so the image does not depend on the tile shape.
+ *   [u - sqrt(tau Sigma2_xx), u + sqrt(tau Sigma2_xx)] x [v - sqrt(tau Sigma2_yy), ...],
+ *   tau = 2 ln(255 o) (the bounding box of its alpha >= 1/255 region), so the image does not
+ *   depend on the tile shape.
  *
  * Memory and ownership.  Every pointer below is a DEVICE pointer unless marked host.
  * The caller owns every buffer; render calls never allocate.  All Gaussian parameter and

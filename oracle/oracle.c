@@ -26,9 +26,10 @@
  *       alpha < alpha_min (1/255) are skipped;
  *     - front to back in depth order (ties by Gaussian index); a Gaussian is composited
  *       and then compositing stops if T < T_stop (1e-4); output C + T bg;
- *     - binning extent of a Gaussian: half-widths k sqrt(Sigma2_xx), k sqrt(Sigma2_yy)
- *       with k = sqrt(2 ln 255), the exact axis-aligned bound of the alpha >= 1/255
- *       region, so the image does not depend on the tile shape.
+ *     - binning extent of a Gaussian: half-widths sqrt(tau Sigma2_xx), sqrt(tau Sigma2_yy)
+ *       with tau = 2 ln(255 o) (no extent when o < 1/255), the exact axis-aligned bound of
+ *       the alpha >= 1/255 region d^T Sigma2^{-1} d <= tau, so the image does not depend
+ *       on the tile shape.
  *   The backward pass is the analytic adjoint of exactly this function.  A "smooth
  *   mode" (alpha_min = 0, T_stop = 0, alpha_max = inf) makes the image a smooth
  *   function of the parameters so central finite differences apply.
@@ -151,8 +152,12 @@ static void project_one(const orc_gaussians *g, int64_t i, const orc_camera *cam
     pr->Q[0] = c / det; pr->Q[1] = -b / det; pr->Q[2] = a / det;
     pr->u = cam->fx * x / z + cam->cx;
     pr->v = cam->fy * y / z + cam->cy;
-    pr->ex = p->ext_k * sqrt(a);
-    pr->ey = p->ext_k * sqrt(c);
+    /* alpha >= alpha_min needs d^T conic d <= tau = 2 ln(o / alpha_min) (ext_k^2 caps it) */
+    double tau = p->alpha_min > 0 ? 2.0 * log(pr->o / p->alpha_min) : p->ext_k * p->ext_k;
+    if (tau > p->ext_k * p->ext_k) tau = p->ext_k * p->ext_k;
+    if (tau < 0) tau = 0;
+    pr->ex = sqrt(tau * a);
+    pr->ey = sqrt(tau * c);
     pr->valid = 1;
 }
 

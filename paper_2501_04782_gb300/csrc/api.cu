@@ -286,7 +286,7 @@ gv_status forward_stages(gv_ctx *ctx, const gv_gaussians *g, const Plan &pl, con
     if (w.L.P > 0) {
         {
             StageTimer tm(ctx, GV_STAGE_PROJECT, s, 1);
-            GV_CUDA(launch_project_fwd(w, gauss_ptrs(g), o.tile_w, o.tile_h, s));
+            GV_CUDA(launch_project_fwd(w, gauss_ptrs(g), o.tile_w, o.tile_h, ctx->num_sms, s));
         }
         int dres = 0;
         {
@@ -341,7 +341,7 @@ gv_status backward_stages(gv_ctx *ctx, const gv_gaussians *g, const Plan &pl, co
     gp.quat = grad->quat; gp.logit = grad->opacity_logit; gp.rgb = grad->rgb;
     {
         StageTimer tm(ctx, GV_STAGE_PROJECT_BWD, s, 2);
-        GV_CUDA(launch_project_bwd(w, gauss_ptrs(g), gp, pl.bwd_mode, s));
+        GV_CUDA(launch_project_bwd(w, gauss_ptrs(g), gp, pl.bwd_mode, ctx->num_sms, s));
     }
     return GV_OK;
 }

@@ -103,8 +103,38 @@ __global__ void __launch_bounds__(1024) count_scan_kernel(Work w) {
     }
 }
 
+// Tile-sort digit counts of one tile-id range [t0, t0 + len) (a row of a pair's tile
+// rectangle): digit 0 through a difference array over its 256 values (the range wraps
+// around len >> 8 times plus a partial run), higher digits directly (a row spans one or two
+// of their values).
+__device__ __forceinline__ void count_tile_run(unsigned t0, unsigned len, int passes, int *s_diff, unsigned *s_full,
+                                               unsigned (*s_h)[kRadix]) {
+    const unsigned full = len >> 8, rem = len & 255u;
+    if (full) atomicAdd(s_full, full);
+    if (rem) {
+        const unsigned a = t0 & 255u, e = a + rem;
+        atomicAdd(s_diff + a, 1);
+        if (e <= 256u) {
+            atomicAdd(s_diff + e, -1);
+        } else {
+            atomicAdd(s_diff + 256, -1);
+            atomicAdd(s_diff + 0, 1);
+            atomicAdd(s_diff + (e - 256u), -1);
+        }
+    }
+    const unsigned t1 = t0 + len - 1u;
+    for (int ps = 1; ps < passes; ps++) {
+        const int sh = 8 * ps;
+        for (unsigned h = t0 >> sh; h <= (t1 >> sh); h++) {
+            const unsigned lo = max(t0, h << sh), hi = min(t1, ((h + 1u) << sh) - 1u);
+            atomicAdd(&s_h[ps][h & 255u], hi - lo + 1u);
+        }
+    }
+}
+
 // Exclusive key offsets of every pair in depth order: off[i] for i < P, off[P] = K.
-// Block b scans its kEmitBlock pairs and adds the block prefix.
+// Block b scans its kEmitBlock pairs and adds the block prefix.  Each pair also records
+// the emission chunks whose first key it owns.
 __global__ void __launch_bounds__(kEmitThreads) offsets_kernel(Work w, const unsigned *order) {
     __shared__ unsigned s_w[8];
     const unsigned b = blockIdx.x, base = b * kEmitBlock;
@@ -144,6 +174,31 @@ __global__ void __launch_bounds__(kEmitThreads) offsets_kernel(Work w, const uns
     if (b == 0 && t == 0) w.offsets[w.L.P] = w.hdr->keys_used;
 }
 
+// Flush a block's tile-sort digit counts: digit 0 from its difference array (prefix sum
+// plus the full wraps), higher digits as counted.
+__device__ __forceinline__ void flush_tile_hist(int passes, int *s_diff, unsigned s_full, unsigned (*s_h)[kRadix],
+                                                unsigned *tile_hist) {
+    const int t = threadIdx.x, lane = t & 31;
+    if (t < 32) {
+        int carry = 0;
+        for (int base8 = 0; base8 < 256; base8 += 32) {
+            int x = s_diff[base8 + lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            s_h[0][base8 + lane] = (unsigned)(x + carry) + s_full;
+            carry += __shfl_sync(0xffffffffu, x, 31);
+        }
+    }
+    __syncthreads();
+    for (int i = t; i < passes * kRadix; i += blockDim.x) {
+        const unsigned v = (&s_h[0][0])[i];
+        if (v) atomicAdd(tile_hist + i, v);
+    }
+}
+
 // Key emission balanced over keys: each block iteration takes kEmitBlock consecutive
 // keys and finds the pair owning every key with a load-balancing search: the pairs whose
 // keys fall in the chunk (a window of the depth-ordered offsets starting at the chunk's
@@ -155,13 +210,17 @@ __global__ void __launch_bounds__(kEmitThreads) offsets_kernel(Work w, const uns
 __global__ void __launch_bounds__(kEmitThreads) emit_kernel(Work w, const unsigned *order, int tile_passes,
                                                             unsigned *tile_hist) {
     __shared__ int s_owner[kEmitBlock];
-    __shared__ unsigned s_off[kEmitBlock];
+    __shared__ unsigned s_off[kEmitBlock + 1];
     __shared__ unsigned s_pair[kEmitBlock];
-    __shared__ unsigned s_hist[4][kRadix];
     __shared__ int s_wmax[kEmitThreads / 32];
     __shared__ unsigned s_lo, s_n;
+    __shared__ int s_diff[257];
+    __shared__ unsigned s_full;
+    __shared__ unsigned s_h[4][kRadix];
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    for (int i = t; i < 4 * kRadix; i += kEmitThreads) (&s_hist[0][0])[i] = 0u;
+    for (int i = t; i < 257; i += kEmitThreads) s_diff[i] = 0;
+    for (int i = t; i < 4 * kRadix; i += kEmitThreads) (&s_h[0][0])[i] = 0u;
+    if (t == 0) s_full = 0u;
     const unsigned K = w.hdr->keys_used;
     const unsigned P = w.L.P;
     const unsigned *off = w.offsets;
@@ -185,10 +244,11 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(Work w, const unsign
         for (int i = t; i < kEmitBlock; i += kEmitThreads) s_owner[i] = -1;
         __syncthreads();
         const unsigned plo = s_lo, np = s_n;
-        for (unsigned i = t; i < np; i += kEmitThreads) {
-            const unsigned o = off[plo + i];
-            const unsigned p = order[plo + i];
+        for (unsigned i = t; i <= np; i += kEmitThreads) {
+            const unsigned o = off[plo + i];  // plo + np <= P: off[P] = K
             s_off[i] = o;
+            if (i == np) break;
+            const unsigned p = order[plo + i];
             s_pair[i] = p < P ? p : 0u;  // in range unless a bounded wait gave up
             const unsigned first = o > k0 ? o - k0 : 0u;
             if (first < kb) s_owner[first] = (int)i;
@@ -221,9 +281,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(Work w, const unsign
         __syncthreads();
         for (unsigned r0 = 0; r0 < (unsigned)kEmitBlock; r0 += kEmitThreads) {
             const unsigned e = r0 + t;
-            const bool ok = e < kb;
-            unsigned tile = 0;
-            if (ok) {
+            if (e < kb) {
                 const int i = max(s_owner[e], 0);
                 const unsigned j = k0 + e - s_off[i];
                 const unsigned p = s_pair[i];
@@ -236,20 +294,21 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(Work w, const unsign
                 int rem = (int)j - (int)(q * wr);
                 if (rem < 0) { q--; rem += (int)wr; }
                 else if (rem >= (int)wr) { q++; rem -= (int)wr; }
-                tile = min(fr.tile_offset + (ty0 + q) * fr.tiles_x + tx0 + (unsigned)rem, w.L.tiles - 1u);
+                const unsigned tile = min(fr.tile_offset + (ty0 + q) * fr.tiles_x + tx0 + (unsigned)rem, w.L.tiles - 1u);
                 w.tkey[0][k0 + e] = tile;
                 w.tval[0][k0 + e] = p;
+                // the key starting a row run (in this chunk) counts the run's tile digits
+                if (tile_passes > 0 && (rem == 0 || e == 0)) {
+                    const unsigned pair_end = min(s_off[i + 1], k0 + kb);  // this pair's keys end here
+                    const unsigned len = min(wr - (unsigned)rem, pair_end - (k0 + e));
+                    count_tile_run(tile, len, tile_passes, s_diff, &s_full, s_h);
+                }
             }
-            const unsigned active = __ballot_sync(0xffffffffu, ok);
-            if (ok)
-                for (int ps = 0; ps < tile_passes; ps++) count_digit(s_hist[ps], (tile >> (8 * ps)) & 255u, active);
         }
     }
+    if (tile_passes == 0) return;
     __syncthreads();
-    for (int i = t; i < tile_passes * kRadix; i += kEmitThreads) {
-        unsigned v = (&s_hist[0][0])[i];
-        if (v) atomicAdd(tile_hist + i, v);
-    }
+    flush_tile_hist(tile_passes, s_diff, s_full, s_h, tile_hist);
 }
 
 __global__ void ranges_kernel(Work w, const unsigned *keys) {
@@ -299,8 +358,8 @@ cudaError_t launch_emit(const Work &w, int depth_buf, int tile_bits, int tile_hi
     const unsigned *order = w.dval[depth_buf];
     count_reduce_kernel<<<w.L.emit_blocks, kEmitThreads, 0, s>>>(w, order);
     count_scan_kernel<<<1, 1024, 0, s>>>(w);
-    offsets_kernel<<<w.L.emit_blocks, kEmitThreads, 0, s>>>(w, order);
     int passes = tile_bits <= 0 ? 0 : (tile_bits + 7) / 8;
+    offsets_kernel<<<w.L.emit_blocks, kEmitThreads, 0, s>>>(w, order);
     unsigned chunks = (w.L.key_cap + kEmitBlock - 1) / kEmitBlock;
     unsigned grid = std::max(1u, std::min(chunks, (unsigned)num_sms * 8u));
     emit_kernel<<<grid, kEmitThreads, 0, s>>>(w, order, passes, w.hist + (size_t)tile_hist_slot * kRadix);

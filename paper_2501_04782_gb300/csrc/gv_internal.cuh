@@ -26,6 +26,7 @@ constexpr float kTStop = 1e-4f;
 constexpr float kEps2d = 0.3f;
 constexpr float kZNear = 0.2f;
 constexpr float kExtK = 3.329042911529541f;          // sqrt(2 ln 255), rounded to FP32
+constexpr float kLn255 = 5.541263545158426f;         // ln 255
 
 // Device error bits (DevHeader::err).
 enum : unsigned { ERR_CAPACITY = 1u, ERR_TIMEOUT = 2u };
@@ -138,12 +139,14 @@ cudaError_t launch_setup(const Work &w, const FrameChunk &chunk, int first, int 
                          long long spin_limit, int drop_signal, cudaStream_t s);
 const void *setup_kernel_ptr();
 // project.cu
-cudaError_t launch_project_fwd(const Work &w, const GaussPtrs &g, int tile_w, int tile_h, cudaStream_t s);
+cudaError_t launch_project_fwd(const Work &w, const GaussPtrs &g, int tile_w, int tile_h, int num_sms,
+                               cudaStream_t s);
 cudaError_t launch_bin_from_screen(const Work &w, long long n, const float *u, const float *v,
                                    const float *ex, const float *ey, const float *depth,
                                    const uint8_t *valid, int tile_w, int tile_h, int32_t *counts,
                                    cudaStream_t s);
-cudaError_t launch_project_bwd(const Work &w, const GaussPtrs &g, const GradPtrs &gr, int mode, cudaStream_t s);
+cudaError_t launch_project_bwd(const Work &w, const GaussPtrs &g, const GradPtrs &gr, int mode, int num_sms,
+                               cudaStream_t s);
 // sort.cu
 int sort_passes(int bits);
 cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2], const unsigned *n_dev,

@@ -7,6 +7,8 @@
 // approximation J W Sigma W^T J^T plus a 0.3 px^2 low-pass, its inverse the conic.
 // Sec. 3.2 / Eq. 3: the mean moves with time (mu_t = mu_0 + t vel), colour and opacity
 // do not.  Both kernels are HBM-bound: one thread per pair, coalesced SoA plane reads.
+#include <algorithm>
+
 #include "gv_internal.cuh"
 
 namespace gvk {
@@ -147,35 +149,47 @@ __device__ __forceinline__ void count_depth_digits(unsigned (*s_h)[kRadix], Work
     }
 }
 
+// Grid-stride over the pairs so each block flushes its depth-digit histograms once.
 __global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, int lw, int lh) {
     __shared__ unsigned s_h[4][kRadix];
     for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0u;
     __syncthreads();
-    const unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool in = p < w.L.P;
-    unsigned key = 0xFFFFFFFFu;
-    if (in) {
-        int f = find_frame_by_pair(w.frames, (int)w.L.F, p);
-        const DevFrame &fr = w.frames[f];
-        long long gi = fr.gauss_offset + (long long)(p - fr.pair_offset);
-        PairState<float> st;
-        load_and_project(g, gi, fr, st);
-        unsigned cnt = 0, lo = 0, hi = 0;
-        float ex = 0.f, ey = 0.f;
-        if (st.valid) {
-            ex = kExtK * sqrtf(st.a);
-            ey = kExtK * sqrtf(st.c);
-            cnt = tile_rect(st.u, st.v, ex, ey, fr.W, fr.H, lw, lh, lo, hi);
+    const unsigned stride = gridDim.x * blockDim.x;
+    // every thread of a block runs the same number of rounds (the warp votes see full warps)
+    for (unsigned base = blockIdx.x * blockDim.x; base < w.L.P; base += stride) {
+        const unsigned p = base + threadIdx.x;
+        const bool in = p < w.L.P;
+        unsigned key = 0xFFFFFFFFu;
+        if (in) {
+            int f = find_frame_by_pair(w.frames, (int)w.L.F, p);
+            const DevFrame &fr = w.frames[f];
+            long long gi = fr.gauss_offset + (long long)(p - fr.pair_offset);
+            PairState<float> st;
+            load_and_project(g, gi, fr, st);
+            unsigned cnt = 0, lo = 0, hi = 0;
+            // alpha >= 1/255 needs d^T conic d <= tau = 2 ln(255 o); the box of that ellipse
+            const float tau = fminf(2.f * (kLn255 + logf(st.o)), kExtK * kExtK);
+            if (st.valid && tau > 0.f) {
+                const float ex = sqrtf(tau * st.a), ey = sqrtf(tau * st.c);
+                cnt = tile_rect(st.u, st.v, ex, ey, fr.W, fr.H, lw, lh, lo, hi);
+            }
+            const long long N = g.N;
+            w.feat0[p] = make_float4(st.u, st.v, -0.5f * kLog2e * st.A, -kLog2e * st.B);
+            w.feat1[p] = make_float4(-0.5f * kLog2e * st.C, log2f(st.o), g.rgb[gi], g.rgb[N + gi]);
+            w.feat2[p] = g.rgb[2 * N + gi];
+            w.rect[p] = make_uint4(lo, hi, cnt, (unsigned)f);
+            key = cnt ? __float_as_uint(st.zc) : 0xFFFFFFFFu;
+            w.dkey[0][p] = key;
         }
-        const long long N = g.N;
-        w.feat0[p] = make_float4(st.u, st.v, -0.5f * kLog2e * st.A, -kLog2e * st.B);
-        w.feat1[p] = make_float4(-0.5f * kLog2e * st.C, log2f(st.o), g.rgb[gi], g.rgb[N + gi]);
-        w.feat2[p] = g.rgb[2 * N + gi];
-        w.rect[p] = make_uint4(lo, hi, cnt, (unsigned)f);
-        key = cnt ? __float_as_uint(st.zc) : 0xFFFFFFFFu;
-        w.dkey[0][p] = key;
+        const unsigned active = __ballot_sync(0xffffffffu, in);
+        if (in)
+            for (int ps = 0; ps < 4; ps++) count_digit(s_h[ps], (key >> (8 * ps)) & 255u, active);
     }
-    count_depth_digits(s_h, w, key, in);  // every thread of the block reaches this call
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) {
+        const unsigned c = (&s_h[0][0])[i];
+        if (c) atomicAdd(w.hist + i, c);
+    }
 }
 
 // Stage-isolated binning: screen-space inputs of one frame given by the caller.
@@ -391,10 +405,12 @@ __global__ void __launch_bounds__(128) project_bwd_fp64_kernel(Work w, GaussPtrs
 
 }  // namespace
 
-cudaError_t launch_project_fwd(const Work &w, const GaussPtrs &g, int tile_w, int tile_h, cudaStream_t s) {
+cudaError_t launch_project_fwd(const Work &w, const GaussPtrs &g, int tile_w, int tile_h, int num_sms,
+                               cudaStream_t s) {
     if (w.L.P == 0) return cudaSuccess;
     int lw = __builtin_ctz(tile_w), lh = __builtin_ctz(tile_h);
-    project_fwd_kernel<<<(w.L.P + 255) / 256, 256, 0, s>>>(w, g, lw, lh);
+    unsigned blocks = std::min((w.L.P + 255u) / 256u, (unsigned)num_sms * 8u);
+    project_fwd_kernel<<<blocks, 256, 0, s>>>(w, g, lw, lh);
     return cudaGetLastError();
 }
 
@@ -409,7 +425,8 @@ cudaError_t launch_bin_from_screen(const Work &w, long long n, const float *u, c
     return cudaGetLastError();
 }
 
-cudaError_t launch_project_bwd(const Work &w, const GaussPtrs &g, const GradPtrs &gr, int mode, cudaStream_t s) {
+cudaError_t launch_project_bwd(const Work &w, const GaussPtrs &g, const GradPtrs &gr, int mode, int num_sms,
+                               cudaStream_t s) {
     if (w.L.P == 0) return cudaSuccess;
     if (mode == 1) {
         // all frames share one set; its size is the first frame's count
@@ -420,7 +437,7 @@ cudaError_t launch_project_bwd(const Work &w, const GaussPtrs &g, const GradPtrs
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    project_bwd_fp64_kernel<<<64, 128, 0, s>>>(w, g, gr);
+    project_bwd_fp64_kernel<<<num_sms * 2, 128, 0, s>>>(w, g, gr);
     return cudaGetLastError();
 }
 

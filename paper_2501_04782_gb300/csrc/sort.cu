@@ -99,7 +99,7 @@ struct PassArgs {
 };
 
 template <int ITEMS>
-__global__ void __launch_bounds__(kSortThreads) sort_pass_kernel(PassArgs a) {
+__global__ void __launch_bounds__(kSortThreads, ITEMS > 8 ? 3 : 4) sort_pass_kernel(PassArgs a) {
     constexpr int TILE = kSortThreads * ITEMS;
     __shared__ unsigned s_keys[TILE];
     __shared__ unsigned s_vals[TILE];
@@ -245,7 +245,7 @@ cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2
         if (e != cudaSuccess) return e;
     }
     const bool small = sort_items(n_cap) == 4;
-    const int per_sm = small ? 4 : 2;  // resident blocks per SM (registers)
+    const int per_sm = small ? 4 : 3;  // resident blocks per SM (launch bounds)
     int grid = (int)std::min<unsigned>(max_tiles, (unsigned)num_sms * per_sm);
     int cur = 0;
     for (int ps = 0; ps < passes; ps++) {

@@ -54,8 +54,9 @@ def test_covariance_is_RS_RS_T_and_ewa_matches_numerical_jacobian():
         assert np.allclose([pr["u"][0], pr["v"][0]], pi(xc), rtol=1e-12)
         assert pr["depth"][0] == pytest.approx(xc[2], rel=1e-14)
         assert pr["o"][0] == pytest.approx(0.5)
-        k = math.sqrt(2 * math.log(255))
-        assert pr["ex"][0] == pytest.approx(k * math.sqrt(S2[0, 0]), rel=1e-7)
+        tau = 2 * math.log(255 * 0.5)  # alpha >= 1/255 region of an o = 0.5 Gaussian
+        assert pr["ex"][0] == pytest.approx(math.sqrt(tau * S2[0, 0]), rel=1e-7)
+        assert pr["ey"][0] == pytest.approx(math.sqrt(tau * S2[1, 1]), rel=1e-7)
 
 
 def test_analytic_footprint_single_isotropic_gaussian():
@@ -233,3 +234,19 @@ def test_clamp_flag_marks_gradient_only_ambiguity():
     assert r["amb"][0] == 8
     assert r["rgb"][0, 0] == pytest.approx(0.99, rel=1e-9)
     assert r["amb"][1] == 0  # one pixel further: alpha ~ 0.37, far from every threshold
+
+
+def test_extent_box_bounds_the_alpha_region_tightly():
+    """The extents are the exact axis-aligned bound of the alpha >= 1/255 region: a pixel
+    just inside the box along the Gaussian's row has alpha >= 1/255 only up to the extent,
+    and an opacity below 1/255 gives no extent."""
+    cam = synth.Camera(400, 50, 100.0, 100.0, 200.5, 25.5)  # mean projects to the centre of pixel (200, 25)
+    for logit in (-1.5, 0.0, 3.0):
+        g = one_gaussian((0, 0, 4.0), [math.log(0.3)] * 3, logit=logit)
+        pr = oracle.project(g, cam)
+        ex = pr["ex"][0]
+        # along the row through the centre alpha = o exp(-dx^2 / (2 a)): alpha(ex) = 1/255 exactly
+        o, a = pr["o"][0], pr["a"][0]
+        assert o * math.exp(-0.5 * ex * ex / a) == pytest.approx(1 / 255, rel=1e-10)
+    g = one_gaussian((0, 0, 4.0), [math.log(0.3)] * 3, logit=-6.0)  # o < 1/255
+    assert oracle.project(g, cam)["ex"][0] == 0.0
