@@ -130,23 +130,37 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_fwd_kernel(Work w, const
                 s_c[i] = w.feat2[p];
             }
             __syncthreads();
-            for (int j = 0; j < n && !(done0 && done1); j++) {
-                const float4 f0 = s_a[j], f1 = s_b[j];
-                float dx;
-                float2 dy;
-                const float2 e = splat_exponent2(f0, f1, px, npy, dx, dy);
-                float a0 = fminf(ex2_approx(e.x), kAlphaMax), a1 = fminf(ex2_approx(e.y), kAlphaMax);
-                // a pixel that is done, or below the cutoff, takes alpha 0: T and colour unchanged
-                a0 = (done0 || a0 < kAlphaMin) ? 0.f : a0;
-                a1 = (done1 || a1 < kAlphaMin) ? 0.f : a1;
-                const float2 wg = __fmul2_rn(make_float2(a0, a1), T);
-                cr = __ffma2_rn(dup2(f1.z), wg, cr);
-                cg = __ffma2_rn(dup2(f1.w), wg, cg);
-                cb = __ffma2_rn(dup2(s_c[j]), wg, cb);
-                T = __fmul2_rn(T, __fadd2_rn(make_float2(1.f, 1.f), make_float2(-a0, -a1)));
-                const int pos = (int)(start + j);
-                if (a0 > 0.f) { last0 = pos; done0 = T.x < kTStop; }
-                if (a1 > 0.f) { last1 = pos; done1 = T.y < kTStop; }
+            // two staged Gaussians per round: their exponents are independent of the pixel
+            // state, so both are evaluated before the two (sequential) compositing updates
+            for (int j = 0; j < n; j += 2) {
+                if (!__any_sync(0xffffffffu, !(done0 && done1))) break;
+                const bool two = j + 1 < n;
+                const float4 fa0 = s_a[j], fa1 = s_b[j];
+                const float4 fb0 = s_a[two ? j + 1 : j], fb1 = s_b[two ? j + 1 : j];
+                float dxa, dxb;
+                float2 dya, dyb;
+                const float2 ea = splat_exponent2(fa0, fa1, px, npy, dxa, dya);
+                const float2 eb = splat_exponent2(fb0, fb1, px, npy, dxb, dyb);
+                const float2 ra = make_float2(fminf(ex2_approx(ea.x), kAlphaMax), fminf(ex2_approx(ea.y), kAlphaMax));
+                const float2 rb = make_float2(fminf(ex2_approx(eb.x), kAlphaMax), fminf(ex2_approx(eb.y), kAlphaMax));
+#pragma unroll
+                for (int k = 0; k < 2; k++) {
+                    if (k == 1 && !two) break;
+                    const float2 rr = k ? rb : ra;
+                    const float4 f1 = k ? fb1 : fa1;
+                    // a pixel that is done, or below the cutoff, takes alpha 0: T and colour unchanged
+                    const float a0 = (done0 || rr.x < kAlphaMin) ? 0.f : rr.x;
+                    const float a1 = (done1 || rr.y < kAlphaMin) ? 0.f : rr.y;
+                    if (!__any_sync(0xffffffffu, a0 > 0.f || a1 > 0.f)) continue;  // no lane composites it
+                    const float2 wg = __fmul2_rn(make_float2(a0, a1), T);
+                    cr = __ffma2_rn(dup2(f1.z), wg, cr);
+                    cg = __ffma2_rn(dup2(f1.w), wg, cg);
+                    cb = __ffma2_rn(dup2(s_c[j + k]), wg, cb);
+                    T = __fmul2_rn(T, __fadd2_rn(make_float2(1.f, 1.f), make_float2(-a0, -a1)));
+                    const int pos = (int)(start + j + k);
+                    if (a0 > 0.f) { last0 = pos; done0 = T.x < kTStop; }
+                    if (a1 > 0.f) { last1 = pos; done1 = T.y < kTStop; }
+                }
             }
         }
         // evaluated entries: up to the stop, or the whole list (composited pairs are
