@@ -120,7 +120,11 @@ typedef struct {
 /* ---- context ---------------------------------------------------------------------- */
 
 /* Create a context bound to the current CUDA device.  opt may be NULL (16x16 tiles,
- * 256 Gaussians per stage, black background).  *ctx is a host object. */
+ * 256 Gaussians per stage, black background).  *ctx is a host object; it owns one
+ * non-blocking CUDA stream and two events on that device, with which a backward call runs
+ * its FP64 chain-rule kernel beside the FP32 one (forked from and joined back into the
+ * call's stream, so the call stays stream-ordered and capturable).  A context is not
+ * thread-safe: one call at a time. */
 GV_API gv_status gv_create(gv_ctx **ctx, const gv_options *opt);
 GV_API gv_status gv_destroy(gv_ctx *ctx);
 GV_API gv_status gv_get_options(const gv_ctx *ctx, gv_options *opt);
@@ -172,10 +176,11 @@ GV_API gv_status gv_read_status(gv_ctx *ctx, const void *workspace, size_t ws_by
                          int64_t *keys_needed);
 
 /* Synchronise `stream` and read the work counters of the last forward / backward on this
- * workspace (HOST out[6]): keys emitted, (frame, Gaussian) pairs, (pixel, Gaussian) pairs
- * the forward evaluated and of those composited (alpha >= 1/255), pairs the backward
- * evaluated and of those replayed.  "Evaluated" counts, per pixel, the list entries up
- * to the pixel's stop (the algorithmic work of compositing). */
+ * workspace (HOST out[6]): [0] keys emitted, [1] (frame, Gaussian) pairs, [2] (pixel,
+ * Gaussian) pairs the forward evaluated, [3] always 0 (the forward does not count the pairs
+ * it composites: they are exactly the pairs the backward replays, [5]), [4] pairs the
+ * backward evaluated, [5] of those the pairs replayed (alpha >= 1/255).  "Evaluated" counts,
+ * per pixel, the list entries up to the pixel's stop (the algorithmic work of compositing). */
 GV_API gv_status gv_read_counters(gv_ctx *ctx, const void *workspace, gv_stream stream, int64_t *out);
 
 /* ---- loss and optimiser (Sec. 4.1) ------------------------------------------------ */

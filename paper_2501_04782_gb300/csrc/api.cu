@@ -30,6 +30,10 @@ struct gv_ctx {
     cudaEvent_t ev[GV_NUM_STAGES][2] = {};
     bool ev_used[GV_NUM_STAGES] = {};
     int launches[GV_NUM_STAGES] = {};
+    // side stream of the backward: the FP64 chain rule of flagged pairs runs beside the
+    // FP32 pass (fork and join by events; also valid inside a stream capture)
+    cudaStream_t side = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
 };
 
 namespace {
@@ -341,7 +345,20 @@ gv_status backward_stages(gv_ctx *ctx, const gv_gaussians *g, const Plan &pl, co
     gp.quat = grad->quat; gp.logit = grad->opacity_logit; gp.rgb = grad->rgb;
     {
         StageTimer tm(ctx, GV_STAGE_PROJECT_BWD, s, 2);
-        GV_CUDA(launch_project_bwd(w, gauss_ptrs(g), gp, pl.bwd_mode, ctx->num_sms, s));
+        const GaussPtrs gptr = gauss_ptrs(g);
+        int dev = -1;
+        GV_CUDA(cudaGetDevice(&dev));
+        if (dev == ctx->device) {  // the side stream belongs to the context's device
+            GV_CUDA(cudaEventRecord(ctx->fork, s));
+            GV_CUDA(cudaStreamWaitEvent(ctx->side, ctx->fork, 0));
+            GV_CUDA(launch_project_bwd_fp64(w, gptr, gp, ctx->num_sms, ctx->side));
+            GV_CUDA(cudaEventRecord(ctx->join, ctx->side));
+            GV_CUDA(launch_project_bwd(w, gptr, gp, pl.bwd_mode, ctx->num_sms, s));
+            GV_CUDA(cudaStreamWaitEvent(s, ctx->join, 0));
+        } else {
+            GV_CUDA(launch_project_bwd(w, gptr, gp, pl.bwd_mode, ctx->num_sms, s));
+            GV_CUDA(launch_project_bwd_fp64(w, gptr, gp, ctx->num_sms, s));
+        }
     }
     return GV_OK;
 }
@@ -438,6 +455,13 @@ gv_status gv_create(gv_ctx **out, const gv_options *opt) {
         delete c;
         return GV_ERR_CUDA;
     }
+    if (cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        gv_destroy(c);
+        return GV_ERR_CUDA;
+    }
     *out = c;
     return GV_OK;
 }
@@ -447,6 +471,9 @@ gv_status gv_destroy(gv_ctx *ctx) {
     for (int i = 0; i < GV_NUM_STAGES; i++)
         for (int j = 0; j < 2; j++)
             if (ctx->ev[i][j]) cudaEventDestroy(ctx->ev[i][j]);
+    if (ctx->fork) cudaEventDestroy(ctx->fork);
+    if (ctx->join) cudaEventDestroy(ctx->join);
+    if (ctx->side) cudaStreamDestroy(ctx->side);
     delete ctx;
     return GV_OK;
 }

@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(Work w, const unsign
                 const unsigned j = k0 + e - s_off[i];
                 const unsigned p = s_pair[i];
                 const uint4 r = w.rect[p];  // consecutive keys mostly share a pair: L1 hits
-                const DevFrame &fr = w.frames[min(r.w, w.L.F - 1u)];
+                const DevFrame &fr = w.frames[min(r.w & kRectFrame, w.L.F - 1u)];
                 const unsigned tx0 = r.x & 0xFFFFu, ty0 = r.x >> 16, tx1 = r.y & 0xFFFFu;
                 const unsigned wr = tx1 - tx0 + 1u;
                 // j / wr through the FP32 reciprocal, corrected to the exact quotient (j < 2^24)
@@ -311,13 +311,40 @@ __global__ void __launch_bounds__(kEmitThreads) emit_kernel(Work w, const unsign
     flush_tile_hist(tile_passes, s_diff, s_full, s_h, tile_hist);
 }
 
-__global__ void ranges_kernel(Work w, const unsigned *keys) {
+// Per-tile [start, end) of the sorted keys.  A warp takes 32 * kRangeItems consecutive keys
+// per round (lane l holds keys l, l + 32, ...: independent coalesced loads in flight) and
+// gets each key's neighbours by shuffles; only the round's two outer neighbours are loaded.
+constexpr int kRangeItems = 8;
+
+__global__ void __launch_bounds__(256) ranges_kernel(Work w, const unsigned *keys) {
     const unsigned n = w.hdr->keys_used;
-    for (unsigned k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        unsigned t = keys[k];
-        if (t >= w.L.tiles) continue;  // only after a bounded wait gave up
-        if (k == 0 || keys[k - 1] != t) w.ranges[t].x = k;
-        if (k == n - 1 || keys[k + 1] != t) w.ranges[t].y = k + 1;
+    const int lane = threadIdx.x & 31;
+    const unsigned warps = gridDim.x * (blockDim.x >> 5);
+    const unsigned span = 32u * kRangeItems;
+    for (unsigned base = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * span; base < n;
+         base += warps * span) {
+        unsigned k[kRangeItems];
+#pragma unroll
+        for (int j = 0; j < kRangeItems; j++) {
+            const unsigned i = base + 32u * j + lane;
+            k[j] = i < n ? keys[i] : 0xFFFFFFFFu;
+        }
+        const unsigned before = base > 0 ? keys[base - 1] : 0xFFFFFFFFu;  // same address for all lanes
+        const unsigned after = base + span < n ? keys[base + span] : 0xFFFFFFFFu;
+#pragma unroll
+        for (int j = 0; j < kRangeItems; j++) {
+            const unsigned i = base + 32u * j + lane;
+            unsigned prev = __shfl_up_sync(0xffffffffu, k[j], 1);
+            const unsigned prev_row = __shfl_sync(0xffffffffu, j > 0 ? k[j > 0 ? j - 1 : 0] : before, 31);
+            if (lane == 0) prev = j > 0 ? prev_row : before;
+            unsigned next = __shfl_down_sync(0xffffffffu, k[j], 1);
+            const unsigned next_row = __shfl_sync(0xffffffffu, j + 1 < kRangeItems ? k[j + 1 < kRangeItems ? j + 1 : j] : after, 0);
+            if (lane == 31) next = j + 1 < kRangeItems ? next_row : after;
+            const unsigned t = k[j];
+            if (i >= n || t >= w.L.tiles) continue;  // tile ids are in range unless a wait gave up
+            if (i == 0 || prev != t) w.ranges[t].x = i;
+            if (i == n - 1 || next != t) w.ranges[t].y = i + 1;
+        }
     }
 }
 
@@ -367,7 +394,7 @@ cudaError_t launch_emit(const Work &w, int depth_buf, int tile_bits, int tile_hi
 }
 
 cudaError_t launch_ranges(const Work &w, int tile_buf, int num_sms, cudaStream_t s) {
-    ranges_kernel<<<num_sms * 4, 256, 0, s>>>(w, w.tkey[tile_buf]);
+    ranges_kernel<<<num_sms * 8, 256, 0, s>>>(w, w.tkey[tile_buf]);
     return cudaGetLastError();
 }
 

@@ -57,12 +57,17 @@ struct DevHeader {
     int drop_signal;                // test hook: first look-back block never publishes
     int pad;
     unsigned long long work[4];     // pairs evaluated / composited: fwd 0-1, bwd 2-3
-    unsigned fp64_count;            // ill-conditioned pairs deferred to the FP64 chain rule
-    unsigned fp64_done;             // blocks of the FP64 pass finished (last one resets)
+    unsigned fp64_count;            // ill-conditioned pairs listed by the projection (FP64 chain rule)
+    unsigned pad1;
 };
 
 // Radix sort geometry (one onesweep pass = one 8-bit digit).  Small sorts use 1024-key
 // block tiles (more blocks in flight), large ones 3840-key tiles (fewer look-back steps).
+// rect.w of a pair: frame index, bit 31 set when the backward runs its geometric chain
+// rule in FP64 (ill-conditioned footprint)
+constexpr unsigned kRectFp64 = 1u << 31;
+constexpr unsigned kRectFrame = kRectFp64 - 1u;
+
 constexpr int kSortThreads = 256;
 constexpr int kRadix = 256;
 constexpr unsigned kSortSmallN = 1u << 20;
@@ -147,6 +152,9 @@ cudaError_t launch_bin_from_screen(const Work &w, long long n, const float *u, c
                                    cudaStream_t s);
 cudaError_t launch_project_bwd(const Work &w, const GaussPtrs &g, const GradPtrs &gr, int mode, int num_sms,
                                cudaStream_t s);
+// FP64 chain rule of the pairs the projection flagged (may run concurrently with the above)
+cudaError_t launch_project_bwd_fp64(const Work &w, const GaussPtrs &g, const GradPtrs &gr, int num_sms,
+                                    cudaStream_t s);
 // sort.cu
 int sort_passes(int bits);
 cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2], const unsigned *n_dev,

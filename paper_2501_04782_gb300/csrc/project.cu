@@ -149,6 +149,19 @@ __device__ __forceinline__ void count_depth_digits(unsigned (*s_h)[kRadix], Work
     }
 }
 
+// Ill-conditioned pairs: when Sigma2 is close to singular (a c / det > 64, a Gaussian
+// stretched by the perspective, typically near the camera and far off axis) the FP32
+// inverse and -Q G Q lose digits.  The projection lists such pairs (and flags them in
+// rect.w); the backward skips their geometric chain rule in FP32 and a small FP64 kernel
+// redoes it, concurrently with the FP32 pass (keeping FP64 registers out of the common
+// FP32 kernel).
+constexpr float kFp64Condition = 64.f;
+
+__device__ __forceinline__ bool ill_conditioned(const PairState<float> &st) {
+    const float det = st.a * st.c - st.b * st.b;
+    return st.a * st.c > kFp64Condition * det;
+}
+
 // Grid-stride over the pairs so each block flushes its depth-digit histograms once.
 __global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, int lw, int lh) {
     __shared__ unsigned s_h[4][kRadix];
@@ -177,7 +190,12 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, i
             w.feat0[p] = make_float4(st.u, st.v, -0.5f * kLog2e * st.A, -kLog2e * st.B);
             w.feat1[p] = make_float4(-0.5f * kLog2e * st.C, log2f(st.o), g.rgb[gi], g.rgb[N + gi]);
             w.feat2[p] = g.rgb[2 * N + gi];
-            w.rect[p] = make_uint4(lo, hi, cnt, (unsigned)f);
+            unsigned fw = (unsigned)f;
+            if (cnt && ill_conditioned(st)) {  // only binned pairs get a gradient
+                w.fp64_list[atomicAdd(&w.hdr->fp64_count, 1u)] = p;
+                fw |= kRectFp64;
+            }
+            w.rect[p] = make_uint4(lo, hi, cnt, fw);
             key = cnt ? __float_as_uint(st.zc) : 0xFFFFFFFFu;
             w.dkey[0][p] = key;
         }
@@ -296,37 +314,29 @@ __device__ __forceinline__ void geometry_backward(const PairState<F> &st, const 
     acc[12] += (float)((dz - z * dot) * st.inv_qn);
 }
 
-// Ill-conditioned pairs: when Sigma2 is close to singular (a c / det > 64, a Gaussian
-// stretched by the perspective, typically near the camera and far off axis) the FP32
-// inverse and -Q G Q lose digits.  Such pairs are listed and their geometric chain rule
-// is redone in FP64 by a second, small kernel (keeping the FP64 registers out of the
-// common FP32 kernel).
-constexpr float kFp64Condition = 64.f;
-
 // Chain rule of one pair: screen-space gradient to the raw-parameter gradients, added
 // into acc[17] (mean 3, vel 3, log_scale 3, quat 4, logit 1, rgb 3).  The compositing
 // backward accumulates (du, dv, da', db', dc', dlog2o, dr, dg, db) for the staged record
 // (a', b', c') = -log2(e) (A/2, B, C/2) and log2 o; converted here to the conic and opacity.
-// Returns false when the geometric part was deferred to the FP64 pass.
-__device__ __forceinline__ void pair_backward(const PairState<float> &st, const Work &w, unsigned p,
-                                              const DevFrame &fr, float4 g0, float4 g1, float g2, float acc[17]) {
+// The geometric part of a pair the projection listed as ill-conditioned is left to the
+// FP64 kernel.
+__device__ __forceinline__ void pair_backward(const PairState<float> &st, bool deferred, const DevFrame &fr,
+                                              float4 g0, float4 g1, float g2, float acc[17]) {
     acc[14] += g1.z;
     acc[15] += g1.w;
     acc[16] += g2;
     // d log2(o) / d logit = (1 - o) / ln 2
     acc[13] += g1.y * (1.f - st.o) * kLog2e;
-    if (!st.valid) return;
-    const float det = st.a * st.c - st.b * st.b;
-    if (st.a * st.c > kFp64Condition * det) {
-        w.fp64_list[atomicAdd(&w.hdr->fp64_count, 1u)] = p;
-        return;
-    }
+    if (!st.valid || deferred) return;
     const float dA = -0.5f * kLog2e * g0.z, dB = -kLog2e * g0.w, dC = -0.5f * kLog2e * g1.x;
     geometry_backward<float>(st, fr, g0.x, g0.y, dA, dB, dC, acc);
 }
 
+// Adds acc into the gradient planes: rows [0, 13) (geometry) atomically when geo_atomic
+// (the FP64 kernel may add into them concurrently), or left alone when skip_geo; rows
+// [13, 17) (opacity, colour) atomically when atomic.
 __device__ __forceinline__ void store_grad(const GradPtrs &gr, long long N, long long gi, const float acc[17],
-                                           bool atomic) {
+                                           bool atomic, bool geo_atomic = false, bool skip_geo = false) {
     float *rows[17] = {gr.mean, gr.mean + N, gr.mean + 2 * N,
                        gr.vel, gr.vel ? gr.vel + N : nullptr, gr.vel ? gr.vel + 2 * N : nullptr,
                        gr.log_scale, gr.log_scale + N, gr.log_scale + 2 * N,
@@ -334,8 +344,8 @@ __device__ __forceinline__ void store_grad(const GradPtrs &gr, long long N, long
                        gr.logit, gr.rgb, gr.rgb + N, gr.rgb + 2 * N};
 #pragma unroll
     for (int k = 0; k < 17; k++) {
-        if (!rows[k]) continue;
-        if (atomic) atomicAdd(rows[k] + gi, acc[k]);
+        if (!rows[k] || (k < 13 && skip_geo)) continue;
+        if (atomic || (k < 13 && geo_atomic)) atomicAdd(rows[k] + gi, acc[k]);
         else rows[k][gi] += acc[k];
     }
 }
@@ -353,8 +363,9 @@ __global__ void __launch_bounds__(128) project_bwd_pairs_kernel(Work w, GaussPtr
     float acc[17];
 #pragma unroll
     for (int k = 0; k < 17; k++) acc[k] = 0.f;
-    pair_backward(st, w, p, fr, w.g0[p], w.g1[p], w.g2[p], acc);
-    store_grad(gr, g.N, gi, acc, atomic != 0);
+    const bool deferred = (w.rect[p].w & kRectFp64) != 0u;
+    pair_backward(st, deferred, fr, w.g0[p], w.g1[p], w.g2[p], acc);
+    store_grad(gr, g.N, gi, acc, atomic != 0, false, deferred);
 }
 
 // mode 1: one shared Gaussian set; one thread per Gaussian sums over all frames.
@@ -366,20 +377,25 @@ __global__ void __launch_bounds__(128) project_bwd_shared_kernel(Work w, GaussPt
     float acc[17];
 #pragma unroll
     for (int k = 0; k < 17; k++) acc[k] = 0.f;
+    bool any_deferred = false;
     for (int f = 0; f < (int)w.L.F; f++) {
         const DevFrame &fr = w.frames[f];
         unsigned p = fr.pair_offset + j;
         PairState<float> st;
         load_and_project(g, gi, fr, st);
-        pair_backward(st, w, p, fr, w.g0[p], w.g1[p], w.g2[p], acc);
+        const bool deferred = (w.rect[p].w & kRectFp64) != 0u;
+        any_deferred |= deferred;
+        pair_backward(st, deferred, fr, w.g0[p], w.g1[p], w.g2[p], acc);
     }
-    store_grad(gr, g.N, gi, acc, false);
+    store_grad(gr, g.N, gi, acc, false, any_deferred);
 }
 
-// FP64 geometric chain rule of the listed ill-conditioned pairs; atomic because several
-// frames of a shared set may list the same Gaussian.  The last block resets the list.
+// FP64 geometric chain rule of the pairs the projection listed as ill-conditioned; atomic
+// because several frames of a shared set may list the same Gaussian, and because the FP32
+// pass runs concurrently.  The list lives until the next forward's setup clears it, so a
+// backward can be repeated.
 __global__ void __launch_bounds__(128) project_bwd_fp64_kernel(Work w, GaussPtrs g, GradPtrs gr) {
-    const unsigned n = w.hdr->fp64_count;
+    const unsigned n = min(w.hdr->fp64_count, w.L.P);
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const unsigned p = min(w.fp64_list[i], w.L.P - 1u);
         const DevFrame &fr = w.frames[find_frame_by_pair(w.frames, (int)w.L.F, p)];
@@ -395,11 +411,6 @@ __global__ void __launch_bounds__(128) project_bwd_fp64_kernel(Work w, GaussPtrs
                                   -(double)kLog2e * g0.w, -0.5 * (double)kLog2e * g1.x, acc);
         acc[13] = acc[14] = acc[15] = acc[16] = 0.f;  // colour and opacity were done in FP32
         store_grad(gr, g.N, gi, acc, true);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && atomicAdd(&w.hdr->fp64_done, 1u) == gridDim.x - 1) {
-        w.hdr->fp64_count = 0u;
-        w.hdr->fp64_done = 0u;
     }
 }
 
@@ -435,9 +446,13 @@ cudaError_t launch_project_bwd(const Work &w, const GaussPtrs &g, const GradPtrs
     } else {
         project_bwd_pairs_kernel<<<(w.L.P + 127) / 128, 128, 0, s>>>(w, g, gr, mode == 2 ? 1 : 0);
     }
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    project_bwd_fp64_kernel<<<num_sms * 2, 128, 0, s>>>(w, g, gr);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project_bwd_fp64(const Work &w, const GaussPtrs &g, const GradPtrs &gr, int num_sms,
+                                    cudaStream_t s) {
+    if (w.L.P == 0) return cudaSuccess;
+    project_bwd_fp64_kernel<<<num_sms, 128, 0, s>>>(w, g, gr);
     return cudaGetLastError();
 }
 
