@@ -115,7 +115,12 @@ def lib():
                                      _dp, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
         L.orc_bin_f32.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 5 + [ctypes.c_int32] * 4 + [ctypes.c_void_p] * 2
         L.orc_bin_f64.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 5 + [ctypes.c_int32] * 4 + [ctypes.c_void_p] * 3
-        for f in (L.orc_project, L.orc_render, L.orc_render_bwd, L.orc_bin_f32, L.orc_bin_f64):
+        L.orc_cull_f32.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 7 + [ctypes.c_int32] * 4 + [ctypes.c_void_p] * 3
+        L.orc_emit_cull_f32.argtypes = ([ctypes.c_int64] + [ctypes.c_void_p] * 7 + [ctypes.c_int32] * 4 +
+                                        [ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_int64])
+        L.orc_emit_cull_f32.restype = ctypes.c_int64
+        for f in (L.orc_project, L.orc_render, L.orc_render_bwd, L.orc_bin_f32, L.orc_bin_f64, L.orc_cull_f32):
             f.restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -272,6 +277,48 @@ def bin_f64(u, v, ex, ey, valid, W: int, H: int, TW: int, TH: int):
     lib().orc_bin_f64(n, u.ctypes.data, v.ctypes.data, ex.ctypes.data, ey.ctypes.data, valid.ctypes.data,
                       W, H, TW, TH, count.ctypes.data, rect.ctypes.data, margin.ctypes.data)
     return count, rect, margin
+
+
+def _f32(*arrs):
+    return [np.ascontiguousarray(a, np.float32) for a in arrs]
+
+
+def cull_f32(u, v, sxx, sxy, syy, tau, valid, W: int, H: int, TW: int, TH: int):
+    """Culled FP32 binning rule: the tiles of the extent box whose band of pixel-centre rows
+    reaches the alpha >= 1/255 ellipse d^T Sigma2^{-1} d <= tau (Sigma2 = [[sxx, sxy],
+    [sxy, syy]]).  Returns count [n] (kept tiles), rect [n,4] (tile rectangle of the extent
+    box) and cells [n] (its area)."""
+    u, v, sxx, sxy, syy, tau = _f32(u, v, sxx, sxy, syy, tau)
+    valid = np.ascontiguousarray(valid, np.uint8)
+    n = u.shape[0]
+    count = np.zeros(n, np.int32)
+    cells = np.zeros(n, np.int32)
+    rect = np.zeros((n, 4), np.int32)
+    lib().orc_cull_f32(n, u.ctypes.data, v.ctypes.data, sxx.ctypes.data, sxy.ctypes.data, syy.ctypes.data,
+                       tau.ctypes.data, valid.ctypes.data, W, H, TW, TH, count.ctypes.data, rect.ctypes.data,
+                       cells.ctypes.data)
+    return count, rect, cells
+
+
+def emit_cull_keys(u, v, sxx, sxy, syy, tau, valid, W: int, H: int, TW: int, TH: int, depth_f32, order=None,
+                   tile_offset: int = 0):
+    """Keys of the culled rule in `order` (default: Gaussian order), each Gaussian's kept
+    tiles row-major: key = tile << 32 | bits(depth), value = Gaussian index."""
+    u, v, sxx, sxy, syy, tau = _f32(u, v, sxx, sxy, syy, tau)
+    valid = np.ascontiguousarray(valid, np.uint8)
+    n = u.shape[0]
+    order = np.arange(n, dtype=np.int64) if order is None else np.ascontiguousarray(order, np.int64)
+    count, _, _ = cull_f32(u, v, sxx, sxy, syy, tau, valid, W, H, TW, TH)
+    cap = int(count.sum())
+    tiles = np.zeros(max(cap, 1), np.uint32)
+    ids = np.zeros(max(cap, 1), np.int64)
+    k = lib().orc_emit_cull_f32(n, u.ctypes.data, v.ctypes.data, sxx.ctypes.data, sxy.ctypes.data, syy.ctypes.data,
+                                tau.ctypes.data, valid.ctypes.data, W, H, TW, TH, tile_offset, order.ctypes.data,
+                                len(order), tiles.ctypes.data, ids.ctypes.data, cap)
+    assert 0 <= k <= cap
+    depth_bits = np.ascontiguousarray(depth_f32, np.float32).view(np.uint32).astype(np.uint64)
+    keys = (tiles[:k].astype(np.uint64) << np.uint64(32)) | depth_bits[ids[:k]]
+    return keys, ids[:k]
 
 
 def emit_keys(count, rect, depth_f32, tiles_x: int, tile_offset: int = 0, ids=None):

@@ -676,3 +676,125 @@ int orc_bin_f64(int64_t n, const double *u, const double *v, const double *ex, c
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------------------ */
+/* Culled binning (FP32): the tiles of the extent box whose pixel-centre band can reach  */
+/* the alpha >= 1/255 ellipse.                                                          */
+/* ------------------------------------------------------------------------------------ */
+
+/* The alpha >= 1/255 region of a Gaussian is the ellipse d^T Sigma2^{-1} d <= tau,
+ * Sigma2 = [[a, b], [b, c]].  Cut by a horizontal line at offset dy from the centre it is
+ * the segment dx in (b/c) dy +- sqrt((tau c - dy^2) det) / c, det = a c - b^2.  Over a band
+ * dy in [d0, d1] (the pixel-centre rows of one tile row, clipped to the extent box) the
+ * right end is largest at dy = clamp(b sqrt(tau / a), d0, d1) (the height of the ellipse's
+ * rightmost point) and the left end smallest at clamp(-b sqrt(tau / a), d0, d1): the
+ * band's pixel columns are those whose centres fall between the two ends, and a tile of
+ * the row is kept when it holds one of them.  This is a superset of the tiles holding a
+ * pixel centre inside the ellipse (the band is continuous).  Per Gaussian the rule uses
+ * kx = b / c, ds = b ex / a (= b sqrt(tau / a) with ex = sqrt(tau a)), tc = tau c and
+ * dn = det / c^2, every operation rounded to FP32 (-ffp-contract=off); a near-singular
+ * footprint (a c > 64 det, where det has lost its digits; also a or c not positive) keeps
+ * the whole extent box. */
+typedef struct {
+    float u, v, kx, ds, tc, dn;
+    int32_t x0, y0, x1, y1; /* pixel box of the extent */
+} cull_f32;
+
+static int cull_setup_f32(float u, float v, float a, float b, float c, float tau, int32_t W, int32_t H,
+                          cull_f32 *q) {
+    if (!(tau > 0.0f)) return 0;
+    float ex = sqrtf(tau * a), ey = sqrtf(tau * c);
+    float x0 = ceilf((u - ex) - 0.5f), x1 = floorf((u + ex) - 0.5f);
+    float y0 = ceilf((v - ey) - 0.5f), y1 = floorf((v + ey) - 0.5f);
+    if (x0 < 0.0f) x0 = 0.0f;
+    if (y0 < 0.0f) y0 = 0.0f;
+    if (x1 > (float)(W - 1)) x1 = (float)(W - 1);
+    if (y1 > (float)(H - 1)) y1 = (float)(H - 1);
+    if (!(x0 <= x1) || !(y0 <= y1)) return 0;
+    q->u = u; q->v = v;
+    q->x0 = (int32_t)x0; q->y0 = (int32_t)y0; q->x1 = (int32_t)x1; q->y1 = (int32_t)y1;
+    float ac = a * c, det = ac - b * b;
+    if (!(a > 0.0f) || !(c > 0.0f) || ac > 64.0f * det) {
+        q->kx = 0.0f; q->ds = 0.0f; q->tc = INFINITY; q->dn = INFINITY;
+    } else {
+        q->kx = b / c;
+        q->ds = (b * ex) / a;
+        q->tc = tau * c;
+        q->dn = det / (c * c);
+    }
+    return 1;
+}
+
+/* Pixel columns [*i0, *i1] of the band of pixel rows [ylo, yhi]; 0 when none. */
+static int cull_row_f32(const cull_f32 *q, int32_t ylo, int32_t yhi, int32_t *i0, int32_t *i1) {
+    float d0 = ((float)ylo + 0.5f) - q->v, d1 = ((float)yhi + 0.5f) - q->v;
+    float dr = fminf(fmaxf(q->ds, d0), d1), dl = fminf(fmaxf(-q->ds, d0), d1);
+    float hr = sqrtf(fmaxf((q->tc - dr * dr) * q->dn, 0.0f));
+    float hl = sqrtf(fmaxf((q->tc - dl * dl) * q->dn, 0.0f));
+    float xr = q->kx * dr + hr, xl = q->kx * dl - hl;
+    float f0 = fmaxf(ceilf((q->u + xl) - 0.5f), (float)q->x0);
+    float f1 = fminf(floorf((q->u + xr) - 0.5f), (float)q->x1);
+    if (!(f0 <= f1)) return 0;
+    *i0 = (int32_t)f0;
+    *i1 = (int32_t)f1;
+    return 1;
+}
+
+/* Live tile columns of tile row ty: [*t0, *t1]; 0 when none. */
+static int cull_tiles_f32(const cull_f32 *q, int32_t ty, int32_t TW, int32_t TH, int32_t *t0, int32_t *t1) {
+    int32_t ylo = ty * TH, yhi = ty * TH + TH - 1, i0, i1;
+    if (ylo < q->y0) ylo = q->y0;
+    if (yhi > q->y1) yhi = q->y1;
+    if (!cull_row_f32(q, ylo, yhi, &i0, &i1)) return 0;
+    *t0 = i0 / TW;
+    *t1 = i1 / TW;
+    return 1;
+}
+
+/* count [n] = kept tiles, rect [n][4] = tile rectangle of the extent box (tx0, ty0, tx1,
+ * ty1; 0, 0, -1, -1 when empty), cells [n] = its area.  sxx, sxy, syy: Sigma2 (FP32). */
+int orc_cull_f32(int64_t n, const float *u, const float *v, const float *sxx, const float *sxy, const float *syy,
+                 const float *tau, const uint8_t *valid, int32_t W, int32_t H, int32_t TW, int32_t TH,
+                 int32_t *count, int32_t *rect, int32_t *cells) {
+    for (int64_t i = 0; i < n; i++) {
+        int32_t *r = rect + i * 4;
+        count[i] = 0; cells[i] = 0; r[0] = 0; r[1] = 0; r[2] = -1; r[3] = -1;
+        cull_f32 q;
+        if (!valid[i] || !cull_setup_f32(u[i], v[i], sxx[i], sxy[i], syy[i], tau[i], W, H, &q)) continue;
+        r[0] = q.x0 / TW; r[1] = q.y0 / TH; r[2] = q.x1 / TW; r[3] = q.y1 / TH;
+        cells[i] = (r[2] - r[0] + 1) * (r[3] - r[1] + 1);
+        int32_t c = 0, t0, t1;
+        for (int32_t ty = r[1]; ty <= r[3]; ty++)
+            if (cull_tiles_f32(&q, ty, TW, TH, &t0, &t1)) c += t1 - t0 + 1;
+        count[i] = c;
+    }
+    return 0;
+}
+
+/* Keys of the Gaussians listed in `order`, in that order, each Gaussian's kept tiles in
+ * row-major order: tile id = tile_offset + ty * tiles_x + tx, value = Gaussian index.
+ * Writes at most cap keys; returns the number of keys (or -1 on a bad index). */
+int64_t orc_emit_cull_f32(int64_t n, const float *u, const float *v, const float *sxx, const float *sxy,
+                          const float *syy, const float *tau, const uint8_t *valid, int32_t W, int32_t H, int32_t TW,
+                          int32_t TH, int64_t tile_offset, const int64_t *order, int64_t n_order, uint32_t *out_tile,
+                          int64_t *out_id, int64_t cap) {
+    const int32_t tiles_x = (W + TW - 1) / TW;
+    int64_t k = 0;
+    for (int64_t o = 0; o < n_order; o++) {
+        int64_t i = order[o];
+        if (i < 0 || i >= n) return -1;
+        cull_f32 q;
+        if (!valid[i] || !cull_setup_f32(u[i], v[i], sxx[i], sxy[i], syy[i], tau[i], W, H, &q)) continue;
+        int32_t t0, t1;
+        for (int32_t ty = q.y0 / TH; ty <= q.y1 / TH; ty++) {
+            if (!cull_tiles_f32(&q, ty, TW, TH, &t0, &t1)) continue;
+            for (int32_t tx = t0; tx <= t1; tx++, k++) {
+                if (k < cap) {
+                    out_tile[k] = (uint32_t)(tile_offset + (int64_t)ty * tiles_x + tx);
+                    out_id[k] = i;
+                }
+            }
+        }
+    }
+    return k;
+}
