@@ -302,8 +302,10 @@ def run_gv(args):
         "composite_bwd": ("alu", OPS_EVAL * counters["bwd_eval"] + OPS_COMP_BWD * counters["bwd_replayed"]),
         "project": ("hbm", (pbytes + 56) * npairs),
         "depth_sort": ("hbm", npairs * (4 + 4 * 16)),
-        "tile_sort": ("hbm", counters["keys"] * tile_passes * 16),
-        "emit": ("hbm", npairs * 20 + counters["keys"] * 8),
+        # the first tile-sort pass is fused into the emission (cells enumerated in depth
+        # order from the pairs' offsets, rect, cull record and mean; kept keys scattered)
+        "tile_sort": ("hbm", counters["keys"] * (tile_passes - 1) * 16),
+        "emit": ("hbm", npairs * (12 + 4 + 48) + counters["keys"] * 8),
         "project_bwd": ("hbm", npairs * (pbytes + 36) + n_gauss * 4 * (14 + (3 if "vel" in params else 0))),
     }
     stages = {}
@@ -499,6 +501,13 @@ def run_training(torch, gv, synth, dev, steps, hbm_peak, alu_peak_gops):
     pidx = torch.empty(total, dtype=torch.int32, device=dev)
     pdl = torch.randn(3 * total, device=dev) * 1e-3
     pws = torch.empty(pctx.workspace_size(fr, int(keys * 1.2) + 65536), dtype=torch.uint8, device=dev)
+    for _ in range(3):  # grow until these frames fit (they may need more keys than the last step's)
+        pctx.render_fwd(tr.params, fr, pws, pimg, pT, pidx)
+        pst, pkeys = pctx.read_status(pws, raise_on_error=False)
+        if pst == gv.GV_OK:
+            break
+        del pws
+        pws = torch.empty(pctx.workspace_size(fr, int(pkeys * 1.1) + 65536), dtype=torch.uint8, device=dev)
     grads = {k: torch.zeros_like(v) for k, v in tr.params.items()}
     ms_acc = {}
     for rep in range(4):
@@ -508,12 +517,13 @@ def run_training(torch, gv, synth, dev, steps, hbm_peak, alu_peak_gops):
         if rep:
             for k, v in ms.items():
                 ms_acc.setdefault(k, []).append(v)
+    pctx.read_status(pws)  # raises unless the profiled calls fitted
     cnt = pctx.read_counters(pws)
     P, K = cnt["pairs"], cnt["keys"]
     tiles = B * math.ceil(TW / 16) * math.ceil(TH / 16)
     tpass = math.ceil(math.ceil(math.log2(tiles)) / 8)
     amounts = {"project": ("hbm", 112 * P), "depth_sort": ("hbm", P * (4 + 4 * 16)),
-               "tile_sort": ("hbm", K * tpass * 16), "emit": ("hbm", P * 20 + K * 8),
+               "tile_sort": ("hbm", K * (tpass - 1) * 16), "emit": ("hbm", P * (12 + 4 + 48) + K * 8),
                "project_bwd": ("hbm", N * 56 * 2 + P * (56 + 36)),
                "composite_fwd": ("alu", OPS_EVAL * cnt["fwd_eval"] + OPS_COMP_FWD * cnt["bwd_replayed"]),
                "composite_bwd": ("alu", OPS_EVAL * cnt["bwd_eval"] + OPS_COMP_BWD * cnt["bwd_replayed"])}

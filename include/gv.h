@@ -23,10 +23,14 @@
  *   alpha = min(0.99, o exp(-1/2 d^T conic d)); alpha < 1/255 is skipped; front to back
  *   by camera depth (ties by Gaussian index); a Gaussian is composited and then the pixel
  *   stops if T < 1e-4.  image = sum_i c_i alpha_i T_i + T_final * bg.
- *   A Gaussian is binned into every tile holding a pixel centre inside
- *   [u - sqrt(tau Sigma2_xx), u + sqrt(tau Sigma2_xx)] x [v - sqrt(tau Sigma2_yy), ...],
- *   tau = 2 ln(255 o) (the bounding box of its alpha >= 1/255 region), so the image does not
- *   depend on the tile shape.
+ *   Binning: the alpha >= 1/255 region of a Gaussian is the ellipse d^T Sigma2^{-1} d <= tau,
+ *   tau = 2 ln(255 o).  Its extent box [u - sqrt(tau Sigma2_xx), u + sqrt(tau Sigma2_xx)] x
+ *   [v - sqrt(tau Sigma2_yy), ...] (pixel centres inside it) gives a rectangle of tiles; a
+ *   tile of that rectangle is kept when one of its pixel columns has its centre between
+ *   the two ends of the ellipse over the band of pixel-centre rows of the tile's row
+ *   (near-singular footprints, Sigma2_xx Sigma2_yy > 64 det, keep the whole rectangle).
+ *   Every pixel that can reach alpha >= 1/255 is therefore in a kept tile, so the image
+ *   does not depend on the tile shape.
  *
  * Memory and ownership.  Every pointer below is a DEVICE pointer unless marked host.
  * The caller owns every buffer; render calls never allocate.  All Gaussian parameter and
@@ -170,8 +174,12 @@ GV_API gv_status gv_render_bwd(gv_ctx *ctx, const gv_gaussians *g, const gv_came
                         const float *dL_dimage, gv_gaussians_grad *grad, gv_stream stream);
 
 /* Synchronise `stream` and report device-side failures recorded in the workspace by the
- * last render call: GV_ERR_CAPACITY (then *keys_needed, if not NULL, is the key count the
- * call needed), GV_ERR_TIMEOUT, else GV_OK.  keys_needed also reports on success. */
+ * last render call: GV_ERR_CAPACITY (then *keys_needed, if not NULL, is the key capacity
+ * the call needs: its kept keys, or more when its cells -- the tiles of the Gaussians'
+ * extent boxes, up to 2 per key of capacity -- did not fit), GV_ERR_TIMEOUT, else GV_OK
+ * (then *keys_needed is the number of keys).  After a failure the call's tile lists are
+ * incomplete: the forward renders every tile empty (background, T = 1, last index -1)
+ * and the backward adds nothing. */
 GV_API gv_status gv_read_status(gv_ctx *ctx, const void *workspace, size_t ws_bytes, gv_stream stream,
                          int64_t *keys_needed);
 
@@ -257,14 +265,15 @@ GV_API gv_status gv_profile_read(gv_ctx *ctx, float *ms, int32_t *launches);
 /* ---- stage-isolated parity hooks -------------------------------------------------- */
 
 /* Binning + sort only, from caller-given screen-space inputs of n Gaussians of ONE frame
- * (W x H): mean2d u, v, extents ex, ey, depth (all FP32 device arrays) and valid (uint8).
- * Writes counts [n] (int32) and the sorted list: sorted_tile [K], sorted_id [K] (uint32,
- * capacity cap) and *K (host).  Uses the same kernels as the render path. */
-GV_API gv_status gv_debug_bin_sort(gv_ctx *ctx, int64_t n, const float *u, const float *v, const float *ex,
-                            const float *ey, const float *depth, const uint8_t *valid, int32_t W,
-                            int32_t H, void *workspace, size_t ws_bytes, int32_t *counts,
-                            uint32_t *sorted_tile, uint32_t *sorted_id, int64_t cap, int64_t *K,
-                            gv_stream stream);
+ * (W x H): mean u, v, 2D covariance sxx, sxy, syy (Sigma2), tau (the alpha >= 1/255 level
+ * 2 ln(255 o)) and depth (all FP32 device arrays), valid (uint8).  Writes counts [n] (int32,
+ * the kept tiles of each Gaussian) and the sorted list: sorted_tile [K], sorted_id [K]
+ * (uint32, capacity cap) and *K (host).  Uses the same kernels as the render path. */
+GV_API gv_status gv_debug_bin_sort(gv_ctx *ctx, int64_t n, const float *u, const float *v, const float *sxx,
+                            const float *sxy, const float *syy, const float *tau, const float *depth,
+                            const uint8_t *valid, int32_t W, int32_t H, void *workspace, size_t ws_bytes,
+                            int32_t *counts, uint32_t *sorted_tile, uint32_t *sorted_id, int64_t cap,
+                            int64_t *K, gv_stream stream);
 
 /* Copy out intermediate state of the last forward on this workspace (device pointers,
  * may be NULL): per (frame, Gaussian) pair: mean2d [2][P], conic [3][P], opacity [P],

@@ -164,6 +164,7 @@ gv_status make_plan(gv_ctx *ctx, const gv_options &o, long long N, const gv_fram
     L.feat1 = take(16 * Pn);
     L.feat2 = take(4 * Pn);
     L.rect = take(16 * Pn);
+    L.ell = take(16 * Pn);
     L.dkey[0] = take(4 * Pn);
     L.dkey[1] = take(4 * Pn);
     L.dval[0] = take(4 * Pn);
@@ -178,13 +179,17 @@ gv_status make_plan(gv_ctx *ctx, const gv_options &o, long long N, const gv_fram
     L.ranges = take(8 * (size_t)L.tiles_alloc);
     L.hist = take(4 * 8 * kRadix);
     const size_t fixed = off;
+    // look-back tiles: those of the sorts, and the emission chunks (which share buffer 0)
+    auto look_tiles_for = [&](unsigned cap) {
+        return std::max(std::max(std::max(sort_tiles(cap, cap), sort_tiles((unsigned)P, (unsigned)P)),
+                                 emit_chunk_cap(cap)), 1u);
+    };
     auto total_for = [&](unsigned long long cap) {
-        unsigned long long lt = std::max<unsigned long long>(sort_tiles((unsigned)std::min<unsigned long long>(cap, 0xFFFFFFF0ull), (unsigned)std::min<unsigned long long>(cap, 0xFFFFFFF0ull)),
-                                                             sort_tiles((unsigned)P, (unsigned)P));
+        const unsigned c = (unsigned)std::min<unsigned long long>(std::max<unsigned long long>(cap, 1), 1ull << 30);
         size_t t = fixed;
-        t += 4 * align_up(4 * std::max<unsigned long long>(cap, 1));
-        t += align_up(4 * (std::max<unsigned long long>(cap, 1) / kEmitBlock + 2));
-        t += align_up(2 * 4 * std::max<unsigned long long>(lt, 1) * kRadix);
+        t += 4 * align_up(4 * (size_t)c);
+        t += align_up(4 * (size_t)emit_chunk_cap(c));
+        t += align_up(2 * 4 * (size_t)look_tiles_for(c) * kRadix);
         return t;
     };
     unsigned long long cap;
@@ -202,13 +207,14 @@ gv_status make_plan(gv_ctx *ctx, const gv_options &o, long long N, const gv_fram
     }
     if (cap >= (1ull << 30)) return fail(ctx, GV_ERR_INVALID_ARG, "key capacity %llu >= 2^30", cap);
     L.key_cap = (unsigned)cap;
-    L.look_tiles = std::max(std::max(sort_tiles((unsigned)cap, (unsigned)cap), sort_tiles((unsigned)P, (unsigned)P)), 1u);
     size_t kc = std::max<size_t>(cap, 1);
+    L.chunk_cap = emit_chunk_cap((unsigned)kc);
+    L.look_tiles = look_tiles_for((unsigned)kc);
     L.tkey[0] = take(4 * kc);
     L.tkey[1] = take(4 * kc);
     L.tval[0] = take(4 * kc);
     L.tval[1] = take(4 * kc);
-    L.chunk_first = take(4 * ((size_t)kc / kEmitBlock + 2));
+    L.chunk_first = take(4 * (size_t)L.chunk_cap);
     L.look = take((size_t)2 * 4 * L.look_tiles * kRadix);
     L.total = off;
     if (key_cap_req <= 0 && L.total > ws_bytes)
@@ -225,6 +231,7 @@ Work make_work(void *ws, const Layout &L) {
     w.feat1 = (float4 *)(b + L.feat1);
     w.feat2 = (float *)(b + L.feat2);
     w.rect = (uint4 *)(b + L.rect);
+    w.ell = (float4 *)(b + L.ell);
     for (int i = 0; i < 2; i++) {
         w.dkey[i] = (unsigned *)(b + L.dkey[i]);
         w.dval[i] = (unsigned *)(b + L.dval[i]);
@@ -278,6 +285,15 @@ gv_status run_setup(gv_ctx *ctx, const Work &w, const Plan &pl, cudaStream_t s) 
 int depth_result_buf() { return sort_passes(32) & 1; }
 int tile_result_buf(const Layout &L) { return sort_passes(L.tile_bits) & 1; }
 
+// The tile-sort passes after the first (which the emission does): buffer 1 onwards.
+cudaError_t tile_sort_rest(gv_ctx *ctx, const Work &w, cudaStream_t s, int *tres) {
+    const unsigned *n_keys =
+        reinterpret_cast<const unsigned *>(reinterpret_cast<const char *>(w.hdr) + offsetof(DevHeader, keys_used));
+    unsigned *tk[2] = {w.tkey[0], w.tkey[1]}, *tv[2] = {w.tval[0], w.tval[1]};
+    return launch_radix_sort(w, tk, tv, n_keys, w.L.key_cap, w.L.tile_bits, false, true, 4, 4, ctx->num_sms, s, tres,
+                             1);
+}
+
 gv_status forward_stages(gv_ctx *ctx, const gv_gaussians *g, const Plan &pl, const Work &w, float *image,
                          float *final_T, int32_t *last_idx, cudaStream_t s) {
     const gv_options &o = ctx->opt;
@@ -302,16 +318,12 @@ gv_status forward_stages(gv_ctx *ctx, const gv_gaussians *g, const Plan &pl, con
         }
         {
             StageTimer tm(ctx, GV_STAGE_EMIT, s, 4);
-            GV_CUDA(launch_emit(w, dres, w.L.tile_bits, 4, ctx->num_sms, s));
+            GV_CUDA(launch_emit(w, dres, o.tile_w, o.tile_h, ctx->num_sms, s));
         }
         int tres = 0;
         {
-            StageTimer tm(ctx, GV_STAGE_TILE_SORT, s, sort_passes(w.L.tile_bits));
-            const unsigned *n_keys = reinterpret_cast<const unsigned *>(reinterpret_cast<const char *>(w.hdr) +
-                                                                          offsetof(DevHeader, keys_used));
-            unsigned *tk[2] = {w.tkey[0], w.tkey[1]}, *tv[2] = {w.tval[0], w.tval[1]};
-            GV_CUDA(launch_radix_sort(w, tk, tv, n_keys, w.L.key_cap, w.L.tile_bits, false, true, 4, 4, ctx->num_sms, s,
-                                      &tres));
+            StageTimer tm(ctx, GV_STAGE_TILE_SORT, s, sort_passes(w.L.tile_bits) - 1);
+            GV_CUDA(tile_sort_rest(ctx, w, s, &tres));
         }
         {
             StageTimer tm(ctx, GV_STAGE_RANGES, s, 1);
@@ -836,12 +848,13 @@ gv_status gv_graph_destroy(gv_graph *G) {
     return GV_OK;
 }
 
-gv_status gv_debug_bin_sort(gv_ctx *ctx, int64_t n, const float *u, const float *v, const float *ex, const float *ey,
-                            const float *depth, const uint8_t *valid, int32_t W, int32_t H, void *workspace,
-                            size_t ws_bytes, int32_t *counts, uint32_t *sorted_tile, uint32_t *sorted_id, int64_t cap,
-                            int64_t *K, gv_stream stream) {
+gv_status gv_debug_bin_sort(gv_ctx *ctx, int64_t n, const float *u, const float *v, const float *sxx, const float *sxy,
+                            const float *syy, const float *tau, const float *depth, const uint8_t *valid, int32_t W,
+                            int32_t H, void *workspace, size_t ws_bytes, int32_t *counts, uint32_t *sorted_tile,
+                            uint32_t *sorted_id, int64_t cap, int64_t *K, gv_stream stream) {
     if (!ctx || n < 0 || !workspace || !K) return GV_ERR_INVALID_ARG;
-    if (n > 0 && (!u || !v || !ex || !ey || !depth || !valid)) return fail(ctx, GV_ERR_INVALID_ARG, "NULL input");
+    if (n > 0 && (!u || !v || !sxx || !sxy || !syy || !tau || !depth || !valid))
+        return fail(ctx, GV_ERR_INVALID_ARG, "NULL input");
     gv_frame_desc d;
     memset(&d, 0, sizeof(d));
     d.cam.W = W; d.cam.H = H; d.cam.fx = d.cam.fy = 1.f;
@@ -853,7 +866,8 @@ gv_status gv_debug_bin_sort(gv_ctx *ctx, int64_t n, const float *u, const float 
     cudaStream_t s = (cudaStream_t)stream;
     st = run_setup(ctx, w, pl, s);
     if (st != GV_OK) return st;
-    GV_CUDA(launch_bin_from_screen(w, n, u, v, ex, ey, depth, valid, ctx->opt.tile_w, ctx->opt.tile_h, counts, s));
+    GV_CUDA(launch_bin_from_screen(w, n, u, v, sxx, sxy, syy, tau, depth, valid, ctx->opt.tile_w, ctx->opt.tile_h,
+                                   counts, ctx->num_sms, s));
     int tres = 0;
     if (n > 0) {
         int dres = 0;
@@ -861,11 +875,8 @@ gv_status gv_debug_bin_sort(gv_ctx *ctx, int64_t n, const float *u, const float 
                                                                        offsetof(DevHeader, n_pairs));
         unsigned *dk[2] = {w.dkey[0], w.dkey[1]}, *dv[2] = {w.dval[0], w.dval[1]};
         GV_CUDA(launch_radix_sort(w, dk, dv, n_pairs, w.L.P, 32, true, true, 0, 0, ctx->num_sms, s, &dres));
-        GV_CUDA(launch_emit(w, dres, w.L.tile_bits, 4, ctx->num_sms, s));
-        const unsigned *n_keys = reinterpret_cast<const unsigned *>(reinterpret_cast<const char *>(w.hdr) +
-                                                                      offsetof(DevHeader, keys_used));
-        unsigned *tk[2] = {w.tkey[0], w.tkey[1]}, *tv[2] = {w.tval[0], w.tval[1]};
-        GV_CUDA(launch_radix_sort(w, tk, tv, n_keys, w.L.key_cap, w.L.tile_bits, false, true, 4, 4, ctx->num_sms, s, &tres));
+        GV_CUDA(launch_emit(w, dres, ctx->opt.tile_w, ctx->opt.tile_h, ctx->num_sms, s));
+        GV_CUDA(tile_sort_rest(ctx, w, s, &tres));
     }
     int64_t needed = 0;
     st = gv_read_status(ctx, workspace, ws_bytes, stream, &needed);

@@ -1,13 +1,16 @@
-// binning.cu -- per-call setup, tile-count prefix scan, key emission and tile ranges.
+// binning.cu -- per-call setup, cell offsets, key emission fused with the first pass of
+// the tile sort, and tile ranges.
 //
 // Binning is two-level.  The pairs are first sorted by camera depth (one 32-bit radix
-// sort over the P pairs), then each pair, in depth order, emits one key per tile its
-// extent rectangle covers (row-major), and the keys are sorted stably by tile id only.
-// The result is the unique list a stable sort of (tile << 32 | depth bits) keys emitted in
-// pair order would give -- ordered by tile, then depth, then pair index -- but the
-// expensive per-key sort touches only the live tile-id bits (one or two 8-bit passes
-// instead of five or six).
+// sort over the P pairs), then each pair, in depth order, enumerates its cells (the tiles
+// of its extent box, row-major) and emits a key for every cell the cull keeps, and the
+// keys are sorted stably by tile id only.  The result is the unique list a stable sort of
+// (tile << 32 | depth bits) keys emitted in pair order would give -- ordered by tile, then
+// depth, then pair index -- but the per-key sort touches only the live tile-id bits, and
+// its first 8-bit pass happens during emission: the emitted keys are ranked by their low
+// tile digit inside each chunk and scattered straight to their first-pass positions.
 #include <algorithm>
+#include <cstddef>
 
 #include "gv_internal.cuh"
 
@@ -59,7 +62,10 @@ __global__ void __launch_bounds__(kEmitThreads) count_reduce_kernel(Work w, cons
     }
 }
 
-// Exclusive scan of the block sums (single block), total key count and capacity check.
+// Exclusive scan of the block cell sums (single block), cell total, chunk count and the
+// capacity checks: the kept keys (counted by the projection) against the key capacity,
+// the cells against the chunk table.  On overflow keys_total reports the key capacity
+// the call needs.
 __global__ void __launch_bounds__(1024) count_scan_kernel(Work w) {
     __shared__ unsigned long long s_w[32];
     __shared__ unsigned long long s_carry;
@@ -89,56 +95,38 @@ __global__ void __launch_bounds__(1024) count_scan_kernel(Work w) {
         }
         __syncthreads();
         unsigned long long ex = s_carry + s_w[wid] + inc - x;
-        // prefixes beyond the capacity are clamped: those blocks emit nothing
-        if (i < nb) w.blockprefix[i] = (unsigned)min(ex, (unsigned long long)w.L.key_cap);
+        // prefixes past 2^32 - 1 cells are clamped (the call fails the capacity check)
+        if (i < nb) w.blockprefix[i] = (unsigned)min(ex, 0xFFFFFFFFull);
         __syncthreads();
         if (threadIdx.x == 1023) s_carry = ex + x;
         __syncthreads();
     }
     if (threadIdx.x == 0) {
-        unsigned long long K = s_carry;
-        w.hdr->keys_total = K;
+        const unsigned long long cells = s_carry, K = w.hdr->keys_total;
+        const unsigned long long chunks = (cells + kEmitBlock - 1) / kEmitBlock;
+        bool over = K > w.L.key_cap;
+        if (chunks > w.L.chunk_cap || cells > 0xFFFFFFFFull) {
+            over = true;
+            const unsigned long long need = (cells + kCellsPerKey - 1) / kCellsPerKey + kEmitBlock;
+            w.hdr->keys_total = max(K, need);
+        }
+        w.hdr->cells = cells;
         w.hdr->keys_used = (unsigned)min(K, (unsigned long long)w.L.key_cap);
-        if (K > w.L.key_cap) atomicOr(&w.hdr->err, ERR_CAPACITY);
+        w.hdr->n_chunks = over && (chunks > w.L.chunk_cap || cells > 0xFFFFFFFFull) ? 0u : (unsigned)chunks;
+        if (over) atomicOr(&w.hdr->err, ERR_CAPACITY);
     }
 }
 
-// Tile-sort digit counts of one tile-id range [t0, t0 + len) (a row of a pair's tile
-// rectangle): digit 0 through a difference array over its 256 values (the range wraps
-// around len >> 8 times plus a partial run), higher digits directly (a row spans one or two
-// of their values).
-__device__ __forceinline__ void count_tile_run(unsigned t0, unsigned len, int passes, int *s_diff, unsigned *s_full,
-                                               unsigned (*s_h)[kRadix]) {
-    const unsigned full = len >> 8, rem = len & 255u;
-    if (full) atomicAdd(s_full, full);
-    if (rem) {
-        const unsigned a = t0 & 255u, e = a + rem;
-        atomicAdd(s_diff + a, 1);
-        if (e <= 256u) {
-            atomicAdd(s_diff + e, -1);
-        } else {
-            atomicAdd(s_diff + 256, -1);
-            atomicAdd(s_diff + 0, 1);
-            atomicAdd(s_diff + (e - 256u), -1);
-        }
-    }
-    const unsigned t1 = t0 + len - 1u;
-    for (int ps = 1; ps < passes; ps++) {
-        const int sh = 8 * ps;
-        for (unsigned h = t0 >> sh; h <= (t1 >> sh); h++) {
-            const unsigned lo = max(t0, h << sh), hi = min(t1, ((h + 1u) << sh) - 1u);
-            atomicAdd(&s_h[ps][h & 255u], hi - lo + 1u);
-        }
-    }
-}
-
-// Exclusive key offsets of every pair in depth order: off[i] for i < P, off[P] = K.
+// Exclusive cell offsets of every pair in depth order: off[i] for i < P, off[P] = cells.
 // Block b scans its kEmitBlock pairs and adds the block prefix.  Each pair also records
-// the emission chunks whose first key it owns.
+// the emission chunks whose first cell it owns.  Also clears look-back buffer 0 for the
+// emission chunks (the depth sort is finished with it).
 __global__ void __launch_bounds__(kEmitThreads) offsets_kernel(Work w, const unsigned *order) {
     __shared__ unsigned s_w[8];
     const unsigned b = blockIdx.x, base = b * kEmitBlock;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const unsigned nchunks = w.hdr->n_chunks;
+    for (unsigned i = b * kEmitThreads + t; i < nchunks * kRadix; i += gridDim.x * kEmitThreads) w.look[i] = 0u;
     // blocked: thread t owns pairs base + t*8 .. +7
     unsigned c[kEmitItems], sum = 0;
 #pragma unroll
@@ -159,156 +147,208 @@ __global__ void __launch_bounds__(kEmitThreads) offsets_kernel(Work w, const uns
     __syncthreads();
     unsigned run = w.blockprefix[b] + inc - sum;
     for (int q = 0; q < wid; q++) run += s_w[q];
-    const unsigned cap = w.L.key_cap;
 #pragma unroll
     for (int i = 0; i < kEmitItems; i++) {
         unsigned idx = base + t * kEmitItems + i;
         if (idx < w.L.P) {
-            const unsigned lo = min(run, cap), hi = min(run + c[i], cap);
+            const unsigned lo = run, hi = run + c[i];
             w.offsets[idx] = lo;
-            // this pair owns the first key of every emission chunk starting in [lo, hi)
-            for (unsigned ch = (lo + kEmitBlock - 1) / kEmitBlock; ch * kEmitBlock < hi; ch++) w.chunk_first[ch] = idx;
+            // this pair owns the first cell of every emission chunk starting in [lo, hi)
+            for (unsigned ch = (lo + kEmitBlock - 1) / kEmitBlock; ch < nchunks && ch * kEmitBlock < hi; ch++)
+                w.chunk_first[ch] = idx;
         }
         run += c[i];
     }
-    if (b == 0 && t == 0) w.offsets[w.L.P] = w.hdr->keys_used;
+    if (b == 0 && t == 0) w.offsets[w.L.P] = (unsigned)min(w.hdr->cells, 0xFFFFFFFFull);
 }
 
-// Flush a block's tile-sort digit counts: digit 0 from its difference array (prefix sum
-// plus the full wraps), higher digits as counted.
-__device__ __forceinline__ void flush_tile_hist(int passes, int *s_diff, unsigned s_full, unsigned (*s_h)[kRadix],
-                                                unsigned *tile_hist) {
-    const int t = threadIdx.x, lane = t & 31;
-    if (t < 32) {
-        int carry = 0;
-        for (int base8 = 0; base8 < 256; base8 += 32) {
-            int x = s_diff[base8 + lane];
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, x, o);
-                if (lane >= o) x += y;
-            }
-            s_h[0][base8 + lane] = (unsigned)(x + carry) + s_full;
-            carry += __shfl_sync(0xffffffffu, x, 31);
-        }
-    }
-    __syncthreads();
-    for (int i = t; i < passes * kRadix; i += blockDim.x) {
-        const unsigned v = (&s_h[0][0])[i];
-        if (v) atomicAdd(tile_hist + i, v);
-    }
-}
+// Key emission fused with the first pass of the tile sort, balanced over cells.  Each
+// block iteration takes the next chunk of kEmitBlock consecutive cells (in the order the
+// offsets define: pairs by depth, each pair's extent-box tiles row-major) from an atomic
+// counter and finds the pair owning every cell with a load-balancing search: the pairs
+// whose cells fall in the chunk (a window of the depth-ordered offsets starting at the
+// chunk's owner recorded by offsets_kernel) mark their first cell, and an inclusive max
+// scan over the chunk carries each mark forward.  A cell is a key when the cull keeps its
+// tile (cull_tiles, as the projection counted).  The keys are ranked stably by their low
+// tile digit inside the chunk (warp match + per-warp histograms, in cell order), the
+// per-digit counts of all earlier chunks come from decoupled look-back, and (tile id, pair
+// id) is scattered to its first-pass position: out of this kernel the kept keys are
+// compacted and sorted by the low tile digit, in depth order within a digit.  The global
+// digit offsets come from the projection's counts of the kept keys.
+struct EmitSortArgs {
+    const unsigned *order;  // depth-sorted pair ids
+    unsigned *keys_out, *vals_out;
+    const unsigned *hist;   // low-digit counts of all kept keys
+    unsigned *ctr;          // chunk counter
+    unsigned *look_next;    // look-back buffer of the next tile-sort pass (cleared here)
+    int lw, lh;
+};
 
-// Key emission balanced over keys: each block iteration takes kEmitBlock consecutive
-// keys and finds the pair owning every key with a load-balancing search: the pairs whose
-// keys fall in the chunk (a window of the depth-ordered offsets starting at the chunk's
-// owner recorded by offsets_kernel; every pair in it owns at least one key, pairs with no
-// key sort last) mark their first key, and an inclusive max scan over the chunk carries
-// each mark forward.  Keys are written coalesced as (tile id,
-// pair id), the tiles of a pair in row-major order.  Also counts the tile-sort digit
-// histograms.
-__global__ void __launch_bounds__(kEmitThreads) emit_kernel(Work w, const unsigned *order, int tile_passes,
-                                                            unsigned *tile_hist) {
-    __shared__ int s_owner[kEmitBlock];
+__global__ void __launch_bounds__(kEmitThreads, 4) emit_sort_kernel(Work w, EmitSortArgs a) {
+    __shared__ int s_owner[kEmitBlock];          // later: the chunk's keys, reordered by digit
     __shared__ unsigned s_off[kEmitBlock + 1];
-    __shared__ unsigned s_pair[kEmitBlock];
+    __shared__ unsigned s_pair[kEmitBlock];      // later: their pair ids
+    __shared__ unsigned s_whist[8][kRadix];
+    __shared__ unsigned s_gexcl[kRadix], s_dstart[kRadix], s_gbase[kRadix];
+    __shared__ unsigned s_scan[24];
     __shared__ int s_wmax[kEmitThreads / 32];
-    __shared__ unsigned s_lo, s_n;
-    __shared__ int s_diff[257];
-    __shared__ unsigned s_full;
-    __shared__ unsigned s_h[4][kRadix];
+    __shared__ unsigned s_chunk, s_lo, s_n;
+    __shared__ int s_abort;
+    unsigned *s_keys = reinterpret_cast<unsigned *>(s_owner);
+    unsigned *s_vals = s_pair;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    for (int i = t; i < 257; i += kEmitThreads) s_diff[i] = 0;
-    for (int i = t; i < 4 * kRadix; i += kEmitThreads) (&s_h[0][0])[i] = 0u;
-    if (t == 0) s_full = 0u;
-    const unsigned K = w.hdr->keys_used;
-    const unsigned P = w.L.P;
+    const unsigned P = w.L.P, nchunks = w.hdr->n_chunks;
+    const unsigned cells = (unsigned)min(w.hdr->cells, 0xFFFFFFFFull);
     const unsigned *off = w.offsets;
-    const unsigned nchunks = (K + kEmitBlock - 1) / kEmitBlock;
-    {   // look-back buffer 0 of the tile sort (the depth sort is finished with it)
-        const unsigned nlook = sort_tiles(K, w.L.key_cap) * kRadix;
-        for (unsigned i = blockIdx.x * blockDim.x + t; i < nlook; i += gridDim.x * blockDim.x) w.look[i] = 0u;
+    const long long limit = w.hdr->spin_limit;
+    const unsigned next_tiles = sort_tiles(w.hdr->keys_used, w.L.key_cap);
+    for (unsigned i = blockIdx.x * kEmitThreads + t; i < next_tiles * kRadix; i += gridDim.x * kEmitThreads)
+        a.look_next[i] = 0u;
+    {
+        unsigned ex;
+        block_excl_scan_256(a.hist[t], s_scan, ex);
+        s_gexcl[t] = ex;
     }
-    for (unsigned chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
-        const unsigned k0 = chunk * kEmitBlock;
-        const unsigned kb = min(K - k0, (unsigned)kEmitBlock);
+    for (;;) {
+        if (t == 0) { s_chunk = atomicAdd(a.ctr, 1u); s_abort = 0; }
+        for (int i = t; i < 8 * kRadix; i += kEmitThreads) (&s_whist[0][0])[i] = 0u;
+        for (int i = t; i < kEmitBlock; i += kEmitThreads) s_owner[i] = -1;
         __syncthreads();
+        const unsigned chunk = s_chunk;
+        if (chunk >= nchunks) break;
+        const unsigned k0 = chunk * kEmitBlock;
+        const unsigned kb = min(cells - k0, (unsigned)kEmitBlock);
         if (t == 0) {
-            // the pairs owning this chunk's keys run from the owner of its first key to the
-            // owner of the next chunk's first key (pairs after the last key own nothing here)
+            // the pairs owning this chunk's cells run from the owner of its first cell to the
+            // owner of the next chunk's first cell (pairs after the last cell own nothing here)
             const unsigned lo = min(w.chunk_first[chunk], P - 1u);
             const unsigned hi = chunk + 1 < nchunks ? min(w.chunk_first[chunk + 1], P - 1u) : P - 1u;
             s_lo = lo;
             s_n = min(hi >= lo ? hi - lo + 1 : 1u, (unsigned)kEmitBlock);
         }
-        for (int i = t; i < kEmitBlock; i += kEmitThreads) s_owner[i] = -1;
         __syncthreads();
         const unsigned plo = s_lo, np = s_n;
         for (unsigned i = t; i <= np; i += kEmitThreads) {
-            const unsigned o = off[plo + i];  // plo + np <= P: off[P] = K
+            const unsigned o = off[plo + i];  // plo + np <= P: off[P] = cells
             s_off[i] = o;
             if (i == np) break;
-            const unsigned p = order[plo + i];
+            const unsigned p = a.order[plo + i];
             s_pair[i] = p < P ? p : 0u;  // in range unless a bounded wait gave up
             const unsigned first = o > k0 ? o - k0 : 0u;
             if (first < kb) s_owner[first] = (int)i;
         }
         __syncthreads();
-        // inclusive max scan of s_owner: thread t owns entries t*8 .. t*8+7
-        int run = -1;
-        int v[kEmitItems];
+        {   // inclusive max scan of s_owner: thread t owns entries t*8 .. t*8+7
+            int run = -1;
+            int v[kEmitItems];
+#pragma unroll
+            for (int i = 0; i < kEmitItems; i++) {
+                v[i] = s_owner[t * kEmitItems + i];
+                run = max(run, v[i]);
+                v[i] = run;
+            }
+            int incl = run;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl = max(incl, y);
+            }
+            if (lane == 31) s_wmax[wid] = incl;
+            __syncthreads();
+            int carry = -1;
+            for (int q = 0; q < wid; q++) carry = max(carry, s_wmax[q]);
+            int excl = __shfl_up_sync(0xffffffffu, incl, 1);
+            if (lane == 0) excl = -1;
+            carry = max(carry, excl);
+#pragma unroll
+            for (int i = 0; i < kEmitItems; i++) s_owner[t * kEmitItems + i] = max(carry, v[i]);
+        }
+        __syncthreads();
+        // cells of this thread: warp w owns cells [256 w, 256 w + 256), lane l cells l, l + 32, ...
+        unsigned key[kEmitItems], val[kEmitItems], rank[kEmitItems];
+        unsigned kept = 0;  // bit i: cell i is a key
 #pragma unroll
         for (int i = 0; i < kEmitItems; i++) {
-            v[i] = s_owner[t * kEmitItems + i];
-            run = max(run, v[i]);
-            v[i] = run;
-        }
-        int incl = run;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl = max(incl, y);
-        }
-        if (lane == 31) s_wmax[wid] = incl;
-        __syncthreads();
-        int carry = -1;
-        for (int q = 0; q < wid; q++) carry = max(carry, s_wmax[q]);
-        int excl = __shfl_up_sync(0xffffffffu, incl, 1);
-        if (lane == 0) excl = -1;
-        carry = max(carry, excl);
-#pragma unroll
-        for (int i = 0; i < kEmitItems; i++) s_owner[t * kEmitItems + i] = max(carry, v[i]);
-        __syncthreads();
-        for (unsigned r0 = 0; r0 < (unsigned)kEmitBlock; r0 += kEmitThreads) {
-            const unsigned e = r0 + t;
+            const unsigned e = wid * (32 * kEmitItems) + i * 32 + lane;
+            key[i] = 0u;
+            val[i] = 0u;
             if (e < kb) {
-                const int i = max(s_owner[e], 0);
-                const unsigned j = k0 + e - s_off[i];
-                const unsigned p = s_pair[i];
-                const uint4 r = w.rect[p];  // consecutive keys mostly share a pair: L1 hits
+                const int oi = max(s_owner[e], 0);
+                const unsigned j = k0 + e - s_off[oi];
+                const unsigned p = s_pair[oi];
+                const uint4 r = w.rect[p];  // consecutive cells mostly share a pair: L1 hits
                 const DevFrame &fr = w.frames[min(r.w & kRectFrame, w.L.F - 1u)];
-                const unsigned tx0 = r.x & 0xFFFFu, ty0 = r.x >> 16, tx1 = r.y & 0xFFFFu;
-                const unsigned wr = tx1 - tx0 + 1u;
+                const PixBox bx = unpack_box(r);
+                const unsigned tx0 = (unsigned)bx.x0 >> a.lw, ty0 = (unsigned)bx.y0 >> a.lh;
+                const unsigned wr = ((unsigned)bx.x1 >> a.lw) - tx0 + 1u;
                 // j / wr through the FP32 reciprocal, corrected to the exact quotient (j < 2^24)
                 unsigned q = (unsigned)((float)j * __frcp_rn((float)wr));
                 int rem = (int)j - (int)(q * wr);
                 if (rem < 0) { q--; rem += (int)wr; }
                 else if (rem >= (int)wr) { q++; rem -= (int)wr; }
-                const unsigned tile = min(fr.tile_offset + (ty0 + q) * fr.tiles_x + tx0 + (unsigned)rem, w.L.tiles - 1u);
-                w.tkey[0][k0 + e] = tile;
-                w.tval[0][k0 + e] = p;
-                // the key starting a row run (in this chunk) counts the run's tile digits
-                if (tile_passes > 0 && (rem == 0 || e == 0)) {
-                    const unsigned pair_end = min(s_off[i + 1], k0 + kb);  // this pair's keys end here
-                    const unsigned len = min(wr - (unsigned)rem, pair_end - (k0 + e));
-                    count_tile_run(tile, len, tile_passes, s_diff, &s_full, s_h);
+                const int tx = (int)tx0 + rem, ty = (int)(ty0 + q);
+                const float4 f0 = w.feat0[p];
+                int t0, t1;
+                if (cull_tiles(f0.x, f0.y, w.ell[p], bx, ty, a.lw, a.lh, t0, t1) && tx >= t0 && tx <= t1) {
+                    key[i] = min(fr.tile_offset + (unsigned)ty * fr.tiles_x + (unsigned)tx, w.L.tiles - 1u);
+                    val[i] = p;
+                    kept |= 1u << i;
                 }
             }
         }
+        // stable rank of the keys inside the warp (by item, then by lane); a cell that is not
+        // a key matches no lane but itself and is not counted
+#pragma unroll
+        for (int i = 0; i < kEmitItems; i++) {
+            const bool live = (kept >> i) & 1u;
+            const unsigned d = key[i] & 255u;
+            const unsigned peers = __match_any_sync(0xffffffffu, live ? d : 0x100u + (unsigned)lane);
+            unsigned before = 0;
+            if (live) before = s_whist[wid][d];
+            rank[i] = before + __popc(peers & lanemask_lt());
+            __syncwarp();
+            if (live && lane == __ffs(peers) - 1) s_whist[wid][d] = before + __popc(peers);
+            __syncwarp();
+        }
+        __syncthreads();
+        // thread t owns digit t: exclusive offsets over warps, chunk total
+        unsigned total = 0;
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const unsigned c = s_whist[q][t];
+            s_whist[q][t] = total;
+            total += c;
+        }
+        bool gave_up = false;
+        const unsigned excl = lookback_digit(w.look, chunk, total, w.hdr, limit, false, gave_up);
+        if (gave_up) s_abort = 1;
+        unsigned dex;
+        const unsigned nkeys = block_excl_scan_256(total, s_scan, dex);
+        s_dstart[t] = dex;
+        s_gbase[t] = s_gexcl[t] + excl;
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kEmitItems; i++) {
+            if (!((kept >> i) & 1u)) continue;
+            const unsigned d = key[i] & 255u;
+            const unsigned pos = s_dstart[d] + s_whist[wid][d] + rank[i];
+            s_keys[pos] = key[i];
+            s_vals[pos] = val[i];
+        }
+        __syncthreads();
+        if (!s_abort) {
+            for (unsigned pos = t; pos < nkeys; pos += kEmitThreads) {
+                const unsigned k = s_keys[pos];
+                const unsigned d = k & 255u;
+                const unsigned gpos = s_gbase[d] + pos - s_dstart[d];
+                if (gpos < w.L.key_cap) {
+                    a.keys_out[gpos] = k;
+                    a.vals_out[gpos] = s_vals[pos];
+                }
+            }
+        }
+        __syncthreads();
     }
-    if (tile_passes == 0) return;
-    __syncthreads();
-    flush_tile_hist(tile_passes, s_diff, s_full, s_h, tile_hist);
 }
 
 // Per-tile [start, end) of the sorted keys.  A warp takes 32 * kRangeItems consecutive keys
@@ -380,16 +420,23 @@ cudaError_t launch_setup(const Work &w, const FrameChunk &chunk, int first, int 
     return cudaGetLastError();
 }
 
-cudaError_t launch_emit(const Work &w, int depth_buf, int tile_bits, int tile_hist_slot, int num_sms, cudaStream_t s) {
+cudaError_t launch_emit(const Work &w, int depth_buf, int tile_w, int tile_h, int num_sms, cudaStream_t s) {
     if (w.L.P == 0) return cudaSuccess;
     const unsigned *order = w.dval[depth_buf];
     count_reduce_kernel<<<w.L.emit_blocks, kEmitThreads, 0, s>>>(w, order);
     count_scan_kernel<<<1, 1024, 0, s>>>(w);
-    int passes = tile_bits <= 0 ? 0 : (tile_bits + 7) / 8;
     offsets_kernel<<<w.L.emit_blocks, kEmitThreads, 0, s>>>(w, order);
-    unsigned chunks = (w.L.key_cap + kEmitBlock - 1) / kEmitBlock;
-    unsigned grid = std::max(1u, std::min(chunks, (unsigned)num_sms * 8u));
-    emit_kernel<<<grid, kEmitThreads, 0, s>>>(w, order, passes, w.hist + (size_t)tile_hist_slot * kRadix);
+    EmitSortArgs a;
+    a.order = order;
+    a.keys_out = w.tkey[1];
+    a.vals_out = w.tval[1];
+    a.hist = w.hist + 4 * kRadix;
+    a.ctr = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(w.hdr) + offsetof(DevHeader, sort_ctr)) + 4;
+    a.look_next = w.look + (size_t)w.L.look_tiles * kRadix;
+    a.lw = __builtin_ctz(tile_w);
+    a.lh = __builtin_ctz(tile_h);
+    const unsigned grid = std::max(1u, std::min(w.L.chunk_cap, (unsigned)num_sms * 4u));
+    emit_sort_kernel<<<grid, kEmitThreads, 0, s>>>(w, a);
     return cudaGetLastError();
 }
 

@@ -100,6 +100,7 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_fwd_kernel(Work w, const
     pixels_of_thread<TW, TH>(threadIdx.x, lx, ly);
     const unsigned ntiles = w.L.tiles;
     const int F = (int)w.L.F;
+    const bool failed = w.hdr->err != 0u;  // lists incomplete: every tile renders empty
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&w.hdr->queue[0], 1u);
         __syncthreads();
@@ -116,7 +117,7 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_fwd_kernel(Work w, const
         const bool in0 = x < W && y0 < H, in1 = x < W && y1 < H;
         const float px = (float)x + 0.5f;
         const float2 npy = make_float2(-((float)y0 + 0.5f), -((float)y1 + 0.5f));
-        const uint2 rg = w.ranges[tile];
+        const uint2 rg = failed ? make_uint2(0u, 0u) : w.ranges[tile];
         float2 T = make_float2(1.f, 1.f), cr = make_float2(0.f, 0.f), cg = cr, cb = cr;
         int last0 = -1, last1 = -1;
         bool done0 = !in0, done1 = !in1;
@@ -208,6 +209,7 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_bwd_kernel(Work w, const
     const int lane = threadIdx.x & 31;
     const unsigned ntiles = w.L.tiles;
     const int F = (int)w.L.F;
+    const bool failed = w.hdr->err != 0u;  // lists incomplete: every tile renders empty
     for (;;) {
         if (threadIdx.x == 0) { s_tile = atomicAdd(&w.hdr->queue[1], 1u); s_max = -1; }
         __syncthreads();
@@ -223,7 +225,7 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_bwd_kernel(Work w, const
         const int y0 = (int)(lt / fr.tiles_x) * TH + ly, y1 = y0 + 4;
         const float px = (float)x + 0.5f;
         const float2 npy = make_float2(-((float)y0 + 0.5f), -((float)y1 + 0.5f));
-        const uint2 rg = w.ranges[tile];
+        const uint2 rg = failed ? make_uint2(0u, 0u) : w.ranges[tile];
         // per-pixel replay state, packed over the thread's two pixels
         float2 T = make_float2(1.f, 1.f), g0 = make_float2(0.f, 0.f), g1 = g0, g2 = g0;
         int last0 = -1, last1 = -1;

@@ -4,10 +4,12 @@
 //   header      DevHeader: error word, key count, work-queue and sort counters
 //   frames      DevFrame[F]: camera and offsets of each frame
 //   per pair    (frame, Gaussian) pairs, P = sum of per-frame Gaussian counts:
-//               feat0 float4 (u, v, conic A, conic B), feat1 float4 (conic C, opacity, r, g),
-//               feat2 float (b), rect uint4 (tile rect + frame tile base), depth keys and
-//               pair ids (double-buffered for the depth sort), grad2d (two float4 + float)
+//               feat0 float4 (u, v, a', b'), feat1 float4 (c', log2 o, r, g), feat2 float
+//               (b) (the staged record, below), rect uint4 (pixel box of the extent, cell
+//               count, frame), ell float4 (the culling record), depth keys and pair ids
+//               (double-buffered for the depth sort), grad2d (two float4 + float)
 //   per key     tile ids and pair ids, double-buffered for the tile sort
+//   per chunk   the depth-ordered pair owning the chunk's first cell (key emission)
 //   per tile    [start, end) ranges into the sorted key list
 //   sort        digit histograms and decoupled look-back status words
 #pragma once
@@ -48,7 +50,8 @@ struct DevFrame {
 struct DevHeader {
     unsigned err;
     unsigned keys_used;             // min(keys_total, capacity)
-    unsigned long long keys_total;  // keys the call needed
+    unsigned long long keys_total;  // keys (after culling) the call emits; on a capacity error,
+                                    // the key capacity it needs
     unsigned n_pairs;               // P, read by the depth sort
     unsigned pad0;
     unsigned sort_ctr[16];          // tile-acquisition counters of the sort passes
@@ -58,11 +61,12 @@ struct DevHeader {
     int pad;
     unsigned long long work[4];     // pairs evaluated / composited: fwd 0-1, bwd 2-3
     unsigned fp64_count;            // ill-conditioned pairs listed by the projection (FP64 chain rule)
-    unsigned pad1;
+    unsigned n_chunks;              // emission chunks of kEmitBlock cells
+    unsigned long long cells;       // cells: tiles of the pairs' extent boxes, before culling
 };
 
 // Radix sort geometry (one onesweep pass = one 8-bit digit).  Small sorts use 1024-key
-// block tiles (more blocks in flight), large ones 3840-key tiles (fewer look-back steps).
+// block tiles (more blocks in flight), large ones 3072-key tiles (fewer look-back steps).
 // rect.w of a pair: frame index, bit 31 set when the backward runs its geometric chain
 // rule in FP64 (ill-conditioned footprint)
 constexpr unsigned kRectFp64 = 1u << 31;
@@ -71,7 +75,7 @@ constexpr unsigned kRectFrame = kRectFp64 - 1u;
 constexpr int kSortThreads = 256;
 constexpr int kRadix = 256;
 constexpr unsigned kSortSmallN = 1u << 20;
-__host__ __device__ constexpr int sort_items(unsigned n_cap) { return n_cap <= kSortSmallN ? 4 : 15; }
+__host__ __device__ constexpr int sort_items(unsigned n_cap) { return n_cap <= kSortSmallN ? 4 : 12; }
 __host__ __device__ constexpr unsigned sort_tile_keys(unsigned n_cap) {
     return (unsigned)(kSortThreads * sort_items(n_cap));
 }
@@ -79,15 +83,21 @@ __host__ __device__ constexpr unsigned sort_tiles(unsigned n, unsigned n_cap) {
     return (n + sort_tile_keys(n_cap) - 1) / sort_tile_keys(n_cap);
 }
 
-// Emission block geometry (count scan + load-balanced key emission).
+// Emission block geometry (count scan + load-balanced key emission).  The emission walks
+// cells (the tiles of each pair's extent box) and keeps those the cull keeps; the chunk
+// table holds up to kCellsPerKey cells per key of capacity.
 constexpr int kEmitThreads = 256;
 constexpr int kEmitItems = 8;
-constexpr int kEmitBlock = kEmitThreads * kEmitItems;  // 2048 pairs per block
+constexpr int kEmitBlock = kEmitThreads * kEmitItems;  // 2048 pairs (or cells) per block
+constexpr unsigned kCellsPerKey = 2;
+__host__ __device__ constexpr unsigned emit_chunk_cap(unsigned key_cap) {
+    return (unsigned)(((unsigned long long)key_cap * kCellsPerKey + kEmitBlock - 1) / kEmitBlock) + 1u;
+}
 
 // Workspace layout (byte offsets), computed on the host.
 struct Layout {
     size_t hdr, frames;
-    size_t feat0, feat1, feat2, rect, dkey[2], dval[2];
+    size_t feat0, feat1, feat2, rect, ell, dkey[2], dval[2];
     size_t blocksum, blockprefix, offsets, chunk_first;
     size_t g0, g1, g2;
     size_t fp64_list;
@@ -98,7 +108,8 @@ struct Layout {
     unsigned P, tiles, F;
     unsigned tiles_alloc;  // ranges capacity (tile count of the finest tiling, 8x8)
     unsigned key_cap;
-    unsigned look_tiles;   // look-back tiles per buffer
+    unsigned chunk_cap;    // emission chunks (emit_chunk_cap(key_cap))
+    unsigned look_tiles;   // look-back tiles per buffer (sort tiles or emission chunks)
     unsigned emit_blocks;
     int tile_bits;         // live bits of the global tile id
 };
@@ -109,11 +120,12 @@ struct Work {
     DevFrame *frames;
     float4 *feat0, *feat1;
     float *feat2;
-    uint4 *rect;
+    uint4 *rect;   // (x0 | y0 << 16, x1 | y1 << 16, cells, frame | kRectFp64): pixel box of the extent
+    float4 *ell;   // culling record (kx, ds, tc, dn), see cull_record
     unsigned *dkey[2], *dval[2];
     unsigned *blocksum, *blockprefix;
-    unsigned *offsets;  // [P + 1] exclusive key offsets of the pairs in depth order
-    unsigned *chunk_first;  // [key_cap / kEmitBlock + 1] depth-ordered pair owning a chunk's first key
+    unsigned *offsets;      // [P + 1] exclusive cell offsets of the pairs in depth order
+    unsigned *chunk_first;  // [chunk_cap] depth-ordered pair owning a chunk's first cell
     float4 *g0, *g1;
     float *g2;
     unsigned *fp64_list;  // [P] pairs whose geometric chain rule runs in FP64
@@ -147,9 +159,9 @@ const void *setup_kernel_ptr();
 cudaError_t launch_project_fwd(const Work &w, const GaussPtrs &g, int tile_w, int tile_h, int num_sms,
                                cudaStream_t s);
 cudaError_t launch_bin_from_screen(const Work &w, long long n, const float *u, const float *v,
-                                   const float *ex, const float *ey, const float *depth,
-                                   const uint8_t *valid, int tile_w, int tile_h, int32_t *counts,
-                                   cudaStream_t s);
+                                   const float *sxx, const float *sxy, const float *syy, const float *tau,
+                                   const float *depth, const uint8_t *valid, int tile_w, int tile_h,
+                                   int32_t *counts, int num_sms, cudaStream_t s);
 cudaError_t launch_project_bwd(const Work &w, const GaussPtrs &g, const GradPtrs &gr, int mode, int num_sms,
                                cudaStream_t s);
 // FP64 chain rule of the pairs the projection flagged (may run concurrently with the above)
@@ -159,15 +171,16 @@ cudaError_t launch_project_bwd_fp64(const Work &w, const GaussPtrs &g, const Gra
 int sort_passes(int bits);
 cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2], const unsigned *n_dev,
                               unsigned n_cap, int bits, bool vals_identity, bool prepared, int hist_slot,
-                              int ctr_slot, int num_sms, cudaStream_t s, int *result_buf);
+                              int ctr_slot, int num_sms, cudaStream_t s, int *result_buf, int first_pass = 0);
 // Warp-aggregated count of one 8-bit digit per lane into a shared histogram row.
 __device__ __forceinline__ void count_digit(unsigned *row, unsigned d, unsigned active) {
     const unsigned peers = __match_any_sync(active, d);
     if ((threadIdx.x & 31) == (unsigned)(__ffs(peers) - 1)) atomicAdd(row + d, (unsigned)__popc(peers));
 }
 // binning.cu
-cudaError_t launch_emit(const Work &w, int depth_buf, int tile_bits, int tile_hist_slot, int num_sms,
-                        cudaStream_t s);
+// Cell offsets, then key emission fused with the first tile-sort pass: the kept keys land
+// in tkey[1] / tval[1] sorted by their low tile digit.
+cudaError_t launch_emit(const Work &w, int depth_buf, int tile_w, int tile_h, int num_sms, cudaStream_t s);
 cudaError_t launch_ranges(const Work &w, int tile_buf, int num_sms, cudaStream_t s);
 // composite.cu
 cudaError_t launch_composite_fwd(const Work &w, int tile_w, int tile_h, int depth, int tile_buf,
@@ -241,6 +254,221 @@ __device__ __forceinline__ float2 splat_exponent2(float4 f0, float4 f1, float px
     const float bdx = __fmul_rn(f0.w, dx);                  // b' dx
     const float2 t = __ffma2_rn(dup2(bdx), dy, dup2(s0));   // + b' dx dy
     return __ffma2_rn(__fmul2_rn(dup2(f1.x), dy), dy, t);   // + c' dy^2
+}
+
+// ---- onesweep building blocks (256-thread blocks; thread t owns digit t) ---------------
+
+__device__ __forceinline__ unsigned lanemask_lt() {
+    unsigned m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// Exclusive scan of one value per thread over a 256-thread block; returns the total.
+// s_warp: 17 words of shared memory.
+__device__ __forceinline__ unsigned block_excl_scan_256(unsigned x, unsigned *s_warp, unsigned &excl) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    unsigned inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    if (lane == 31) s_warp[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+        unsigned t = lane < 8 ? s_warp[lane] : 0u;
+        unsigned ti = t;
+#pragma unroll
+        for (int o = 1; o < 8; o <<= 1) {
+            unsigned y = __shfl_up_sync(0xffffffffu, ti, o);
+            if (lane >= o) ti += y;
+        }
+        if (lane < 8) s_warp[8 + lane] = ti - t;
+        if (lane == 7) s_warp[16] = ti;
+    }
+    __syncthreads();
+    excl = s_warp[8 + wid] + inc - x;
+    unsigned total = s_warp[16];
+    __syncthreads();
+    return total;
+}
+
+// Status word of one (tile, digit) in a look-back buffer: flag in the top two bits, count
+// below.  Buffers are zeroed (no flag) before a pass uses them.
+constexpr unsigned kFlagAgg = 1u << 30;
+constexpr unsigned kFlagInc = 2u << 30;
+constexpr unsigned kValMask = (1u << 30) - 1u;
+
+// Decoupled look-back of digit t = threadIdx.x for `tile` of a pass over look[tile][256]:
+// publishes the tile's own count (aggregate, then inclusive prefix) and returns the sum
+// of the counts of all earlier tiles.  Every wait is bounded by `limit` polls; a wait that
+// gives up (or finds ERR_TIMEOUT already set) sets ERR_TIMEOUT and gave_up, publishes anyway
+// and returns a partial sum: the caller then writes nothing.  drop (test hook): tile 0
+// never publishes.
+__device__ __forceinline__ unsigned lookback_digit(unsigned *look, unsigned tile, unsigned mine, DevHeader *hdr,
+                                                   long long limit, bool drop, bool &gave_up) {
+    const unsigned t = threadIdx.x;
+    unsigned excl = 0;
+    gave_up = false;
+    if (tile == 0) {
+        if (!drop) atomicExch(look + t, kFlagInc | mine);
+        return 0u;
+    }
+    atomicExch(look + (size_t)tile * kRadix + t, kFlagAgg | mine);
+    long long spins = 0;
+    int j = (int)tile - 1;
+    while (j >= 0) {
+        const unsigned st = *((volatile unsigned *)(look + (size_t)j * kRadix + t));
+        const unsigned fl = st & ~kValMask;
+        if (fl == kFlagInc) { excl += st & kValMask; break; }
+        if (fl == kFlagAgg) { excl += st & kValMask; j--; spins = 0; continue; }
+        if (++spins > limit || (*((volatile unsigned *)&hdr->err) & ERR_TIMEOUT)) {
+            gave_up = true;
+            break;
+        }
+        __nanosleep(32);
+    }
+    if (gave_up) atomicOr(&hdr->err, ERR_TIMEOUT);
+    atomicExch(look + (size_t)tile * kRadix + t, kFlagInc | ((excl + mine) & kValMask));
+    return excl;
+}
+
+// ---- culled tile binning (integer decisions, every FP32 operation explicitly rounded) --
+//
+// A pair is binned from the extent box of its alpha >= 1/255 ellipse d^T Sigma2^-1 d <= tau
+// (half-widths ex = sqrt(tau a), ey = sqrt(tau c) for Sigma2 = [[a, b], [b, c]]): pixel
+// centres x + 0.5 in [u - ex, u + ex], x0 = ceil((u - ex) - 0.5), x1 = floor((u + ex) - 0.5),
+// clipped to the image (same in y).  Its cells are the tiles of that box; a cell is kept
+// when one of its pixel columns has its centre between the two ends of the ellipse over
+// the band of pixel-centre rows of the cell's tile row (clipped to the box).  At offset dy
+// the ellipse spans dx = kx dy +- sqrt((tc - dy^2) dn) with kx = b / c, tc = tau c,
+// dn = det / c^2; over a band [d0, d1] the right end peaks at dy = clamp(ds, d0, d1) and
+// the left end at clamp(-ds, d0, d1), ds = b ex / a (the height of the rightmost point).
+// A near-singular footprint (a c > 64 det) keeps its whole box.  Fixed operation order and
+// rounding, so the FP32 CPU reference reproduces every decision.
+
+struct PixBox {
+    int x0, y0, x1, y1;
+};
+
+// Extent box; false when empty (or tau <= 0: the Gaussian never reaches alpha 1/255).
+__device__ __forceinline__ bool extent_box(float u, float v, float a, float c, float tau, int W, int H, float &ex,
+                                           PixBox &b) {
+    if (!(tau > 0.f)) return false;
+    ex = __fsqrt_rn(__fmul_rn(tau, a));
+    const float ey = __fsqrt_rn(__fmul_rn(tau, c));
+    float x0 = ceilf(__fsub_rn(__fsub_rn(u, ex), 0.5f));
+    float x1 = floorf(__fsub_rn(__fadd_rn(u, ex), 0.5f));
+    float y0 = ceilf(__fsub_rn(__fsub_rn(v, ey), 0.5f));
+    float y1 = floorf(__fsub_rn(__fadd_rn(v, ey), 0.5f));
+    if (x0 < 0.f) x0 = 0.f;
+    if (y0 < 0.f) y0 = 0.f;
+    if (x1 > (float)(W - 1)) x1 = (float)(W - 1);
+    if (y1 > (float)(H - 1)) y1 = (float)(H - 1);
+    if (!(x0 <= x1) || !(y0 <= y1)) return false;
+    b.x0 = (int)x0; b.y0 = (int)y0; b.x1 = (int)x1; b.y1 = (int)y1;
+    return true;
+}
+
+__device__ __forceinline__ float4 cull_record(float a, float b, float c, float tau, float ex) {
+    const float ac = __fmul_rn(a, c), det = __fsub_rn(ac, __fmul_rn(b, b));
+    if (!(a > 0.f) || !(c > 0.f) || ac > __fmul_rn(64.f, det))
+        return make_float4(0.f, 0.f, __int_as_float(0x7f800000), __int_as_float(0x7f800000));
+    return make_float4(__fdiv_rn(b, c), __fdiv_rn(__fmul_rn(b, ex), a), __fmul_rn(tau, c),
+                       __fdiv_rn(det, __fmul_rn(c, c)));
+}
+
+// Pixel columns [i0, i1] of the band of pixel rows [ylo, yhi]; false when none.
+__device__ __forceinline__ bool cull_row(float u, float v, float4 e, int ylo, int yhi, int x0, int x1, int &i0,
+                                         int &i1) {
+    const float d0 = __fsub_rn(__fadd_rn((float)ylo, 0.5f), v), d1 = __fsub_rn(__fadd_rn((float)yhi, 0.5f), v);
+    const float dr = fminf(fmaxf(e.y, d0), d1), dl = fminf(fmaxf(-e.y, d0), d1);
+    const float hr = __fsqrt_rn(fmaxf(__fmul_rn(__fsub_rn(e.z, __fmul_rn(dr, dr)), e.w), 0.f));
+    const float hl = __fsqrt_rn(fmaxf(__fmul_rn(__fsub_rn(e.z, __fmul_rn(dl, dl)), e.w), 0.f));
+    const float xr = __fadd_rn(__fmul_rn(e.x, dr), hr), xl = __fsub_rn(__fmul_rn(e.x, dl), hl);
+    const float f0 = fmaxf(ceilf(__fsub_rn(__fadd_rn(u, xl), 0.5f)), (float)x0);
+    const float f1 = fminf(floorf(__fsub_rn(__fadd_rn(u, xr), 0.5f)), (float)x1);
+    if (!(f0 <= f1)) return false;
+    i0 = (int)f0;
+    i1 = (int)f1;
+    return true;
+}
+
+// Kept tile columns [t0, t1] of tile row ty of a box; false when none.
+__device__ __forceinline__ bool cull_tiles(float u, float v, float4 e, const PixBox &b, int ty, int lw, int lh,
+                                           int &t0, int &t1) {
+    const int ylo = max(ty << lh, b.y0), yhi = min((ty << lh) + (1 << lh) - 1, b.y1);
+    int i0, i1;
+    if (!cull_row(u, v, e, ylo, yhi, b.x0, b.x1, i0, i1)) return false;
+    t0 = i0 >> lw;
+    t1 = i1 >> lw;
+    return true;
+}
+
+__device__ __forceinline__ uint2 pack_box(const PixBox &b) {
+    return make_uint2((unsigned)b.x0 | ((unsigned)b.y0 << 16), (unsigned)b.x1 | ((unsigned)b.y1 << 16));
+}
+
+__device__ __forceinline__ PixBox unpack_box(uint4 r) {
+    PixBox b;
+    b.x0 = (int)(r.x & 0xFFFFu); b.y0 = (int)(r.x >> 16);
+    b.x1 = (int)(r.y & 0xFFFFu); b.y1 = (int)(r.y >> 16);
+    return b;
+}
+
+// Tile-sort digit counts of one tile-id range [t0, t0 + len) (a row run of a pair's kept
+// tiles): digit 0 through a difference array over its 256 values (the range wraps around
+// len >> 8 times plus a partial run), higher digits directly (a run spans one or two of
+// their values).
+__device__ __forceinline__ void count_tile_run(unsigned t0, unsigned len, int passes, int *s_diff, unsigned *s_full,
+                                               unsigned (*s_h)[kRadix]) {
+    const unsigned full = len >> 8, rem = len & 255u;
+    if (full) atomicAdd(s_full, full);
+    if (rem) {
+        const unsigned a = t0 & 255u, e = a + rem;
+        atomicAdd(s_diff + a, 1);
+        if (e <= 256u) {
+            atomicAdd(s_diff + e, -1);
+        } else {
+            atomicAdd(s_diff + 256, -1);
+            atomicAdd(s_diff + 0, 1);
+            atomicAdd(s_diff + (e - 256u), -1);
+        }
+    }
+    const unsigned t1 = t0 + len - 1u;
+    for (int ps = 1; ps < passes; ps++) {
+        const int sh = 8 * ps;
+        for (unsigned h = t0 >> sh; h <= (t1 >> sh); h++) {
+            const unsigned lo = max(t0, h << sh), hi = min(t1, ((h + 1u) << sh) - 1u);
+            atomicAdd(&s_h[ps][h & 255u], hi - lo + 1u);
+        }
+    }
+}
+
+// Flush a block's tile-sort digit counts: digit 0 from its difference array (prefix sum
+// plus the full wraps), higher digits as counted.  Every thread of the block calls it.
+__device__ __forceinline__ void flush_tile_hist(int passes, int *s_diff, unsigned s_full, unsigned (*s_h)[kRadix],
+                                                unsigned *tile_hist) {
+    const int t = threadIdx.x, lane = t & 31;
+    if (t < 32) {
+        int carry = 0;
+        for (int base8 = 0; base8 < 256; base8 += 32) {
+            int x = s_diff[base8 + lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            s_h[0][base8 + lane] = (unsigned)(x + carry) + s_full;
+            carry += __shfl_sync(0xffffffffu, x, 31);
+        }
+    }
+    __syncthreads();
+    for (int i = t; i < passes * kRadix; i += blockDim.x) {
+        const unsigned v = (&s_h[0][0])[i];
+        if (v) atomicAdd(tile_hist + i, v);
+    }
 }
 
 }  // namespace gvk

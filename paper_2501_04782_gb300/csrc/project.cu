@@ -113,40 +113,67 @@ __device__ __forceinline__ void load_and_project(const GaussPtrs &g, long long g
         st.valid = false;
 }
 
-// Tile rectangle of the extent box [u - ex, u + ex] x [v - ey, v + ey]: pixel centres
-// x + 0.5 inside it, x0 = ceil((u - ex) - 0.5), x1 = floor((u + ex) - 0.5), clipped to the
-// image, then divided by the (power-of-two) tile size.  Every operation is rounded to FP32
-// explicitly so the integer result is reproducible.  Returns the tile count (0: empty).
-__device__ __forceinline__ unsigned tile_rect(float u, float v, float ex, float ey, int W, int H,
-                                              int lw, int lh, unsigned &lo, unsigned &hi) {
-    float x0 = ceilf(__fsub_rn(__fsub_rn(u, ex), 0.5f));
-    float x1 = floorf(__fsub_rn(__fadd_rn(u, ex), 0.5f));
-    float y0 = ceilf(__fsub_rn(__fsub_rn(v, ey), 0.5f));
-    float y1 = floorf(__fsub_rn(__fadd_rn(v, ey), 0.5f));
-    if (x0 < 0.f) x0 = 0.f;
-    if (y0 < 0.f) y0 = 0.f;
-    if (x1 > (float)(W - 1)) x1 = (float)(W - 1);
-    if (y1 > (float)(H - 1)) y1 = (float)(H - 1);
-    lo = hi = 0;
-    if (!(x0 <= x1) || !(y0 <= y1)) return 0u;
-    unsigned tx0 = (unsigned)(int)x0 >> lw, tx1 = (unsigned)(int)x1 >> lw;
-    unsigned ty0 = (unsigned)(int)y0 >> lh, ty1 = (unsigned)(int)y1 >> lh;
-    lo = tx0 | (ty0 << 16);
-    hi = tx1 | (ty1 << 16);
-    return (tx1 - tx0 + 1u) * (ty1 - ty0 + 1u);
+// Per-block binning counters of the projection: depth-sort digits (4 passes), tile-sort
+// digits of the kept keys (digit 0 through a difference array), kept-key total.
+struct BinShared {
+    unsigned depth[4][kRadix];
+    unsigned tile[4][kRadix];
+    int diff[257];
+    unsigned full;
+    unsigned long long live;
+};
+
+__device__ __forceinline__ void bin_shared_init(BinShared &sb) {
+    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) {
+        (&sb.depth[0][0])[i] = 0u;
+        (&sb.tile[0][0])[i] = 0u;
+    }
+    for (int i = threadIdx.x; i < 257; i += blockDim.x) sb.diff[i] = 0;
+    if (threadIdx.x == 0) { sb.full = 0u; sb.live = 0ull; }
 }
 
-// Digit histograms of the depth keys for the depth sort (4 passes of 8 bits), counted in
-// shared memory and added to histogram rows 0-3.
-__device__ __forceinline__ void count_depth_digits(unsigned (*s_h)[kRadix], Work &w, unsigned key, bool ok) {
-    const unsigned active = __ballot_sync(0xffffffffu, ok);
-    if (ok)
-        for (int ps = 0; ps < 4; ps++) count_digit(s_h[ps], (key >> (8 * ps)) & 255u, active);
+// Bins one pair (culled rule, see gv_internal.cuh): writes rect and ell, counts the
+// tile-sort digits of its kept row runs; returns its kept-key count (cells in *cells).
+__device__ __forceinline__ unsigned bin_pair(const Work &w, unsigned p, float u, float v, float a, float b, float c,
+                                             float tau, const DevFrame &fr, unsigned frame_word, int lw, int lh,
+                                             int tile_passes, BinShared &sb, unsigned &cells) {
+    float ex;
+    PixBox bx;
+    cells = 0u;
+    unsigned live = 0u;
+    if (!extent_box(u, v, a, c, tau, fr.W, fr.H, ex, bx)) {
+        w.rect[p] = make_uint4(0u, 0u, 0u, frame_word);
+        return 0u;
+    }
+    const int tx0 = bx.x0 >> lw, tx1 = bx.x1 >> lw, ty0 = bx.y0 >> lh, ty1 = bx.y1 >> lh;
+    cells = (unsigned)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+    const float4 e = cull_record(a, b, c, tau, ex);
+    for (int ty = ty0; ty <= ty1; ty++) {
+        int t0, t1;
+        if (!cull_tiles(u, v, e, bx, ty, lw, lh, t0, t1)) continue;
+        const unsigned len = (unsigned)(t1 - t0 + 1);
+        live += len;
+        count_tile_run(fr.tile_offset + (unsigned)ty * fr.tiles_x + (unsigned)t0, len, tile_passes, sb.diff, &sb.full,
+                       sb.tile);
+    }
+    const uint2 pb = pack_box(bx);
+    w.rect[p] = make_uint4(pb.x, pb.y, cells, frame_word);
+    w.ell[p] = e;
+    return live;
+}
+
+// Adds a block's binning counters to the workspace: depth digits to histogram rows 0-3,
+// tile digits to rows 4.., the kept-key total to keys_total.  Every thread calls it.
+__device__ __forceinline__ void bin_shared_flush(const Work &w, BinShared &sb, unsigned live, int tile_passes) {
+    const unsigned long long lsum = __reduce_add_sync(0xffffffffu, live);
+    if ((threadIdx.x & 31) == 0 && lsum) atomicAdd(&sb.live, lsum);
     __syncthreads();
     for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) {
-        const unsigned c = (&s_h[0][0])[i];
+        const unsigned c = (&sb.depth[0][0])[i];
         if (c) atomicAdd(w.hist + i, c);
     }
+    if (threadIdx.x == 0 && sb.live) atomicAdd(&w.hdr->keys_total, sb.live);
+    flush_tile_hist(tile_passes, sb.diff, sb.full, sb.tile, w.hist + 4 * kRadix);
 }
 
 // Ill-conditioned pairs: when Sigma2 is close to singular (a c / det > 64, a Gaussian
@@ -162,12 +189,13 @@ __device__ __forceinline__ bool ill_conditioned(const PairState<float> &st) {
     return st.a * st.c > kFp64Condition * det;
 }
 
-// Grid-stride over the pairs so each block flushes its depth-digit histograms once.
-__global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, int lw, int lh) {
-    __shared__ unsigned s_h[4][kRadix];
-    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0u;
+// Grid-stride over the pairs so each block flushes its counters once.
+__global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, int lw, int lh, int tile_passes) {
+    __shared__ BinShared sb;
+    bin_shared_init(sb);
     __syncthreads();
     const unsigned stride = gridDim.x * blockDim.x;
+    unsigned live_sum = 0;
     // every thread of a block runs the same number of rounds (the warp votes see full warps)
     for (unsigned base = blockIdx.x * blockDim.x; base < w.L.P; base += stride) {
         const unsigned p = base + threadIdx.x;
@@ -179,59 +207,66 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, i
             long long gi = fr.gauss_offset + (long long)(p - fr.pair_offset);
             PairState<float> st;
             load_and_project(g, gi, fr, st);
-            unsigned cnt = 0, lo = 0, hi = 0;
-            // alpha >= 1/255 needs d^T conic d <= tau = 2 ln(255 o); the box of that ellipse
-            const float tau = fminf(2.f * (kLn255 + logf(st.o)), kExtK * kExtK);
-            if (st.valid && tau > 0.f) {
-                const float ex = sqrtf(tau * st.a), ey = sqrtf(tau * st.c);
-                cnt = tile_rect(st.u, st.v, ex, ey, fr.W, fr.H, lw, lh, lo, hi);
+            // alpha >= 1/255 needs d^T conic d <= tau = 2 ln(255 o)
+            const float tau = st.valid ? fminf(2.f * (kLn255 + logf(st.o)), kExtK * kExtK) : 0.f;
+            unsigned cells;
+            const unsigned live = bin_pair(w, p, st.u, st.v, st.a, st.b, st.c, tau, fr, (unsigned)f, lw, lh,
+                                           tile_passes, sb, cells);
+            if (live && ill_conditioned(st)) {  // only kept pairs get a gradient
+                w.fp64_list[atomicAdd(&w.hdr->fp64_count, 1u)] = p;
+                w.rect[p].w = (unsigned)f | kRectFp64;
             }
+            live_sum += live;
             const long long N = g.N;
             w.feat0[p] = make_float4(st.u, st.v, -0.5f * kLog2e * st.A, -kLog2e * st.B);
             w.feat1[p] = make_float4(-0.5f * kLog2e * st.C, log2f(st.o), g.rgb[gi], g.rgb[N + gi]);
             w.feat2[p] = g.rgb[2 * N + gi];
-            unsigned fw = (unsigned)f;
-            if (cnt && ill_conditioned(st)) {  // only binned pairs get a gradient
-                w.fp64_list[atomicAdd(&w.hdr->fp64_count, 1u)] = p;
-                fw |= kRectFp64;
-            }
-            w.rect[p] = make_uint4(lo, hi, cnt, fw);
-            key = cnt ? __float_as_uint(st.zc) : 0xFFFFFFFFu;
+            key = cells ? __float_as_uint(st.zc) : 0xFFFFFFFFu;
             w.dkey[0][p] = key;
         }
         const unsigned active = __ballot_sync(0xffffffffu, in);
         if (in)
-            for (int ps = 0; ps < 4; ps++) count_digit(s_h[ps], (key >> (8 * ps)) & 255u, active);
+            for (int ps = 0; ps < 4; ps++) count_digit(sb.depth[ps], (key >> (8 * ps)) & 255u, active);
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) {
-        const unsigned c = (&s_h[0][0])[i];
-        if (c) atomicAdd(w.hist + i, c);
-    }
+    bin_shared_flush(w, sb, live_sum, tile_passes);
 }
 
-// Stage-isolated binning: screen-space inputs of one frame given by the caller.
-__global__ void __launch_bounds__(256) bin_from_screen_kernel(Work w, long long n, const float *u,
-                                                              const float *v, const float *ex,
-                                                              const float *ey, const float *depth,
-                                                              const uint8_t *valid, int lw, int lh,
+// Stage-isolated binning: screen-space inputs of one frame given by the caller (mean,
+// Sigma2, tau, depth); counts[p] receives the kept-key count.
+__global__ void __launch_bounds__(256) bin_from_screen_kernel(Work w, long long n, const float *u, const float *v,
+                                                              const float *sxx, const float *sxy, const float *syy,
+                                                              const float *tau, const float *depth,
+                                                              const uint8_t *valid, int lw, int lh, int tile_passes,
                                                               int32_t *counts) {
-    __shared__ unsigned s_h[4][kRadix];
-    for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0u;
+    __shared__ BinShared sb;
+    bin_shared_init(sb);
     __syncthreads();
-    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const bool in = p < n;
-    unsigned key = 0xFFFFFFFFu;
-    if (in) {
-        const DevFrame &fr = w.frames[0];
-        unsigned lo = 0, hi = 0, cnt = 0;
-        if (valid[p]) cnt = tile_rect(u[p], v[p], ex[p], ey[p], fr.W, fr.H, lw, lh, lo, hi);
-        w.rect[p] = make_uint4(lo, hi, cnt, 0u);
-        key = cnt ? __float_as_uint(depth[p]) : 0xFFFFFFFFu;
-        w.dkey[0][p] = key;
-        if (counts) counts[p] = (int32_t)cnt;
+    const unsigned stride = gridDim.x * blockDim.x;
+    unsigned live_sum = 0;
+    const DevFrame &fr = w.frames[0];
+    for (unsigned base = blockIdx.x * blockDim.x; base < (unsigned)n; base += stride) {
+        const unsigned p = base + threadIdx.x;
+        const bool in = p < (unsigned)n;
+        unsigned key = 0xFFFFFFFFu;
+        if (in) {
+            unsigned cells = 0, live = 0;
+            if (valid[p]) {
+                live = bin_pair(w, p, u[p], v[p], sxx[p], sxy[p], syy[p], tau[p], fr, 0u, lw, lh, tile_passes, sb,
+                                cells);
+            } else {
+                w.rect[p] = make_uint4(0u, 0u, 0u, 0u);
+            }
+            live_sum += live;
+            w.feat0[p] = make_float4(u[p], v[p], 0.f, 0.f);
+            key = cells ? __float_as_uint(depth[p]) : 0xFFFFFFFFu;
+            w.dkey[0][p] = key;
+            if (counts) counts[p] = (int32_t)live;
+        }
+        const unsigned active = __ballot_sync(0xffffffffu, in);
+        if (in)
+            for (int ps = 0; ps < 4; ps++) count_digit(sb.depth[ps], (key >> (8 * ps)) & 255u, active);
     }
-    count_depth_digits(s_h, w, key, in);  // every thread of the block reaches this call
+    bin_shared_flush(w, sb, live_sum, tile_passes);
 }
 
 // Chain rule of the geometric part of one pair: gradients w.r.t. the screen mean (du, dv)
@@ -416,23 +451,26 @@ __global__ void __launch_bounds__(128) project_bwd_fp64_kernel(Work w, GaussPtrs
 
 }  // namespace
 
+int tile_sort_passes(const Work &w) { return std::max(1, (w.L.tile_bits + 7) / 8); }
+
 cudaError_t launch_project_fwd(const Work &w, const GaussPtrs &g, int tile_w, int tile_h, int num_sms,
                                cudaStream_t s) {
     if (w.L.P == 0) return cudaSuccess;
     int lw = __builtin_ctz(tile_w), lh = __builtin_ctz(tile_h);
     unsigned blocks = std::min((w.L.P + 255u) / 256u, (unsigned)num_sms * 8u);
-    project_fwd_kernel<<<blocks, 256, 0, s>>>(w, g, lw, lh);
+    project_fwd_kernel<<<blocks, 256, 0, s>>>(w, g, lw, lh, tile_sort_passes(w));
     return cudaGetLastError();
 }
 
-cudaError_t launch_bin_from_screen(const Work &w, long long n, const float *u, const float *v,
-                                   const float *ex, const float *ey, const float *depth,
-                                   const uint8_t *valid, int tile_w, int tile_h, int32_t *counts,
+cudaError_t launch_bin_from_screen(const Work &w, long long n, const float *u, const float *v, const float *sxx,
+                                   const float *sxy, const float *syy, const float *tau, const float *depth,
+                                   const uint8_t *valid, int tile_w, int tile_h, int32_t *counts, int num_sms,
                                    cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     int lw = __builtin_ctz(tile_w), lh = __builtin_ctz(tile_h);
-    bin_from_screen_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w, n, u, v, ex, ey, depth, valid,
-                                                                        lw, lh, counts);
+    unsigned blocks = std::min((unsigned)((n + 255) / 256), (unsigned)num_sms * 8u);
+    bin_from_screen_kernel<<<blocks, 256, 0, s>>>(w, n, u, v, sxx, sxy, syy, tau, depth, valid, lw, lh,
+                                                   tile_sort_passes(w), counts);
     return cudaGetLastError();
 }
 

@@ -1,6 +1,6 @@
 // sort.cu -- stable LSD radix sort of (32-bit key, 32-bit value) pairs, 8 bits per pass.
 //
-// One pass is a single "onesweep" kernel: each block takes the next 3840-key tile from an
+// One pass is a single "onesweep" kernel: each block takes the next 3072-key tile from an
 // atomic counter, ranks its keys stably per digit (warp match + per-warp histograms),
 // publishes its per-digit counts, obtains the exclusive prefix of all earlier tiles by
 // decoupled look-back, and scatters.  The per-digit global offsets come from one
@@ -18,45 +18,6 @@
 namespace gvk {
 
 namespace {
-
-constexpr unsigned kFlagAgg = 1u << 30;
-constexpr unsigned kFlagInc = 2u << 30;
-constexpr unsigned kValMask = (1u << 30) - 1u;
-
-__device__ __forceinline__ unsigned lanemask_lt() {
-    unsigned m;
-    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-    return m;
-}
-
-// Exclusive scan of one value per thread over a 256-thread block; returns the total.
-__device__ __forceinline__ unsigned block_excl_scan_256(unsigned x, unsigned *s_warp, unsigned &excl) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned inc = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) s_warp[wid] = inc;
-    __syncthreads();
-    if (wid == 0) {
-        unsigned t = lane < 8 ? s_warp[lane] : 0u;
-        unsigned ti = t;
-#pragma unroll
-        for (int o = 1; o < 8; o <<= 1) {
-            unsigned y = __shfl_up_sync(0xffffffffu, ti, o);
-            if (lane >= o) ti += y;
-        }
-        if (lane < 8) s_warp[8 + lane] = ti - t;
-        if (lane == 7) s_warp[16] = ti;
-    }
-    __syncthreads();
-    excl = s_warp[8 + wid] + inc - x;
-    unsigned total = s_warp[16];
-    __syncthreads();
-    return total;
-}
 
 // Per-pass digit histograms of n keys (passes of 8 bits starting at bit 0); also clears
 // look-back buffer 0 for the tiles this sort will use.
@@ -99,7 +60,7 @@ struct PassArgs {
 };
 
 template <int ITEMS>
-__global__ void __launch_bounds__(kSortThreads, ITEMS > 8 ? 3 : 4) sort_pass_kernel(PassArgs a) {
+__global__ void __launch_bounds__(kSortThreads, 4) sort_pass_kernel(PassArgs a) {
     constexpr int TILE = kSortThreads * ITEMS;
     __shared__ unsigned s_keys[TILE];
     __shared__ unsigned s_vals[TILE];
@@ -164,31 +125,9 @@ __global__ void __launch_bounds__(kSortThreads, ITEMS > 8 ? 3 : 4) sort_pass_ker
         if (t == 255 && base + TILE > n) tail = base + TILE - n;
         const unsigned mine = total - tail;
         // decoupled look-back for digit t
-        unsigned excl = 0;
-        if (tile == 0) {
-            if (!drop) atomicExch(a.look_cur + t, kFlagInc | mine);
-        } else {
-            atomicExch(a.look_cur + (size_t)tile * kRadix + t, kFlagAgg | mine);
-            long long spins = 0;
-            int j = (int)tile - 1;
-            bool gave_up = false;
-            while (j >= 0) {
-                unsigned st = *((volatile unsigned *)(a.look_cur + (size_t)j * kRadix + t));
-                unsigned fl = st & ~kValMask;
-                if (fl == kFlagInc) { excl += st & kValMask; break; }
-                if (fl == kFlagAgg) { excl += st & kValMask; j--; spins = 0; continue; }
-                if (++spins > limit || (*((volatile unsigned *)&a.hdr->err) & ERR_TIMEOUT)) {
-                    gave_up = true;
-                    break;
-                }
-                __nanosleep(32);
-            }
-            if (gave_up) {
-                atomicOr(&a.hdr->err, ERR_TIMEOUT);
-                s_abort = 1;
-            }
-            atomicExch(a.look_cur + (size_t)tile * kRadix + t, kFlagInc | ((excl + mine) & kValMask));
-        }
+        bool gave_up = false;
+        const unsigned excl = lookback_digit(a.look_cur, tile, mine, a.hdr, limit, drop, gave_up);
+        if (gave_up) s_abort = 1;
         unsigned dex;
         block_excl_scan_256(total, s_scan, dex);
         s_dstart[t] = dex;
@@ -227,28 +166,30 @@ int sort_passes(int bits) { return bits <= 0 ? 0 : (bits + 7) / 8; }
 // workspace (0 or 4), ctr_slot 4 tile counters (both zero on entry: the setup kernel
 // clears them).  prepared: the producer of the keys already counted every pass's digits
 // into those rows and cleared look-back buffer 0 for sort_tiles(n, n_cap) tiles;
-// otherwise a histogram kernel does both first.
+// otherwise a histogram kernel does both first.  first_pass > 0: the first passes were
+// done by the producer (the keys sorted by their low 8 * first_pass bits are in buffer
+// first_pass & 1, and the look-back buffer of pass first_pass is cleared).
 cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2], const unsigned *n_dev,
                               unsigned n_cap, int bits, bool vals_identity, bool prepared, int hist_slot,
-                              int ctr_slot, int num_sms, cudaStream_t s, int *result_buf) {
+                              int ctr_slot, int num_sms, cudaStream_t s, int *result_buf, int first_pass) {
     int passes = sort_passes(bits);
-    *result_buf = 0;
-    if (passes == 0 || n_cap == 0) return cudaSuccess;
+    *result_buf = first_pass & 1;
+    if (passes <= first_pass || n_cap == 0) return cudaSuccess;
     unsigned *hist = w.hist + (size_t)hist_slot * kRadix;
     const unsigned max_tiles = sort_tiles(n_cap, n_cap);
     unsigned *look[2] = {w.look, w.look + (size_t)w.L.look_tiles * kRadix};
     cudaError_t e;
-    if (!prepared) {
+    if (!prepared && first_pass == 0) {
         int hist_blocks = (int)std::min<unsigned>((n_cap + 255) / 256, (unsigned)num_sms * 4u);
         sort_hist_kernel<<<hist_blocks, 256, 0, s>>>(keys[0], n_dev, n_cap, passes, hist, look[0]);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
     const bool small = sort_items(n_cap) == 4;
-    const int per_sm = small ? 4 : 3;  // resident blocks per SM (launch bounds)
+    const int per_sm = 4;  // resident blocks per SM (launch bounds)
     int grid = (int)std::min<unsigned>(max_tiles, (unsigned)num_sms * per_sm);
-    int cur = 0;
-    for (int ps = 0; ps < passes; ps++) {
+    int cur = first_pass & 1;
+    for (int ps = first_pass; ps < passes; ps++) {
         PassArgs a;
         a.keys_in = keys[cur];
         a.vals_in = (ps == 0 && vals_identity) ? nullptr : vals[cur];
@@ -264,7 +205,7 @@ cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2
                 ctr_slot + ps;
         a.hdr = w.hdr;
         if (small) sort_pass_kernel<4><<<grid, kSortThreads, 0, s>>>(a);
-        else sort_pass_kernel<15><<<grid, kSortThreads, 0, s>>>(a);
+        else sort_pass_kernel<12><<<grid, kSortThreads, 0, s>>>(a);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         cur ^= 1;

@@ -98,7 +98,8 @@ _SIGS = {
     "gv_graph_set_frames": [_vp, ctypes.POINTER(FrameDesc), ctypes.c_int32],
     "gv_graph_launch": [_vp, _vp],
     "gv_graph_destroy": [_vp],
-    "gv_debug_bin_sort": [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32, _vp,
+    "gv_debug_bin_sort": [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32,
+                          _vp,
                           ctypes.c_size_t, _vp, _vp, _vp, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), _vp],
     "gv_debug_read": [_vp, ctypes.POINTER(FrameDesc), ctypes.c_int32, _vp, ctypes.c_size_t, _vp, _vp, _vp, _vp, _vp,
                       _vp, _vp, _vp, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
@@ -352,13 +353,13 @@ class Context:
     def debug_set_wait(self, spin_limit: int = 0, drop_signal: bool = False):
         self.check(self.lib.gv_debug_set_wait(self.h, int(spin_limit), 1 if drop_signal else 0))
 
-    def debug_bin_sort(self, u, v, ex, ey, depth, valid, W: int, H: int, ws, counts, sorted_tile, sorted_id,
-                       stream=None) -> int:
+    def debug_bin_sort(self, u, v, sxx, sxy, syy, tau, depth, valid, W: int, H: int, ws, counts, sorted_tile,
+                       sorted_id, stream=None) -> int:
         K = ctypes.c_int64()
-        self.check(self.lib.gv_debug_bin_sort(self.h, u.numel(), _ptr(u), _ptr(v), _ptr(ex), _ptr(ey), _ptr(depth),
-                                              _ptr(valid), int(W), int(H), _ptr(ws), ws.numel(), _ptr(counts),
-                                              _ptr(sorted_tile), _ptr(sorted_id), sorted_id.numel(),
-                                              ctypes.byref(K), _stream_handle(stream)))
+        self.check(self.lib.gv_debug_bin_sort(self.h, u.numel(), _ptr(u), _ptr(v), _ptr(sxx), _ptr(sxy), _ptr(syy),
+                                              _ptr(tau), _ptr(depth), _ptr(valid), int(W), int(H), _ptr(ws),
+                                              ws.numel(), _ptr(counts), _ptr(sorted_tile), _ptr(sorted_id),
+                                              sorted_id.numel(), ctypes.byref(K), _stream_handle(stream)))
         return K.value
 
     def debug_read(self, frames, ws, P: int, K_cap: int, tiles_cap: int, stream=None) -> dict:

@@ -14,30 +14,40 @@ TILES = [(8, 8), (16, 8), (16, 16)]
 
 
 def screen_inputs(seed, n, W, H, tie_depths=False, frac_invalid=0.05):
+    """Screen-space Gaussians as the projection makes them: Sigma2 = R diag(s^2) R^T + 0.3 I
+    (anisotropic, any angle, some near-singular), tau = 2 ln(255 o) capped at 2 ln 255."""
     rng = np.random.default_rng(seed)
-    u = rng.uniform(-30, W + 30, n).astype(np.float32)
-    v = rng.uniform(-30, H + 30, n).astype(np.float32)
-    ex = (rng.lognormal(1.5, 1.0, n)).astype(np.float32)
-    ey = (rng.lognormal(1.5, 1.0, n)).astype(np.float32)
+    u = rng.uniform(-30, W + 30, n)
+    v = rng.uniform(-30, H + 30, n)
+    s1 = np.exp(rng.normal(1.5, 1.0, n))
+    s2 = s1 * np.exp(-rng.exponential(1.0, n))
+    th = rng.uniform(0, np.pi, n)
+    c, s_ = np.cos(th), np.sin(th)
+    sxx = c * c * s1 ** 2 + s_ * s_ * s2 ** 2 + 0.3
+    syy = s_ * s_ * s1 ** 2 + c * c * s2 ** 2 + 0.3
+    sxy = c * s_ * (s1 ** 2 - s2 ** 2)
+    tau = np.minimum(2 * np.log(255 * rng.uniform(0.002, 0.995, n)), 2 * np.log(255.0))
     if tie_depths:
         depth = rng.choice(np.array([0.5, 1.25, 3.0, 7.5], np.float32), n)
     else:
         depth = rng.uniform(0.2, 50.0, n).astype(np.float32)
     valid = (rng.uniform(size=n) > frac_invalid).astype(np.uint8)
-    return u, v, ex, ey, depth, valid
+    f = lambda x: x.astype(np.float32)
+    return f(u), f(v), f(sxx), f(sxy), f(syy), f(tau), depth, valid
 
 
-def run_bin_sort(ctx, u, v, ex, ey, depth, valid, W, H):
+def run_bin_sort(ctx, u, v, sxx, sxy, syy, tau, depth, valid, W, H):
     n = len(u)
     t = lambda a, dt=torch.float32: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt)
     frames = [gv.Frame(synth.Camera(W, H, 1.0, 1.0, 0.0, 0.0), 0, n, 0)]
-    cnt_ref, _ = oracle.bin_f32(u, v, ex, ey, valid, W, H, *ctx_tile(ctx))
+    cnt_ref, _, _ = oracle.cull_f32(u, v, sxx, sxy, syy, tau, valid, W, H, *ctx_tile(ctx))
     K_ref = int(cnt_ref.sum())
     ws = torch.empty(ctx.workspace_size(frames, K_ref + 16), dtype=torch.uint8, device="cuda")
     counts = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
     st = torch.empty(max(K_ref, 1), dtype=torch.int32, device="cuda")
     si = torch.empty(max(K_ref, 1), dtype=torch.int32, device="cuda")
-    K = ctx.debug_bin_sort(t(u), t(v), t(ex), t(ey), t(depth), t(valid, torch.uint8), W, H, ws, counts, st, si)
+    K = ctx.debug_bin_sort(t(u), t(v), t(sxx), t(sxy), t(syy), t(tau), t(depth), t(valid, torch.uint8), W, H, ws,
+                           counts, st, si)
     return K, counts.cpu().numpy()[:n], st.cpu().numpy()[:K].view(np.uint32), si.cpu().numpy()[:K].view(np.uint32)
 
 
@@ -52,14 +62,15 @@ def test_binning_and_sort_bit_exact(tile, case):
     W, H = {"random": (300, 200), "ties": (256, 128), "ragged_small": (37, 21), "one": (64, 64),
             "many_keys": (1000, 700)}[case]
     n = {"random": 20000, "ties": 9001, "ragged_small": 57, "one": 1, "many_keys": 60000}[case]
-    u, v, ex, ey, depth, valid = screen_inputs(hash((case, tile)) % 2**31, n, W, H, tie_depths=(case == "ties"))
+    u, v, sxx, sxy, syy, tau, depth, valid = screen_inputs(hash((case, tile)) % 2**31, n, W, H,
+                                                           tie_depths=(case == "ties"))
     if case == "one":
-        u[:], v[:], ex[:], ey[:], valid[:] = 32.0, 32.0, 100.0, 100.0, 1
+        u[:], v[:], sxx[:], sxy[:], syy[:], tau[:], valid[:] = 32.0, 32.0, 900.0, 0.0, 900.0, 11.0, 1
     ctx = gv.Context(tile, 64)
-    K, counts, s_tile, s_id = run_bin_sort(ctx, u, v, ex, ey, depth, valid, W, H)
-    cnt_ref, rect_ref = oracle.bin_f32(u, v, ex, ey, valid, W, H, *tile)
+    K, counts, s_tile, s_id = run_bin_sort(ctx, u, v, sxx, sxy, syy, tau, depth, valid, W, H)
+    cnt_ref, rect_ref, cells_ref = oracle.cull_f32(u, v, sxx, sxy, syy, tau, valid, W, H, *tile)
     assert np.array_equal(counts, cnt_ref)
-    keys, vals = oracle.emit_keys(cnt_ref, rect_ref, depth, (W + tile[0] - 1) // tile[0])
+    keys, vals = oracle.emit_cull_keys(u, v, sxx, sxy, syy, tau, valid, W, H, *tile, depth)
     sk, sv = oracle.sorted_keys(keys, vals)
     assert K == len(sk)
     assert np.array_equal(s_tile.astype(np.uint64), sk >> np.uint64(32))
@@ -67,14 +78,16 @@ def test_binning_and_sort_bit_exact(tile, case):
     # the 64-bit keys rebuilt from (tile, id) equal the reference keys
     rebuilt = (s_tile.astype(np.uint64) << np.uint64(32)) | depth.view(np.uint32)[s_id].astype(np.uint64)
     assert np.array_equal(rebuilt, sk)
+    if case in ("random", "many_keys"):
+        assert cnt_ref.sum() < cells_ref.sum()  # the cull removed cells
     if case == "many_keys":
-        assert K > 3 * 3840  # several sort tiles and a ragged tail
+        assert K > 3 * 3072  # several sort tiles and a ragged tail
 
 
 def test_binning_empty_input():
     ctx = gv.Context((16, 16), 64)
     e = np.zeros(0, np.float32)
-    K, counts, st, si = run_bin_sort(ctx, e, e, e, e, e, np.zeros(0, np.uint8), 64, 48)
+    K, counts, st, si = run_bin_sort(ctx, e, e, e, e, e, e, e, np.zeros(0, np.uint8), 64, 48)
     assert K == 0
 
 
@@ -102,7 +115,8 @@ def test_projection_matches_fp64(wl):
         assert np.all(np.abs(co[i, vis] - ref[k][vis]) <= 2e-5 * scale), k
     assert np.allclose(op, ref["o"], rtol=2e-6, atol=1e-7)
     assert np.allclose(dep[vis], ref["depth"][vis], rtol=2e-6)
-    # tile counts: bit-exact against the FP64 rule except within 1e-3 px of a pixel-centre edge
+    # cell counts (tiles of the extent box): bit-exact against the FP64 rule except within
+    # 1e-3 px of a pixel-centre edge
     diff = cnt_gpu != cnt64
     print(f"[counts {wl}] mismatches {diff.sum()} of {len(diff)}; margins {margin[diff][:10]}")
     assert np.all(margin[diff] < 1e-3)
@@ -110,7 +124,13 @@ def test_projection_matches_fp64(wl):
     # the whole pipeline's sorted list equals the reference list built from the GPU's own
     # screen-space outputs (stage-isolated reference of the sort)
     K = d["K"]
-    assert K == int(cnt_gpu.sum())
+    assert 0 < K <= int(cnt_gpu.sum())
+    # kept keys: the culled rule on the FP64 projection (rounded to FP32) agrees up to pairs
+    # whose decisions sit within rounding of a threshold
+    tau = np.minimum(2 * np.log(255 * ref["o"]), 2 * np.log(255.0))
+    live_ref, _, _ = oracle.cull_f32(ref["u"], ref["v"], ref["a"], ref["b"], ref["c"], tau, valid, cam.W, cam.H,
+                                     16, 16)
+    assert abs(K - int(live_ref.sum())) <= max(4, 2e-4 * K), (K, int(live_ref.sum()))
     s_id = d["sorted_id"].cpu().numpy().view(np.uint32).astype(np.int64)
     s_tile = d["sorted_tile"].cpu().numpy().view(np.uint32).astype(np.int64)
     assert np.all(np.diff(s_tile) >= 0)
