@@ -302,10 +302,14 @@ constexpr unsigned kValMask = (1u << 30) - 1u;
 
 // Decoupled look-back of digit t = threadIdx.x for `tile` of a pass over look[tile][256]:
 // publishes the tile's own count (aggregate, then inclusive prefix) and returns the sum
-// of the counts of all earlier tiles.  Every wait is bounded by `limit` polls; a wait that
-// gives up (or finds ERR_TIMEOUT already set) sets ERR_TIMEOUT and gave_up, publishes anyway
-// and returns a partial sum: the caller then writes nothing.  drop (test hook): tile 0
-// never publishes.
+// of the counts of all earlier tiles.  The predecessors are read kLookWindow at a time
+// (independent loads in flight), their aggregates summed until an inclusive prefix is
+// found; an unpublished predecessor is polled again.  Every wait is bounded by `limit`
+// polls without progress; a wait that gives up (or finds ERR_TIMEOUT already set) sets
+// ERR_TIMEOUT and gave_up, publishes anyway and returns a partial sum: the caller then
+// writes nothing.  drop (test hook): tile 0 never publishes.
+constexpr int kLookWindow = 4;
+
 __device__ __forceinline__ unsigned lookback_digit(unsigned *look, unsigned tile, unsigned mine, DevHeader *hdr,
                                                    long long limit, bool drop, bool &gave_up) {
     const unsigned t = threadIdx.x;
@@ -318,11 +322,31 @@ __device__ __forceinline__ unsigned lookback_digit(unsigned *look, unsigned tile
     atomicExch(look + (size_t)tile * kRadix + t, kFlagAgg | mine);
     long long spins = 0;
     int j = (int)tile - 1;
-    while (j >= 0) {
-        const unsigned st = *((volatile unsigned *)(look + (size_t)j * kRadix + t));
-        const unsigned fl = st & ~kValMask;
-        if (fl == kFlagInc) { excl += st & kValMask; break; }
-        if (fl == kFlagAgg) { excl += st & kValMask; j--; spins = 0; continue; }
+    bool found = false;
+    while (!found) {
+        unsigned st[kLookWindow];
+#pragma unroll
+        for (int k = 0; k < kLookWindow; k++)
+            st[k] = j - k >= 0 ? *((volatile unsigned *)(look + (size_t)(j - k) * kRadix + t)) : 0u;
+        int adv = 0;
+#pragma unroll
+        for (int k = 0; k < kLookWindow; k++) {
+            if (found || adv < k || j - k < 0) continue;  // stop at the first unpublished status
+            const unsigned fl = st[k] & ~kValMask;
+            if (fl == kFlagInc) {
+                excl += st[k] & kValMask;
+                found = true;
+            } else if (fl == kFlagAgg) {
+                excl += st[k] & kValMask;
+                adv = k + 1;
+            }
+        }
+        if (found) break;
+        j -= adv;
+        if (adv > 0) {
+            spins = 0;
+            continue;
+        }
         if (++spins > limit || (*((volatile unsigned *)&hdr->err) & ERR_TIMEOUT)) {
             gave_up = true;
             break;

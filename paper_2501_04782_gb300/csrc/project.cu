@@ -132,33 +132,84 @@ __device__ __forceinline__ void bin_shared_init(BinShared &sb) {
     if (threadIdx.x == 0) { sb.full = 0u; sb.live = 0ull; }
 }
 
-// Bins one pair (culled rule, see gv_internal.cuh): writes rect and ell, counts the
-// tile-sort digits of its kept row runs; returns its kept-key count (cells in *cells).
+// Bins one pair (culled rule, see gv_internal.cuh), the per-pair part: extent box, cells,
+// cull record (rect and ell written).  Returns the number of tile rows of its box (0 when
+// it bins nothing); the rows are culled by warp_cull_rows.
+struct PairBin {
+    float u, v;
+    float4 e;
+    uint2 box;
+    unsigned tile_offset, tiles_x;
+    int rows;
+};
+
 __device__ __forceinline__ unsigned bin_pair(const Work &w, unsigned p, float u, float v, float a, float b, float c,
                                              float tau, const DevFrame &fr, unsigned frame_word, int lw, int lh,
-                                             int tile_passes, BinShared &sb, unsigned &cells) {
+                                             PairBin &pb) {
     float ex;
     PixBox bx;
-    cells = 0u;
-    unsigned live = 0u;
+    pb.u = u; pb.v = v; pb.rows = 0;
+    pb.tile_offset = fr.tile_offset; pb.tiles_x = fr.tiles_x;
     if (!extent_box(u, v, a, c, tau, fr.W, fr.H, ex, bx)) {
         w.rect[p] = make_uint4(0u, 0u, 0u, frame_word);
+        pb.box = make_uint2(0u, 0u);
+        pb.e = make_float4(0.f, 0.f, 0.f, 0.f);
         return 0u;
     }
     const int tx0 = bx.x0 >> lw, tx1 = bx.x1 >> lw, ty0 = bx.y0 >> lh, ty1 = bx.y1 >> lh;
-    cells = (unsigned)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
-    const float4 e = cull_record(a, b, c, tau, ex);
-    for (int ty = ty0; ty <= ty1; ty++) {
-        int t0, t1;
-        if (!cull_tiles(u, v, e, bx, ty, lw, lh, t0, t1)) continue;
-        const unsigned len = (unsigned)(t1 - t0 + 1);
-        live += len;
-        count_tile_run(fr.tile_offset + (unsigned)ty * fr.tiles_x + (unsigned)t0, len, tile_passes, sb.diff, &sb.full,
-                       sb.tile);
+    const unsigned cells = (unsigned)((tx1 - tx0 + 1) * (ty1 - ty0 + 1));
+    pb.e = cull_record(a, b, c, tau, ex);
+    pb.box = pack_box(bx);
+    pb.rows = ty1 - ty0 + 1;
+    w.rect[p] = make_uint4(pb.box.x, pb.box.y, cells, frame_word);
+    w.ell[p] = pb.e;
+    return cells;
+}
+
+// The rows of the warp's 32 pairs, culled by the warp together (lane l takes rows l,
+// l + 32, ... of the concatenated row list, so a pair with many tile rows does not hold
+// the other lanes back): counts the tile-sort digits of the kept row runs.  Returns the
+// kept keys of the rows this lane processed; with PER_PAIR, also adds each row's kept
+// keys to s_pair_live[owner lane].  Every lane of the warp calls it.
+template <bool PER_PAIR>
+__device__ __forceinline__ unsigned warp_cull_rows(const PairBin &pb, int lw, int lh, int tile_passes, BinShared &sb,
+                                                   unsigned *s_pair_live) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    int inc = pb.rows;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
     }
-    const uint2 pb = pack_box(bx);
-    w.rect[p] = make_uint4(pb.x, pb.y, cells, frame_word);
-    w.ell[p] = e;
+    const int start = inc - pb.rows, R = __shfl_sync(FULL, inc, 31);
+    unsigned live = 0;
+    for (int base = 0; base < R; base += 32) {
+        const int r = base + lane;
+        int lo = 0, hi = 31;  // owner: the last lane whose rows start at or before r
+#pragma unroll
+        for (int it = 0; it < 5; it++) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (__shfl_sync(FULL, start, mid) <= r) lo = mid; else hi = mid - 1;
+        }
+        const float u = __shfl_sync(FULL, pb.u, lo), v = __shfl_sync(FULL, pb.v, lo);
+        const float4 e = make_float4(__shfl_sync(FULL, pb.e.x, lo), __shfl_sync(FULL, pb.e.y, lo),
+                                     __shfl_sync(FULL, pb.e.z, lo), __shfl_sync(FULL, pb.e.w, lo));
+        const uint4 rb = make_uint4(__shfl_sync(FULL, pb.box.x, lo), __shfl_sync(FULL, pb.box.y, lo), 0u, 0u);
+        const unsigned toff = __shfl_sync(FULL, pb.tile_offset, lo), tx = __shfl_sync(FULL, pb.tiles_x, lo);
+        const int ostart = __shfl_sync(FULL, start, lo);
+        if (r < R) {
+            const PixBox bx = unpack_box(rb);
+            const int ty = (bx.y0 >> lh) + (r - ostart);
+            int t0, t1;
+            if (cull_tiles(u, v, e, bx, ty, lw, lh, t0, t1)) {
+                const unsigned len = (unsigned)(t1 - t0 + 1);
+                live += len;
+                count_tile_run(toff + (unsigned)ty * tx + (unsigned)t0, len, tile_passes, sb.diff, &sb.full, sb.tile);
+                if (PER_PAIR) atomicAdd(s_pair_live + lo, len);
+            }
+        }
+    }
     return live;
 }
 
@@ -201,6 +252,8 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, i
         const unsigned p = base + threadIdx.x;
         const bool in = p < w.L.P;
         unsigned key = 0xFFFFFFFFu;
+        PairBin pb;
+        pb.rows = 0;
         if (in) {
             int f = find_frame_by_pair(w.frames, (int)w.L.F, p);
             const DevFrame &fr = w.frames[f];
@@ -209,14 +262,11 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, i
             load_and_project(g, gi, fr, st);
             // alpha >= 1/255 needs d^T conic d <= tau = 2 ln(255 o)
             const float tau = st.valid ? fminf(2.f * (kLn255 + logf(st.o)), kExtK * kExtK) : 0.f;
-            unsigned cells;
-            const unsigned live = bin_pair(w, p, st.u, st.v, st.a, st.b, st.c, tau, fr, (unsigned)f, lw, lh,
-                                           tile_passes, sb, cells);
-            if (live && ill_conditioned(st)) {  // only kept pairs get a gradient
+            const unsigned cells = bin_pair(w, p, st.u, st.v, st.a, st.b, st.c, tau, fr, (unsigned)f, lw, lh, pb);
+            if (cells && ill_conditioned(st)) {  // only binned pairs get a gradient
                 w.fp64_list[atomicAdd(&w.hdr->fp64_count, 1u)] = p;
                 w.rect[p].w = (unsigned)f | kRectFp64;
             }
-            live_sum += live;
             const long long N = g.N;
             w.feat0[p] = make_float4(st.u, st.v, -0.5f * kLog2e * st.A, -kLog2e * st.B);
             w.feat1[p] = make_float4(-0.5f * kLog2e * st.C, log2f(st.o), g.rgb[gi], g.rgb[N + gi]);
@@ -224,6 +274,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, i
             key = cells ? __float_as_uint(st.zc) : 0xFFFFFFFFu;
             w.dkey[0][p] = key;
         }
+        live_sum += warp_cull_rows<false>(pb, lw, lh, tile_passes, sb, nullptr);
         const unsigned active = __ballot_sync(0xffffffffu, in);
         if (in)
             for (int ps = 0; ps < 4; ps++) count_digit(sb.depth[ps], (key >> (8 * ps)) & 255u, active);
@@ -239,29 +290,32 @@ __global__ void __launch_bounds__(256) bin_from_screen_kernel(Work w, long long 
                                                               const uint8_t *valid, int lw, int lh, int tile_passes,
                                                               int32_t *counts) {
     __shared__ BinShared sb;
+    __shared__ unsigned s_live[256];
     bin_shared_init(sb);
     __syncthreads();
     const unsigned stride = gridDim.x * blockDim.x;
     unsigned live_sum = 0;
     const DevFrame &fr = w.frames[0];
+    unsigned *s_warp_live = s_live + (threadIdx.x & ~31u);
     for (unsigned base = blockIdx.x * blockDim.x; base < (unsigned)n; base += stride) {
         const unsigned p = base + threadIdx.x;
         const bool in = p < (unsigned)n;
         unsigned key = 0xFFFFFFFFu;
+        PairBin pb;
+        pb.rows = 0;
+        s_live[threadIdx.x] = 0u;
         if (in) {
-            unsigned cells = 0, live = 0;
-            if (valid[p]) {
-                live = bin_pair(w, p, u[p], v[p], sxx[p], sxy[p], syy[p], tau[p], fr, 0u, lw, lh, tile_passes, sb,
-                                cells);
-            } else {
-                w.rect[p] = make_uint4(0u, 0u, 0u, 0u);
-            }
-            live_sum += live;
+            unsigned cells = 0;
+            if (valid[p]) cells = bin_pair(w, p, u[p], v[p], sxx[p], sxy[p], syy[p], tau[p], fr, 0u, lw, lh, pb);
+            else w.rect[p] = make_uint4(0u, 0u, 0u, 0u);
             w.feat0[p] = make_float4(u[p], v[p], 0.f, 0.f);
             key = cells ? __float_as_uint(depth[p]) : 0xFFFFFFFFu;
             w.dkey[0][p] = key;
-            if (counts) counts[p] = (int32_t)live;
         }
+        __syncwarp();
+        live_sum += warp_cull_rows<true>(pb, lw, lh, tile_passes, sb, s_warp_live);
+        __syncwarp();
+        if (in && counts) counts[p] = (int32_t)s_live[threadIdx.x];
         const unsigned active = __ballot_sync(0xffffffffu, in);
         if (in)
             for (int ps = 0; ps < 4; ps++) count_digit(sb.depth[ps], (key >> (8 * ps)) & 255u, active);
