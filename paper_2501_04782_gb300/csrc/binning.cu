@@ -175,6 +175,8 @@ __global__ void __launch_bounds__(kEmitThreads) offsets_kernel(Work w, const uns
 // id) is scattered to its first-pass position: out of this kernel the kept keys are
 // compacted and sorted by the low tile digit, in depth order within a digit.  The global
 // digit offsets come from the projection's counts of the kept keys.
+constexpr int kEmitSmemFrames = 64;
+
 struct EmitSortArgs {
     const unsigned *order;  // depth-sorted pair ids
     unsigned *keys_out, *vals_out;
@@ -194,6 +196,7 @@ __global__ void __launch_bounds__(kEmitThreads, 4) emit_sort_kernel(Work w, Emit
     __shared__ int s_wmax[kEmitThreads / 32];
     __shared__ unsigned s_chunk, s_lo, s_n;
     __shared__ int s_abort;
+    __shared__ uint2 s_frames[kEmitSmemFrames];  // (tile_offset, tiles_x) of the first frames
     unsigned *s_keys = reinterpret_cast<unsigned *>(s_owner);
     unsigned *s_vals = s_pair;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
@@ -204,6 +207,8 @@ __global__ void __launch_bounds__(kEmitThreads, 4) emit_sort_kernel(Work w, Emit
     const unsigned next_tiles = sort_tiles(w.hdr->keys_used, w.L.key_cap);
     for (unsigned i = blockIdx.x * kEmitThreads + t; i < next_tiles * kRadix; i += gridDim.x * kEmitThreads)
         a.look_next[i] = 0u;
+    for (int i = t; i < (int)min(w.L.F, (unsigned)kEmitSmemFrames); i += kEmitThreads)
+        s_frames[i] = make_uint2(w.frames[i].tile_offset, w.frames[i].tiles_x);
     {
         unsigned ex;
         block_excl_scan_256(a.hist[t], s_scan, ex);
@@ -277,7 +282,9 @@ __global__ void __launch_bounds__(kEmitThreads, 4) emit_sort_kernel(Work w, Emit
                 const unsigned j = k0 + e - s_off[oi];
                 const unsigned p = s_pair[oi];
                 const uint4 r = w.rect[p];  // consecutive cells mostly share a pair: L1 hits
-                const DevFrame &fr = w.frames[min(r.w & kRectFrame, w.L.F - 1u)];
+                const unsigned fi = min(r.w & kRectFrame, w.L.F - 1u);
+                const uint2 fg =
+                    fi < (unsigned)kEmitSmemFrames ? s_frames[fi] : make_uint2(w.frames[fi].tile_offset, w.frames[fi].tiles_x);
                 const PixBox bx = unpack_box(r);
                 const unsigned tx0 = (unsigned)bx.x0 >> a.lw, ty0 = (unsigned)bx.y0 >> a.lh;
                 const unsigned wr = ((unsigned)bx.x1 >> a.lw) - tx0 + 1u;
@@ -290,7 +297,7 @@ __global__ void __launch_bounds__(kEmitThreads, 4) emit_sort_kernel(Work w, Emit
                 const float4 f0 = w.feat0[p];
                 int t0, t1;
                 if (cull_tiles(f0.x, f0.y, w.ell[p], bx, ty, a.lw, a.lh, t0, t1) && tx >= t0 && tx <= t1) {
-                    key[i] = min(fr.tile_offset + (unsigned)ty * fr.tiles_x + (unsigned)tx, w.L.tiles - 1u);
+                    key[i] = min(fg.x + (unsigned)ty * fg.y + (unsigned)tx, w.L.tiles - 1u);
                     val[i] = p;
                     kept |= 1u << i;
                 }

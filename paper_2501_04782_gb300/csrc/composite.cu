@@ -33,6 +33,12 @@ __device__ __forceinline__ void add_work(unsigned long long *ctr, unsigned n_eva
     }
 }
 
+// A replayed Gaussian with at most this many lanes of the warp contributing adds each
+// lane's nine values with its own atomics; denser ones go through warp_reduce9 (one
+// atomic per value).  Many lanes adding to one address contend, so the direct path
+// is for sparse warps only.
+constexpr int kSparseLanes = 8;
+
 // A block leaving the persistent loop counts itself done; the last one resets the work
 // queue and the done count, so the next launch on this workspace starts from zero.
 __device__ __forceinline__ void queue_done(unsigned *queue, unsigned *done) {
@@ -280,7 +286,8 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_bwd_kernel(Work w, const
                 float a0 = fminf(r0, kAlphaMax), a1 = fminf(r1, kAlphaMax);
                 const bool v0 = pos <= last0 && a0 >= kAlphaMin;
                 const bool v1 = pos <= last1 && a1 >= kAlphaMin;
-                if (!__any_sync(0xffffffffu, v0 || v1)) continue;
+                const unsigned act = __ballot_sync(0xffffffffu, v0 || v1);
+                if (!act) continue;
                 n_comp += (unsigned)v0 + (unsigned)v1;
                 a0 = v0 ? a0 : 0.f;
                 a1 = v1 ? a1 : 0.f;
@@ -313,12 +320,22 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_bwd_kernel(Work w, const
                 const float2 dr = __fmul2_rn(wg, g0), dg = __fmul2_rn(wg, g1), db = __fmul2_rn(wg, g2);
                 float v[9] = {cu.x + cu.y, cv.x + cv.y, ca.x + ca.y, cbb.x + cbb.y, cc.x + cc.y,
                               de.x + de.y, dr.x + dr.y, dg.x + dg.y, db.x + db.y};
-                int slot;
-                const float sum = warp_reduce9(v, lane, slot);
-                if (slot < 9 && !(lane & 1)) {
-                    const unsigned p = s_p[j];
-                    float *dst = slot < 4 ? &w.g0[p].x + slot : (slot < 8 ? &w.g1[p].x + (slot - 4) : w.g2 + p);
-                    atomicAdd(dst, sum);
+                if (__popc(act) <= kSparseLanes) {
+                    if (v0 || v1) {
+                        const unsigned p = s_p[j];
+                        float *a = &w.g0[p].x, *b = &w.g1[p].x;
+                        atomicAdd(a, v[0]); atomicAdd(a + 1, v[1]); atomicAdd(a + 2, v[2]); atomicAdd(a + 3, v[3]);
+                        atomicAdd(b, v[4]); atomicAdd(b + 1, v[5]); atomicAdd(b + 2, v[6]); atomicAdd(b + 3, v[7]);
+                        atomicAdd(w.g2 + p, v[8]);
+                    }
+                } else {
+                    int slot;
+                    const float sum = warp_reduce9(v, lane, slot);
+                    if (slot < 9 && !(lane & 1)) {
+                        const unsigned p = s_p[j];
+                        float *dst = slot < 4 ? &w.g0[p].x + slot : (slot < 8 ? &w.g1[p].x + (slot - 4) : w.g2 + p);
+                        atomicAdd(dst, sum);
+                    }
                 }
             }
         }

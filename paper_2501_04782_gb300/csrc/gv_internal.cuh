@@ -65,17 +65,20 @@ struct DevHeader {
     unsigned long long cells;       // cells: tiles of the pairs' extent boxes, before culling
 };
 
-// Radix sort geometry (one onesweep pass = one 8-bit digit).  Small sorts use 1024-key
-// block tiles (more blocks in flight), large ones 3072-key tiles (fewer look-back steps).
 // rect.w of a pair: frame index, bit 31 set when the backward runs its geometric chain
 // rule in FP64 (ill-conditioned footprint)
 constexpr unsigned kRectFp64 = 1u << 31;
 constexpr unsigned kRectFrame = kRectFp64 - 1u;
 
+// Radix sort geometry (one onesweep pass = one 8-bit digit): keys per thread by sort size.
+// Up to 2^18 keys 2048-key block tiles (few tiles: a short look-back chain), up to 2^20
+// 1024-key tiles (more blocks in flight), above 3072-key tiles (fewer look-back steps).
 constexpr int kSortThreads = 256;
 constexpr int kRadix = 256;
 constexpr unsigned kSortSmallN = 1u << 20;
-__host__ __device__ constexpr int sort_items(unsigned n_cap) { return n_cap <= kSortSmallN ? 4 : 12; }
+__host__ __device__ constexpr int sort_items(unsigned n_cap) {
+    return n_cap <= (1u << 18) ? 8 : (n_cap <= kSortSmallN ? 4 : 12);
+}
 __host__ __device__ constexpr unsigned sort_tile_keys(unsigned n_cap) {
     return (unsigned)(kSortThreads * sort_items(n_cap));
 }

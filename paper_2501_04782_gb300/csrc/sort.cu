@@ -185,7 +185,7 @@ cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    const bool small = sort_items(n_cap) == 4;
+    const int items = sort_items(n_cap);
     const int per_sm = 4;  // resident blocks per SM (launch bounds)
     int grid = (int)std::min<unsigned>(max_tiles, (unsigned)num_sms * per_sm);
     int cur = first_pass & 1;
@@ -204,7 +204,8 @@ cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2
         a.ctr = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(w.hdr) + offsetof(DevHeader, sort_ctr)) +
                 ctr_slot + ps;
         a.hdr = w.hdr;
-        if (small) sort_pass_kernel<4><<<grid, kSortThreads, 0, s>>>(a);
+        if (items == 8) sort_pass_kernel<8><<<grid, kSortThreads, 0, s>>>(a);
+        else if (items == 4) sort_pass_kernel<4><<<grid, kSortThreads, 0, s>>>(a);
         else sort_pass_kernel<12><<<grid, kSortThreads, 0, s>>>(a);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
