@@ -11,12 +11,15 @@
 // A block is one tile, two pixels per thread, each warp an 8x8 pixel block so a warp
 // covers a compact footprint (more warps skip a Gaussian entirely in the backward).
 // Gaussians are staged through shared memory in batches of DEPTH (the stage depth); every
-// lane then reads the same staged Gaussian (broadcast).  The forward stops a tile once
-// every pixel is done (__syncthreads_and).  The backward keeps per-pixel state in
-// registers, recovers T_i = T_{i+1} / (1 - alpha_i) (alpha recomputed bit-identically),
-// reduces the nine per-Gaussian gradients of a warp with a transposed shuffle reduction,
-// and adds them with one atomic instruction (nine lanes, nine addresses).  Nothing here
-// is a dense contraction: no tensor cores.
+// lane then reads the same staged Gaussian (broadcast).  The forward takes two Gaussians
+// per round; a pixel's cutoff test compares alpha with a per-pixel threshold (1/255, or 2
+// once the pixel is done), so the stop rule costs no extra test per Gaussian; a warp
+// leaves the tile once all its pixels are done and a block once every pixel is
+// (__syncthreads_and).  The backward keeps per-pixel state in registers, recovers
+// T_i = T_{i+1} / (1 - alpha_i) (alpha recomputed bit-identically), reduces the nine
+// per-Gaussian gradients of a warp with a transposed shuffle reduction and adds them with
+// one atomic instruction (nine lanes, nine addresses), or, when few lanes contribute, adds
+// each lane's values directly.  Nothing here is a dense contraction: no tensor cores.
 #include "gv_internal.cuh"
 
 namespace gvk {
@@ -98,9 +101,9 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_fwd_kernel(Work w, const
                                                                    float bg2, float *image, float *final_T,
                                                                    int32_t *last_idx) {
     constexpr int NT = TW * TH / 2;
-    __shared__ float4 s_a[DEPTH];
-    __shared__ float4 s_b[DEPTH];
-    __shared__ float s_c[DEPTH];
+    __shared__ float4 s_a[DEPTH + 1];
+    __shared__ float4 s_b[DEPTH + 1];
+    __shared__ float s_c[DEPTH + 1];
     __shared__ unsigned s_tile;
     int lx, ly;
     pixels_of_thread<TW, TH>(threadIdx.x, lx, ly);
@@ -126,9 +129,10 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_fwd_kernel(Work w, const
         const uint2 rg = failed ? make_uint2(0u, 0u) : w.ranges[tile];
         float2 T = make_float2(1.f, 1.f), cr = make_float2(0.f, 0.f), cg = cr, cb = cr;
         int last0 = -1, last1 = -1;
-        bool done0 = !in0, done1 = !in1;
+        // per-pixel alpha threshold: 1/255, or 2 (above any alpha) once the pixel is done
+        float2 thr = make_float2(in0 ? kAlphaMin : 2.f, in1 ? kAlphaMin : 2.f);
         for (unsigned start = rg.x; start < rg.y; start += DEPTH) {
-            if (__syncthreads_and(done0 && done1)) break;
+            if (__syncthreads_and(thr.x > 1.f && thr.y > 1.f)) break;
             const int n = (int)min((unsigned)DEPTH, rg.y - start);
             for (int i = threadIdx.x; i < n; i += NT) {
                 const unsigned p = min(ids[start + i], w.L.P - 1u);  // in range unless a wait gave up
@@ -136,14 +140,18 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_fwd_kernel(Work w, const
                 s_b[i] = w.feat1[p];
                 s_c[i] = w.feat2[p];
             }
+            if (threadIdx.x == 0 && (n & 1)) {  // pad to pairs: a Gaussian of opacity 0 (2^-inf)
+                s_a[n] = make_float4(0.f, 0.f, 0.f, 0.f);
+                s_b[n] = make_float4(0.f, -__int_as_float(0x7f800000), 0.f, 0.f);
+                s_c[n] = 0.f;
+            }
             __syncthreads();
             // two staged Gaussians per round: their exponents are independent of the pixel
             // state, so both are evaluated before the two (sequential) compositing updates
             for (int j = 0; j < n; j += 2) {
-                if (!__any_sync(0xffffffffu, !(done0 && done1))) break;
-                const bool two = j + 1 < n;
+                if (!__any_sync(0xffffffffu, thr.x < 1.f || thr.y < 1.f)) break;
                 const float4 fa0 = s_a[j], fa1 = s_b[j];
-                const float4 fb0 = s_a[two ? j + 1 : j], fb1 = s_b[two ? j + 1 : j];
+                const float4 fb0 = s_a[j + 1], fb1 = s_b[j + 1];
                 float dxa, dxb;
                 float2 dya, dyb;
                 const float2 ea = splat_exponent2(fa0, fa1, px, npy, dxa, dya);
@@ -152,21 +160,20 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_fwd_kernel(Work w, const
                 const float2 rb = make_float2(fminf(ex2_approx(eb.x), kAlphaMax), fminf(ex2_approx(eb.y), kAlphaMax));
 #pragma unroll
                 for (int k = 0; k < 2; k++) {
-                    if (k == 1 && !two) break;
                     const float2 rr = k ? rb : ra;
                     const float4 f1 = k ? fb1 : fa1;
                     // a pixel that is done, or below the cutoff, takes alpha 0: T and colour unchanged
-                    const float a0 = (done0 || rr.x < kAlphaMin) ? 0.f : rr.x;
-                    const float a1 = (done1 || rr.y < kAlphaMin) ? 0.f : rr.y;
-                    if (!__any_sync(0xffffffffu, a0 > 0.f || a1 > 0.f)) continue;  // no lane composites it
+                    const bool c0 = rr.x >= thr.x, c1 = rr.y >= thr.y;
+                    if (!__any_sync(0xffffffffu, c0 || c1)) continue;  // no lane composites it
+                    const float a0 = c0 ? rr.x : 0.f, a1 = c1 ? rr.y : 0.f;
                     const float2 wg = __fmul2_rn(make_float2(a0, a1), T);
                     cr = __ffma2_rn(dup2(f1.z), wg, cr);
                     cg = __ffma2_rn(dup2(f1.w), wg, cg);
                     cb = __ffma2_rn(dup2(s_c[j + k]), wg, cb);
                     T = __fmul2_rn(T, __fadd2_rn(make_float2(1.f, 1.f), make_float2(-a0, -a1)));
                     const int pos = (int)(start + j + k);
-                    if (a0 > 0.f) { last0 = pos; done0 = T.x < kTStop; }
-                    if (a1 > 0.f) { last1 = pos; done1 = T.y < kTStop; }
+                    if (c0) { last0 = pos; if (T.x < kTStop) thr.x = 2.f; }
+                    if (c1) { last1 = pos; if (T.y < kTStop) thr.y = 2.f; }
                 }
             }
         }
