@@ -37,6 +37,8 @@ ZNEAR = 0.2
 EXT_K = math.sqrt(2.0 * math.log(255.0))
 NGRAD = 17
 N2D = 9
+NCAM = 16  # camera gradient: dR (row-major, R as a general matrix), dt, dfx, dfy, dcx, dcy
+CAM_KEYS = ("R", "t", "fx", "fy", "cx", "cy")
 GRAD_ROWS = dict(mean=(0, 3), vel=(3, 6), log_scale=(6, 9), quat=(9, 13), opacity_logit=(13, 14), rgb=(14, 17))
 
 
@@ -112,7 +114,8 @@ def lib():
                                  _dp, _dp, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
         L.orc_render_bwd.argtypes = [ctypes.POINTER(_Gaussians), ctypes.POINTER(_Camera), ctypes.POINTER(_Params),
                                      ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, _dp,
-                                     _dp, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+                                     _dp, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                                     ctypes.c_int]
         L.orc_bin_f32.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 5 + [ctypes.c_int32] * 4 + [ctypes.c_void_p] * 2
         L.orc_bin_f64.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 5 + [ctypes.c_int32] * 4 + [ctypes.c_void_p] * 3
         L.orc_cull_f32.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 7 + [ctypes.c_int32] * 4 + [ctypes.c_void_p] * 3
@@ -211,7 +214,8 @@ def render_image(g: dict, cam, params: Params | None = None, nthreads: int | Non
 def render_bwd_pixels(g: dict, cam, px, py, dL_dC, params: Params | None = None,
                       nthreads: int | None = None, want_abs: bool = True, want_2d: bool = True) -> dict:
     """Gradient of L = sum_k dL_dC[k] . C(pixel k).  dL_dC [n,3].
-    Returns grad [17,N] and optionally gabs [17,N] and grad2d [9,N]."""
+    Returns grad [17,N], cam_grad [16] (camera: dR row-major with R as a general matrix, dt,
+    dfx, dfy, dcx, dcy) and optionally gabs [17,N], cam_gabs [16] and grad2d [9,N]."""
     params = params or Params()
     px = np.ascontiguousarray(px, np.int32)
     py = np.ascontiguousarray(py, np.int32)
@@ -221,15 +225,19 @@ def render_bwd_pixels(g: dict, cam, px, py, dL_dC, params: Params | None = None,
     grad = np.zeros((NGRAD, h.N), np.float64)
     gabs = np.zeros((NGRAD, h.N), np.float64) if want_abs else None
     g2d = np.zeros((N2D, h.N), np.float64) if want_2d else None
+    cam_grad = np.zeros(NCAM, np.float64)
+    cam_gabs = np.zeros(NCAM, np.float64)
     rc = lib().orc_render_bwd(ctypes.byref(h.c), ctypes.byref(_camera(cam)), ctypes.byref(params._c()), n,
                               px.ctypes.data, py.ctypes.data, dL.ctypes.data_as(_dp), grad.ctypes.data_as(_dp),
                               gabs.ctypes.data if gabs is not None else None,
-                              g2d.ctypes.data if g2d is not None else None, nthreads or default_threads())
+                              g2d.ctypes.data if g2d is not None else None, cam_grad.ctypes.data,
+                              cam_gabs.ctypes.data, nthreads or default_threads())
     if rc:
         raise MemoryError("oracle backward failed")
-    out = dict(grad=grad)
+    out = dict(grad=grad, cam_grad=cam_grad)
     if gabs is not None:
         out["gabs"] = gabs
+        out["cam_gabs"] = cam_gabs
     if g2d is not None:
         out["grad2d"] = g2d
     return out

@@ -71,6 +71,8 @@ typedef struct {
 #define ORC_NGRAD 17
 /* screen-space gradient record: du, dv, dA, dB, dC, do, dr, dg, db */
 #define ORC_N2D 9
+/* camera gradient: dR (9, row-major), dt (3), dfx, dfy, dcx, dcy */
+#define ORC_NCAM 16
 /* projection output record stride */
 #define ORC_PROJ 20
 
@@ -321,7 +323,12 @@ int orc_render(const orc_gaussians *g, const orc_camera *cam, const orc_params *
 
 /* Chain rule from a screen-space gradient (du, dv, dA, dB, dC, do, dr, dg, db) of one
  * Gaussian to its 17 raw-parameter gradients (mean, vel, log_scale, quat, logit, rgb). */
-static void chain_rule(const orc_proj *q, const orc_camera *cam, const double d2[ORC_N2D], double out[ORC_NGRAD]) {
+/* Chain rule of one Gaussian's screen-space gradient d2 to its parameters (out, 17 rows)
+ * and, when cam_out is not NULL, to the camera (Sec. 3.4: extrinsics R, t and intrinsics
+ * fx, fy, cx, cy), added into cam_out[ORC_NCAM] = dR (row-major, R taken as a general
+ * matrix), dt, dfx, dfy, dcx, dcy. */
+static void chain_rule(const orc_proj *q, const orc_camera *cam, const double d2[ORC_N2D], double out[ORC_NGRAD],
+                       double *cam_out) {
     double gu = d2[0], gv = d2[1], gA = d2[2], gB = d2[3], gC = d2[4], go = d2[5];
     memset(out, 0, sizeof(double) * ORC_NGRAD);
     /* colour */
@@ -378,6 +385,22 @@ static void chain_rule(const orc_proj *q, const orc_camera *cam, const double d2
     gz += gJ[4] * (-fy / (z * z));
     gy += gJ[5] * (-fy / (z * z));
     gz += gJ[5] * (2.0 * fy * y / (z * z * z));
+    if (cam_out) {
+        /* x_c = W mu + t: dW += dxc mu^T, dt += dxc; T = J W: dW += J^T dT */
+        const double gxc[3] = {gx, gy, gz};
+        for (int r = 0; r < 3; r++) {
+            for (int k = 0; k < 3; k++) cam_out[r * 3 + k] += gxc[r] * q->mu[k];
+            cam_out[9 + r] += gxc[r];
+        }
+        for (int k = 0; k < 3; k++)
+            for (int c2 = 0; c2 < 3; c2++)
+                cam_out[k * 3 + c2] += q->J[0 * 3 + k] * gT[0 * 3 + c2] + q->J[1 * 3 + k] * gT[1 * 3 + c2];
+        /* u = fx x/z + cx, J00 = fx/z, J02 = -fx x/z^2 (and the same in y) */
+        cam_out[12] += gu * x / z + gJ[0] / z - gJ[2] * x / (z * z);
+        cam_out[13] += gv * y / z + gJ[4] / z - gJ[5] * y / (z * z);
+        cam_out[14] += gu;
+        cam_out[15] += gv;
+    }
     /* x_c = W mu + t  ->  dmu = W^T dxc */
     double gmu[3];
     for (int k = 0; k < 3; k++) gmu[k] = W[0 * 3 + k] * gx + W[1 * 3 + k] * gy + W[2 * 3 + k] * gz;
@@ -511,6 +534,7 @@ typedef struct {
     double *grad, *gabs, *grad2d;
     int tid, nthreads;
     int err;
+    double cam_part[ORC_NCAM], cam_abs_part[ORC_NCAM]; /* this thread's camera sums */
 } bwd_job;
 
 static void *bwd_pixels_worker(void *arg) {
@@ -549,7 +573,7 @@ static void *bwd_accum_worker(void *arg) {
             if (i % j->nthreads != j->tid) continue;
             const double *d = L->d2 + e * ORC_N2D;
             double out[ORC_NGRAD];
-            chain_rule(&j->pr[i], j->cam, d, out);
+            chain_rule(&j->pr[i], j->cam, d, out, j->cam_part);
             for (int k = 0; k < ORC_NGRAD; k++) j->grad[k * N + i] += out[k];
             if (abs2d)
                 for (int k = 0; k < ORC_N2D; k++) abs2d[k * N + i] += L->da[e * ORC_N2D + k];
@@ -567,10 +591,11 @@ static void *bwd_accum_worker(void *arg) {
             for (int c = 0; c < ORC_N2D; c++) {
                 double a = abs2d[c * N + i];
                 if (a == 0) continue;
-                double unit[ORC_N2D] = {0}, col[ORC_NGRAD];
+                double unit[ORC_N2D] = {0}, col[ORC_NGRAD], ccol[ORC_NCAM] = {0};
                 unit[c] = 1.0;
-                chain_rule(&j->pr[i], j->cam, unit, col);
+                chain_rule(&j->pr[i], j->cam, unit, col, ccol);
                 for (int k = 0; k < ORC_NGRAD; k++) j->gabs[k * N + i] += fabs(col[k]) * a;
+                for (int k = 0; k < ORC_NCAM; k++) j->cam_abs_part[k] += fabs(ccol[k]) * a;
             }
         }
         free(abs2d);
@@ -582,10 +607,13 @@ static void *bwd_accum_worker(void *arg) {
  * grad [17][N] (overwritten), gabs [17][N] error scale of each element: |J| times the
  * summed absolute elementary terms of the screen-space adjoint (may be NULL),
  * grad2d [9][N] screen-space gradients (may be NULL).  If the Gaussians have no velocity,
- * the vel rows are still written (time * dmu) and may be ignored. */
+ * the vel rows are still written (time * dmu) and may be ignored.  cam_grad [16]
+ * (overwritten, may be NULL): the camera gradient dR (row-major, R as a general matrix),
+ * dt, dfx, dfy, dcx, dcy; cam_gabs [16] its error scale (computed with gabs). */
 int orc_render_bwd(const orc_gaussians *g, const orc_camera *cam, const orc_params *p,
                    int64_t npix, const int32_t *px, const int32_t *py, const double *dL_dC,
-                   double *grad, double *gabs, double *grad2d, int nthreads) {
+                   double *grad, double *gabs, double *grad2d, double *cam_grad, double *cam_gabs,
+                   int nthreads) {
     if (nthreads < 1) nthreads = 1;
     int64_t N = g->N;
     memset(grad, 0, sizeof(double) * ORC_NGRAD * (size_t)N);
@@ -597,7 +625,7 @@ int orc_render_bwd(const orc_gaussians *g, const orc_camera *cam, const orc_para
     pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
     bwd_job *jobs = (bwd_job *)malloc(sizeof(bwd_job) * (size_t)nthreads);
     for (int t = 0; t < nthreads; t++) {
-        bwd_job jb = {pr, N, p, cam, npix, px, py, dL_dC, lists, grad, gabs, grad2d, t, nthreads, 0};
+        bwd_job jb = {pr, N, p, cam, npix, px, py, dL_dC, lists, grad, gabs, grad2d, t, nthreads, 0, {0}, {0}};
         jobs[t] = jb;
         pthread_create(&th[t], NULL, bwd_pixels_worker, &jobs[t]);
     }
@@ -607,6 +635,13 @@ int orc_render_bwd(const orc_gaussians *g, const orc_camera *cam, const orc_para
         for (int t = 0; t < nthreads; t++) pthread_create(&th[t], NULL, bwd_accum_worker, &jobs[t]);
         for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
     }
+    if (cam_grad) memset(cam_grad, 0, sizeof(double) * ORC_NCAM);
+    if (cam_gabs) memset(cam_gabs, 0, sizeof(double) * ORC_NCAM);
+    for (int t = 0; t < nthreads && !err; t++)
+        for (int k = 0; k < ORC_NCAM; k++) {
+            if (cam_grad) cam_grad[k] += jobs[t].cam_part[k];
+            if (cam_gabs) cam_gabs[k] += jobs[t].cam_abs_part[k];
+        }
     for (int t = 0; t < nthreads; t++) { free(lists[t].idx); free(lists[t].d2); free(lists[t].da); }
     free(lists); free(th); free(jobs); free(pr);
     return err;

@@ -138,3 +138,57 @@ def test_l2_loss_gradient_and_adam_first_step():
     gg = rng.normal(size=10)
     t1, m1, v1 = oracle.adam_step(th, gg, np.zeros(10), np.zeros(10), 1, 0.01)
     assert np.allclose(t1, th - 0.01 * gg / (np.abs(gg) + 1e-8), rtol=1e-12)
+
+
+def cam_with(cam, key, idx, delta):
+    """A copy of the camera with one parameter moved (R as a general 3x3 matrix)."""
+    import dataclasses
+    R = np.array(cam.R, np.float64).reshape(3, 3).copy()
+    t = np.array(cam.t, np.float64).copy()
+    kw = {}
+    if key == "R":
+        R[idx // 3, idx % 3] += delta
+    elif key == "t":
+        t[idx] += delta
+    else:
+        kw[key] = getattr(cam, key) + delta
+    return dataclasses.replace(cam, R=R, t=t, **kw)
+
+
+CAM_SLOTS = [("R", i, i) for i in range(9)] + [("t", i, 9 + i) for i in range(3)] + \
+            [("fx", 0, 12), ("fy", 0, 13), ("cx", 0, 14), ("cy", 0, 15)]
+
+
+def test_camera_adjoint_matches_central_differences():
+    """The camera gradient (Sec. 3.4: per-frame extrinsics R, t and the intrinsics fx, fy, cx,
+    cy; R perturbed as a general matrix) against FP64 central differences of the oracle's
+    forward, in smooth mode and with the cutoffs on (away from thresholds)."""
+    for params, rel_tol, h in ((oracle.Params.smooth(bg=(0.2, 0.1, 0.4)), 2e-6, 1e-6),
+                               (oracle.Params(), 5e-5, 1e-8)):
+        g, cam, rng = small_scene(7, 6, 24, 20, with_vel=True, time=0.6)
+        wts = rng.normal(size=(3, 20, 24))
+        res = oracle.render_bwd_image(g, cam, wts, params)
+        cg = res["cam_grad"]
+        assert cg.shape == (oracle.NCAM,) and np.all(np.isfinite(cg))
+        for key, idx, slot in CAM_SLOTS:
+            fd = (loss_fn(g, cam_with(cam, key, idx, h), wts, params) -
+                  loss_fn(g, cam_with(cam, key, idx, -h), wts, params)) / (2 * h)
+            scale = max(abs(fd), abs(cg[slot]), 1e-3)
+            assert abs(fd - cg[slot]) / scale < rel_tol, (key, idx, fd, cg[slot])
+
+
+def test_camera_translation_gradient_closed_forms():
+    """Moving the camera by dt moves every camera-space mean by dt, so dL/dt equals the sum
+    over Gaussians of dL/dx_c = R dL/dmu (x_c = R mu + t); and a shift of the principal
+    point moves the image: dL/dcx = sum of the screen-space dL/du."""
+    g, cam, rng = small_scene(8, 5, 20, 16, with_vel=False)
+    wts = rng.normal(size=(3, 16, 20))
+    p = oracle.Params.smooth()
+    res = oracle.render_bwd_image(g, cam, wts, p)
+    R = np.array(cam.R, np.float64).reshape(3, 3)
+    dmu = oracle.split_grad(res["grad"])["mean"]  # [3, N]
+    dxc = R @ dmu  # dL/dx_c = R dL/dmu for x_c = R mu + t
+    assert np.allclose(res["cam_grad"][9:12], dxc.sum(axis=1), rtol=1e-10, atol=1e-12)
+    g2d = res["grad2d"]
+    assert np.isclose(res["cam_grad"][14], g2d[0].sum(), rtol=1e-10, atol=1e-12)
+    assert np.isclose(res["cam_grad"][15], g2d[1].sum(), rtol=1e-10, atol=1e-12)
