@@ -359,6 +359,7 @@ def run_gv(args):
         "work_counters": counters,
     }
     if not args.no_extras and args.workload == "frame540p":
+        out["camera_adjoint"] = run_camera_adjoint(torch, ctx, step, grads, flush, P, max(50, args.steps // 4))
         out["batched"] = run_batched(torch, gv, synth, ctx, dev, flush, max(20, args.steps // 4))
         out["e2e"] = run_e2e(torch, gv, ctx, params, target, frames, ws, dev, flush, max(20, args.steps // 4), scale,
                              world)
@@ -374,6 +375,43 @@ def run_gv(args):
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out))
+
+
+def run_camera_adjoint(torch, ctx, step, grads, flush, P, steps):
+    """The same per-frame step with the camera gradient (extrinsics and intrinsics of the
+    frame, Sec. 3.4) also requested: its throughput and the projection-backward stage time
+    with and without it."""
+    def timed(n):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+        for i in range(n):
+            flush.zero_()
+            ev[i][0].record()
+            step()
+            ev[i][1].record()
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / n
+
+    def stage_ms(n):
+        ctx.profile_enable(True)
+        acc = []
+        for _ in range(n):
+            step()
+            ms, _ = ctx.profile_read()
+            acc.append(ms["project_bwd"])
+        ctx.profile_enable(False)
+        return statistics.median(acc)
+
+    base_stage = stage_ms(20)
+    grads["camera"] = torch.zeros(1, 16, device=grads["mean"].device)
+    for _ in range(3):
+        step()
+    ms = timed(steps)
+    cam_stage = stage_ms(20)
+    del grads["camera"]
+    return {"value": round(P / (ms / 1000) / 1e6, 2), "unit": "Mpix/s", "ms_per_step": round(ms, 4),
+            "project_bwd_ms": round(cam_stage, 4), "project_bwd_ms_without": round(base_stage, 4),
+            "workload": "the per-frame step above with the frame's camera gradient (dR, dt, dfx, dfy, dcx, dcy) "
+                        "also accumulated"}
 
 
 def run_batched(torch, gv, synth, ctx, dev, flush, steps):

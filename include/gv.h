@@ -96,9 +96,14 @@ typedef struct {
 } gv_gaussians;
 
 /* Gradient planes, same layout; the backward ACCUMULATES (+=) into them.  vel may be
- * NULL (its gradient is then dropped). */
+ * NULL (its gradient is then dropped).  camera, if not NULL, is [F][16] FP32 (device):
+ * per frame of the call the gradient w.r.t. its camera (Sec. 3.4: the extrinsics and the
+ * intrinsics), dR[9] (R row-major, taken as a general matrix: the caller maps it to its
+ * rotation parameters), dt[3], dfx, dfy, dcx, dcy; also accumulated (+=). */
+#define GV_CAMERA_GRAD 16
 typedef struct {
     float *mean, *vel, *log_scale, *quat, *opacity_logit, *rgb;
+    float *camera;
 } gv_gaussians_grad;
 
 /* One frame of a batch: its camera, the Gaussian subset [gauss_offset, gauss_offset +

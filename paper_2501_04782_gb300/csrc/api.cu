@@ -355,6 +355,7 @@ gv_status backward_stages(gv_ctx *ctx, const gv_gaussians *g, const Plan &pl, co
     GradPtrs gp;
     gp.mean = grad->mean; gp.vel = grad->vel; gp.log_scale = grad->log_scale;
     gp.quat = grad->quat; gp.logit = grad->opacity_logit; gp.rgb = grad->rgb;
+    gp.cam = grad->camera;
     {
         StageTimer tm(ctx, GV_STAGE_PROJECT_BWD, s, 2);
         const GaussPtrs gptr = gauss_ptrs(g);

@@ -146,7 +146,11 @@ struct GaussPtrs {
 
 struct GradPtrs {
     float *mean, *vel, *log_scale, *quat, *logit, *rgb;
+    float *cam;  // [F][kCamGrad] or NULL
 };
+
+// Camera gradient per frame: dR (9, row-major), dt (3), dfx, dfy, dcx, dcy.
+constexpr int kCamGrad = 16;
 
 struct FrameChunk {
     DevFrame f[kMaxFramesPerSetup];

@@ -325,10 +325,13 @@ __global__ void __launch_bounds__(256) bin_from_screen_kernel(Work w, long long 
 
 // Chain rule of the geometric part of one pair: gradients w.r.t. the screen mean (du, dv)
 // and the conic (dA, dB, dC) to mean, velocity, log-scale and quaternion, added into acc
-// (rows 0-12 of the 17-row layout: mean 3, vel 3, log_scale 3, quat 4).
+// (rows 0-12 of the 17-row layout: mean 3, vel 3, log_scale 3, quat 4), and, when cam is
+// not NULL, to the frame's camera (Sec. 3.4), added into cam[kCamGrad]: x_c = R mu + t
+// gives dR += dx_c mu^T and dt += dx_c, T = J R gives dR += J^T dT, and u = fx x/z + cx,
+// J00 = fx/z, J02 = -fx x/z^2 give dfx (likewise fy, cy).
 template <typename F>
 __device__ __forceinline__ void geometry_backward(const PairState<F> &st, const DevFrame &fr, F du, F dv, F dA,
-                                                  F dB, F dC, float acc[17]) {
+                                                  F dB, F dC, float acc[17], float *cam = nullptr) {
     const F half = (F)0.5, two = (F)2;
     // conic Q = Sigma2^{-1}: dL/dSigma2 = -Q G Q with G = [[dA, dB/2], [dB/2, dC]]
     F X00 = st.A * dA + half * st.B * dB, X01 = half * st.A * dB + st.B * dC;
@@ -368,6 +371,26 @@ __device__ __forceinline__ void geometry_backward(const PairState<F> &st, const 
     F dyc = dv * fy * iz - dJ12 * fy * iz2;
     F dzc = -du * fx * st.xc * iz2 - dv * fy * st.yc * iz2 - dJ00 * fx * iz2 - dJ11 * fy * iz2 +
             two * (dJ02 * fx * st.xc + dJ12 * fy * st.yc) * iz3;
+    if (cam) {
+        const F J00 = fx * iz, J02 = -fx * st.xc * iz2, J11 = fy * iz, J12 = -fy * st.yc * iz2;
+        const F m[3] = {st.mx, st.my, st.mz}, dx3[3] = {dxc, dyc, dzc};
+#pragma unroll
+        for (int r = 0; r < 3; r++) {
+#pragma unroll
+            for (int k = 0; k < 3; k++) cam[r * 3 + k] += (float)(dx3[r] * m[k]);
+            cam[9 + r] += (float)dx3[r];
+        }
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+            cam[c] += (float)(J00 * dT0[c]);
+            cam[3 + c] += (float)(J11 * dT1[c]);
+            cam[6 + c] += (float)(J02 * dT0[c] + J12 * dT1[c]);
+        }
+        cam[12] += (float)(du * st.xc * iz + dJ00 * iz - dJ02 * st.xc * iz2);
+        cam[13] += (float)(dv * st.yc * iz + dJ11 * iz - dJ12 * st.yc * iz2);
+        cam[14] += (float)du;
+        cam[15] += (float)dv;
+    }
     // x_c = W mu + t
     F dmx = W[0] * dxc + W[3] * dyc + W[6] * dzc;
     F dmy = W[1] * dxc + W[4] * dyc + W[7] * dzc;
@@ -410,7 +433,8 @@ __device__ __forceinline__ void geometry_backward(const PairState<F> &st, const 
 // The geometric part of a pair the projection listed as ill-conditioned is left to the
 // FP64 kernel.
 __device__ __forceinline__ void pair_backward(const PairState<float> &st, bool deferred, const DevFrame &fr,
-                                              float4 g0, float4 g1, float g2, float acc[17]) {
+                                              float4 g0, float4 g1, float g2, float acc[17],
+                                              float *cam = nullptr) {
     acc[14] += g1.z;
     acc[15] += g1.w;
     acc[16] += g2;
@@ -418,7 +442,7 @@ __device__ __forceinline__ void pair_backward(const PairState<float> &st, bool d
     acc[13] += g1.y * (1.f - st.o) * kLog2e;
     if (!st.valid || deferred) return;
     const float dA = -0.5f * kLog2e * g0.z, dB = -kLog2e * g0.w, dC = -0.5f * kLog2e * g1.x;
-    geometry_backward<float>(st, fr, g0.x, g0.y, dA, dB, dC, acc);
+    geometry_backward<float>(st, fr, g0.x, g0.y, dA, dB, dC, acc, cam);
 }
 
 // Adds acc into the gradient planes: rows [0, 13) (geometry) atomically when geo_atomic
@@ -439,44 +463,126 @@ __device__ __forceinline__ void store_grad(const GradPtrs &gr, long long N, long
     }
 }
 
-// mode 0: one thread per pair, each Gaussian in at most one frame (plain +=)
-// mode 2: one thread per pair, overlapping sets (atomicAdd)
-__global__ void __launch_bounds__(128) project_bwd_pairs_kernel(Work w, GaussPtrs g, GradPtrs gr, int atomic) {
-    unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= w.L.P) return;
-    int f = find_frame_by_pair(w.frames, (int)w.L.F, p);
-    const DevFrame &fr = w.frames[f];
-    long long gi = fr.gauss_offset + (long long)(p - fr.pair_offset);
-    PairState<float> st;
-    load_and_project(g, gi, fr, st);
-    float acc[17];
+// Camera gradients: per block, one slot of kCamGrad floats per frame in shared memory for
+// the first kCamSmemFrames frames (global atomics beyond), added to gr.cam once per block.
+constexpr int kCamSmemFrames = 32;
+
+// Transposed warp sum of 16 values: returns the sum of slot lane >> 1 (lanes 2s and 2s + 1
+// hold slot s).
+__device__ __forceinline__ float warp_reduce16(const float v[16], int lane) {
+    const unsigned FULL = 0xffffffffu;
+    const bool h4 = lane & 16, h3 = lane & 8, h2 = lane & 4, h1 = lane & 2;
+    float a[8], b[4], c[2];
 #pragma unroll
-    for (int k = 0; k < 17; k++) acc[k] = 0.f;
-    const bool deferred = (w.rect[p].w & kRectFp64) != 0u;
-    pair_backward(st, deferred, fr, w.g0[p], w.g1[p], w.g2[p], acc);
-    store_grad(gr, g.N, gi, acc, atomic != 0, false, deferred);
+    for (int i = 0; i < 8; i++) a[i] = (h4 ? v[i + 8] : v[i]) + __shfl_xor_sync(FULL, h4 ? v[i] : v[i + 8], 16);
+#pragma unroll
+    for (int i = 0; i < 4; i++) b[i] = (h3 ? a[i + 4] : a[i]) + __shfl_xor_sync(FULL, h3 ? a[i] : a[i + 4], 8);
+#pragma unroll
+    for (int i = 0; i < 2; i++) c[i] = (h2 ? b[i + 2] : b[i]) + __shfl_xor_sync(FULL, h2 ? b[i] : b[i + 2], 4);
+    float d = (h1 ? c[1] : c[0]) + __shfl_xor_sync(FULL, h1 ? c[0] : c[1], 2);
+    return d + __shfl_xor_sync(FULL, d, 1);
 }
 
-// mode 1: one shared Gaussian set; one thread per Gaussian sums over all frames.
-__global__ void __launch_bounds__(128) project_bwd_shared_kernel(Work w, GaussPtrs g, GradPtrs gr) {
-    const DevFrame &f0 = w.frames[0];
-    unsigned j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= f0.gauss_count) return;
-    long long gi = f0.gauss_offset + j;
-    float acc[17];
+// Adds each lane's camera gradient cam (of frame f) to the block's slots: a warp whose
+// lanes share one frame sums first; a warp that straddles frames adds lane by lane.
+// Every lane of the warp calls it.
+__device__ __forceinline__ void cam_add(const float cam[kCamGrad], int f, float (*s_cam)[kCamGrad], float *gcam) {
+    const int lane = threadIdx.x & 31;
+    const int f0 = __shfl_sync(0xffffffffu, f, 0);
+    if (__all_sync(0xffffffffu, f == f0)) {
+        const float sum = warp_reduce16(cam, lane);
+        if (!(lane & 1)) {
+            const int slot = lane >> 1;
+            if (f0 < kCamSmemFrames) atomicAdd(&s_cam[f0][slot], sum);
+            else atomicAdd(gcam + (size_t)f0 * kCamGrad + slot, sum);
+        }
+    } else {
 #pragma unroll
-    for (int k = 0; k < 17; k++) acc[k] = 0.f;
-    bool any_deferred = false;
-    for (int f = 0; f < (int)w.L.F; f++) {
-        const DevFrame &fr = w.frames[f];
-        unsigned p = fr.pair_offset + j;
-        PairState<float> st;
-        load_and_project(g, gi, fr, st);
-        const bool deferred = (w.rect[p].w & kRectFp64) != 0u;
-        any_deferred |= deferred;
-        pair_backward(st, deferred, fr, w.g0[p], w.g1[p], w.g2[p], acc);
+        for (int k = 0; k < kCamGrad; k++) {
+            if (f < kCamSmemFrames) atomicAdd(&s_cam[f][k], cam[k]);
+            else atomicAdd(gcam + (size_t)f * kCamGrad + k, cam[k]);
+        }
     }
-    store_grad(gr, g.N, gi, acc, false, any_deferred);
+}
+
+__device__ __forceinline__ void cam_block_init(float (*s_cam)[kCamGrad], int F) {
+    for (int i = threadIdx.x; i < min(F, kCamSmemFrames) * kCamGrad; i += blockDim.x) (&s_cam[0][0])[i] = 0.f;
+    __syncthreads();
+}
+
+__device__ __forceinline__ void cam_block_flush(float (*s_cam)[kCamGrad], int F, float *gcam) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < min(F, kCamSmemFrames) * kCamGrad; i += blockDim.x) {
+        const float v = (&s_cam[0][0])[i];
+        if (v != 0.f) atomicAdd(gcam + i, v);
+    }
+}
+
+// mode 0: one thread per pair, each Gaussian in at most one frame (plain +=)
+// mode 2: one thread per pair, overlapping sets (atomicAdd)
+// Grid-stride over the pairs; CAM: also the camera gradients of the frames.
+template <bool CAM>
+__global__ void __launch_bounds__(128) project_bwd_pairs_kernel(Work w, GaussPtrs g, GradPtrs gr, int atomic) {
+    __shared__ float s_cam[CAM ? kCamSmemFrames : 1][kCamGrad];
+    const int F = (int)w.L.F;
+    if (CAM) cam_block_init(s_cam, F);
+    for (unsigned base = blockIdx.x * blockDim.x; base < w.L.P; base += gridDim.x * blockDim.x) {
+        const unsigned p = base + threadIdx.x;
+        float cam[kCamGrad];
+#pragma unroll
+        for (int k = 0; k < kCamGrad; k++) cam[k] = 0.f;
+        int f = F - 1;
+        if (p < w.L.P) {
+            f = find_frame_by_pair(w.frames, F, p);
+            const DevFrame &fr = w.frames[f];
+            long long gi = fr.gauss_offset + (long long)(p - fr.pair_offset);
+            PairState<float> st;
+            load_and_project(g, gi, fr, st);
+            float acc[17];
+#pragma unroll
+            for (int k = 0; k < 17; k++) acc[k] = 0.f;
+            const bool deferred = (w.rect[p].w & kRectFp64) != 0u;
+            pair_backward(st, deferred, fr, w.g0[p], w.g1[p], w.g2[p], acc, CAM ? cam : nullptr);
+            store_grad(gr, g.N, gi, acc, atomic != 0, false, deferred);
+        }
+        if (CAM) cam_add(cam, f, s_cam, gr.cam);
+    }
+    if (CAM) cam_block_flush(s_cam, F, gr.cam);
+}
+
+// mode 1: one shared Gaussian set; one thread per Gaussian sums over all frames (grid-stride).
+template <bool CAM>
+__global__ void __launch_bounds__(128) project_bwd_shared_kernel(Work w, GaussPtrs g, GradPtrs gr) {
+    __shared__ float s_cam[CAM ? kCamSmemFrames : 1][kCamGrad];
+    const int F = (int)w.L.F;
+    if (CAM) cam_block_init(s_cam, F);
+    const DevFrame &f0 = w.frames[0];
+    for (unsigned base = blockIdx.x * blockDim.x; base < f0.gauss_count; base += gridDim.x * blockDim.x) {
+        const unsigned j = base + threadIdx.x;
+        const bool in = j < f0.gauss_count;
+        const long long gi = f0.gauss_offset + j;
+        float acc[17];
+#pragma unroll
+        for (int k = 0; k < 17; k++) acc[k] = 0.f;
+        bool any_deferred = false;
+        for (int f = 0; f < F; f++) {
+            float cam[kCamGrad];
+#pragma unroll
+            for (int k = 0; k < kCamGrad; k++) cam[k] = 0.f;
+            if (in) {
+                const DevFrame &fr = w.frames[f];
+                unsigned p = fr.pair_offset + j;
+                PairState<float> st;
+                load_and_project(g, gi, fr, st);
+                const bool deferred = (w.rect[p].w & kRectFp64) != 0u;
+                any_deferred |= deferred;
+                pair_backward(st, deferred, fr, w.g0[p], w.g1[p], w.g2[p], acc, CAM ? cam : nullptr);
+            }
+            if (CAM) cam_add(cam, f, s_cam, gr.cam);
+        }
+        if (in) store_grad(gr, g.N, gi, acc, false, any_deferred);
+    }
+    if (CAM) cam_block_flush(s_cam, F, gr.cam);
 }
 
 // FP64 geometric chain rule of the pairs the projection listed as ill-conditioned; atomic
@@ -496,10 +602,18 @@ __global__ void __launch_bounds__(128) project_bwd_fp64_kernel(Work w, GaussPtrs
         float acc[17];
 #pragma unroll
         for (int k = 0; k < 17; k++) acc[k] = 0.f;
+        float cam[kCamGrad];
+#pragma unroll
+        for (int k = 0; k < kCamGrad; k++) cam[k] = 0.f;
         geometry_backward<double>(sd, fr, (double)g0.x, (double)g0.y, -0.5 * (double)kLog2e * g0.z,
-                                  -(double)kLog2e * g0.w, -0.5 * (double)kLog2e * g1.x, acc);
+                                  -(double)kLog2e * g0.w, -0.5 * (double)kLog2e * g1.x, acc,
+                                  gr.cam ? cam : nullptr);
         acc[13] = acc[14] = acc[15] = acc[16] = 0.f;  // colour and opacity were done in FP32
         store_grad(gr, g.N, gi, acc, true);
+        if (gr.cam) {
+            const int f = find_frame_by_pair(w.frames, (int)w.L.F, p);
+            for (int k = 0; k < kCamGrad; k++) atomicAdd(gr.cam + (size_t)f * kCamGrad + k, cam[k]);
+        }
     }
 }
 
@@ -534,9 +648,13 @@ cudaError_t launch_project_bwd(const Work &w, const GaussPtrs &g, const GradPtrs
     if (mode == 1) {
         // all frames share one set; its size is the first frame's count
         unsigned n = w.L.P / w.L.F;
-        project_bwd_shared_kernel<<<(n + 127) / 128, 128, 0, s>>>(w, g, gr);
+        unsigned blocks = std::min((n + 127) / 128, (unsigned)num_sms * 16u);
+        if (gr.cam) project_bwd_shared_kernel<true><<<blocks, 128, 0, s>>>(w, g, gr);
+        else project_bwd_shared_kernel<false><<<blocks, 128, 0, s>>>(w, g, gr);
     } else {
-        project_bwd_pairs_kernel<<<(w.L.P + 127) / 128, 128, 0, s>>>(w, g, gr, mode == 2 ? 1 : 0);
+        unsigned blocks = std::min((w.L.P + 127) / 128, (unsigned)num_sms * 16u);
+        if (gr.cam) project_bwd_pairs_kernel<true><<<blocks, 128, 0, s>>>(w, g, gr, mode == 2 ? 1 : 0);
+        else project_bwd_pairs_kernel<false><<<blocks, 128, 0, s>>>(w, g, gr, mode == 2 ? 1 : 0);
     }
     return cudaGetLastError();
 }

@@ -56,7 +56,10 @@ class Gaussians(ctypes.Structure):
 
 
 class GaussiansGrad(ctypes.Structure):
-    _fields_ = [(k, ctypes.c_void_p) for k in ("mean", "vel", "log_scale", "quat", "opacity_logit", "rgb")]
+    _fields_ = [(k, ctypes.c_void_p) for k in ("mean", "vel", "log_scale", "quat", "opacity_logit", "rgb",
+                                               "camera")]
+
+CAMERA_GRAD = 16  # per frame: dR (row-major, R as a general matrix), dt, dfx, dfy, dcx, dcy
 
 
 class FrameDesc(ctypes.Structure):
@@ -213,8 +216,9 @@ def gaussians_struct(params: dict) -> Gaussians:
 
 
 def grad_struct(grads: dict) -> GaussiansGrad:
+    """grads: the parameter planes, and optionally "camera" ([F, 16] device tensor)."""
     g = GaussiansGrad()
-    for k in PARAM_KEYS:
+    for k in PARAM_KEYS + ("camera",):
         v = grads.get(k)
         setattr(g, k, _ptr(v) if v is not None else None)
     return g

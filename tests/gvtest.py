@@ -57,9 +57,12 @@ class GpuRun:
             self.ctx.check(st)
         return self
 
-    def backward(self, dL_flat: np.ndarray) -> dict:
+    def backward(self, dL_flat: np.ndarray, camera: bool = False) -> dict:
+        """Gradients of sum(dL_flat * image); with camera, also "camera" [F, 16]."""
         dL = torch.from_numpy(np.ascontiguousarray(dL_flat, np.float32)).cuda()
         grads = {k: torch.zeros_like(v) for k, v in self.params.items()}
+        if camera:
+            grads["camera"] = torch.zeros(len(self.frames), gv.CAMERA_GRAD, device="cuda")
         self.ctx.render_bwd(self.params, self.frames, self.ws, self.T, self.idx, dL, grads)
         torch.cuda.synchronize()
         return {k: v.cpu().numpy() for k, v in grads.items()}
@@ -130,6 +133,17 @@ def compare_grads(gpu: dict, ref: np.ndarray, gabs: np.ndarray, label: str = "",
     assert total_fail == 0, f"{label} gradient mismatches: {stats}"
     assert total_cancel <= max(2, max_cancel_frac * total), f"{label} too many cancellation-limited: {stats}"
     return stats
+
+
+def compare_camera(gpu: np.ndarray, ref: np.ndarray, gabs: np.ndarray, label: str = "") -> None:
+    """Camera gradient of one frame: |g - g_ref| <= 1e-3 |g_ref| + CANCEL_REL * g_abs (a sum
+    over every contributing pair, so FP32 accumulation error scales with the summed absolute
+    terms, not with the possibly cancelled total)."""
+    d = np.abs(gpu.astype(np.float64) - ref)
+    bound = GRAD_REL * np.abs(ref) + CANCEL_REL * gabs + 1e-9
+    rel = d / np.maximum(np.abs(ref), 1e-30)
+    print(f"[camera {label}] max |d|/bound {np.max(d / bound):.2e}, max relative error {np.max(rel):.2e}")
+    assert np.all(d <= bound), (label, list(zip(gpu.tolist(), ref.tolist(), gabs.tolist())))
 
 
 def oracle_pixels_for_frame(g, cam, px, py, params=None):
