@@ -64,7 +64,8 @@ _dp = ctypes.POINTER(ctypes.c_double)
 
 class _Gaussians(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("mean", _dp), ("vel", _dp), ("log_scale", _dp),
-                ("quat", _dp), ("logit", _dp), ("rgb", _dp)]
+                ("quat", _dp), ("logit", _dp), ("rgb", _dp), ("n_ctrl", ctypes.c_int32),
+                ("ctrl", _dp), ("log_scale_t", _dp), ("quat_t", _dp)]
 
 
 @dataclass
@@ -115,7 +116,9 @@ def lib():
         L.orc_render_bwd.argtypes = [ctypes.POINTER(_Gaussians), ctypes.POINTER(_Camera), ctypes.POINTER(_Params),
                                      ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, _dp,
                                      _dp, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                     ctypes.c_int]
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+        L.orc_bspline_basis.argtypes = [ctypes.c_int32, ctypes.c_double, _dp]
+        L.orc_bspline_basis.restype = ctypes.c_int
         L.orc_bin_f32.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 5 + [ctypes.c_int32] * 4 + [ctypes.c_void_p] * 2
         L.orc_bin_f64.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 5 + [ctypes.c_int32] * 4 + [ctypes.c_void_p] * 3
         L.orc_cull_f32.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 7 + [ctypes.c_int32] * 4 + [ctypes.c_void_p] * 3
@@ -139,15 +142,18 @@ class _GaussHolder:
     def __init__(self, g: dict):
         self.arrs = {}
         N = int(np.asarray(g["opacity_logit"]).shape[-1])
-        for k in ("mean", "vel", "log_scale", "quat", "opacity_logit", "rgb"):
+        for k in ("mean", "vel", "log_scale", "quat", "opacity_logit", "rgb", "ctrl", "log_scale_t", "quat_t"):
             if k in g and g[k] is not None:
                 self.arrs[k] = np.ascontiguousarray(np.asarray(g[k], dtype=np.float64))
         self.N = N
+        self.n_ctrl = int(self.arrs["ctrl"].shape[1]) if "ctrl" in self.arrs else 0
         s = _Gaussians()
         s.N = N
         ptr = lambda k: self.arrs[k].ctypes.data_as(_dp) if k in self.arrs else None
         s.mean, s.vel, s.log_scale = ptr("mean"), ptr("vel"), ptr("log_scale")
         s.quat, s.logit, s.rgb = ptr("quat"), ptr("opacity_logit"), ptr("rgb")
+        s.n_ctrl = self.n_ctrl
+        s.ctrl, s.log_scale_t, s.quat_t = ptr("ctrl"), ptr("log_scale_t"), ptr("quat_t")
         self.c = s
 
 
@@ -227,17 +233,25 @@ def render_bwd_pixels(g: dict, cam, px, py, dL_dC, params: Params | None = None,
     g2d = np.zeros((N2D, h.N), np.float64) if want_2d else None
     cam_grad = np.zeros(NCAM, np.float64)
     cam_gabs = np.zeros(NCAM, np.float64)
+    nt = 3 * h.n_ctrl + 21 if h.n_ctrl else 0
+    grad_t = np.zeros((max(nt, 1), h.N), np.float64)
+    gabs_t = np.zeros((max(nt, 1), h.N), np.float64)
     rc = lib().orc_render_bwd(ctypes.byref(h.c), ctypes.byref(_camera(cam)), ctypes.byref(params._c()), n,
                               px.ctypes.data, py.ctypes.data, dL.ctypes.data_as(_dp), grad.ctypes.data_as(_dp),
                               gabs.ctypes.data if gabs is not None else None,
                               g2d.ctypes.data if g2d is not None else None, cam_grad.ctypes.data,
-                              cam_gabs.ctypes.data, nthreads or default_threads())
+                              cam_gabs.ctypes.data, grad_t.ctypes.data if nt else None,
+                              gabs_t.ctypes.data if nt else None, nthreads or default_threads())
     if rc:
         raise MemoryError("oracle backward failed")
     out = dict(grad=grad, cam_grad=cam_grad)
+    if nt:
+        out["grad_t"] = grad_t
     if gabs is not None:
         out["gabs"] = gabs
         out["cam_gabs"] = cam_gabs
+        if nt:
+            out["gabs_t"] = gabs_t
     if g2d is not None:
         out["grad2d"] = g2d
     return out
@@ -249,6 +263,23 @@ def render_bwd_image(g: dict, cam, dL_dC_img, params: Params | None = None, nthr
     yy, xx = np.mgrid[0:H, 0:W]
     d = np.asarray(dL_dC_img, np.float64).reshape(3, H * W).T
     return render_bwd_pixels(g, cam, xx.ravel(), yy.ravel(), d, params, nthreads, **kw)
+
+
+def bspline_basis(n_ctrl: int, t: float) -> np.ndarray:
+    """The clamped cubic B-spline basis N_{i,3}(t) of n_ctrl control points (Sec. 3.2, Eq. 2)."""
+    w = np.zeros(n_ctrl, np.float64)
+    if lib().orc_bspline_basis(n_ctrl, float(t), w.ctypes.data_as(_dp)):
+        raise ValueError("n_ctrl must be in [4, 64]")
+    return w
+
+
+def split_grad_t(grad_t: np.ndarray, n_ctrl: int) -> dict:
+    """Rows of the time-parameterised gradient: ctrl [3, n_ctrl, N], log_scale_t [3, 3, N]
+    (powers t, t^2, t^3 by axis), quat_t [3, 4, N]."""
+    N = grad_t.shape[-1]
+    C = n_ctrl
+    return dict(ctrl=grad_t[:3 * C].reshape(3, C, N), log_scale_t=grad_t[3 * C:3 * C + 9].reshape(3, 3, N),
+                quat_t=grad_t[3 * C + 9:3 * C + 21].reshape(3, 4, N))
 
 
 def split_grad(grad: np.ndarray) -> dict:

@@ -65,6 +65,13 @@ typedef struct {
 typedef struct {
     int64_t N;
     const double *mean, *vel, *log_scale, *quat, *logit, *rgb; /* SoA [k][N]; vel may be NULL */
+    /* Time-parameterised form (Sec. 3.2, Eq. 2-3), used when n_ctrl > 0 (mean and vel are
+     * then ignored): mu(t) = sum_i N_{i,3}(t) P_i over ctrl [3][n_ctrl][N] (clamped cubic
+     * B-spline, uniform interior knots); log_scale(t) = log_scale + sum_{j=1..3} t^j
+     * log_scale_t[j-1] with log_scale_t [3][3][N]; quat(t) likewise with quat_t [3][4][N]
+     * (NULL: constant).  t is the camera's time, in [0, 1]. */
+    int32_t n_ctrl;
+    const double *ctrl, *log_scale_t, *quat_t;
 } orc_gaussians;
 
 /* number of per-Gaussian parameter gradients: mean 3, vel 3, log_scale 3, quat 4, logit 1, rgb 3 */
@@ -102,20 +109,76 @@ static void quat_to_rot(const double q[4], double R[9]) {
     R[6] = 2 * (x * z - w * y);     R[7] = 2 * (y * z + w * x);     R[8] = 1 - 2 * (x * x + y * y);
 }
 
+/* Cubic B-spline basis on the clamped knot vector of n_ctrl control points (Sec. 3.2,
+ * Eq. 2: the first p + 1 = 4 knots at 0, the last 4 at 1, the n_ctrl - 4 others evenly
+ * spaced), by the Cox-de Boor recursion: N_{i,0} = 1 on [u_i, u_{i+1}), then
+ * N_{i,p} = (t - u_i)/(u_{i+p} - u_i) N_{i,p-1} + (u_{i+p+1} - t)/(u_{i+p+1} - u_{i+1}) N_{i+1,p-1}
+ * with 0/0 = 0.  t = 1 falls in the last non-empty interval (the curve ends at the last
+ * control point).  w [n_ctrl] receives N_{i,3}(t). */
+#define ORC_MAX_CTRL 64
+static void bspline_basis(int n_ctrl, double t, double *w) {
+    double u[ORC_MAX_CTRL + 4], Nb[ORC_MAX_CTRL + 4];
+    const int m = n_ctrl + 4; /* knots */
+    for (int i = 0; i < m; i++) {
+        if (i < 4) u[i] = 0.0;
+        else if (i >= n_ctrl) u[i] = 1.0;
+        else u[i] = (double)(i - 3) / (double)(n_ctrl - 3);
+    }
+    if (t < 0.0) t = 0.0;
+    if (t > 1.0) t = 1.0;
+    for (int i = 0; i < m - 1; i++) {
+        int in = u[i] <= t && t < u[i + 1];
+        if (t == 1.0) in = (i == n_ctrl - 1); /* last non-empty interval [u_{n-1}, u_n] */
+        Nb[i] = in ? 1.0 : 0.0;
+    }
+    for (int p = 1; p <= 3; p++)
+        for (int i = 0; i < m - 1 - p; i++) {
+            double a = 0.0, b = 0.0;
+            if (u[i + p] > u[i]) a = (t - u[i]) / (u[i + p] - u[i]) * Nb[i];
+            if (u[i + p + 1] > u[i + 1]) b = (u[i + p + 1] - t) / (u[i + p + 1] - u[i + 1]) * Nb[i + 1];
+            Nb[i] = a + b;
+        }
+    for (int i = 0; i < n_ctrl; i++) w[i] = Nb[i];
+}
+
+/* Exported for the tests: the basis at t (w [n_ctrl]). */
+int orc_bspline_basis(int32_t n_ctrl, double t, double *w) {
+    if (n_ctrl < 4 || n_ctrl > ORC_MAX_CTRL) return 1;
+    bspline_basis(n_ctrl, t, w);
+    return 0;
+}
+
 /* Projection of Gaussian i under the camera (Sec. 3.1 parameterisation, EWA splatting). */
 static void project_one(const orc_gaussians *g, int64_t i, const orc_camera *cam,
                         const orc_params *p, orc_proj *pr) {
     int64_t N = g->N;
     memset(pr, 0, sizeof(*pr));
+    const double t = cam->time;
+    double w[ORC_MAX_CTRL];
+    if (g->n_ctrl > 0) bspline_basis(g->n_ctrl, t, w);
     for (int k = 0; k < 3; k++) {
-        pr->mu[k] = g->mean[k * N + i] + (g->vel ? cam->time * g->vel[k * N + i] : 0.0);
-        pr->s[k] = exp(g->log_scale[k * N + i]);
+        if (g->n_ctrl > 0) {
+            double acc = 0.0;
+            for (int c = 0; c < g->n_ctrl; c++) acc += w[c] * g->ctrl[((int64_t)k * g->n_ctrl + c) * N + i];
+            pr->mu[k] = acc;
+        } else {
+            pr->mu[k] = g->mean[k * N + i] + (g->vel ? t * g->vel[k * N + i] : 0.0);
+        }
+        double ls = g->log_scale[k * N + i];
+        if (g->log_scale_t)
+            for (int j = 1; j <= 3; j++) ls += pow(t, j) * g->log_scale_t[((int64_t)(j - 1) * 3 + k) * N + i];
+        pr->s[k] = exp(ls);
         pr->c[k] = g->rgb[k * N + i];
     }
-    double qq = 0;
-    for (int k = 0; k < 4; k++) qq += g->quat[k * N + i] * g->quat[k * N + i];
+    double qraw[4], qq = 0;
+    for (int k = 0; k < 4; k++) {
+        qraw[k] = g->quat[k * N + i];
+        if (g->quat_t)
+            for (int j = 1; j <= 3; j++) qraw[k] += pow(t, j) * g->quat_t[((int64_t)(j - 1) * 4 + k) * N + i];
+        qq += qraw[k] * qraw[k];
+    }
     pr->qnorm = sqrt(qq);
-    for (int k = 0; k < 4; k++) pr->qn[k] = g->quat[k * N + i] / pr->qnorm;
+    for (int k = 0; k < 4; k++) pr->qn[k] = qraw[k] / pr->qnorm;
     pr->o = 1.0 / (1.0 + exp(-g->logit[i]));
     quat_to_rot(pr->qn, pr->Rq);
     for (int r = 0; r < 3; r++)
@@ -524,6 +587,7 @@ static int list_push(contrib_list *L, int64_t n_new, const int64_t *idx, const d
 
 typedef struct {
     const orc_proj *pr;
+    const orc_gaussians *g;
     int64_t N;
     const orc_params *p;
     const orc_camera *cam;
@@ -532,10 +596,32 @@ typedef struct {
     const double *dL_dC;
     contrib_list *lists; /* one per thread */
     double *grad, *gabs, *grad2d;
+    double *grad_t, *gabs_t; /* time-parameterised form: [3 n_ctrl + 21][N] */
     int tid, nthreads;
     int err;
     double cam_part[ORC_NCAM], cam_abs_part[ORC_NCAM]; /* this thread's camera sums */
 } bwd_job;
+
+/* Rows of the time-parameterised gradient: control points [3][n_ctrl], then log_scale_t
+ * [3][3] (t, t^2, t^3 of each axis), then quat_t [3][4]. */
+static int64_t rows_t(int n_ctrl) { return 3 * (int64_t)n_ctrl + 9 + 12; }
+
+/* Maps a gradient w.r.t. mu(t), log_scale(t), quat(t) (rows 0-2, 6-8, 9-12 of v) onto the
+ * time-parameterised parameters: dP_c = N_c(t) dmu, d(log_scale_t[j]) = t^j dlog_scale,
+ * d(quat_t[j]) = t^j dquat (the weights are non-negative, so the same map carries the
+ * error scale). */
+static void to_time_rows(const orc_gaussians *g, double t, const double *v, double *out_t, int64_t N, int64_t i) {
+    double w[ORC_MAX_CTRL];
+    bspline_basis(g->n_ctrl, t, w);
+    const int64_t C = g->n_ctrl;
+    for (int k = 0; k < 3; k++)
+        for (int64_t c = 0; c < C; c++) out_t[(k * C + c) * N + i] += w[c] * v[k];
+    for (int j = 1; j <= 3; j++) {
+        const double tj = pow(t, j);
+        for (int k = 0; k < 3; k++) out_t[(3 * C + (j - 1) * 3 + k) * N + i] += tj * v[6 + k];
+        for (int k = 0; k < 4; k++) out_t[(3 * C + 9 + (j - 1) * 4 + k) * N + i] += tj * v[9 + k];
+    }
+}
 
 static void *bwd_pixels_worker(void *arg) {
     bwd_job *j = (bwd_job *)arg;
@@ -574,6 +660,10 @@ static void *bwd_accum_worker(void *arg) {
             const double *d = L->d2 + e * ORC_N2D;
             double out[ORC_NGRAD];
             chain_rule(&j->pr[i], j->cam, d, out, j->cam_part);
+            if (j->g->n_ctrl > 0) {
+                if (j->grad_t) to_time_rows(j->g, j->cam->time, out, j->grad_t, N, i);
+                for (int k = 0; k < 6; k++) out[k] = 0.0; /* mean and vel are not parameters then */
+            }
             for (int k = 0; k < ORC_NGRAD; k++) j->grad[k * N + i] += out[k];
             if (abs2d)
                 for (int k = 0; k < ORC_N2D; k++) abs2d[k * N + i] += L->da[e * ORC_N2D + k];
@@ -594,7 +684,12 @@ static void *bwd_accum_worker(void *arg) {
                 double unit[ORC_N2D] = {0}, col[ORC_NGRAD], ccol[ORC_NCAM] = {0};
                 unit[c] = 1.0;
                 chain_rule(&j->pr[i], j->cam, unit, col, ccol);
-                for (int k = 0; k < ORC_NGRAD; k++) j->gabs[k * N + i] += fabs(col[k]) * a;
+                for (int k = 0; k < ORC_NGRAD; k++) col[k] = fabs(col[k]) * a;
+                if (j->g->n_ctrl > 0) {
+                    if (j->gabs_t) to_time_rows(j->g, j->cam->time, col, j->gabs_t, N, i);
+                    for (int k = 0; k < 6; k++) col[k] = 0.0;
+                }
+                for (int k = 0; k < ORC_NGRAD; k++) j->gabs[k * N + i] += col[k];
                 for (int k = 0; k < ORC_NCAM; k++) j->cam_abs_part[k] += fabs(ccol[k]) * a;
             }
         }
@@ -613,19 +708,27 @@ static void *bwd_accum_worker(void *arg) {
 int orc_render_bwd(const orc_gaussians *g, const orc_camera *cam, const orc_params *p,
                    int64_t npix, const int32_t *px, const int32_t *py, const double *dL_dC,
                    double *grad, double *gabs, double *grad2d, double *cam_grad, double *cam_gabs,
-                   int nthreads) {
+                   double *grad_t, double *gabs_t, int nthreads) {
     if (nthreads < 1) nthreads = 1;
     int64_t N = g->N;
     memset(grad, 0, sizeof(double) * ORC_NGRAD * (size_t)N);
     if (gabs) memset(gabs, 0, sizeof(double) * ORC_NGRAD * (size_t)N);
     if (grad2d) memset(grad2d, 0, sizeof(double) * ORC_N2D * (size_t)N);
+    if (g->n_ctrl > ORC_MAX_CTRL || (g->n_ctrl > 0 && g->n_ctrl < 4)) return 1;
+    if (g->n_ctrl > 0) {
+        if (grad_t) memset(grad_t, 0, sizeof(double) * (size_t)rows_t(g->n_ctrl) * (size_t)N);
+        if (gabs_t) memset(gabs_t, 0, sizeof(double) * (size_t)rows_t(g->n_ctrl) * (size_t)N);
+    } else {
+        grad_t = gabs_t = NULL;
+    }
     orc_proj *pr = project_all(g, cam, p);
     if (!pr) return 1;
     contrib_list *lists = (contrib_list *)calloc((size_t)nthreads, sizeof(contrib_list));
     pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
     bwd_job *jobs = (bwd_job *)malloc(sizeof(bwd_job) * (size_t)nthreads);
     for (int t = 0; t < nthreads; t++) {
-        bwd_job jb = {pr, N, p, cam, npix, px, py, dL_dC, lists, grad, gabs, grad2d, t, nthreads, 0, {0}, {0}};
+        bwd_job jb = {pr, g, N, p, cam, npix, px, py, dL_dC, lists, grad, gabs, grad2d, grad_t,
+                      gabs ? gabs_t : NULL, t, nthreads, 0, {0}, {0}};
         jobs[t] = jb;
         pthread_create(&th[t], NULL, bwd_pixels_worker, &jobs[t]);
     }
