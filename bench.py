@@ -360,6 +360,7 @@ def run_gv(args):
     }
     if not args.no_extras and args.workload == "frame540p":
         out["camera_adjoint"] = run_camera_adjoint(torch, ctx, step, grads, flush, P, max(50, args.steps // 4))
+        out["motion"] = run_motion(torch, gv, synth, ctx, dev, flush, frames[0].cam, target, max(50, args.steps // 4))
         out["batched"] = run_batched(torch, gv, synth, ctx, dev, flush, max(20, args.steps // 4))
         out["e2e"] = run_e2e(torch, gv, ctx, params, target, frames, ws, dev, flush, max(20, args.steps // 4), scale,
                              world)
@@ -412,6 +413,63 @@ def run_camera_adjoint(torch, ctx, step, grads, flush, P, steps):
             "project_bwd_ms": round(cam_stage, 4), "project_bwd_ms_without": round(base_stage, 4),
             "workload": "the per-frame step above with the frame's camera gradient (dR, dt, dfx, dfy, dcx, dcy) "
                         "also accumulated"}
+
+
+def run_motion(torch, gv, synth, ctx, dev, flush, cam0, target, steps):
+    """The per-frame step on time-parameterised Gaussians (the paper's Eq. 2-3: means on a
+    cubic B-spline over 8 control points, cubic log-scale and quaternion terms), same frame
+    size, Gaussian count and camera, at t = 0.4: throughput and the projection stages."""
+    import dataclasses
+    rng = np.random.default_rng(synth.SEED_BASE + 9)
+    g = synth.spline_gaussians(rng, N_GAUSS, 8)
+    params = {k: torch.from_numpy(v).to(dev) for k, v in g.items()}
+    cam = dataclasses.replace(cam0, time=0.4)
+    frames = [gv.Frame(cam, 0, N_GAUSS, 0)]
+    P = cam.W * cam.H
+    image = torch.empty(3 * P, device=dev)
+    T = torch.empty(P, device=dev)
+    idx = torch.empty(P, dtype=torch.int32, device=dev)
+    dL = torch.empty(3 * P, device=dev)
+    loss = torch.zeros(1, device=dev)
+    grads = {k: torch.zeros_like(v) for k, v in params.items()}
+    ws = torch.empty(ctx.workspace_size(frames, 0), dtype=torch.uint8, device=dev)
+    ctx.render_fwd(params, frames, ws, image, T, idx)
+    st, keys = ctx.read_status(ws, raise_on_error=False)
+    ws = torch.empty(ctx.workspace_size(frames, int(keys * 1.2) + 65536), dtype=torch.uint8, device=dev)
+    scale = 1.0 / (3 * P)
+
+    def step():
+        ctx.render_fwd(params, frames, ws, image, T, idx)
+        loss.zero_()
+        ctx.l2_loss_grad(image, target, scale, dL, loss)
+        for v in grads.values():
+            v.zero_()
+        ctx.render_bwd(params, frames, ws, T, idx, dL, grads)
+
+    for _ in range(5):
+        step()
+    ctx.read_status(ws)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        flush.zero_()
+        ev[i][0].record()
+        step()
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / steps
+    ctx.profile_enable(True)
+    acc = {}
+    for _ in range(20):
+        step()
+        st_ms, _ = ctx.profile_read()
+        for k in ("project", "project_bwd"):
+            acc.setdefault(k, []).append(st_ms[k])
+    ctx.profile_enable(False)
+    return {"value": round(P / (ms / 1000) / 1e6, 2), "unit": "Mpix/s", "ms_per_step": round(ms, 4),
+            "project_ms": round(statistics.median(acc["project"]), 4),
+            "project_bwd_ms": round(statistics.median(acc["project_bwd"]), 4),
+            "workload": "one 960x540 frame, 200,000 time-parameterised Gaussians (8 B-spline control points, "
+                        "cubic log-scale and quaternion terms) at t = 0.4, fwd+L2 loss+bwd"}
 
 
 def run_batched(torch, gv, synth, ctx, dev, flush, steps):

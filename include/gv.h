@@ -93,10 +93,22 @@ typedef struct {
     const float *quat;          /* [4][N] (w,x,y,z), need not be normalised */
     const float *opacity_logit; /* [N] */
     const float *rgb;           /* [3][N] */
+    /* Time-parameterised form (Sec. 3.2): used when n_ctrl > 0, then mean and vel are
+     * ignored (may be NULL) and the camera's time t is read in [0, 1] (clamped).
+     * Eq. 2: mu(t) = sum_i N_{i,3}(t) P_i, a clamped cubic B-spline over n_ctrl in [4, 64]
+     * control points ctrl [3][n_ctrl][N] (knots: four at 0, four at 1, the others evenly
+     * spaced).  Eq. 3: log_scale(t) = log_scale + t a1 + t^2 a2 + t^3 a3 with log_scale_t
+     * [3][3][N] = (a1, a2, a3) by axis, quat(t) likewise with quat_t [3][4][N] (each NULL:
+     * constant in time).  Colour and opacity stay constant. */
+    int32_t n_ctrl;
+    const float *ctrl;
+    const float *log_scale_t;
+    const float *quat_t;
 } gv_gaussians;
 
 /* Gradient planes, same layout; the backward ACCUMULATES (+=) into them.  vel may be
- * NULL (its gradient is then dropped).  camera, if not NULL, is [F][16] FP32 (device):
+ * NULL (its gradient is then dropped); with the time-parameterised form, mean and vel
+ * get nothing and ctrl, log_scale_t, quat_t receive the gradients of those planes.  camera, if not NULL, is [F][16] FP32 (device):
  * per frame of the call the gradient w.r.t. its camera (Sec. 3.4: the extrinsics and the
  * intrinsics), dR[9] (R row-major, taken as a general matrix: the caller maps it to its
  * rotation parameters), dt[3], dfx, dfy, dcx, dcy; also accumulated (+=). */
@@ -104,6 +116,7 @@ typedef struct {
 typedef struct {
     float *mean, *vel, *log_scale, *quat, *opacity_logit, *rgb;
     float *camera;
+    float *ctrl, *log_scale_t, *quat_t; /* time-parameterised form: same layouts, or NULL */
 } gv_gaussians_grad;
 
 /* One frame of a batch: its camera, the Gaussian subset [gauss_offset, gauss_offset +

@@ -153,7 +153,7 @@ static void project_one(const orc_gaussians *g, int64_t i, const orc_camera *cam
                         const orc_params *p, orc_proj *pr) {
     int64_t N = g->N;
     memset(pr, 0, sizeof(*pr));
-    const double t = cam->time;
+    const double t = g->n_ctrl > 0 ? fmin(1.0, fmax(0.0, cam->time)) : cam->time; /* [0, 1] for Eq. 2-3 */
     double w[ORC_MAX_CTRL];
     if (g->n_ctrl > 0) bspline_basis(g->n_ctrl, t, w);
     for (int k = 0; k < 3; k++) {
@@ -661,7 +661,7 @@ static void *bwd_accum_worker(void *arg) {
             double out[ORC_NGRAD];
             chain_rule(&j->pr[i], j->cam, d, out, j->cam_part);
             if (j->g->n_ctrl > 0) {
-                if (j->grad_t) to_time_rows(j->g, j->cam->time, out, j->grad_t, N, i);
+                if (j->grad_t) to_time_rows(j->g, fmin(1.0, fmax(0.0, j->cam->time)), out, j->grad_t, N, i);
                 for (int k = 0; k < 6; k++) out[k] = 0.0; /* mean and vel are not parameters then */
             }
             for (int k = 0; k < ORC_NGRAD; k++) j->grad[k * N + i] += out[k];
@@ -686,7 +686,7 @@ static void *bwd_accum_worker(void *arg) {
                 chain_rule(&j->pr[i], j->cam, unit, col, ccol);
                 for (int k = 0; k < ORC_NGRAD; k++) col[k] = fabs(col[k]) * a;
                 if (j->g->n_ctrl > 0) {
-                    if (j->gabs_t) to_time_rows(j->g, j->cam->time, col, j->gabs_t, N, i);
+                    if (j->gabs_t) to_time_rows(j->g, fmin(1.0, fmax(0.0, j->cam->time)), col, j->gabs_t, N, i);
                     for (int k = 0; k < 6; k++) col[k] = 0.0;
                 }
                 for (int k = 0; k < ORC_NGRAD; k++) j->gabs[k * N + i] += col[k];

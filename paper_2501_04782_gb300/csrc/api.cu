@@ -95,8 +95,34 @@ struct Plan {
 
 // Frame table, sizes and byte offsets of one call.  key_cap_req > 0 fixes the key
 // capacity; otherwise it is the largest that fits in ws_bytes.
+// The four non-zero cubic B-spline weights at t of the clamped, uniformly knotted spline
+// over n_ctrl control points (Sec. 3.2, Eq. 2), by the Cox-de Boor recursion on the span
+// [u_k, u_{k+1}) holding t (t = 1: the last span); lo = k - 3 is the first control point.
+void spline_weights(int n_ctrl, double t, int &lo, float w[4]) {
+    auto u = [n_ctrl](int i) {
+        return i < 4 ? 0.0 : (i >= n_ctrl ? 1.0 : (double)(i - 3) / (double)(n_ctrl - 3));
+    };
+    t = std::min(1.0, std::max(0.0, t));
+    int k = 3;
+    while (k < n_ctrl - 1 && !(t < u(k + 1))) k++;
+    double N[4] = {1.0, 0.0, 0.0, 0.0};  // N[j] = N_{k-p+j, p} for the current degree p
+    for (int p = 1; p <= 3; p++) {
+        double nx[4] = {0.0, 0.0, 0.0, 0.0};
+        for (int j = 0; j <= p; j++) {
+            const int i = k - p + j;
+            double a = 0.0, b = 0.0;
+            if (j >= 1 && u(i + p) > u(i)) a = (t - u(i)) / (u(i + p) - u(i)) * N[j - 1];
+            if (j < p && u(i + p + 1) > u(i + 1)) b = (u(i + p + 1) - t) / (u(i + p + 1) - u(i + 1)) * N[j];
+            nx[j] = a + b;
+        }
+        for (int j = 0; j < 4; j++) N[j] = nx[j];
+    }
+    lo = k - 3;
+    for (int j = 0; j < 4; j++) w[j] = (float)N[j];
+}
+
 gv_status make_plan(gv_ctx *ctx, const gv_options &o, long long N, const gv_frame_desc *fd, int F,
-                    long long key_cap_req, size_t ws_bytes, Plan &pl) {
+                    long long key_cap_req, size_t ws_bytes, Plan &pl, int n_ctrl = 0) {
     if (F < 1 || F > GV_MAX_FRAMES) return fail(ctx, GV_ERR_INVALID_ARG, "frame count %d out of [1, %d]", F, GV_MAX_FRAMES);
     if (!fd) return fail(ctx, GV_ERR_INVALID_ARG, "frames is NULL");
     pl.frames.resize(F);
@@ -117,6 +143,10 @@ gv_status make_plan(gv_ctx *ctx, const gv_options &o, long long N, const gv_fram
         for (int i = 0; i < 9; i++) x.R[i] = c.R[i];
         for (int i = 0; i < 3; i++) x.t[i] = c.t[i];
         x.time = c.time;
+        if (n_ctrl > 0) {
+            x.time = std::min(1.f, std::max(0.f, c.time));
+            spline_weights(n_ctrl, c.time, x.spline_lo, x.spline_w);
+        }
         x.gauss_offset = d.gauss_offset;
         x.gauss_count = (unsigned)d.gauss_count;
         x.pixel_offset = d.pixel_offset;
@@ -258,13 +288,18 @@ GaussPtrs gauss_ptrs(const gv_gaussians *g) {
     p.mean = g->mean; p.vel = g->vel; p.log_scale = g->log_scale;
     p.quat = g->quat; p.logit = g->opacity_logit; p.rgb = g->rgb;
     p.N = g->N;
+    p.n_ctrl = g->n_ctrl;
+    p.ctrl = g->ctrl; p.log_scale_t = g->log_scale_t; p.quat_t = g->quat_t;
+    if (p.n_ctrl > 0) p.vel = nullptr;
     return p;
 }
 
 gv_status check_gaussians(gv_ctx *ctx, const gv_gaussians *g) {
     if (!g) return fail(ctx, GV_ERR_INVALID_ARG, "gaussians is NULL");
     if (g->N < 0) return fail(ctx, GV_ERR_INVALID_ARG, "negative Gaussian count");
-    if (g->N > 0 && (!g->mean || !g->log_scale || !g->quat || !g->opacity_logit || !g->rgb))
+    if (g->n_ctrl != 0 && (g->n_ctrl < 4 || g->n_ctrl > 64))
+        return fail(ctx, GV_ERR_INVALID_ARG, "n_ctrl %d outside [4, 64]", g->n_ctrl);
+    if (g->N > 0 && ((g->n_ctrl ? !g->ctrl : !g->mean) || !g->log_scale || !g->quat || !g->opacity_logit || !g->rgb))
         return fail(ctx, GV_ERR_INVALID_ARG, "a required Gaussian parameter plane is NULL");
     return GV_OK;
 }
@@ -356,6 +391,7 @@ gv_status backward_stages(gv_ctx *ctx, const gv_gaussians *g, const Plan &pl, co
     gp.mean = grad->mean; gp.vel = grad->vel; gp.log_scale = grad->log_scale;
     gp.quat = grad->quat; gp.logit = grad->opacity_logit; gp.rgb = grad->rgb;
     gp.cam = grad->camera;
+    gp.ctrl = grad->ctrl; gp.log_scale_t = grad->log_scale_t; gp.quat_t = grad->quat_t;
     {
         StageTimer tm(ctx, GV_STAGE_PROJECT_BWD, s, 2);
         const GaussPtrs gptr = gauss_ptrs(g);
@@ -376,8 +412,11 @@ gv_status backward_stages(gv_ctx *ctx, const gv_gaussians *g, const Plan &pl, co
     return GV_OK;
 }
 
-gv_status check_grad(gv_ctx *ctx, const gv_gaussians_grad *grad) {
-    if (!grad || !grad->mean || !grad->log_scale || !grad->quat || !grad->opacity_logit || !grad->rgb)
+// The time-parameterised form needs the control-point plane instead of the mean plane.
+gv_status check_grad(gv_ctx *ctx, const gv_gaussians_grad *grad, const gv_gaussians *g) {
+    const bool spline = g && g->n_ctrl > 0;
+    if (!grad || (spline ? !grad->ctrl : !grad->mean) || !grad->log_scale || !grad->quat || !grad->opacity_logit ||
+        !grad->rgb)
         return fail(ctx, GV_ERR_INVALID_ARG, "a required gradient plane is NULL");
     return GV_OK;
 }
@@ -433,6 +472,7 @@ struct gv_graph {
     cudaGraphExec_t exec = nullptr;
     std::vector<cudaGraphNode_t> setup_nodes;  // in launch order, one per frame chunk
     Plan plan;
+    int n_ctrl = 0;  // time-parameterised means: the frames' spline weights follow their times
     Work work;
     std::vector<gv_frame_desc> frames;
 };
@@ -557,7 +597,7 @@ gv_status gv_render_batch_fwd(gv_ctx *ctx, const gv_gaussians *g, const gv_frame
     if (st != GV_OK) return st;
     if (!workspace || !image || !final_T || !last_idx) return fail(ctx, GV_ERR_INVALID_ARG, "NULL buffer");
     Plan pl;
-    st = make_plan(ctx, ctx->opt, g->N, frames, F, 0, ws_bytes, pl);
+    st = make_plan(ctx, ctx->opt, g->N, frames, F, 0, ws_bytes, pl, g->n_ctrl);
     if (st != GV_OK) return st;
     Work w = make_work(workspace, pl.L);
     return forward_stages(ctx, g, pl, w, image, final_T, last_idx, (cudaStream_t)stream);
@@ -569,11 +609,11 @@ gv_status gv_render_batch_bwd(gv_ctx *ctx, const gv_gaussians *g, const gv_frame
     if (!ctx) return GV_ERR_INVALID_ARG;
     gv_status st = check_gaussians(ctx, g);
     if (st != GV_OK) return st;
-    st = check_grad(ctx, grad);
+    st = check_grad(ctx, grad, g);
     if (st != GV_OK) return st;
     if (!workspace || !final_T || !last_idx || !dL_dimage) return fail(ctx, GV_ERR_INVALID_ARG, "NULL buffer");
     Plan pl;
-    st = make_plan(ctx, ctx->opt, g->N, frames, F, 0, ws_bytes, pl);
+    st = make_plan(ctx, ctx->opt, g->N, frames, F, 0, ws_bytes, pl, g->n_ctrl);
     if (st != GV_OK) return st;
     Work w = make_work(workspace, pl.L);
     return backward_stages(ctx, g, pl, w, final_T, last_idx, dL_dimage, grad, (cudaStream_t)stream);
@@ -607,7 +647,7 @@ gv_status gv_render_fwd_noalloc(gv_ctx *ctx, const gv_gaussians *g, const gv_cam
     GV_CUDA(noalloc_scratch(device, &scratch));
     gv_frame_desc d = single_frame(cam, g->N);
     Plan pl;
-    st = make_plan(ctx, ctx->opt, g->N, &d, 1, 0, GV_NOALLOC_SCRATCH_BYTES, pl);
+    st = make_plan(ctx, ctx->opt, g->N, &d, 1, 0, GV_NOALLOC_SCRATCH_BYTES, pl, g->n_ctrl);
     if (st != GV_OK)
         return fail(ctx, GV_ERR_INVALID_ARG,
                     "%d Gaussians on a %dx%d frame need more than the %u-byte static scratch (%s)", (int)g->N,
@@ -738,13 +778,14 @@ gv_status gv_graph_capture(gv_ctx *ctx, const gv_gaussians *g, const gv_frame_de
     gv_status st = check_gaussians(ctx, g);
     if (st != GV_OK) return st;
     if (dL_dimage) {
-        st = check_grad(ctx, grad);
+        st = check_grad(ctx, grad, g);
         if (st != GV_OK) return st;
     }
     gv_graph *G = new (std::nothrow) gv_graph();
     if (!G) return fail(ctx, GV_ERR_INVALID_ARG, "out of host memory");
     G->ctx = ctx;
-    st = make_plan(ctx, ctx->opt, g->N, frames, F, 0, ws_bytes, G->plan);
+    st = make_plan(ctx, ctx->opt, g->N, frames, F, 0, ws_bytes, G->plan, g->n_ctrl);
+    G->n_ctrl = g->n_ctrl;
     if (st != GV_OK) { delete G; return st; }
     G->work = make_work(workspace, G->plan.L);
     G->frames.assign(frames, frames + F);
@@ -810,7 +851,7 @@ gv_status gv_graph_set_frames(gv_graph *G, const gv_frame_desc *frames, int32_t 
     Plan pl;
     long long N = 0;
     for (int f = 0; f < F; f++) N = std::max<long long>(N, frames[f].gauss_offset + frames[f].gauss_count);
-    gv_status st = make_plan(ctx, ctx->opt, N, frames, F, G->plan.L.key_cap, 0, pl);
+    gv_status st = make_plan(ctx, ctx->opt, N, frames, F, G->plan.L.key_cap, 0, pl, G->n_ctrl);
     if (st != GV_OK) return st;
     int ci = 0;
     for (int first = 0; first < F; first += kMaxFramesPerSetup, ci++) {

@@ -45,6 +45,10 @@ struct DevFrame {
     long long pixel_offset;
     unsigned pair_offset, gauss_count;
     unsigned tile_offset, tiles_x, tiles_y, pad;
+    // time-parameterised means: the four control points ctrl[spline_lo .. + 3] carry the
+    // non-zero cubic B-spline weights spline_w at this frame's time (host-computed)
+    int spline_lo;
+    float spline_w[4];
 };
 
 struct DevHeader {
@@ -142,11 +146,14 @@ struct Work {
 struct GaussPtrs {
     const float *mean, *vel, *log_scale, *quat, *logit, *rgb;
     long long N;
+    int n_ctrl;  // > 0: means on the B-spline over ctrl; log_scale_t / quat_t: cubic terms (or NULL)
+    const float *ctrl, *log_scale_t, *quat_t;
 };
 
 struct GradPtrs {
     float *mean, *vel, *log_scale, *quat, *logit, *rgb;
     float *cam;  // [F][kCamGrad] or NULL
+    float *ctrl, *log_scale_t, *quat_t;  // time-parameterised form
 };
 
 // Camera gradient per frame: dR (9, row-major), dt (3), dfx, dfy, dcx, dcy.

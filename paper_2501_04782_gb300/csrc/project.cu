@@ -41,23 +41,49 @@ struct PairState {
     bool valid;
 };
 
-template <typename F>
+// SPLINE: the time-parameterised form (g.n_ctrl > 0: B-spline means, cubic log-scale and
+// quaternion); otherwise mean + t vel and constant log-scale and quaternion.
+template <typename F, bool SPLINE = false>
 __device__ __forceinline__ void load_and_project(const GaussPtrs &g, long long gi, const DevFrame &fr,
                                                  PairState<F> &st) {
     const long long N = g.N;
     const F time = (F)fr.time;
-    st.mx = (F)g.mean[gi];
-    st.my = (F)g.mean[N + gi];
-    st.mz = (F)g.mean[2 * N + gi];
-    if (g.vel) {
-        st.mx = fma_(time, (F)g.vel[gi], st.mx);
-        st.my = fma_(time, (F)g.vel[N + gi], st.my);
-        st.mz = fma_(time, (F)g.vel[2 * N + gi], st.mz);
+    if constexpr (SPLINE) {  // Eq. 2: mu(t) = sum_i N_{i,3}(t) P_i over the four non-zero weights
+        const long long C = g.n_ctrl;
+        F m[3] = {(F)0, (F)0, (F)0};
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const F wj = (F)fr.spline_w[j];
+            const long long c = fr.spline_lo + j;
+#pragma unroll
+            for (int k = 0; k < 3; k++) m[k] = fma_(wj, (F)g.ctrl[(k * C + c) * N + gi], m[k]);
+        }
+        st.mx = m[0]; st.my = m[1]; st.mz = m[2];
+    } else {
+        st.mx = (F)g.mean[gi];
+        st.my = (F)g.mean[N + gi];
+        st.mz = (F)g.mean[2 * N + gi];
+        if (g.vel) {
+            st.mx = fma_(time, (F)g.vel[gi], st.mx);
+            st.my = fma_(time, (F)g.vel[N + gi], st.my);
+            st.mz = fma_(time, (F)g.vel[2 * N + gi], st.mz);
+        }
     }
-    st.s0 = exp_((F)g.log_scale[gi]);
-    st.s1 = exp_((F)g.log_scale[N + gi]);
-    st.s2 = exp_((F)g.log_scale[2 * N + gi]);
-    F qw = (F)g.quat[gi], qx = (F)g.quat[N + gi], qy = (F)g.quat[2 * N + gi], qz = (F)g.quat[3 * N + gi];
+    // Eq. 3: log-scale and quaternion as cubic polynomials of t (t^0 term: the plain plane)
+    auto cubic = [&](const float *base, const float *terms, int rows, int k) -> F {
+        F v = (F)base[k * N + gi];
+        if (SPLINE && terms) {
+            const F a1 = (F)terms[(0 * rows + k) * N + gi], a2 = (F)terms[(1 * rows + k) * N + gi],
+                    a3 = (F)terms[(2 * rows + k) * N + gi];
+            v = fma_(time, fma_(time, fma_(time, a3, a2), a1), v);
+        }
+        return v;
+    };
+    st.s0 = exp_(cubic(g.log_scale, g.log_scale_t, 3, 0));
+    st.s1 = exp_(cubic(g.log_scale, g.log_scale_t, 3, 1));
+    st.s2 = exp_(cubic(g.log_scale, g.log_scale_t, 3, 2));
+    F qw = cubic(g.quat, g.quat_t, 4, 0), qx = cubic(g.quat, g.quat_t, 4, 1), qy = cubic(g.quat, g.quat_t, 4, 2),
+      qz = cubic(g.quat, g.quat_t, 4, 3);
     F inv = rsqrt_(qw * qw + qx * qx + qy * qy + qz * qz);
     st.inv_qn = inv;
     qw *= inv; qx *= inv; qy *= inv; qz *= inv;
@@ -241,6 +267,7 @@ __device__ __forceinline__ bool ill_conditioned(const PairState<float> &st) {
 }
 
 // Grid-stride over the pairs so each block flushes its counters once.
+template <bool SPLINE>
 __global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, int lw, int lh, int tile_passes) {
     __shared__ BinShared sb;
     bin_shared_init(sb);
@@ -259,7 +286,7 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, i
             const DevFrame &fr = w.frames[f];
             long long gi = fr.gauss_offset + (long long)(p - fr.pair_offset);
             PairState<float> st;
-            load_and_project(g, gi, fr, st);
+            load_and_project<float, SPLINE>(g, gi, fr, st);
             // alpha >= 1/255 needs d^T conic d <= tau = 2 ln(255 o)
             const float tau = st.valid ? fminf(2.f * (kLn255 + logf(st.o)), kExtK * kExtK) : 0.f;
             const unsigned cells = bin_pair(w, p, st.u, st.v, st.a, st.b, st.c, tau, fr, (unsigned)f, lw, lh, pb);
@@ -449,9 +476,11 @@ __device__ __forceinline__ void pair_backward(const PairState<float> &st, bool d
 // (the FP64 kernel may add into them concurrently), or left alone when skip_geo; rows
 // [13, 17) (opacity, colour) atomically when atomic.
 __device__ __forceinline__ void store_grad(const GradPtrs &gr, long long N, long long gi, const float acc[17],
-                                           bool atomic, bool geo_atomic = false, bool skip_geo = false) {
-    float *rows[17] = {gr.mean, gr.mean + N, gr.mean + 2 * N,
-                       gr.vel, gr.vel ? gr.vel + N : nullptr, gr.vel ? gr.vel + 2 * N : nullptr,
+                                           bool atomic, bool geo_atomic = false, bool skip_geo = false,
+                                           bool spline = false) {
+    float *mean = spline ? nullptr : gr.mean, *vel = spline ? nullptr : gr.vel;
+    float *rows[17] = {mean, mean ? mean + N : nullptr, mean ? mean + 2 * N : nullptr,
+                       vel, vel ? vel + N : nullptr, vel ? vel + 2 * N : nullptr,
                        gr.log_scale, gr.log_scale + N, gr.log_scale + 2 * N,
                        gr.quat, gr.quat + N, gr.quat + 2 * N, gr.quat + 3 * N,
                        gr.logit, gr.rgb, gr.rgb + N, gr.rgb + 2 * N};
@@ -460,6 +489,35 @@ __device__ __forceinline__ void store_grad(const GradPtrs &gr, long long N, long
         if (!rows[k] || (k < 13 && skip_geo)) continue;
         if (atomic || (k < 13 && geo_atomic)) atomicAdd(rows[k] + gi, acc[k]);
         else rows[k][gi] += acc[k];
+    }
+}
+
+// The time-parameterised planes of one pair's geometric gradient (rows 0-2: d mu(t), rows
+// 6-8: d log_scale(t), rows 9-12: d quat(t)): dP_{lo+j} += w_j d mu for the frame's four
+// spline weights, and the t, t^2, t^3 coefficients get t^p times the log-scale and
+// quaternion gradients (their t^0 terms are the plain planes, written by store_grad).
+__device__ __forceinline__ void store_grad_time(const GradPtrs &gr, const GaussPtrs &g, const DevFrame &fr,
+                                                long long gi, const float acc[17], bool atomic) {
+    const long long N = g.N, C = g.n_ctrl;
+    auto add = [atomic](float *dst, float v) {
+        if (atomic) atomicAdd(dst, v);
+        else *dst += v;
+    };
+    if (gr.ctrl)
+#pragma unroll
+        for (int j = 0; j < 4; j++)
+#pragma unroll
+            for (int k = 0; k < 3; k++) add(gr.ctrl + (k * C + fr.spline_lo + j) * N + gi, fr.spline_w[j] * acc[k]);
+    const float t = fr.time;
+    float tp = t;
+#pragma unroll
+    for (int p = 0; p < 3; p++, tp *= t) {
+        if (gr.log_scale_t && g.log_scale_t)
+#pragma unroll
+            for (int k = 0; k < 3; k++) add(gr.log_scale_t + (p * 3 + k) * N + gi, tp * acc[6 + k]);
+        if (gr.quat_t && g.quat_t)
+#pragma unroll
+            for (int k = 0; k < 4; k++) add(gr.quat_t + (p * 4 + k) * N + gi, tp * acc[9 + k]);
     }
 }
 
@@ -520,8 +578,9 @@ __device__ __forceinline__ void cam_block_flush(float (*s_cam)[kCamGrad], int F,
 
 // mode 0: one thread per pair, each Gaussian in at most one frame (plain +=)
 // mode 2: one thread per pair, overlapping sets (atomicAdd)
-// Grid-stride over the pairs; CAM: also the camera gradients of the frames.
-template <bool CAM>
+// Grid-stride over the pairs; CAM: also the camera gradients of the frames; SPLINE: the
+// time-parameterised form.
+template <bool CAM, bool SPLINE>
 __global__ void __launch_bounds__(128) project_bwd_pairs_kernel(Work w, GaussPtrs g, GradPtrs gr, int atomic) {
     __shared__ float s_cam[CAM ? kCamSmemFrames : 1][kCamGrad];
     const int F = (int)w.L.F;
@@ -537,13 +596,14 @@ __global__ void __launch_bounds__(128) project_bwd_pairs_kernel(Work w, GaussPtr
             const DevFrame &fr = w.frames[f];
             long long gi = fr.gauss_offset + (long long)(p - fr.pair_offset);
             PairState<float> st;
-            load_and_project(g, gi, fr, st);
+            load_and_project<float, SPLINE>(g, gi, fr, st);
             float acc[17];
 #pragma unroll
             for (int k = 0; k < 17; k++) acc[k] = 0.f;
             const bool deferred = (w.rect[p].w & kRectFp64) != 0u;
             pair_backward(st, deferred, fr, w.g0[p], w.g1[p], w.g2[p], acc, CAM ? cam : nullptr);
-            store_grad(gr, g.N, gi, acc, atomic != 0, false, deferred);
+            store_grad(gr, g.N, gi, acc, atomic != 0, false, deferred, SPLINE);
+            if (SPLINE && !deferred) store_grad_time(gr, g, fr, gi, acc, atomic != 0);
         }
         if (CAM) cam_add(cam, f, s_cam, gr.cam);
     }
@@ -551,7 +611,8 @@ __global__ void __launch_bounds__(128) project_bwd_pairs_kernel(Work w, GaussPtr
 }
 
 // mode 1: one shared Gaussian set; one thread per Gaussian sums over all frames (grid-stride).
-template <bool CAM>
+// SPLINE: the time-parameterised form (g.n_ctrl > 0).
+template <bool CAM, bool SPLINE>
 __global__ void __launch_bounds__(128) project_bwd_shared_kernel(Work w, GaussPtrs g, GradPtrs gr) {
     __shared__ float s_cam[CAM ? kCamSmemFrames : 1][kCamGrad];
     const int F = (int)w.L.F;
@@ -573,14 +634,27 @@ __global__ void __launch_bounds__(128) project_bwd_shared_kernel(Work w, GaussPt
                 const DevFrame &fr = w.frames[f];
                 unsigned p = fr.pair_offset + j;
                 PairState<float> st;
-                load_and_project(g, gi, fr, st);
+                load_and_project<float, SPLINE>(g, gi, fr, st);
                 const bool deferred = (w.rect[p].w & kRectFp64) != 0u;
                 any_deferred |= deferred;
-                pair_backward(st, deferred, fr, w.g0[p], w.g1[p], w.g2[p], acc, CAM ? cam : nullptr);
+                if (SPLINE) {
+                    // the frame's spline weights and powers of t differ: map this frame's
+                    // geometric gradient now (the FP64 kernel adds atomically to the same
+                    // planes when any frame of this Gaussian was deferred)
+                    float accf[17];
+#pragma unroll
+                    for (int k = 0; k < 17; k++) accf[k] = 0.f;
+                    pair_backward(st, deferred, fr, w.g0[p], w.g1[p], w.g2[p], accf, CAM ? cam : nullptr);
+                    if (!deferred) store_grad_time(gr, g, fr, gi, accf, true);
+#pragma unroll
+                    for (int k = 6; k < 17; k++) acc[k] += accf[k];
+                } else {
+                    pair_backward(st, deferred, fr, w.g0[p], w.g1[p], w.g2[p], acc, CAM ? cam : nullptr);
+                }
             }
             if (CAM) cam_add(cam, f, s_cam, gr.cam);
         }
-        if (in) store_grad(gr, g.N, gi, acc, false, any_deferred);
+        if (in) store_grad(gr, g.N, gi, acc, false, any_deferred, false, SPLINE);
     }
     if (CAM) cam_block_flush(s_cam, F, gr.cam);
 }
@@ -596,7 +670,8 @@ __global__ void __launch_bounds__(128) project_bwd_fp64_kernel(Work w, GaussPtrs
         const DevFrame &fr = w.frames[find_frame_by_pair(w.frames, (int)w.L.F, p)];
         const long long gi = fr.gauss_offset + (long long)(p - fr.pair_offset);
         PairState<double> sd;
-        load_and_project(g, gi, fr, sd);
+        if (g.n_ctrl > 0) load_and_project<double, true>(g, gi, fr, sd);
+        else load_and_project<double, false>(g, gi, fr, sd);
         if (!sd.valid) continue;
         const float4 g0 = w.g0[p], g1 = w.g1[p];
         float acc[17];
@@ -609,7 +684,8 @@ __global__ void __launch_bounds__(128) project_bwd_fp64_kernel(Work w, GaussPtrs
                                   -(double)kLog2e * g0.w, -0.5 * (double)kLog2e * g1.x, acc,
                                   gr.cam ? cam : nullptr);
         acc[13] = acc[14] = acc[15] = acc[16] = 0.f;  // colour and opacity were done in FP32
-        store_grad(gr, g.N, gi, acc, true);
+        store_grad(gr, g.N, gi, acc, true, false, false, g.n_ctrl > 0);
+        if (g.n_ctrl > 0) store_grad_time(gr, g, fr, gi, acc, true);
         if (gr.cam) {
             const int f = find_frame_by_pair(w.frames, (int)w.L.F, p);
             for (int k = 0; k < kCamGrad; k++) atomicAdd(gr.cam + (size_t)f * kCamGrad + k, cam[k]);
@@ -626,7 +702,8 @@ cudaError_t launch_project_fwd(const Work &w, const GaussPtrs &g, int tile_w, in
     if (w.L.P == 0) return cudaSuccess;
     int lw = __builtin_ctz(tile_w), lh = __builtin_ctz(tile_h);
     unsigned blocks = std::min((w.L.P + 255u) / 256u, (unsigned)num_sms * 8u);
-    project_fwd_kernel<<<blocks, 256, 0, s>>>(w, g, lw, lh, tile_sort_passes(w));
+    if (g.n_ctrl > 0) project_fwd_kernel<true><<<blocks, 256, 0, s>>>(w, g, lw, lh, tile_sort_passes(w));
+    else project_fwd_kernel<false><<<blocks, 256, 0, s>>>(w, g, lw, lh, tile_sort_passes(w));
     return cudaGetLastError();
 }
 
@@ -649,12 +726,19 @@ cudaError_t launch_project_bwd(const Work &w, const GaussPtrs &g, const GradPtrs
         // all frames share one set; its size is the first frame's count
         unsigned n = w.L.P / w.L.F;
         unsigned blocks = std::min((n + 127) / 128, (unsigned)num_sms * 16u);
-        if (gr.cam) project_bwd_shared_kernel<true><<<blocks, 128, 0, s>>>(w, g, gr);
-        else project_bwd_shared_kernel<false><<<blocks, 128, 0, s>>>(w, g, gr);
+        const bool spline = g.n_ctrl > 0;
+        if (gr.cam && spline) project_bwd_shared_kernel<true, true><<<blocks, 128, 0, s>>>(w, g, gr);
+        else if (gr.cam) project_bwd_shared_kernel<true, false><<<blocks, 128, 0, s>>>(w, g, gr);
+        else if (spline) project_bwd_shared_kernel<false, true><<<blocks, 128, 0, s>>>(w, g, gr);
+        else project_bwd_shared_kernel<false, false><<<blocks, 128, 0, s>>>(w, g, gr);
     } else {
         unsigned blocks = std::min((w.L.P + 127) / 128, (unsigned)num_sms * 16u);
-        if (gr.cam) project_bwd_pairs_kernel<true><<<blocks, 128, 0, s>>>(w, g, gr, mode == 2 ? 1 : 0);
-        else project_bwd_pairs_kernel<false><<<blocks, 128, 0, s>>>(w, g, gr, mode == 2 ? 1 : 0);
+        const int at = mode == 2 ? 1 : 0;
+        const bool spline = g.n_ctrl > 0;
+        if (gr.cam && spline) project_bwd_pairs_kernel<true, true><<<blocks, 128, 0, s>>>(w, g, gr, at);
+        else if (gr.cam) project_bwd_pairs_kernel<true, false><<<blocks, 128, 0, s>>>(w, g, gr, at);
+        else if (spline) project_bwd_pairs_kernel<false, true><<<blocks, 128, 0, s>>>(w, g, gr, at);
+        else project_bwd_pairs_kernel<false, false><<<blocks, 128, 0, s>>>(w, g, gr, at);
     }
     return cudaGetLastError();
 }

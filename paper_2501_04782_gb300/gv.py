@@ -52,12 +52,13 @@ class Camera(ctypes.Structure):
 
 class Gaussians(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64)] + [(k, ctypes.c_void_p) for k in
-                                          ("mean", "vel", "log_scale", "quat", "opacity_logit", "rgb")]
+                                          ("mean", "vel", "log_scale", "quat", "opacity_logit", "rgb")] + \
+               [("n_ctrl", ctypes.c_int32)] + [(k, ctypes.c_void_p) for k in ("ctrl", "log_scale_t", "quat_t")]
 
 
 class GaussiansGrad(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in ("mean", "vel", "log_scale", "quat", "opacity_logit", "rgb",
-                                               "camera")]
+                                               "camera", "ctrl", "log_scale_t", "quat_t")]
 
 CAMERA_GRAD = 16  # per frame: dR (row-major, R as a general matrix), dt, dfx, dfy, dcx, dcy
 
@@ -206,19 +207,28 @@ def layout_frames(frames) -> tuple[list[Frame], int]:
 PARAM_KEYS = ("mean", "vel", "log_scale", "quat", "opacity_logit", "rgb")
 
 
+TIME_KEYS = ("ctrl", "log_scale_t", "quat_t")  # time-parameterised form (Sec. 3.2, Eq. 2-3)
+
+
 def gaussians_struct(params: dict) -> Gaussians:
+    """params: the SoA planes; with "ctrl" ([3, n_ctrl, N]) the time-parameterised form
+    (means on the cubic B-spline over ctrl; optional "log_scale_t" [3, 3, N] and "quat_t"
+    [3, 4, N] cubic terms), the camera time then in [0, 1]."""
     g = Gaussians()
     g.N = int(params["opacity_logit"].shape[-1])
-    for k in PARAM_KEYS:
+    for k in PARAM_KEYS + TIME_KEYS:
         v = params.get(k)
         setattr(g, k, _ptr(v) if v is not None else None)
+    ctrl = params.get("ctrl")
+    g.n_ctrl = int(ctrl.shape[1]) if ctrl is not None else 0
     return g
 
 
 def grad_struct(grads: dict) -> GaussiansGrad:
-    """grads: the parameter planes, and optionally "camera" ([F, 16] device tensor)."""
+    """grads: the parameter planes, optionally "camera" ([F, 16] device tensor) and the
+    time-parameterised planes."""
     g = GaussiansGrad()
-    for k in PARAM_KEYS + ("camera",):
+    for k in PARAM_KEYS + ("camera",) + TIME_KEYS:
         v = grads.get(k)
         setattr(g, k, _ptr(v) if v is not None else None)
     return g

@@ -146,6 +146,36 @@ def workload_clip_shared(seed_offset: int = 0, F: int = 16, N: int = 300_000, W:
     return dict(name=f"clip_{F}x{W}x{H}_{N // 1000}k_shared", gaussians=g, frames=frames, targets=targets)
 
 
+def spline_gaussians(rng: np.random.Generator, N: int, n_ctrl: int = 8, box=((-4.0, 4.0), (-4.0, 4.0), (2.0, 12.0)),
+                     step_std: float = 0.05, ls_std: float = 0.1, q_std: float = 0.1) -> dict:
+    """Time-parameterised Gaussians (the paper's Eq. 2-3 form): control points of a cubic
+    B-spline as a random walk of N(0, step_std) steps from a uniform start in the box,
+    cubic-term coefficients of the log-scale and quaternion N(0, ls_std) / N(0, q_std); the
+    constant parts as in gaussians().  No random draw here depends on the rendering."""
+    g = gaussians(rng, N, box=box)
+    start = g.pop("mean")
+    steps = rng.normal(0.0, step_std, size=(3, n_ctrl, N))
+    steps[:, 0, :] = 0.0
+    g["ctrl"] = (start[:, None, :] + np.cumsum(steps, axis=1)).astype(np.float32)
+    g["log_scale_t"] = rng.normal(0.0, ls_std, size=(3, 3, N)).astype(np.float32)
+    g["quat_t"] = rng.normal(0.0, q_std, size=(3, 4, N)).astype(np.float32)
+    return g
+
+
+def workload_spline_clip(seed_offset: int = 0, F: int = 8, N: int = 50_000, W: int = 480, H: int = 270,
+                         n_ctrl: int = 8) -> dict:
+    """F frames at times t = f / (F - 1) in [0, 1] sharing N time-parameterised Gaussians,
+    on the clip trajectory."""
+    rng = np.random.default_rng(SEED_BASE + 7 + seed_offset)
+    g = spline_gaussians(rng, N, n_ctrl)
+    frames, targets = [], []
+    for f in range(F):
+        R, t = trajectory_pose(f, F)
+        frames.append((centred_camera(W, H, float(W), R, t, time=f / max(F - 1, 1)), 0, N))
+        targets.append(target_image(rng, W, H))
+    return dict(name=f"spline_{F}x{W}x{H}_{N // 1000}k", gaussians=g, frames=frames, targets=targets)
+
+
 def workload_uneven(seed_offset: int = 0, F: int = 32, n_lo: float = 5e4, n_hi: float = 1e6,
                     resolutions=((480, 270), (960, 540), (1920, 1080))) -> dict:
     """Uneven batch: per-frame resolution drawn from the list, per-frame Gaussian set with a

@@ -105,20 +105,26 @@ def compare_pixels(gpu_rgb: np.ndarray, ref_rgb: np.ndarray, amb: np.ndarray, la
 
 
 def compare_grads(gpu: dict, ref: np.ndarray, gabs: np.ndarray, label: str = "", keys=None,
-                  max_cancel_frac: float = 0.002) -> dict:
+                  max_cancel_frac: float = 0.002, cancel_rel: float = CANCEL_REL) -> dict:
     """gpu: dict of parameter arrays; ref, gabs: [17, N] from the oracle."""
-    refs = oracle.split_grad(ref)
-    abss = oracle.split_grad(gabs)
+    return compare_split(gpu, oracle.split_grad(ref), oracle.split_grad(gabs), label,
+                         keys or ("mean", "log_scale", "quat", "opacity_logit", "rgb", "vel"), max_cancel_frac,
+                         cancel_rel)
+
+
+def compare_split(gpu: dict, refs: dict, abss: dict, label: str, keys, max_cancel_frac: float = 0.002,
+                  cancel_rel: float = CANCEL_REL) -> dict:
+    """The gradient rule on named arrays: refs, abss from the oracle, same shapes as gpu."""
     stats = {}
     total_fail, total_cancel, total = 0, 0, 0
-    for k in keys or ("mean", "log_scale", "quat", "opacity_logit", "rgb", "vel"):
+    for k in keys:
         if k not in gpu:
             continue
         a = gpu[k].astype(np.float64).reshape(refs[k].shape)
         b = refs[k]
         d = np.abs(a - b)
         ok = (d <= GRAD_REL * np.abs(b)) | (d <= GRAD_ABS)
-        cancel = ~ok & (d <= CANCEL_REL * abss[k])
+        cancel = ~ok & (d <= cancel_rel * abss[k])
         fail = ~ok & ~cancel
         stats[k] = dict(n=int(a.size), cancel=int(cancel.sum()), fail=int(fail.sum()),
                         worst_rel=float(np.max(d / np.maximum(np.abs(b), GRAD_ABS / GRAD_REL))))
