@@ -397,6 +397,28 @@ def l2_loss_grad(image, target, scale: float):
     return float(scale * np.sum(d * d)), 2.0 * scale * d
 
 
+def adan_step(theta, grad, m, v, n, g_prev, step: int, lr: float, beta1: float = 0.02, beta2: float = 0.08,
+              beta3: float = 0.01, eps: float = 1e-8, weight_decay: float = 0.0):
+    """One step of Adan (the optimiser of the paper's Sec. 4.1; Xie et al., Adan: Adaptive
+    Nesterov Momentum Algorithm, Algorithm 1), FP64, betas in that paper's convention
+    (beta = weight of the new term).  With d = g_k - g_{k-1}:
+        m_k = (1 - b1) m + b1 g,  v_k = (1 - b2) v + b2 d,
+        n_k = (1 - b3) n + b3 (g + (1 - b2) d)^2,
+        theta <- (theta - lr (m_k + (1 - b2) v_k) / (sqrt(n_k) + eps)) / (1 + weight_decay lr).
+    Step 1 starts the moments from the first gradient: m = g, v = 0, n = g^2 (no previous
+    gradient).  Returns (theta, m, v, n, g_prev = g)."""
+    theta, grad, m, v, n, g_prev = (np.asarray(a, np.float64) for a in (theta, grad, m, v, n, g_prev))
+    if step == 1:
+        m, v, n = grad.copy(), np.zeros_like(grad), grad * grad
+    else:
+        d = grad - g_prev
+        m = (1 - beta1) * m + beta1 * grad
+        v = (1 - beta2) * v + beta2 * d
+        n = (1 - beta3) * n + beta3 * (grad + (1 - beta2) * d) ** 2
+    theta = (theta - lr * (m + (1 - beta2) * v) / (np.sqrt(n) + eps)) / (1 + weight_decay * lr)
+    return theta, m, v, n, grad.copy()
+
+
 def adam_step(theta, grad, m, v, step: int, lr: float, b1: float = 0.9, b2: float = 0.999, eps: float = 1e-8):
     """One Adam update with bias correction (Kingma & Ba, Algorithm 1), FP64."""
     theta, grad, m, v = (np.asarray(a, np.float64) for a in (theta, grad, m, v))

@@ -192,3 +192,29 @@ def test_camera_translation_gradient_closed_forms():
     g2d = res["grad2d"]
     assert np.isclose(res["cam_grad"][14], g2d[0].sum(), rtol=1e-10, atol=1e-12)
     assert np.isclose(res["cam_grad"][15], g2d[1].sum(), rtol=1e-10, atol=1e-12)
+
+
+def test_adan_closed_forms():
+    """Adan (the paper's optimiser, Sec. 4.1; Algorithm 1 of its authors): the first step is
+    theta - lr g / (|g| + eps); with beta1 = beta2 = beta3 = 1 every step is the same
+    normalised step of the current gradient (m = g, v = g - g_prev, and the (1 - b2) terms
+    vanish); with a zero gradient after a zero start only the weight decay acts; a
+    hand-worked two-step scalar case."""
+    rng = np.random.default_rng(3)
+    th, g = rng.normal(size=50), rng.normal(size=50)
+    z = np.zeros(50)
+    t1, m, v, n, gp = oracle.adan_step(th, g, z, z, z, z, 1, 0.01, eps=0.0)
+    assert np.allclose(t1, th - 0.01 * np.sign(g), rtol=1e-14, atol=1e-15)
+    assert np.array_equal(m, g) and np.array_equal(v, z) and np.allclose(n, g * g) and np.array_equal(gp, g)
+    g2 = rng.normal(size=50)
+    t2, *_ = oracle.adan_step(t1, g2, m, v, n, gp, 2, 0.01, 1.0, 1.0, 1.0, eps=0.0)
+    assert np.allclose(t2, t1 - 0.01 * np.sign(g2), rtol=1e-14, atol=1e-15)
+    t3, *_ = oracle.adan_step(th, z, z, z, z, z, 1, 0.01, weight_decay=0.5, eps=1e-8)
+    assert np.allclose(t3, th / (1 + 0.5 * 0.01), rtol=1e-14)
+    # scalar: theta = 1, g1 = 2, g2 = 1, b = (0.5, 0.5, 0.5), lr = 0.1, eps = 0
+    t, m, v, n, gp = oracle.adan_step([1.0], [2.0], [0.0], [0.0], [0.0], [0.0], 1, 0.1, 0.5, 0.5, 0.5, 0.0)
+    assert np.isclose(t[0], 1.0 - 0.1 * 2.0 / 2.0)                  # m = 2, v = 0, n = 4
+    t, m, v, n, gp = oracle.adan_step(t, [1.0], m, v, n, gp, 2, 0.1, 0.5, 0.5, 0.5, 0.0)
+    # d = -1: m = 1.5, v = -0.5, n = 0.5 * 4 + 0.5 * (1 - 0.5)^2 = 2.125
+    assert np.isclose(m[0], 1.5) and np.isclose(v[0], -0.5) and np.isclose(n[0], 2.125)
+    assert np.isclose(t[0], 0.9 - 0.1 * (1.5 - 0.25) / np.sqrt(2.125))
