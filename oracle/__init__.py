@@ -398,7 +398,7 @@ def l2_loss_grad(image, target, scale: float):
 
 
 def adan_step(theta, grad, m, v, n, g_prev, step: int, lr: float, beta1: float = 0.02, beta2: float = 0.08,
-              beta3: float = 0.01, eps: float = 1e-8, weight_decay: float = 0.0):
+              beta3: float = 0.01, eps: float = 1e-8, weight_decay: float = 0.0, bias_correction: bool = False):
     """One step of Adan (the optimiser of the paper's Sec. 4.1; Xie et al., Adan: Adaptive
     Nesterov Momentum Algorithm, Algorithm 1), FP64, betas in that paper's convention
     (beta = weight of the new term).  With d = g_k - g_{k-1}:
@@ -406,16 +406,30 @@ def adan_step(theta, grad, m, v, n, g_prev, step: int, lr: float, beta1: float =
         n_k = (1 - b3) n + b3 (g + (1 - b2) d)^2,
         theta <- (theta - lr (m_k + (1 - b2) v_k) / (sqrt(n_k) + eps)) / (1 + weight_decay lr).
     Step 1 starts the moments from the first gradient: m = g, v = 0, n = g^2 (no previous
-    gradient).  Returns (theta, m, v, n, g_prev = g)."""
+    gradient).
+    bias_correction: the moments start from zero instead, the first step takes d = 0, and
+    the update uses the debiased moments m_k / (1 - (1 - b1)^k), v_k / (1 - (1 - b2)^k),
+    n_k / (1 - (1 - b3)^k) (the Adam-style correction the Adan authors apply in practice).
+    Returns (theta, m, v, n, g_prev = g)."""
     theta, grad, m, v, n, g_prev = (np.asarray(a, np.float64) for a in (theta, grad, m, v, n, g_prev))
-    if step == 1:
-        m, v, n = grad.copy(), np.zeros_like(grad), grad * grad
-    else:
+    if bias_correction:
+        if step == 1:
+            m, v, n, g_prev = np.zeros_like(grad), np.zeros_like(grad), np.zeros_like(grad), grad
         d = grad - g_prev
         m = (1 - beta1) * m + beta1 * grad
         v = (1 - beta2) * v + beta2 * d
         n = (1 - beta3) * n + beta3 * (grad + (1 - beta2) * d) ** 2
-    theta = (theta - lr * (m + (1 - beta2) * v) / (np.sqrt(n) + eps)) / (1 + weight_decay * lr)
+        mh, vh, nh = (x / (1 - (1 - b) ** step) for x, b in ((m, beta1), (v, beta2), (n, beta3)))
+    else:
+        if step == 1:
+            m, v, n = grad.copy(), np.zeros_like(grad), grad * grad
+        else:
+            d = grad - g_prev
+            m = (1 - beta1) * m + beta1 * grad
+            v = (1 - beta2) * v + beta2 * d
+            n = (1 - beta3) * n + beta3 * (grad + (1 - beta2) * d) ** 2
+        mh, vh, nh = m, v, n
+    theta = (theta - lr * (mh + (1 - beta2) * vh) / (np.sqrt(nh) + eps)) / (1 + weight_decay * lr)
     return theta, m, v, n, grad.copy()
 
 

@@ -218,3 +218,38 @@ def test_adan_closed_forms():
     # d = -1: m = 1.5, v = -0.5, n = 0.5 * 4 + 0.5 * (1 - 0.5)^2 = 2.125
     assert np.isclose(m[0], 1.5) and np.isclose(v[0], -0.5) and np.isclose(n[0], 2.125)
     assert np.isclose(t[0], 0.9 - 0.1 * (1.5 - 0.25) / np.sqrt(2.125))
+
+
+def test_adan_bias_corrected_closed_forms():
+    """Adan with debiased moments: the first step is again theta - lr g / |g|; a constant
+    gradient keeps m_hat = g, v = 0, n_hat = g^2, so every step is the same normalised step;
+    m_hat equals the exponentially weighted mean of the gradients so far (weights
+    (1 - b1)^(k - j), normalised), summed here term by term; a hand-worked two-step scalar."""
+    rng = np.random.default_rng(4)
+    th, g = rng.normal(size=40), rng.normal(size=40)
+    z = np.zeros(40)
+    t, m, v, n, gp = oracle.adan_step(th, g, z, z, z, z, 1, 0.01, eps=0.0, bias_correction=True)
+    assert np.allclose(t, th - 0.01 * np.sign(g), rtol=1e-14, atol=1e-15)
+    for k in range(2, 8):
+        t_prev = t
+        t, m, v, n, gp = oracle.adan_step(t, g, m, v, n, gp, k, 0.01, eps=0.0, bias_correction=True)
+        assert np.allclose(t, t_prev - 0.01 * np.sign(g), rtol=1e-13, atol=1e-15), k
+        assert np.allclose(v, 0.0)
+    gs = [rng.normal(size=40) for _ in range(6)]
+    st = (th, z, z, z, z)
+    b1 = 0.3
+    for k, gk in enumerate(gs, 1):
+        th_k, m, v, n, gp = oracle.adan_step(st[0], gk, *st[1:], k, 0.01, b1, 0.08, 0.01, bias_correction=True)
+        st = (th_k, m, v, n, gp)
+        w = np.array([(1 - b1) ** (k - j) for j in range(1, k + 1)])
+        mean = sum(wj * gj for wj, gj in zip(w, gs[:k])) / w.sum()
+        assert np.allclose(m / (1 - (1 - b1) ** k), mean, rtol=1e-12, atol=1e-14), k
+    # scalar: theta = 1, g1 = 2, g2 = 1, b = (0.5, 0.5, 0.5), lr = 0.1, eps = 0
+    t, m, v, n, gp = oracle.adan_step([1.0], [2.0], [0.0], [0.0], [0.0], [0.0], 1, 0.1, 0.5, 0.5, 0.5, 0.0,
+                                      bias_correction=True)
+    assert np.isclose(m[0], 1.0) and np.isclose(v[0], 0.0) and np.isclose(n[0], 2.0)
+    assert np.isclose(t[0], 0.9)                                     # m_hat = 2, n_hat = 4
+    t, m, v, n, gp = oracle.adan_step(t, [1.0], m, v, n, gp, 2, 0.1, 0.5, 0.5, 0.5, 0.0, bias_correction=True)
+    # d = -1: m = 1, v = -0.5, n = 0.5 * 2 + 0.5 * 0.5^2 = 1.125; debiased by 1 - 0.25 = 0.75
+    assert np.isclose(m[0], 1.0) and np.isclose(v[0], -0.5) and np.isclose(n[0], 1.125)
+    assert np.isclose(t[0], 0.9 - 0.1 * (4 / 3 - 0.5 * 2 / 3) / np.sqrt(1.5))
