@@ -223,6 +223,23 @@ GV_API gv_status gv_adam_step(gv_ctx *ctx, float *param, float *grad, float *m, 
                        int64_t step, float lr, float beta1, float beta2, float eps,
                        int32_t zero_grad, gv_stream stream);
 
+/* One fused Adan step (Sec. 4.1: the paper trains with Adan; the update of Algorithm 1 of
+ * its authors, betas as the weights of the new term, e.g. 0.02, 0.08, 0.01) over n
+ * parameters: with d = grad - g_prev,
+ *   m = (1-b1) m + b1 grad,  v = (1-b2) v + b2 d,  nsq = (1-b3) nsq + b3 (grad + (1-b2) d)^2,
+ *   param = (param - lr (m + (1-b2) v) / (sqrt(nsq) + eps)) / (1 + weight_decay lr),
+ * then g_prev = grad (and grad = 0 if zero_grad).  step is 1-based; step 1 starts the
+ * moments from grad (m = grad, v = 0, nsq = grad^2).
+ * bias_correction != 0: the debiased form the Adan authors use in practice -- step 1
+ * starts the moments from zero with d = 0 (m = b1 grad, v = 0, nsq = b3 grad^2), and the
+ * update uses m / (1-(1-b1)^step), v / (1-(1-b2)^step), nsq / (1-(1-b3)^step) in place of
+ * m, v, nsq (every beta must then be > 0, else GV_ERR_INVALID_ARG).
+ * All arrays device FP32 [n]; the moments and g_prev are state owned by the caller, kept
+ * between steps (their contents before step 1 are ignored). */
+GV_API gv_status gv_adan_step(gv_ctx *ctx, float *param, float *grad, float *m, float *v, float *nsq, float *g_prev,
+                              int64_t n, int64_t step, float lr, float beta1, float beta2, float beta3, float eps,
+                              float weight_decay, int32_t bias_correction, int32_t zero_grad, gv_stream stream);
+
 /* ---- autotuner -------------------------------------------------------------------- */
 
 /* Time forward + backward of this batch for every tile shape {8x8, 16x8, 16x16} and stage

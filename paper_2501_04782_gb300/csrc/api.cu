@@ -711,6 +711,16 @@ gv_status gv_adam_step(gv_ctx *ctx, float *param, float *grad, float *m, float *
     return GV_OK;
 }
 
+gv_status gv_adan_step(gv_ctx *ctx, float *param, float *grad, float *m, float *v, float *nsq, float *g_prev,
+                       int64_t n, int64_t step, float lr, float beta1, float beta2, float beta3, float eps,
+                       float weight_decay, int32_t bias_correction, int32_t zero_grad, gv_stream stream) {
+    if (!ctx || !param || !grad || !m || !v || !nsq || !g_prev || n < 0 || step < 1) return GV_ERR_INVALID_ARG;
+    if (bias_correction && !(beta1 > 0.f && beta2 > 0.f && beta3 > 0.f)) return GV_ERR_INVALID_ARG;
+    GV_CUDA(launch_adan(param, grad, m, v, nsq, g_prev, n, lr, beta1, beta2, beta3, eps, weight_decay, step,
+                        bias_correction != 0, zero_grad, (cudaStream_t)stream));
+    return GV_OK;
+}
+
 gv_status gv_autotune(gv_ctx *ctx, const gv_gaussians *g, const gv_frame_desc *frames, int32_t F, void *workspace,
                       size_t ws_bytes, float *image, float *final_T, int32_t *last_idx, const float *dL_dimage,
                       gv_gaussians_grad *grad, int32_t reps, gv_options *best, float *ms_out, gv_stream stream) {

@@ -1,7 +1,11 @@
-// optim.cu -- the L2 reconstruction loss and the optimiser step (Sec. 4.1: "standard L2
-// reconstruction loss"; the paper's optimiser is Adan, the fused step here is Adam with
+// optim.cu -- the L2 reconstruction loss and the optimiser steps (Sec. 4.1: the L2
+// reconstruction loss; the paper's optimiser is Adan, fused here, beside a fused Adam with
 // bias correction).  Both are elementwise and HBM-bound: float4 vector loads where the
-// pointers allow, grid-stride loops sized to the SM count.
+// pointers allow, grid-stride loops of at most 4096 blocks.
+#include <cmath>
+#include <cstdint>
+#include <initializer_list>
+
 #include "gv_internal.cuh"
 
 namespace gvk {
@@ -30,21 +34,128 @@ __global__ void __launch_bounds__(256) l2_loss_kernel(const float *img, const fl
     }
 }
 
-__global__ void __launch_bounds__(256) adam_kernel(float *p, float *g, float *m, float *v, long long n, float lr,
-                                                   float b1, float b2, float eps, float bc1, float bc2,
-                                                   int zero_grad) {
-    long long stride = (long long)gridDim.x * blockDim.x;
-    const float ib1 = 1.f - b1, ib2 = 1.f - b2;
-    const float rbc1 = 1.f / bc1, rbc2 = 1.f / bc2;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
-        float gi = g[i];
-        float mi = fmaf(b1, m[i], ib1 * gi);
-        float vi = fmaf(b2, v[i], ib2 * gi * gi);
+// Elementwise optimiser kernels: VEC = every array 16-byte aligned, so a thread moves float4
+// vectors (four parameters per load of each array); the n % 4 tail goes element by element.
+template <class Op, bool VEC>
+__device__ __forceinline__ void elementwise(const Op &op, long long n) {
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    long long done = 0;
+    if (VEC) {
+        const long long n4 = n >> 2;
+        for (long long i = tid; i < n4; i += stride) op.vec4(i);
+        done = n4 << 2;
+    }
+    for (long long i = done + tid; i < n; i += stride) op.one(i);
+}
+
+struct AdamOp {
+    float *p, *g, *m, *v;
+    float lr, b1, b2, ib1, ib2, eps, rbc1, rbc2;
+    int zero_grad;
+    __device__ __forceinline__ void upd(float &pi, float gi, float &mi, float &vi) const {
+        mi = fmaf(b1, mi, ib1 * gi);
+        vi = fmaf(b2, vi, ib2 * gi * gi);
+        pi -= lr * (mi * rbc1) / (sqrtf(vi * rbc2) + eps);
+    }
+    __device__ __forceinline__ void one(long long i) const {
+        float pi = p[i], mi = m[i], vi = v[i];
+        upd(pi, g[i], mi, vi);
+        p[i] = pi;
         m[i] = mi;
         v[i] = vi;
-        p[i] -= lr * (mi * rbc1) / (sqrtf(vi * rbc2) + eps);
         if (zero_grad) g[i] = 0.f;
     }
+    __device__ __forceinline__ void vec4(long long i) const {
+        float4 P = reinterpret_cast<float4 *>(p)[i], G = reinterpret_cast<const float4 *>(g)[i];
+        float4 M = reinterpret_cast<float4 *>(m)[i], V = reinterpret_cast<float4 *>(v)[i];
+        upd(P.x, G.x, M.x, V.x);
+        upd(P.y, G.y, M.y, V.y);
+        upd(P.z, G.z, M.z, V.z);
+        upd(P.w, G.w, M.w, V.w);
+        reinterpret_cast<float4 *>(p)[i] = P;
+        reinterpret_cast<float4 *>(m)[i] = M;
+        reinterpret_cast<float4 *>(v)[i] = V;
+        if (zero_grad) reinterpret_cast<float4 *>(g)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+};
+
+// Adan (Sec. 4.1's optimiser; Algorithm 1 of Xie et al.), betas as weights of the new
+// term: with d = g - g_prev, m = (1-b1) m + b1 g, v = (1-b2) v + b2 d,
+// n = (1-b3) n + b3 (g + (1-b2) d)^2, p = (p - lr (c1 m + c2 v) / (c3 sqrt(n) + eps)) / (1 + wd lr).
+// Algorithm 1: c1 = 1, c2 = 1-b2, c3 = 1, and the first step starts the moments from g
+// (f1 = f3 = 1: m = g, v = 0, n = g^2).  Debiased form: moments from zero with d = 0 on the
+// first step (f1 = b1, f3 = b3), c1 = 1/(1-(1-b1)^k), c2 = (1-b2)/(1-(1-b2)^k),
+// c3 = 1/sqrt(1-(1-b3)^k).  g_prev keeps g.  The first step reads neither the moments nor
+// g_prev.
+struct AdanOp {
+    float *p, *g, *m, *v, *nn, *gp;
+    float lr, b1, b2, b3, ib1, ib2, ib3, eps, shrink, c1, c2, c3, f1, f3;
+    int first, zero_grad;
+    __device__ __forceinline__ void upd(float &pi, float gi, float &mi, float &vi, float &ni, float gpi) const {
+        if (first) {
+            mi = f1 * gi;
+            vi = 0.f;
+            ni = f3 * (gi * gi);
+        } else {
+            const float d = gi - gpi;
+            mi = fmaf(ib1, mi, b1 * gi);
+            vi = fmaf(ib2, vi, b2 * d);
+            const float q = fmaf(ib2, d, gi);
+            ni = fmaf(ib3, ni, b3 * q * q);
+        }
+        pi = (pi - lr * fmaf(c2, vi, c1 * mi) / fmaf(c3, sqrtf(ni), eps)) * shrink;
+    }
+    __device__ __forceinline__ void one(long long i) const {
+        const float gi = g[i];
+        float pi = p[i], mi = 0.f, vi = 0.f, ni = 0.f, gpi = 0.f;
+        if (!first) {
+            mi = m[i];
+            vi = v[i];
+            ni = nn[i];
+            gpi = gp[i];
+        }
+        upd(pi, gi, mi, vi, ni, gpi);
+        p[i] = pi;
+        m[i] = mi;
+        v[i] = vi;
+        nn[i] = ni;
+        gp[i] = gi;
+        if (zero_grad) g[i] = 0.f;
+    }
+    __device__ __forceinline__ void vec4(long long i) const {
+        const float4 G = reinterpret_cast<const float4 *>(g)[i];
+        float4 P = reinterpret_cast<float4 *>(p)[i];
+        const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 M = z, V = z, N = z, Q = z;
+        if (!first) {
+            M = reinterpret_cast<float4 *>(m)[i];
+            V = reinterpret_cast<float4 *>(v)[i];
+            N = reinterpret_cast<float4 *>(nn)[i];
+            Q = reinterpret_cast<float4 *>(gp)[i];
+        }
+        upd(P.x, G.x, M.x, V.x, N.x, Q.x);
+        upd(P.y, G.y, M.y, V.y, N.y, Q.y);
+        upd(P.z, G.z, M.z, V.z, N.z, Q.z);
+        upd(P.w, G.w, M.w, V.w, N.w, Q.w);
+        reinterpret_cast<float4 *>(p)[i] = P;
+        reinterpret_cast<float4 *>(m)[i] = M;
+        reinterpret_cast<float4 *>(v)[i] = V;
+        reinterpret_cast<float4 *>(nn)[i] = N;
+        reinterpret_cast<float4 *>(gp)[i] = G;
+        if (zero_grad) reinterpret_cast<float4 *>(g)[i] = z;
+    }
+};
+
+template <class Op, bool VEC>
+__global__ void __launch_bounds__(256) optim_kernel(Op op, long long n) {
+    elementwise<Op, VEC>(op, n);
+}
+
+bool aligned16(std::initializer_list<const void *> ptrs) {
+    for (const void *q : ptrs)
+        if (reinterpret_cast<uintptr_t>(q) & 15u) return false;
+    return true;
 }
 
 __global__ void grad2d_debug_kernel(Work w, float *out) {
@@ -76,7 +187,31 @@ cudaError_t launch_l2_loss(const float *image, const float *target, long long n,
 cudaError_t launch_adam(float *p, float *g, float *m, float *v, long long n, float lr, float b1, float b2, float eps,
                         float bc1, float bc2, int zero_grad, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    adam_kernel<<<grid_for(n), 256, 0, s>>>(p, g, m, v, n, lr, b1, b2, eps, bc1, bc2, zero_grad);
+    AdamOp op{p, g, m, v, lr, b1, b2, 1.f - b1, 1.f - b2, eps, 1.f / bc1, 1.f / bc2, zero_grad};
+    const int grid = grid_for((n + 3) / 4);
+    if (aligned16({p, g, m, v})) optim_kernel<AdamOp, true><<<grid, 256, 0, s>>>(op, n);
+    else optim_kernel<AdamOp, false><<<grid, 256, 0, s>>>(op, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adan(float *p, float *g, float *m, float *v, float *nn, float *g_prev, long long n, float lr,
+                        float b1, float b2, float b3, float eps, float wd, long long step, bool debias, int zero_grad,
+                        cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    float c1 = 1.f, c2 = 1.f - b2, c3 = 1.f, f1 = 1.f, f3 = 1.f;
+    if (debias) {
+        const double k = (double)step;
+        c1 = (float)(1.0 / (1.0 - std::pow(1.0 - (double)b1, k)));
+        c2 = (float)((1.0 - (double)b2) / (1.0 - std::pow(1.0 - (double)b2, k)));
+        c3 = (float)(1.0 / std::sqrt(1.0 - std::pow(1.0 - (double)b3, k)));
+        f1 = b1;
+        f3 = b3;
+    }
+    AdanOp op{p, g, m, v, nn, g_prev, lr, b1, b2, b3, 1.f - b1, 1.f - b2, 1.f - b3, eps, 1.f / (1.f + wd * lr),
+              c1, c2, c3, f1, f3, step == 1 ? 1 : 0, zero_grad};
+    const int grid = grid_for((n + 3) / 4);
+    if (aligned16({p, g, m, v, nn, g_prev})) optim_kernel<AdanOp, true><<<grid, 256, 0, s>>>(op, n);
+    else optim_kernel<AdanOp, false><<<grid, 256, 0, s>>>(op, n);
     return cudaGetLastError();
 }
 

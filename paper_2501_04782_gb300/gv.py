@@ -20,7 +20,7 @@ GV_OK, GV_ERR_INVALID_ARG, GV_ERR_CAPACITY, GV_ERR_TIMEOUT, GV_ERR_CUDA, GV_ERR_
 EXPORTS = [
     "gv_create", "gv_destroy", "gv_get_options", "gv_set_options", "gv_last_error", "gv_status_string",
     "gv_workspace_size", "gv_render_batch_fwd", "gv_render_batch_bwd", "gv_render_fwd", "gv_render_bwd",
-    "gv_read_status", "gv_l2_loss_grad", "gv_adam_step", "gv_autotune", "gv_graph_capture",
+    "gv_read_status", "gv_l2_loss_grad", "gv_adam_step", "gv_adan_step", "gv_autotune", "gv_graph_capture",
     "gv_graph_set_frames", "gv_graph_launch", "gv_graph_destroy", "gv_debug_bin_sort", "gv_debug_read",
     "gv_debug_set_wait", "gv_debug_read_grad2d", "gv_profile_enable", "gv_profile_read",
     "gv_read_counters", "gv_render_fwd_noalloc",
@@ -91,6 +91,9 @@ _SIGS = {
     "gv_l2_loss_grad": [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_float, _vp, _vp, _vp],
     "gv_adam_step": [_vp, _vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
                      ctypes.c_float, ctypes.c_float, ctypes.c_int32, _vp],
+    "gv_adan_step": [_vp, _vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_float,
+                     ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_int32,
+                     ctypes.c_int32, _vp],
     "gv_autotune": [_vp, ctypes.POINTER(Gaussians), ctypes.POINTER(FrameDesc), ctypes.c_int32, _vp, ctypes.c_size_t,
                     _vp, _vp, _vp, _vp, ctypes.POINTER(GaussiansGrad), ctypes.c_int32, ctypes.POINTER(Options),
                     ctypes.POINTER(ctypes.c_float), _vp],
@@ -342,6 +345,15 @@ class Context:
         self.check(self.lib.gv_adam_step(self.h, _ptr(param), _ptr(grad), _ptr(m), _ptr(v), param.numel(),
                                          int(step), float(lr), float(beta1), float(beta2), float(eps),
                                          1 if zero_grad else 0, _stream_handle(stream)))
+
+    def adan_step(self, param, grad, m, v, nsq, g_prev, step: int, lr: float, betas=(0.02, 0.08, 0.01),
+                  eps=1e-8, weight_decay=0.0, bias_correction: bool = False, zero_grad: bool = True, stream=None):
+        """Adan (the paper's optimiser), betas as the weights of the new term; bias_correction
+        selects the debiased form (moments from zero, each divided by 1 - (1 - beta)^step)."""
+        self.check(self.lib.gv_adan_step(self.h, _ptr(param), _ptr(grad), _ptr(m), _ptr(v), _ptr(nsq),
+                                         _ptr(g_prev), param.numel(), int(step), float(lr), float(betas[0]),
+                                         float(betas[1]), float(betas[2]), float(eps), float(weight_decay),
+                                         1 if bias_correction else 0, 1 if zero_grad else 0, _stream_handle(stream)))
 
     def autotune(self, params, frames, ws, image, final_T, last_idx, dL_dimage, grads, reps: int = 3, stream=None):
         arr = frame_array(frames)

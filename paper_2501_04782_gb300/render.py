@@ -121,7 +121,7 @@ def params_to_device(g: dict, device="cuda") -> dict:
 class Trainer:
     """Batched training step (Sec. 4.1: L2 reconstruction loss, optimiser step): each step
     renders `batch` frames of a clip in one CUDA graph (forward, L2 loss, backward, all
-    libgv kernels), then updates every Gaussian parameter with one fused Adam launch.
+    libgv kernels), then updates every Gaussian parameter with one fused Adam or Adan launch.
 
     The parameter planes live in one flat buffer (so one Adam launch covers them all) and
     the graph is captured once; a step replaces the frames' cameras in the instantiated
@@ -130,8 +130,15 @@ class Trainer:
     KEYS = ("mean", "vel", "log_scale", "quat", "opacity_logit", "rgb")
 
     def __init__(self, params: dict, cams: list, targets: torch.Tensor, batch: int = 8, lr: float = 0.01,
-                 betas=(0.9, 0.999), eps: float = 1e-8, tile=(16, 16), stage_depth: int = 128,
-                 key_capacity: int = 0, seed: int = 0):
+                 betas=None, eps: float = 1e-8, tile=(16, 16), stage_depth: int = 128,
+                 key_capacity: int = 0, seed: int = 0, optimizer: str = "adam", lr_decay: float = 1.0,
+                 adan_bias_correction: bool = True):
+        """optimizer: "adam" (betas default (0.9, 0.999)) or "adan" (the paper's, Sec. 4.1;
+        betas default (0.02, 0.08, 0.01); adan_bias_correction selects the debiased form
+        over Algorithm 1's first-gradient start); the learning rate of step k is
+        lr * lr_decay^k (the paper decays 0.01 by 0.99995 per step)."""
+        if optimizer not in ("adam", "adan"):
+            raise ValueError("optimizer must be 'adam' or 'adan'")
         dev = params["mean"].device
         self.N = int(params["opacity_logit"].shape[-1])
         self.keys = [k for k in self.KEYS if params.get(k) is not None]
@@ -140,6 +147,10 @@ class Trainer:
         self.grad = torch.zeros_like(self.flat)
         self.m = torch.zeros_like(self.flat)
         self.v = torch.zeros_like(self.flat)
+        self.optimizer, self.lr_decay, self.adan_bias_correction = optimizer, lr_decay, adan_bias_correction
+        if optimizer == "adan":
+            self.nsq = torch.zeros_like(self.flat)
+            self.g_prev = torch.zeros_like(self.flat)
         self.params, self.grads, off = {}, {}, 0
         for k, n in zip(self.keys, sizes):
             shape = params[k].shape
@@ -149,7 +160,8 @@ class Trainer:
         self.cams = cams
         self.targets = targets  # [F, 3*H*W] device
         self.batch = batch
-        self.lr, self.betas, self.eps = lr, betas, eps
+        self.lr, self.eps = lr, eps
+        self.betas = betas if betas is not None else ((0.9, 0.999) if optimizer == "adam" else (0.02, 0.08, 0.01))
         self.step_count = 0
         self.rng = torch.Generator().manual_seed(seed)
         self.ctx = gv.Context(tile, stage_depth)
@@ -190,8 +202,14 @@ class Trainer:
             self.target_buf.view(self.batch, -1).copy_(self.targets[ids])
             self.graph.launch(self.stream)
             self.step_count += 1
-            self.ctx.adam_step(self.flat, self.grad, self.m, self.v, self.step_count, self.lr, self.betas[0],
-                               self.betas[1], self.eps, zero_grad=True, stream=self.stream)
+            lr = self.lr * self.lr_decay ** (self.step_count - 1)
+            if self.optimizer == "adan":
+                self.ctx.adan_step(self.flat, self.grad, self.m, self.v, self.nsq, self.g_prev, self.step_count, lr,
+                                   self.betas, self.eps, bias_correction=self.adan_bias_correction,
+                                   zero_grad=True, stream=self.stream)
+            else:
+                self.ctx.adam_step(self.flat, self.grad, self.m, self.v, self.step_count, lr, self.betas[0],
+                                   self.betas[1], self.eps, zero_grad=True, stream=self.stream)
         torch.cuda.current_stream().wait_stream(self.stream)
         return self.loss
 

@@ -1,4 +1,4 @@
-"""L2 loss, fused Adam and the torch.autograd.Function against the oracle / direct calls."""
+"""L2 loss, fused Adam and Adan, and the torch.autograd.Function against the oracle / direct calls."""
 import numpy as np
 import pytest
 import torch
@@ -25,22 +25,66 @@ def test_l2_loss_and_gradient():
     assert np.allclose(dL.cpu().numpy(), g, rtol=1e-6, atol=1e-12)
 
 
-def test_adam_matches_oracle_over_steps():
+@pytest.mark.parametrize("offset", [0, 1])
+def test_adam_matches_oracle_over_steps(offset):
+    """n = 10007: float4 vectors and a ragged tail; offset 1: arrays not 16-byte aligned."""
     rng = np.random.default_rng(1)
     n = 10007
     th = rng.normal(size=n).astype(np.float32)
     ctx = gv.Context()
-    p = torch.from_numpy(th).cuda()
-    m = torch.zeros(n, device="cuda")
-    v = torch.zeros(n, device="cuda")
+
+    def dev(a):
+        buf = torch.empty(n + offset, device="cuda")
+        buf[offset:] = torch.from_numpy(a)
+        return buf[offset:]
+
+    p = dev(th)
+    m = dev(np.zeros(n, np.float32))
+    v = dev(np.zeros(n, np.float32))
     rt, rm, rv = th.astype(np.float64), np.zeros(n), np.zeros(n)
     for step in range(1, 6):
         gr = rng.normal(size=n).astype(np.float32)
-        gd = torch.from_numpy(gr).cuda()
+        gd = dev(gr)
         ctx.adam_step(p, gd, m, v, step, 0.01)
         assert torch.all(gd == 0)  # zero_grad
         rt, rm, rv = oracle.adam_step(rt, gr, rm, rv, step, 0.01)
     assert np.allclose(p.cpu().numpy(), rt, rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("wd,debias,offset", [(0.0, False, 0), (0.02, False, 0), (0.0, True, 0), (0.02, True, 0),
+                                              (0.02, True, 1)])
+def test_adan_matches_oracle_over_steps(wd, debias, offset):
+    """The fused Adan step (the paper's optimiser; Algorithm 1 of its authors, or the
+    debiased form) against the FP64 oracle over six steps with the paper's exponentially
+    decayed learning rate (0.01 * 0.99995^k); the state's contents before step 1 are
+    ignored (filled with noise here).  n = 10007 leaves a ragged tail after the float4
+    vectors; offset 1 makes every array 4-byte but not 16-byte aligned (the scalar path)."""
+    rng = np.random.default_rng(2)
+    n = 10007
+    th = rng.normal(size=n).astype(np.float32)
+    ctx = gv.Context()
+    def dev(a):
+        buf = torch.empty(n + offset, device="cuda")
+        buf[offset:] = torch.from_numpy(a)
+        return buf[offset:]
+
+    p = dev(th)
+    m, v, nsq, gprev = (dev(rng.uniform(0.5, 2.0, n).astype(np.float32)) for _ in range(4))
+    rt = th.astype(np.float64)
+    rm = rv = rn = rg = np.zeros(n)
+    for step in range(1, 7):
+        lr = 0.01 * 0.99995 ** (step - 1)
+        gr = rng.normal(size=n).astype(np.float32)
+        gd = dev(gr)
+        ctx.adan_step(p, gd, m, v, nsq, gprev, step, lr, weight_decay=wd, bias_correction=debias)
+        assert torch.all(gd == 0)  # zero_grad
+        rt, rm, rv, rn, rg = oracle.adan_step(rt, gr, rm, rv, rn, rg, step, lr, weight_decay=wd,
+                                              bias_correction=debias)
+        assert np.allclose(p.cpu().numpy(), rt, rtol=1e-5, atol=1e-6), step
+    assert np.allclose(m.cpu().numpy(), rm, rtol=1e-5, atol=1e-7)
+    assert np.allclose(v.cpu().numpy(), rv, rtol=1e-5, atol=1e-7)
+    assert np.allclose(nsq.cpu().numpy(), rn, rtol=1e-5, atol=1e-7)
+    assert np.array_equal(gprev.cpu().numpy(), rg.astype(np.float32))
 
 
 def test_autograd_function_matches_direct_backward():
