@@ -104,6 +104,13 @@ typedef struct {
     const float *ctrl;
     const float *log_scale_t;
     const float *quat_t;
+    /* Optional OUTPUT of the forward (device, [N] bytes, or NULL): for every Gaussian i with
+     * at least one kept (tile, Gaussian) key on some frame of the call -- its alpha can
+     * reach 1/255 on a pixel of that frame -- the forward sets visible[i] = 1.  It never
+     * clears: zero the array, render any number of frames, and the Gaussians left at 0
+     * were drawn on none of them (the candidates of the paper's warping of invisible
+     * Gaussians, Sec. 4.1).  The backward ignores it. */
+    uint8_t *visible;
 } gv_gaussians;
 
 /* Gradient planes, same layout; the backward ACCUMULATES (+=) into them.  vel may be

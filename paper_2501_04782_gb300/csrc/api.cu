@@ -290,6 +290,7 @@ GaussPtrs gauss_ptrs(const gv_gaussians *g) {
     p.N = g->N;
     p.n_ctrl = g->n_ctrl;
     p.ctrl = g->ctrl; p.log_scale_t = g->log_scale_t; p.quat_t = g->quat_t;
+    p.visible = g->visible;
     if (p.n_ctrl > 0) p.vel = nullptr;
     return p;
 }

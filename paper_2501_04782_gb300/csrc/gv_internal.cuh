@@ -148,6 +148,7 @@ struct GaussPtrs {
     long long N;
     int n_ctrl;  // > 0: means on the B-spline over ctrl; log_scale_t / quat_t: cubic terms (or NULL)
     const float *ctrl, *log_scale_t, *quat_t;
+    uint8_t *visible;  // [N] or NULL: set to 1 for Gaussians with a kept key (forward)
 };
 
 struct GradPtrs {

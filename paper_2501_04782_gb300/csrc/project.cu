@@ -196,10 +196,11 @@ __device__ __forceinline__ unsigned bin_pair(const Work &w, unsigned p, float u,
 // l + 32, ... of the concatenated row list, so a pair with many tile rows does not hold
 // the other lanes back): counts the tile-sort digits of the kept row runs.  Returns the
 // kept keys of the rows this lane processed; with PER_PAIR, also adds each row's kept
-// keys to s_pair_live[owner lane].  Every lane of the warp calls it.
+// keys to s_pair_live[owner lane].  kept_lanes receives (in every lane) the mask of the
+// lanes whose pair kept at least one key.  Every lane of the warp calls it.
 template <bool PER_PAIR>
 __device__ __forceinline__ unsigned warp_cull_rows(const PairBin &pb, int lw, int lh, int tile_passes, BinShared &sb,
-                                                   unsigned *s_pair_live) {
+                                                   unsigned *s_pair_live, unsigned &kept_lanes) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     int inc = pb.rows;
@@ -209,7 +210,7 @@ __device__ __forceinline__ unsigned warp_cull_rows(const PairBin &pb, int lw, in
         if (lane >= o) inc += y;
     }
     const int start = inc - pb.rows, R = __shfl_sync(FULL, inc, 31);
-    unsigned live = 0;
+    unsigned live = 0, owners = 0;
     for (int base = 0; base < R; base += 32) {
         const int r = base + lane;
         int lo = 0, hi = 31;  // owner: the last lane whose rows start at or before r
@@ -231,11 +232,13 @@ __device__ __forceinline__ unsigned warp_cull_rows(const PairBin &pb, int lw, in
             if (cull_tiles(u, v, e, bx, ty, lw, lh, t0, t1)) {
                 const unsigned len = (unsigned)(t1 - t0 + 1);
                 live += len;
+                owners |= 1u << lo;
                 count_tile_run(toff + (unsigned)ty * tx + (unsigned)t0, len, tile_passes, sb.diff, &sb.full, sb.tile);
                 if (PER_PAIR) atomicAdd(s_pair_live + lo, len);
             }
         }
     }
+    kept_lanes = __reduce_or_sync(FULL, owners);
     return live;
 }
 
@@ -281,10 +284,11 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, i
         unsigned key = 0xFFFFFFFFu;
         PairBin pb;
         pb.rows = 0;
+        long long gi = 0;
         if (in) {
             int f = find_frame_by_pair(w.frames, (int)w.L.F, p);
             const DevFrame &fr = w.frames[f];
-            long long gi = fr.gauss_offset + (long long)(p - fr.pair_offset);
+            gi = fr.gauss_offset + (long long)(p - fr.pair_offset);
             PairState<float> st;
             load_and_project<float, SPLINE>(g, gi, fr, st);
             // alpha >= 1/255 needs d^T conic d <= tau = 2 ln(255 o)
@@ -301,7 +305,9 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, i
             key = cells ? __float_as_uint(st.zc) : 0xFFFFFFFFu;
             w.dkey[0][p] = key;
         }
-        live_sum += warp_cull_rows<false>(pb, lw, lh, tile_passes, sb, nullptr);
+        unsigned kept_lanes;
+        live_sum += warp_cull_rows<false>(pb, lw, lh, tile_passes, sb, nullptr, kept_lanes);
+        if (g.visible && ((kept_lanes >> (threadIdx.x & 31)) & 1u)) g.visible[gi] = 1;  // benign same-value race
         const unsigned active = __ballot_sync(0xffffffffu, in);
         if (in)
             for (int ps = 0; ps < 4; ps++) count_digit(sb.depth[ps], (key >> (8 * ps)) & 255u, active);
@@ -340,7 +346,8 @@ __global__ void __launch_bounds__(256) bin_from_screen_kernel(Work w, long long 
             w.dkey[0][p] = key;
         }
         __syncwarp();
-        live_sum += warp_cull_rows<true>(pb, lw, lh, tile_passes, sb, s_warp_live);
+        unsigned kept_lanes;
+        live_sum += warp_cull_rows<true>(pb, lw, lh, tile_passes, sb, s_warp_live, kept_lanes);
         __syncwarp();
         if (in && counts) counts[p] = (int32_t)s_live[threadIdx.x];
         const unsigned active = __ballot_sync(0xffffffffu, in);

@@ -53,7 +53,8 @@ class Camera(ctypes.Structure):
 class Gaussians(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64)] + [(k, ctypes.c_void_p) for k in
                                           ("mean", "vel", "log_scale", "quat", "opacity_logit", "rgb")] + \
-               [("n_ctrl", ctypes.c_int32)] + [(k, ctypes.c_void_p) for k in ("ctrl", "log_scale_t", "quat_t")]
+               [("n_ctrl", ctypes.c_int32)] + [(k, ctypes.c_void_p) for k in ("ctrl", "log_scale_t", "quat_t")] + \
+               [("visible", ctypes.c_void_p)]
 
 
 class GaussiansGrad(ctypes.Structure):
@@ -213,11 +214,13 @@ PARAM_KEYS = ("mean", "vel", "log_scale", "quat", "opacity_logit", "rgb")
 TIME_KEYS = ("ctrl", "log_scale_t", "quat_t")  # time-parameterised form (Sec. 3.2, Eq. 2-3)
 
 
-def gaussians_struct(params: dict) -> Gaussians:
+def gaussians_struct(params: dict, visible=None) -> Gaussians:
     """params: the SoA planes; with "ctrl" ([3, n_ctrl, N]) the time-parameterised form
     (means on the cubic B-spline over ctrl; optional "log_scale_t" [3, 3, N] and "quat_t"
-    [3, 4, N] cubic terms), the camera time then in [0, 1]."""
+    [3, 4, N] cubic terms), the camera time then in [0, 1].  visible: optional uint8 [N]
+    device tensor the forward sets to 1 for every Gaussian with a kept key (never cleared)."""
     g = Gaussians()
+    g.visible = _ptr(visible) if visible is not None else None
     g.N = int(params["opacity_logit"].shape[-1])
     for k in PARAM_KEYS + TIME_KEYS:
         v = params.get(k)
@@ -294,9 +297,10 @@ class Context:
         self.check(self.lib.gv_workspace_size(self.h, arr, len(frames), int(key_capacity), ctypes.byref(n)))
         return n.value
 
-    def render_fwd(self, params: dict, frames: list[Frame], ws: torch.Tensor, image, final_T, last_idx, stream=None):
+    def render_fwd(self, params: dict, frames: list[Frame], ws: torch.Tensor, image, final_T, last_idx, stream=None,
+                   visible=None):
         arr = frame_array(frames)
-        g = gaussians_struct(params)
+        g = gaussians_struct(params, visible)
         self.check(self.lib.gv_render_batch_fwd(self.h, ctypes.byref(g), arr, len(frames), _ptr(ws), ws.numel(),
                                                 _ptr(image), _ptr(final_T), _ptr(last_idx), _stream_handle(stream)))
 
@@ -309,8 +313,8 @@ class Context:
                                                 _ptr(final_T), _ptr(last_idx), _ptr(dL_dimage), ctypes.byref(gr),
                                                 _stream_handle(stream)))
 
-    def render_fwd_single(self, params: dict, cam, ws, image, final_T, last_idx, stream=None):
-        g = gaussians_struct(params)
+    def render_fwd_single(self, params: dict, cam, ws, image, final_T, last_idx, stream=None, visible=None):
+        g = gaussians_struct(params, visible)
         c = camera_struct(cam)
         self.check(self.lib.gv_render_fwd(self.h, ctypes.byref(g), ctypes.byref(c), _ptr(ws), ws.numel(),
                                           _ptr(image), _ptr(final_T), _ptr(last_idx), _stream_handle(stream)))
@@ -421,11 +425,12 @@ class Graph:
     """A captured CUDA graph of the batched forward (+ backward)."""
 
     def __init__(self, ctx: Context, params, frames, ws, image, final_T, last_idx, dL_dimage=None, grads=None,
-                 stream: torch.cuda.Stream | None = None, target=None, loss_scale: float = 1.0, loss=None):
+                 stream: torch.cuda.Stream | None = None, target=None, loss_scale: float = 1.0, loss=None,
+                 visible=None):
         self.ctx = ctx
-        self._keep = (params, frames, ws, image, final_T, last_idx, dL_dimage, grads, target, loss)
+        self._keep = (params, frames, ws, image, final_T, last_idx, dL_dimage, grads, target, loss, visible)
         arr = frame_array(frames)
-        g = gaussians_struct(params)
+        g = gaussians_struct(params, visible)
         gr = grad_struct(grads) if grads is not None else None
         h = ctypes.c_void_p()
         s = stream or torch.cuda.current_stream()

@@ -175,6 +175,8 @@ class Trainer:
         self.dL = torch.empty(3 * self.total, device=dev)
         self.loss = torch.zeros(1, device=dev)
         self.target_buf = torch.empty(3 * self.total, device=dev)
+        # Gaussians drawn (a kept tile key) on some frame since the last take_invisible()
+        self.visible = torch.zeros(self.N, dtype=torch.uint8, device=dev)
         self.stream = torch.cuda.Stream(device=dev)
         # size the key capacity from a forward of the first batch
         if not cap:
@@ -187,8 +189,18 @@ class Trainer:
         with torch.cuda.stream(self.stream):
             self.graph = gv.Graph(self.ctx, self.params, self.frames, self.ws, self.image, self.T, self.idx,
                                   self.dL, self.grads, self.stream, target=self.target_buf,
-                                  loss_scale=self.scale, loss=self.loss)
+                                  loss_scale=self.scale, loss=self.loss, visible=self.visible)
         self.W, self.H = W, H
+
+    def take_invisible(self) -> torch.Tensor:
+        """Indices of the Gaussians drawn on none of the frames rendered since the last call
+        (the candidates the paper warps toward high-error regions, Sec. 4.1); restarts the
+        record."""
+        with torch.cuda.stream(self.stream):
+            idx = torch.nonzero(self.visible == 0).flatten()
+            self.visible.zero_()
+        torch.cuda.current_stream().wait_stream(self.stream)
+        return idx
 
     def pick(self) -> list[int]:
         return torch.randperm(len(self.cams), generator=self.rng)[:self.batch].sort().values.tolist()

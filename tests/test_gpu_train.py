@@ -51,6 +51,14 @@ def test_step_gradient_and_update_match_direct_computation():
     got = tr.flat.cpu().numpy()
     assert np.allclose(got, expect, rtol=1e-5, atol=1e-6)
     assert np.all(tr.grad.cpu().numpy() == 0)  # fused zeroing
+    # the per-Gaussian drawn flag recorded by the step's graph equals that of a direct forward
+    vis = torch.zeros(tr.N, dtype=torch.uint8, device="cuda")
+    ctx = gv.Context((16, 16), 128)
+    ctx.render_fwd(run.params, run.frames, run.ws, run.image, run.T, run.idx, visible=vis)
+    torch.cuda.synchronize()
+    assert torch.equal(tr.visible, vis) and int(vis.sum()) > 0
+    invisible = tr.take_invisible()
+    assert torch.equal(invisible, torch.nonzero(vis == 0).flatten()) and int(tr.visible.sum()) == 0
 
 
 def test_training_fits_the_clip():
