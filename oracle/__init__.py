@@ -65,7 +65,7 @@ _dp = ctypes.POINTER(ctypes.c_double)
 class _Gaussians(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64), ("mean", _dp), ("vel", _dp), ("log_scale", _dp),
                 ("quat", _dp), ("logit", _dp), ("rgb", _dp), ("n_ctrl", ctypes.c_int32),
-                ("ctrl", _dp), ("log_scale_t", _dp), ("quat_t", _dp)]
+                ("ctrl", _dp), ("log_scale_t", _dp), ("quat_t", _dp), ("sh_degree", ctypes.c_int32), ("sh", _dp)]
 
 
 @dataclass
@@ -116,7 +116,9 @@ def lib():
         L.orc_render_bwd.argtypes = [ctypes.POINTER(_Gaussians), ctypes.POINTER(_Camera), ctypes.POINTER(_Params),
                                      ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, _dp,
                                      _dp, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
-                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+                                     ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+        L.orc_sh_basis.argtypes = [ctypes.c_int32, _dp, _dp, ctypes.c_void_p]
+        L.orc_sh_basis.restype = ctypes.c_int
         L.orc_bspline_basis.argtypes = [ctypes.c_int32, ctypes.c_double, _dp]
         L.orc_bspline_basis.restype = ctypes.c_int
         L.orc_bin_f32.argtypes = [ctypes.c_int64] + [ctypes.c_void_p] * 5 + [ctypes.c_int32] * 4 + [ctypes.c_void_p] * 2
@@ -142,7 +144,7 @@ class _GaussHolder:
     def __init__(self, g: dict):
         self.arrs = {}
         N = int(np.asarray(g["opacity_logit"]).shape[-1])
-        for k in ("mean", "vel", "log_scale", "quat", "opacity_logit", "rgb", "ctrl", "log_scale_t", "quat_t"):
+        for k in ("mean", "vel", "log_scale", "quat", "opacity_logit", "rgb", "ctrl", "log_scale_t", "quat_t", "sh"):
             if k in g and g[k] is not None:
                 self.arrs[k] = np.ascontiguousarray(np.asarray(g[k], dtype=np.float64))
         self.N = N
@@ -154,6 +156,9 @@ class _GaussHolder:
         s.quat, s.logit, s.rgb = ptr("quat"), ptr("opacity_logit"), ptr("rgb")
         s.n_ctrl = self.n_ctrl
         s.ctrl, s.log_scale_t, s.quat_t = ptr("ctrl"), ptr("log_scale_t"), ptr("quat_t")
+        self.nsh = int(self.arrs["sh"].shape[1]) if "sh" in self.arrs else 0
+        self.sh_degree = sh_degree_of(self.nsh)
+        s.sh_degree, s.sh = self.sh_degree, ptr("sh")
         self.c = s
 
 
@@ -221,7 +226,9 @@ def render_bwd_pixels(g: dict, cam, px, py, dL_dC, params: Params | None = None,
                       nthreads: int | None = None, want_abs: bool = True, want_2d: bool = True) -> dict:
     """Gradient of L = sum_k dL_dC[k] . C(pixel k).  dL_dC [n,3].
     Returns grad [17,N], cam_grad [16] (camera: dR row-major with R as a general matrix, dt,
-    dfx, dfy, dcx, dcy) and optionally gabs [17,N], cam_gabs [16] and grad2d [9,N]."""
+    dfx, dfy, dcx, dcy) and optionally gabs [17,N], cam_gabs [16] and grad2d [9,N]; with
+    the time-parameterised form grad_t (gabs_t), with "sh" coefficients grad_sh [3,nsh,N]
+    (gabs_sh)."""
     params = params or Params()
     px = np.ascontiguousarray(px, np.int32)
     py = np.ascontiguousarray(py, np.int32)
@@ -236,22 +243,30 @@ def render_bwd_pixels(g: dict, cam, px, py, dL_dC, params: Params | None = None,
     nt = 3 * h.n_ctrl + 21 if h.n_ctrl else 0
     grad_t = np.zeros((max(nt, 1), h.N), np.float64)
     gabs_t = np.zeros((max(nt, 1), h.N), np.float64)
+    ns = h.nsh
+    grad_sh = np.zeros((3, max(ns, 1), h.N), np.float64)
+    gabs_sh = np.zeros((3, max(ns, 1), h.N), np.float64)
     rc = lib().orc_render_bwd(ctypes.byref(h.c), ctypes.byref(_camera(cam)), ctypes.byref(params._c()), n,
                               px.ctypes.data, py.ctypes.data, dL.ctypes.data_as(_dp), grad.ctypes.data_as(_dp),
                               gabs.ctypes.data if gabs is not None else None,
                               g2d.ctypes.data if g2d is not None else None, cam_grad.ctypes.data,
                               cam_gabs.ctypes.data, grad_t.ctypes.data if nt else None,
-                              gabs_t.ctypes.data if nt else None, nthreads or default_threads())
+                              gabs_t.ctypes.data if nt else None, grad_sh.ctypes.data if ns else None,
+                              gabs_sh.ctypes.data if ns else None, nthreads or default_threads())
     if rc:
         raise MemoryError("oracle backward failed")
     out = dict(grad=grad, cam_grad=cam_grad)
     if nt:
         out["grad_t"] = grad_t
+    if ns:
+        out["grad_sh"] = grad_sh
     if gabs is not None:
         out["gabs"] = gabs
         out["cam_gabs"] = cam_gabs
         if nt:
             out["gabs_t"] = gabs_t
+        if ns:
+            out["gabs_sh"] = gabs_sh
     if g2d is not None:
         out["grad2d"] = g2d
     return out
@@ -263,6 +278,31 @@ def render_bwd_image(g: dict, cam, dL_dC_img, params: Params | None = None, nthr
     yy, xx = np.mgrid[0:H, 0:W]
     d = np.asarray(dL_dC_img, np.float64).reshape(3, H * W).T
     return render_bwd_pixels(g, cam, xx.ravel(), yy.ravel(), d, params, nthreads, **kw)
+
+
+def sh_degree_of(nsh: int) -> int:
+    """Degree d_c of a set of (d_c + 1)^2 - 1 spherical-harmonic terms above degree 0."""
+    for d in range(4):
+        if (d + 1) ** 2 - 1 == nsh:
+            return d
+    raise ValueError(f"{nsh} SH terms is not (d + 1)^2 - 1 for a degree d <= 3")
+
+
+def sh_basis(deg: int, dirs) -> tuple[np.ndarray, np.ndarray]:
+    """Real spherical harmonics of degrees 1..deg (Sec. 3.1's view-dependent colour) at unit
+    vectors dirs [n,3]: Y [n, (deg+1)^2 - 1] in the order (l, m = -l..l) and their
+    derivatives dY [n, (deg+1)^2 - 1, 3] along the three coordinates."""
+    dirs = np.ascontiguousarray(np.asarray(dirs, np.float64).reshape(-1, 3))
+    nsh = (deg + 1) ** 2 - 1
+    Y = np.zeros((len(dirs), nsh))
+    dY = np.zeros((len(dirs), nsh, 3))
+    for i, d in enumerate(dirs):
+        yi = np.zeros(nsh)
+        di = np.zeros((nsh, 3))
+        if lib().orc_sh_basis(deg, d.ctypes.data_as(_dp), yi.ctypes.data_as(_dp), di.ctypes.data):
+            raise ValueError("degree must be in [1, 3]")
+        Y[i], dY[i] = yi, di
+    return Y, dY
 
 
 def bspline_basis(n_ctrl: int, t: float) -> np.ndarray:

@@ -72,6 +72,12 @@ typedef struct {
      * (NULL: constant).  t is the camera's time, in [0, 1]. */
     int32_t n_ctrl;
     const double *ctrl, *log_scale_t, *quat_t;
+    /* View-dependent colour (Sec. 3.1: colour as spherical harmonics of order d_c), used
+     * when sh_degree in [1, 3]: sh [3][(d_c + 1)^2 - 1][N] holds, per channel, the
+     * coefficients of degrees 1..d_c in the order (l, m = -l..l); the degree-0 term is the
+     * plain colour plane rgb. */
+    int32_t sh_degree;
+    const double *sh;
 } orc_gaussians;
 
 /* number of per-Gaussian parameter gradients: mean 3, vel 3, log_scale 3, quat 4, logit 1, rgb 3 */
@@ -100,6 +106,11 @@ typedef struct {
     double Q[3];         /* conic A, B, C */
     double u, v, ex, ey, o;
     double c[3];
+    int nsh;             /* spherical-harmonic terms above degree 0: (d_c + 1)^2 - 1 */
+    double dir[3];       /* unit view direction (mean - camera centre), world frame */
+    double vnorm;        /* |mean - camera centre| */
+    double Y[15];        /* real SH basis of degrees 1..d_c at dir */
+    double dcdd[3][3];   /* d colour[ch] / d dir[j] (dir taken as a free vector) */
 } orc_proj;
 
 static void quat_to_rot(const double q[4], double R[9]) {
@@ -139,6 +150,67 @@ static void bspline_basis(int n_ctrl, double t, double *w) {
             Nb[i] = a + b;
         }
     for (int i = 0; i < n_ctrl; i++) w[i] = Nb[i];
+}
+
+/* Real spherical harmonics of degrees 1..deg (deg <= 3) at the unit vector d, from their
+ * definition: the complex Y_l^m = K_l^m P_l^m(cos theta) e^{i m phi} with the Condon-Shortley
+ * phase in P_l^m and K_l^m = sqrt((2l + 1)/(4 pi) (l - m)!/(l + m)!), made real as
+ * sqrt(2) Re Y_l^m (m > 0), Y_l^0, sqrt(2) Im Y_l^{|m|} (m < 0).  On the unit sphere
+ * P_l^m(z) e^{i m phi} = Q_l^m(z) (x + i y)^m with Q_l^m = P_l^m / (1 - z^2)^{m/2} a
+ * polynomial, from the standard recurrences Q_m^m = (-1)^m (2m - 1)!!,
+ * Q_{m+1}^m = (2m + 1) z Q_m^m, (l - m) Q_l^m = (2l - 1) z Q_{l-1}^m - (l + m - 1) Q_{l-2}^m.
+ * Y[k - 1] is term k = l^2 + l + m; dY[k - 1][j] its derivative along coordinate j of d,
+ * the polynomial taken as a function of three free variables (may be NULL). */
+static void sh_basis(int deg, const double d[3], double *Y, double (*dY)[3]) {
+    const double x = d[0], y = d[1], z = d[2];
+    double Re[4] = {1, 0, 0, 0}, Im[4] = {0, 0, 0, 0};
+    for (int m = 1; m <= 3; m++) {
+        Re[m] = x * Re[m - 1] - y * Im[m - 1];
+        Im[m] = x * Im[m - 1] + y * Re[m - 1];
+    }
+    for (int m = 0; m <= deg; m++) {
+        double Q[4] = {0, 0, 0, 0}, dQ[4] = {0, 0, 0, 0}; /* Q_l^m, dQ/dz for l = m..deg */
+        double dfact = 1.0;
+        for (int k = 1; k <= 2 * m - 1; k += 2) dfact *= k;
+        Q[m] = (m % 2 ? -1.0 : 1.0) * dfact;
+        if (m + 1 <= deg) { Q[m + 1] = (2 * m + 1) * z * Q[m]; dQ[m + 1] = (2 * m + 1) * Q[m]; }
+        for (int l = m + 2; l <= deg; l++) {
+            Q[l] = ((2 * l - 1) * z * Q[l - 1] - (l + m - 1) * Q[l - 2]) / (l - m);
+            dQ[l] = ((2 * l - 1) * (Q[l - 1] + z * dQ[l - 1]) - (l + m - 1) * dQ[l - 2]) / (l - m);
+        }
+        for (int l = (m > 1 ? m : 1); l <= deg; l++) {
+            double ratio = 1.0; /* (l - m)! / (l + m)! */
+            for (int k = l - m + 1; k <= l + m; k++) ratio /= k;
+            const double K = sqrt((2 * l + 1) / (4.0 * acos(-1.0)) * ratio);
+            if (m == 0) {
+                const int k = l * l + l;
+                Y[k - 1] = K * Q[l];
+                if (dY) { dY[k - 1][0] = 0.0; dY[k - 1][1] = 0.0; dY[k - 1][2] = K * dQ[l]; }
+                continue;
+            }
+            const double c = sqrt(2.0) * K;
+            const int kp = l * l + l + m, kn = l * l + l - m;
+            Y[kp - 1] = c * Q[l] * Re[m];
+            Y[kn - 1] = c * Q[l] * Im[m];
+            if (dY) {
+                /* d(x + iy)^m / dx = m (x + iy)^{m-1}, d/dy = i m (x + iy)^{m-1} */
+                dY[kp - 1][0] = c * Q[l] * m * Re[m - 1];
+                dY[kp - 1][1] = -c * Q[l] * m * Im[m - 1];
+                dY[kp - 1][2] = c * dQ[l] * Re[m];
+                dY[kn - 1][0] = c * Q[l] * m * Im[m - 1];
+                dY[kn - 1][1] = c * Q[l] * m * Re[m - 1];
+                dY[kn - 1][2] = c * dQ[l] * Im[m];
+            }
+        }
+    }
+}
+
+/* Exported for the tests: the basis of degrees 1..deg at d (Y [(deg+1)^2 - 1],
+ * dY [(deg+1)^2 - 1][3] or NULL). */
+int orc_sh_basis(int32_t deg, const double *d, double *Y, double *dY) {
+    if (deg < 1 || deg > 3) return 1;
+    sh_basis(deg, d, Y, (double (*)[3])dY);
+    return 0;
 }
 
 /* Exported for the tests: the basis at t (w [n_ctrl]). */
@@ -215,6 +287,29 @@ static void project_one(const orc_gaussians *g, int64_t i, const orc_camera *cam
     double det = a * c - b * b;
     if (!(det > 0)) { pr->valid = 0; return; }
     pr->Q[0] = c / det; pr->Q[1] = -b / det; pr->Q[2] = a / det;
+    if (g->sh_degree > 0) {
+        /* view direction from the camera centre -W^T t to the mean, in the world frame */
+        const int nsh = (g->sh_degree + 1) * (g->sh_degree + 1) - 1;
+        double vv[3], n2 = 0;
+        for (int j = 0; j < 3; j++) {
+            const double cj = -(W[0 * 3 + j] * cam->t[0] + W[1 * 3 + j] * cam->t[1] + W[2 * 3 + j] * cam->t[2]);
+            vv[j] = pr->mu[j] - cj;
+            n2 += vv[j] * vv[j];
+        }
+        pr->nsh = nsh;
+        pr->vnorm = sqrt(n2);
+        for (int j = 0; j < 3; j++) pr->dir[j] = vv[j] / pr->vnorm;
+        double dY[15][3];
+        sh_basis(g->sh_degree, pr->dir, pr->Y, dY);
+        for (int ch = 0; ch < 3; ch++) {
+            for (int j = 0; j < 3; j++) pr->dcdd[ch][j] = 0;
+            for (int k = 0; k < nsh; k++) {
+                const double coef = g->sh[((int64_t)ch * nsh + k) * N + i];
+                pr->c[ch] += pr->Y[k] * coef;
+                for (int j = 0; j < 3; j++) pr->dcdd[ch][j] += dY[k][j] * coef;
+            }
+        }
+    }
     pr->u = cam->fx * x / z + cam->cx;
     pr->v = cam->fy * y / z + cam->cy;
     /* alpha >= alpha_min needs d^T conic d <= tau = 2 ln(o / alpha_min) (ext_k^2 caps it) */
@@ -229,6 +324,7 @@ static void project_one(const orc_gaussians *g, int64_t i, const orc_camera *cam
 /* Exported: projection records, ORC_PROJ doubles per Gaussian:
  * valid, depth, u, v, a, b, c, A, B, C, ex, ey, o, xc0, xc1, xc2, r, g, b, 0 */
 int orc_project(const orc_gaussians *g, const orc_camera *cam, const orc_params *p, double *out) {
+    if (g->sh_degree < 0 || g->sh_degree > 3 || (g->sh_degree > 0 && !g->sh)) return 1;
     for (int64_t i = 0; i < g->N; i++) {
         orc_proj pr;
         project_one(g, i, cam, p, &pr);
@@ -365,6 +461,7 @@ int orc_render(const orc_gaussians *g, const orc_camera *cam, const orc_params *
                double *out_rgb, double *out_T, int64_t *out_last, int32_t *out_amb, int32_t *out_n,
                int nthreads) {
     if (nthreads < 1) nthreads = 1;
+    if (g->sh_degree < 0 || g->sh_degree > 3 || (g->sh_degree > 0 && !g->sh)) return 1;
     orc_proj *pr = project_all(g, cam, p);
     if (!pr) return 1;
     pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
@@ -391,11 +488,31 @@ int orc_render(const orc_gaussians *g, const orc_camera *cam, const orc_params *
  * fx, fy, cx, cy), added into cam_out[ORC_NCAM] = dR (row-major, R taken as a general
  * matrix), dt, dfx, dfy, dcx, dcy. */
 static void chain_rule(const orc_proj *q, const orc_camera *cam, const double d2[ORC_N2D], double out[ORC_NGRAD],
-                       double *cam_out) {
+                       double *cam_out, double *out_sh) {
     double gu = d2[0], gv = d2[1], gA = d2[2], gB = d2[3], gC = d2[4], go = d2[5];
     memset(out, 0, sizeof(double) * ORC_NGRAD);
     /* colour */
     out[14] = d2[6]; out[15] = d2[7]; out[16] = d2[8];
+    /* view-dependent colour: c = rgb + sum_k Y_k(dir) sh_k with dir = v / |v|, v = mu - o,
+     * o = -W^T t the camera centre: d sh_k = Y_k dc; d dir = sum_ch dc_ch dc_ch/d dir,
+     * dv = (I - dir dir^T) d dir / |v|, which adds to dmu, and do = -dv */
+    double gv_sh[3] = {0, 0, 0};
+    if (q->nsh > 0) {
+        double gd[3];
+        for (int j = 0; j < 3; j++) gd[j] = d2[6] * q->dcdd[0][j] + d2[7] * q->dcdd[1][j] + d2[8] * q->dcdd[2][j];
+        const double along = gd[0] * q->dir[0] + gd[1] * q->dir[1] + gd[2] * q->dir[2];
+        for (int j = 0; j < 3; j++) gv_sh[j] = (gd[j] - q->dir[j] * along) / q->vnorm;
+        if (out_sh)
+            for (int ch = 0; ch < 3; ch++)
+                for (int k = 0; k < q->nsh; k++) out_sh[ch * q->nsh + k] = q->Y[k] * d2[6 + ch];
+        if (cam_out)
+            /* o_j = -sum_r W_rj t_r: dW_rj += -t_r do_j = t_r dv_j, dt_r += -sum_j W_rj do_j */
+            for (int r = 0; r < 3; r++)
+                for (int j = 0; j < 3; j++) {
+                    cam_out[r * 3 + j] += cam->t[r] * gv_sh[j];
+                    cam_out[9 + r] += cam->R[r * 3 + j] * gv_sh[j];
+                }
+    }
     /* opacity = sigmoid(logit) */
     out[13] = go * q->o * (1.0 - q->o);
     /* conic (A,B,C) = inverse of Sigma2 (a,b,c), written out entry by entry */
@@ -466,7 +583,7 @@ static void chain_rule(const orc_proj *q, const orc_camera *cam, const double d2
     }
     /* x_c = W mu + t  ->  dmu = W^T dxc */
     double gmu[3];
-    for (int k = 0; k < 3; k++) gmu[k] = W[0 * 3 + k] * gx + W[1 * 3 + k] * gy + W[2 * 3 + k] * gz;
+    for (int k = 0; k < 3; k++) gmu[k] = W[0 * 3 + k] * gx + W[1 * 3 + k] * gy + W[2 * 3 + k] * gz + gv_sh[k];
     for (int k = 0; k < 3; k++) { out[k] = gmu[k]; out[3 + k] = cam->time * gmu[k]; }
     /* S3 = M M^T  ->  dM = (gS3 + gS3^T) M */
     double gM[9];
@@ -597,6 +714,7 @@ typedef struct {
     contrib_list *lists; /* one per thread */
     double *grad, *gabs, *grad2d;
     double *grad_t, *gabs_t; /* time-parameterised form: [3 n_ctrl + 21][N] */
+    double *grad_sh, *gabs_sh; /* spherical-harmonic coefficients: [3][nsh][N] */
     int tid, nthreads;
     int err;
     double cam_part[ORC_NCAM], cam_abs_part[ORC_NCAM]; /* this thread's camera sums */
@@ -658,8 +776,10 @@ static void *bwd_accum_worker(void *arg) {
             int64_t i = L->idx[e];
             if (i % j->nthreads != j->tid) continue;
             const double *d = L->d2 + e * ORC_N2D;
-            double out[ORC_NGRAD];
-            chain_rule(&j->pr[i], j->cam, d, out, j->cam_part);
+            double out[ORC_NGRAD], osh[45];
+            chain_rule(&j->pr[i], j->cam, d, out, j->cam_part, osh);
+            if (j->grad_sh)
+                for (int k = 0; k < 3 * j->pr[i].nsh; k++) j->grad_sh[k * N + i] += osh[k];
             if (j->g->n_ctrl > 0) {
                 if (j->grad_t) to_time_rows(j->g, fmin(1.0, fmax(0.0, j->cam->time)), out, j->grad_t, N, i);
                 for (int k = 0; k < 6; k++) out[k] = 0.0; /* mean and vel are not parameters then */
@@ -681,9 +801,11 @@ static void *bwd_accum_worker(void *arg) {
             for (int c = 0; c < ORC_N2D; c++) {
                 double a = abs2d[c * N + i];
                 if (a == 0) continue;
-                double unit[ORC_N2D] = {0}, col[ORC_NGRAD], ccol[ORC_NCAM] = {0};
+                double unit[ORC_N2D] = {0}, col[ORC_NGRAD], ccol[ORC_NCAM] = {0}, csh[45];
                 unit[c] = 1.0;
-                chain_rule(&j->pr[i], j->cam, unit, col, ccol);
+                chain_rule(&j->pr[i], j->cam, unit, col, ccol, csh);
+                if (j->gabs_sh)
+                    for (int k = 0; k < 3 * j->pr[i].nsh; k++) j->gabs_sh[k * N + i] += fabs(csh[k]) * a;
                 for (int k = 0; k < ORC_NGRAD; k++) col[k] = fabs(col[k]) * a;
                 if (j->g->n_ctrl > 0) {
                     if (j->gabs_t) to_time_rows(j->g, fmin(1.0, fmax(0.0, j->cam->time)), col, j->gabs_t, N, i);
@@ -704,11 +826,14 @@ static void *bwd_accum_worker(void *arg) {
  * grad2d [9][N] screen-space gradients (may be NULL).  If the Gaussians have no velocity,
  * the vel rows are still written (time * dmu) and may be ignored.  cam_grad [16]
  * (overwritten, may be NULL): the camera gradient dR (row-major, R as a general matrix),
- * dt, dfx, dfy, dcx, dcy; cam_gabs [16] its error scale (computed with gabs). */
+ * dt, dfx, dfy, dcx, dcy; cam_gabs [16] its error scale (computed with gabs).
+ * grad_t / gabs_t: the time-parameterised planes (n_ctrl > 0); grad_sh / gabs_sh
+ * [3][(d_c + 1)^2 - 1][N]: the spherical-harmonic coefficients (sh_degree > 0); each may
+ * be NULL. */
 int orc_render_bwd(const orc_gaussians *g, const orc_camera *cam, const orc_params *p,
                    int64_t npix, const int32_t *px, const int32_t *py, const double *dL_dC,
                    double *grad, double *gabs, double *grad2d, double *cam_grad, double *cam_gabs,
-                   double *grad_t, double *gabs_t, int nthreads) {
+                   double *grad_t, double *gabs_t, double *grad_sh, double *gabs_sh, int nthreads) {
     if (nthreads < 1) nthreads = 1;
     int64_t N = g->N;
     memset(grad, 0, sizeof(double) * ORC_NGRAD * (size_t)N);
@@ -721,6 +846,14 @@ int orc_render_bwd(const orc_gaussians *g, const orc_camera *cam, const orc_para
     } else {
         grad_t = gabs_t = NULL;
     }
+    if (g->sh_degree < 0 || g->sh_degree > 3 || (g->sh_degree > 0 && !g->sh)) return 1;
+    const int64_t nsh = (int64_t)(g->sh_degree + 1) * (g->sh_degree + 1) - 1;
+    if (nsh > 0) {
+        if (grad_sh) memset(grad_sh, 0, sizeof(double) * 3 * (size_t)nsh * (size_t)N);
+        if (gabs_sh) memset(gabs_sh, 0, sizeof(double) * 3 * (size_t)nsh * (size_t)N);
+    } else {
+        grad_sh = gabs_sh = NULL;
+    }
     orc_proj *pr = project_all(g, cam, p);
     if (!pr) return 1;
     contrib_list *lists = (contrib_list *)calloc((size_t)nthreads, sizeof(contrib_list));
@@ -728,7 +861,7 @@ int orc_render_bwd(const orc_gaussians *g, const orc_camera *cam, const orc_para
     bwd_job *jobs = (bwd_job *)malloc(sizeof(bwd_job) * (size_t)nthreads);
     for (int t = 0; t < nthreads; t++) {
         bwd_job jb = {pr, g, N, p, cam, npix, px, py, dL_dC, lists, grad, gabs, grad2d, grad_t,
-                      gabs ? gabs_t : NULL, t, nthreads, 0, {0}, {0}};
+                      gabs ? gabs_t : NULL, grad_sh, gabs ? gabs_sh : NULL, t, nthreads, 0, {0}, {0}};
         jobs[t] = jb;
         pthread_create(&th[t], NULL, bwd_pixels_worker, &jobs[t]);
     }
