@@ -361,6 +361,8 @@ def run_gv(args):
     if not args.no_extras and args.workload == "frame540p":
         out["camera_adjoint"] = run_camera_adjoint(torch, ctx, step, grads, flush, P, max(50, args.steps // 4))
         out["motion"] = run_motion(torch, gv, synth, ctx, dev, flush, frames[0].cam, target, max(50, args.steps // 4))
+        out["sh3"] = run_sh(torch, gv, synth, ctx, dev, flush, params, frames, target, max(50, args.steps // 4),
+                            hbm_peak)
         out["batched"] = run_batched(torch, gv, synth, ctx, dev, flush, max(20, args.steps // 4))
         out["e2e"] = run_e2e(torch, gv, ctx, params, target, frames, ws, dev, flush, max(20, args.steps // 4), scale,
                              world)
@@ -415,16 +417,11 @@ def run_camera_adjoint(torch, ctx, step, grads, flush, P, steps):
                         "also accumulated"}
 
 
-def run_motion(torch, gv, synth, ctx, dev, flush, cam0, target, steps):
-    """The per-frame step on time-parameterised Gaussians (the paper's Eq. 2-3: means on a
-    cubic B-spline over 8 control points, cubic log-scale and quaternion terms), same frame
-    size, Gaussian count and camera, at t = 0.4: throughput and the projection stages."""
-    import dataclasses
-    rng = np.random.default_rng(synth.SEED_BASE + 9)
-    g = synth.spline_gaussians(rng, N_GAUSS, 8)
-    params = {k: torch.from_numpy(v).to(dev) for k, v in g.items()}
-    cam = dataclasses.replace(cam0, time=0.4)
-    frames = [gv.Frame(cam, 0, N_GAUSS, 0)]
+def time_variant(torch, ctx, dev, flush, params, frames, target, steps, workload, hbm_peak=None, proj_bytes=None):
+    """The per-frame step (fwd + L2 loss + bwd) on another parameterisation of the same
+    frame: throughput, and the projection stages' times (with their HBM rates when the
+    algorithmic bytes per Gaussian are given: proj_bytes = (forward, backward))."""
+    cam = frames[0].cam
     P = cam.W * cam.H
     image = torch.empty(3 * P, device=dev)
     T = torch.empty(P, device=dev)
@@ -465,11 +462,44 @@ def run_motion(torch, gv, synth, ctx, dev, flush, cam0, target, steps):
         for k in ("project", "project_bwd"):
             acc.setdefault(k, []).append(st_ms[k])
     ctx.profile_enable(False)
-    return {"value": round(P / (ms / 1000) / 1e6, 2), "unit": "Mpix/s", "ms_per_step": round(ms, 4),
-            "project_ms": round(statistics.median(acc["project"]), 4),
-            "project_bwd_ms": round(statistics.median(acc["project_bwd"]), 4),
-            "workload": "one 960x540 frame, 200,000 time-parameterised Gaussians (8 B-spline control points, "
-                        "cubic log-scale and quaternion terms) at t = 0.4, fwd+L2 loss+bwd"}
+    out = {"value": round(P / (ms / 1000) / 1e6, 2), "unit": "Mpix/s", "ms_per_step": round(ms, 4),
+           "project_ms": round(statistics.median(acc["project"]), 4),
+           "project_bwd_ms": round(statistics.median(acc["project_bwd"]), 4), "workload": workload}
+    if proj_bytes:
+        n = int(params["opacity_logit"].shape[-1])
+        for key, b in zip(("project", "project_bwd"), proj_bytes):
+            gbs = b * n / (out[key + "_ms"] / 1000) / 1e9
+            out[key + "_gbs"] = round(gbs, 1)
+            out[key + "_frac"] = round(gbs / hbm_peak, 4)
+        out["l2_resident"] = True
+    return out
+
+
+def run_motion(torch, gv, synth, ctx, dev, flush, cam0, target, steps):
+    """The per-frame step on time-parameterised Gaussians (the paper's Eq. 2-3: means on a
+    cubic B-spline over 8 control points, cubic log-scale and quaternion terms), same frame
+    size, Gaussian count and camera, at t = 0.4: throughput and the projection stages."""
+    import dataclasses
+    rng = np.random.default_rng(synth.SEED_BASE + 9)
+    g = synth.spline_gaussians(rng, N_GAUSS, 8)
+    params = {k: torch.from_numpy(v).to(dev) for k, v in g.items()}
+    cam = dataclasses.replace(cam0, time=0.4)
+    return time_variant(torch, ctx, dev, flush, params, [gv.Frame(cam, 0, N_GAUSS, 0)], target, steps,
+                        "one 960x540 frame, 200,000 time-parameterised Gaussians (8 B-spline control points, "
+                        "cubic log-scale and quaternion terms) at t = 0.4, fwd+L2 loss+bwd")
+
+
+def run_sh(torch, gv, synth, ctx, dev, flush, params0, frames, target, steps, hbm_peak):
+    """The per-frame step with view-dependent colour (Sec. 3.1: spherical harmonics of
+    degree 3, 15 terms per channel above the plain colour) on the headline frame and its
+    200k Gaussians.  Projection bytes per Gaussian: forward 112 + 180 (the coefficients);
+    backward 148 + 180 (coefficients read again) + 360 (their gradient read and written)."""
+    rng = np.random.default_rng(synth.SEED_BASE + 10)
+    params = dict(params0)
+    params["sh"] = torch.from_numpy(synth.sh_coefficients(rng, N_GAUSS, 3)).to(dev)
+    return time_variant(torch, ctx, dev, flush, params, frames, target, steps,
+                        "one 960x540 frame, 200,000 Gaussians with degree-3 spherical-harmonic colour, "
+                        "fwd+L2 loss+bwd", hbm_peak, (112 + 180, 148 + 180 + 360))
 
 
 def run_batched(torch, gv, synth, ctx, dev, flush, steps):

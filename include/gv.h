@@ -104,6 +104,17 @@ typedef struct {
     const float *ctrl;
     const float *log_scale_t;
     const float *quat_t;
+    /* View-dependent colour (Sec. 3.1: colour as spherical harmonics of order d_c), used
+     * when sh_degree is 1, 2 or 3 (0: the colour is rgb alone).  sh [3][K][N] with
+     * K = (sh_degree + 1)^2 - 1: per channel the coefficients of degrees 1..sh_degree in
+     * the order (l, m = -l..l); the degree-0 term is rgb itself, so
+     *   colour = rgb + sum_k Y_k(d) sh[ch][k],
+     * Y_k the real spherical harmonics (orthonormal on the sphere, Condon-Shortley phase:
+     * Y_{1,-1} = -sqrt(3/(4 pi)) y, Y_{1,0} = sqrt(3/(4 pi)) z, Y_{1,1} = -sqrt(3/(4 pi)) x,
+     * ...) at the unit direction d from the camera centre -R^T t to the mean, in the
+     * world frame.  No offset and no clamp. */
+    int32_t sh_degree;
+    const float *sh;
     /* Optional OUTPUT of the forward (device, [N] bytes, or NULL): for every Gaussian i with
      * at least one kept (tile, Gaussian) key on some frame of the call -- its alpha can
      * reach 1/255 on a pixel of that frame -- the forward sets visible[i] = 1.  It never
@@ -124,6 +135,7 @@ typedef struct {
     float *mean, *vel, *log_scale, *quat, *opacity_logit, *rgb;
     float *camera;
     float *ctrl, *log_scale_t, *quat_t; /* time-parameterised form: same layouts, or NULL */
+    float *sh;                          /* spherical-harmonic coefficients, [3][K][N], or NULL */
 } gv_gaussians_grad;
 
 /* One frame of a batch: its camera, the Gaussian subset [gauss_offset, gauss_offset +

@@ -142,6 +142,8 @@ gv_status make_plan(gv_ctx *ctx, const gv_options &o, long long N, const gv_fram
         x.fx = c.fx; x.fy = c.fy; x.cx = c.cx; x.cy = c.cy;
         for (int i = 0; i < 9; i++) x.R[i] = c.R[i];
         for (int i = 0; i < 3; i++) x.t[i] = c.t[i];
+        for (int j = 0; j < 3; j++)
+            x.campos[j] = (float)-((double)c.R[j] * c.t[0] + (double)c.R[3 + j] * c.t[1] + (double)c.R[6 + j] * c.t[2]);
         x.time = c.time;
         if (n_ctrl > 0) {
             x.time = std::min(1.f, std::max(0.f, c.time));
@@ -290,6 +292,8 @@ GaussPtrs gauss_ptrs(const gv_gaussians *g) {
     p.N = g->N;
     p.n_ctrl = g->n_ctrl;
     p.ctrl = g->ctrl; p.log_scale_t = g->log_scale_t; p.quat_t = g->quat_t;
+    p.sh_degree = g->sh_degree;
+    p.sh = g->sh_degree > 0 ? g->sh : nullptr;
     p.visible = g->visible;
     if (p.n_ctrl > 0) p.vel = nullptr;
     return p;
@@ -302,6 +306,10 @@ gv_status check_gaussians(gv_ctx *ctx, const gv_gaussians *g) {
         return fail(ctx, GV_ERR_INVALID_ARG, "n_ctrl %d outside [4, 64]", g->n_ctrl);
     if (g->N > 0 && ((g->n_ctrl ? !g->ctrl : !g->mean) || !g->log_scale || !g->quat || !g->opacity_logit || !g->rgb))
         return fail(ctx, GV_ERR_INVALID_ARG, "a required Gaussian parameter plane is NULL");
+    if (g->sh_degree < 0 || g->sh_degree > 3)
+        return fail(ctx, GV_ERR_INVALID_ARG, "sh_degree %d outside [0, 3]", g->sh_degree);
+    if (g->N > 0 && g->sh_degree > 0 && !g->sh)
+        return fail(ctx, GV_ERR_INVALID_ARG, "sh_degree %d with NULL sh", g->sh_degree);
     return GV_OK;
 }
 
@@ -393,6 +401,7 @@ gv_status backward_stages(gv_ctx *ctx, const gv_gaussians *g, const Plan &pl, co
     gp.quat = grad->quat; gp.logit = grad->opacity_logit; gp.rgb = grad->rgb;
     gp.cam = grad->camera;
     gp.ctrl = grad->ctrl; gp.log_scale_t = grad->log_scale_t; gp.quat_t = grad->quat_t;
+    gp.sh = g->sh_degree > 0 ? grad->sh : nullptr;
     {
         StageTimer tm(ctx, GV_STAGE_PROJECT_BWD, s, 2);
         const GaussPtrs gptr = gauss_ptrs(g);

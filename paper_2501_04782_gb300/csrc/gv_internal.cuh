@@ -49,6 +49,7 @@ struct DevFrame {
     // non-zero cubic B-spline weights spline_w at this frame's time (host-computed)
     int spline_lo;
     float spline_w[4];
+    float campos[3];  // camera centre -R^T t (view direction of the spherical harmonics)
 };
 
 struct DevHeader {
@@ -148,6 +149,8 @@ struct GaussPtrs {
     long long N;
     int n_ctrl;  // > 0: means on the B-spline over ctrl; log_scale_t / quat_t: cubic terms (or NULL)
     const float *ctrl, *log_scale_t, *quat_t;
+    int sh_degree;     // 0..3; > 0: colour = rgb + sum_k Y_k(dir) sh[ch][k]
+    const float *sh;   // [3][(sh_degree + 1)^2 - 1][N]
     uint8_t *visible;  // [N] or NULL: set to 1 for Gaussians with a kept key (forward)
 };
 
@@ -155,6 +158,7 @@ struct GradPtrs {
     float *mean, *vel, *log_scale, *quat, *logit, *rgb;
     float *cam;  // [F][kCamGrad] or NULL
     float *ctrl, *log_scale_t, *quat_t;  // time-parameterised form
+    float *sh;                           // spherical-harmonic coefficients or NULL
 };
 
 // Camera gradient per frame: dR (9, row-major), dt (3), dfx, dfy, dcx, dcy.

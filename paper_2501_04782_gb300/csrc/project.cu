@@ -9,6 +9,8 @@
 // do not.  Both kernels are HBM-bound: one thread per pair, coalesced SoA plane reads.
 #include <algorithm>
 
+#include <type_traits>
+
 #include "gv_internal.cuh"
 
 namespace gvk {
@@ -158,6 +160,100 @@ __device__ __forceinline__ void bin_shared_init(BinShared &sb) {
     if (threadIdx.x == 0) { sb.full = 0u; sb.live = 0ull; }
 }
 
+// View-dependent colour (Sec. 3.1: colour as spherical harmonics of order d_c <= 3; the
+// degree-0 term is the plain colour plane): colour = rgb + sum_k Y_k(d) sh[ch][k], Y_k the
+// real spherical harmonics of degrees 1..d_c in the order (l, m = -l..l) with the
+// Condon-Shortley phase, written out as Cartesian polynomials of the unit direction d from
+// the camera centre to the mean (world frame).  Normalisations sqrt((2l+1)/(4 pi) ...):
+constexpr float kSh1 = 0.48860251190291992f;   // sqrt(3/(4 pi))
+constexpr float kSh2a = 1.0925484305920792f;   // sqrt(15/(4 pi))
+constexpr float kSh20 = 0.31539156525252005f;  // sqrt(5/(16 pi))
+constexpr float kSh22 = 0.54627421529603959f;  // sqrt(15/(16 pi))
+constexpr float kSh33 = 0.59004358992664352f;  // sqrt(35/(32 pi))
+constexpr float kSh32a = 2.8906114426405538f;  // sqrt(105/(4 pi))
+constexpr float kSh31 = 0.45704579946446572f;  // sqrt(21/(32 pi))
+constexpr float kSh30 = 0.37317633259011540f;  // sqrt(7/(16 pi))
+constexpr float kSh32 = 1.4453057213202769f;   // sqrt(105/(16 pi))
+constexpr int kShMax = 15;                      // terms above degree 0 at degree 3
+
+__device__ __forceinline__ int sh_terms(int deg) { return (deg + 1) * (deg + 1) - 1; }
+
+__device__ __forceinline__ void sh_eval(int deg, float x, float y, float z, float Y[kShMax]) {
+    Y[0] = -kSh1 * y;
+    Y[1] = kSh1 * z;
+    Y[2] = -kSh1 * x;
+    if (deg < 2) return;
+    const float xx = x * x, yy = y * y, zz = z * z;
+    Y[3] = kSh2a * x * y;
+    Y[4] = -kSh2a * y * z;
+    Y[5] = kSh20 * (3.f * zz - 1.f);
+    Y[6] = -kSh2a * x * z;
+    Y[7] = kSh22 * (xx - yy);
+    if (deg < 3) return;
+    Y[8] = -kSh33 * y * (3.f * xx - yy);
+    Y[9] = kSh32a * x * y * z;
+    Y[10] = -kSh31 * y * (5.f * zz - 1.f);
+    Y[11] = kSh30 * z * (5.f * zz - 3.f);
+    Y[12] = -kSh31 * x * (5.f * zz - 1.f);
+    Y[13] = kSh32 * z * (xx - yy);
+    Y[14] = -kSh33 * x * (xx - 3.f * yy);
+}
+
+// sum_k s_k grad Y_k at (x, y, z), the polynomials taken as functions of three variables.
+__device__ __forceinline__ void sh_dir_grad(int deg, float x, float y, float z, const float s[kShMax], float g[3]) {
+    float gx = -kSh1 * s[2], gy = -kSh1 * s[0], gz = kSh1 * s[1];
+    if (deg >= 2) {
+        gx += kSh2a * (y * s[3] - z * s[6]) + 2.f * kSh22 * x * s[7];
+        gy += kSh2a * (x * s[3] - z * s[4]) - 2.f * kSh22 * y * s[7];
+        gz += -kSh2a * (y * s[4] + x * s[6]) + 6.f * kSh20 * z * s[5];
+    }
+    if (deg >= 3) {
+        const float xx = x * x, yy = y * y, zz = z * z, q = 5.f * zz - 1.f;
+        gx += -6.f * kSh33 * x * y * s[8] + kSh32a * y * z * s[9] - kSh31 * q * s[12] + 2.f * kSh32 * x * z * s[13] -
+              3.f * kSh33 * (xx - yy) * s[14];
+        gy += -3.f * kSh33 * (xx - yy) * s[8] + kSh32a * x * z * s[9] - kSh31 * q * s[10] - 2.f * kSh32 * y * z * s[13] +
+              6.f * kSh33 * x * y * s[14];
+        gz += kSh32a * x * y * s[9] - 10.f * kSh31 * y * z * s[10] + kSh30 * (15.f * zz - 3.f) * s[11] -
+              10.f * kSh31 * x * z * s[12] + kSh32 * (xx - yy) * s[13];
+    }
+    g[0] = gx;
+    g[1] = gy;
+    g[2] = gz;
+}
+
+// Unit view direction d = (mu - c) / |mu - c| from the frame's camera centre c, and 1/|mu - c|.
+__device__ __forceinline__ void view_dir(const PairState<float> &st, const DevFrame &fr, float d[3], float &rn) {
+    const float vx = st.mx - fr.campos[0], vy = st.my - fr.campos[1], vz = st.mz - fr.campos[2];
+    rn = rsqrtf(vx * vx + vy * vy + vz * vz);
+    d[0] = vx * rn;
+    d[1] = vy * rn;
+    d[2] = vz * rn;
+}
+
+// The pair's colour: rgb, plus the spherical-harmonic terms when SH (valid pairs only: a
+// culled pair's colour is never read).
+template <bool SH>
+__device__ __forceinline__ void pair_colour(const GaussPtrs &g, long long gi, const PairState<float> &st,
+                                            const DevFrame &fr, float col[3]) {
+    const long long N = g.N;
+    col[0] = g.rgb[gi];
+    col[1] = g.rgb[N + gi];
+    col[2] = g.rgb[2 * N + gi];
+    if constexpr (SH) {
+        if (!st.valid) return;
+        float d[3], rn, Y[kShMax];
+        view_dir(st, fr, d, rn);
+        sh_eval(g.sh_degree, d[0], d[1], d[2], Y);
+        const int K = sh_terms(g.sh_degree);
+#pragma unroll
+        for (int k = 0; k < kShMax; k++) {
+            if (k >= K) break;
+#pragma unroll
+            for (int ch = 0; ch < 3; ch++) col[ch] = fmaf(Y[k], g.sh[((long long)ch * K + k) * N + gi], col[ch]);
+        }
+    }
+}
+
 // Bins one pair (culled rule, see gv_internal.cuh), the per-pair part: extent box, cells,
 // cull record (rect and ell written).  Returns the number of tile rows of its box (0 when
 // it bins nothing); the rows are culled by warp_cull_rows.
@@ -270,7 +366,7 @@ __device__ __forceinline__ bool ill_conditioned(const PairState<float> &st) {
 }
 
 // Grid-stride over the pairs so each block flushes its counters once.
-template <bool SPLINE>
+template <bool SPLINE, bool SH>
 __global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, int lw, int lh, int tile_passes) {
     __shared__ BinShared sb;
     bin_shared_init(sb);
@@ -298,10 +394,11 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, i
                 w.fp64_list[atomicAdd(&w.hdr->fp64_count, 1u)] = p;
                 w.rect[p].w = (unsigned)f | kRectFp64;
             }
-            const long long N = g.N;
+            float col[3];
+            pair_colour<SH>(g, gi, st, fr, col);
             w.feat0[p] = make_float4(st.u, st.v, -0.5f * kLog2e * st.A, -kLog2e * st.B);
-            w.feat1[p] = make_float4(-0.5f * kLog2e * st.C, log2f(st.o), g.rgb[gi], g.rgb[N + gi]);
-            w.feat2[p] = g.rgb[2 * N + gi];
+            w.feat1[p] = make_float4(-0.5f * kLog2e * st.C, log2f(st.o), col[0], col[1]);
+            w.feat2[p] = col[2];
             key = cells ? __float_as_uint(st.zc) : 0xFFFFFFFFu;
             w.dkey[0][p] = key;
         }
@@ -466,17 +563,67 @@ __device__ __forceinline__ void geometry_backward(const PairState<F> &st, const 
 // (a', b', c') = -log2(e) (A/2, B, C/2) and log2 o; converted here to the conic and opacity.
 // The geometric part of a pair the projection listed as ill-conditioned is left to the
 // FP64 kernel.
-__device__ __forceinline__ void pair_backward(const PairState<float> &st, bool deferred, const DevFrame &fr,
+// SH: the colour's spherical-harmonic terms.  Returns true when the pair has a colour
+// gradient, then shY[k] = Y_k(d) (the coefficients' gradient is dsh[ch][k] = Y_k dc_ch,
+// added by the caller); through the direction d = v / |v|, v = mu - c: dv = (I - d d^T) dd
+// / |v| adds to the mean and, c = -R^T t being the camera centre, to the camera
+// (dR_rj += t_r dv_j, dt_r += sum_j R_rj dv_j).  Done in FP32 for deferred pairs too.
+template <bool SH = false>
+__device__ __forceinline__ bool pair_backward(const PairState<float> &st, bool deferred, const DevFrame &fr,
                                               float4 g0, float4 g1, float g2, float acc[17],
-                                              float *cam = nullptr) {
+                                              float *cam = nullptr, const GaussPtrs *gp = nullptr,
+                                              long long gi = 0, float *shY = nullptr) {
+    bool sh_live = false;
     acc[14] += g1.z;
     acc[15] += g1.w;
     acc[16] += g2;
     // d log2(o) / d logit = (1 - o) / ln 2
     acc[13] += g1.y * (1.f - st.o) * kLog2e;
-    if (!st.valid || deferred) return;
+    if constexpr (SH) {
+        if (st.valid && (g1.z != 0.f || g1.w != 0.f || g2 != 0.f)) {
+            sh_live = true;
+            const GaussPtrs &g = *gp;
+            const long long N = g.N;
+            const int K = sh_terms(g.sh_degree);
+            float d[3], rn, sk[kShMax];
+            view_dir(st, fr, d, rn);
+            sh_eval(g.sh_degree, d[0], d[1], d[2], shY);
+            const float dc[3] = {g1.z, g1.w, g2};
+#pragma unroll
+            for (int k = 0; k < kShMax; k++) {
+                sk[k] = 0.f;
+                if (k >= K) continue;
+#pragma unroll
+                for (int ch = 0; ch < 3; ch++) sk[k] = fmaf(dc[ch], g.sh[((long long)ch * K + k) * N + gi], sk[k]);
+            }
+            float dd[3];
+            sh_dir_grad(g.sh_degree, d[0], d[1], d[2], sk, dd);
+            const float along = dd[0] * d[0] + dd[1] * d[1] + dd[2] * d[2];
+            float dv[3];
+#pragma unroll
+            for (int j = 0; j < 3; j++) dv[j] = (dd[j] - d[j] * along) * rn;
+            const float time = fr.time;
+#pragma unroll
+            for (int j = 0; j < 3; j++) {
+                acc[j] += dv[j];
+                acc[3 + j] += time * dv[j];
+            }
+            if (cam) {
+#pragma unroll
+                for (int r = 0; r < 3; r++) {
+#pragma unroll
+                    for (int j = 0; j < 3; j++) {
+                        cam[r * 3 + j] += fr.t[r] * dv[j];
+                        cam[9 + r] += fr.R[r * 3 + j] * dv[j];
+                    }
+                }
+            }
+        }
+    }
+    if (!st.valid || deferred) return sh_live;
     const float dA = -0.5f * kLog2e * g0.z, dB = -kLog2e * g0.w, dC = -0.5f * kLog2e * g1.x;
     geometry_backward<float>(st, fr, g0.x, g0.y, dA, dB, dC, acc, cam);
+    return sh_live;
 }
 
 // Adds acc into the gradient planes: rows [0, 13) (geometry) atomically when geo_atomic
@@ -525,6 +672,26 @@ __device__ __forceinline__ void store_grad_time(const GradPtrs &gr, const GaussP
         if (gr.quat_t && g.quat_t)
 #pragma unroll
             for (int k = 0; k < 4; k++) add(gr.quat_t + (p * 4 + k) * N + gi, tp * acc[9 + k]);
+    }
+}
+
+// Adds the spherical-harmonic coefficient gradients dsh[ch][k] = Y[k] c[ch] of one
+// Gaussian (c: one pair's colour gradient), or acc[(ch * kShMax + k) * stride] when Y is NULL.
+__device__ __forceinline__ void store_grad_sh(const GradPtrs &gr, const GaussPtrs &g, long long gi, const float *Y,
+                                              const float c[3], const float *acc, bool atomic, int stride = 1) {
+    if (!gr.sh) return;
+    const long long N = g.N;
+    const int K = sh_terms(g.sh_degree);
+#pragma unroll
+    for (int k = 0; k < kShMax; k++) {
+        if (k >= K) break;
+#pragma unroll
+        for (int ch = 0; ch < 3; ch++) {
+            float *dst = gr.sh + ((long long)ch * K + k) * N + gi;
+            const float v = Y ? Y[k] * c[ch] : acc[(ch * kShMax + k) * stride];
+            if (atomic) atomicAdd(dst, v);
+            else *dst += v;
+        }
     }
 }
 
@@ -583,11 +750,26 @@ __device__ __forceinline__ void cam_block_flush(float (*s_cam)[kCamGrad], int F,
     }
 }
 
+// acc[(ch * kShMax + k) * stride] += Y[k] dc_ch (the coefficient gradients of one pair,
+// summed over the frames of a shared set; K terms).
+template <bool SH>
+__device__ __forceinline__ void sh_accumulate(const float *Y, int K, float4 g1, float g2, float *acc, int stride) {
+    if constexpr (SH) {
+        const float dc[3] = {g1.z, g1.w, g2};
+#pragma unroll
+        for (int k = 0; k < kShMax; k++) {
+            if (k >= K) break;
+#pragma unroll
+            for (int ch = 0; ch < 3; ch++) acc[(ch * kShMax + k) * stride] += Y[k] * dc[ch];
+        }
+    }
+}
+
 // mode 0: one thread per pair, each Gaussian in at most one frame (plain +=)
 // mode 2: one thread per pair, overlapping sets (atomicAdd)
 // Grid-stride over the pairs; CAM: also the camera gradients of the frames; SPLINE: the
 // time-parameterised form.
-template <bool CAM, bool SPLINE>
+template <bool CAM, bool SPLINE, bool SH>
 __global__ void __launch_bounds__(128) project_bwd_pairs_kernel(Work w, GaussPtrs g, GradPtrs gr, int atomic) {
     __shared__ float s_cam[CAM ? kCamSmemFrames : 1][kCamGrad];
     const int F = (int)w.L.F;
@@ -608,9 +790,22 @@ __global__ void __launch_bounds__(128) project_bwd_pairs_kernel(Work w, GaussPtr
 #pragma unroll
             for (int k = 0; k < 17; k++) acc[k] = 0.f;
             const bool deferred = (w.rect[p].w & kRectFp64) != 0u;
-            pair_backward(st, deferred, fr, w.g0[p], w.g1[p], w.g2[p], acc, CAM ? cam : nullptr);
-            store_grad(gr, g.N, gi, acc, atomic != 0, false, deferred, SPLINE);
-            if (SPLINE && !deferred) store_grad_time(gr, g, fr, gi, acc, atomic != 0);
+            float shY[SH ? kShMax : 1];
+            const float4 g1 = w.g1[p];
+            const float g2 = w.g2[p];
+            const bool live = pair_backward<SH>(st, deferred, fr, w.g0[p], g1, g2, acc, CAM ? cam : nullptr, &g, gi,
+                                                shY);
+            if (SH) {
+                // a deferred pair's mean rows hold the direction term only; the FP64 kernel
+                // adds the geometric part to the same planes concurrently
+                store_grad(gr, g.N, gi, acc, atomic != 0, deferred, false, SPLINE);
+                if (SPLINE) store_grad_time(gr, g, fr, gi, acc, atomic != 0 || deferred);
+                const float dc[3] = {g1.z, g1.w, g2};
+                if (live) store_grad_sh(gr, g, gi, shY, dc, nullptr, atomic != 0);
+            } else {
+                store_grad(gr, g.N, gi, acc, atomic != 0, false, deferred, SPLINE);
+                if (SPLINE && !deferred) store_grad_time(gr, g, fr, gi, acc, atomic != 0);
+            }
         }
         if (CAM) cam_add(cam, f, s_cam, gr.cam);
     }
@@ -619,9 +814,13 @@ __global__ void __launch_bounds__(128) project_bwd_pairs_kernel(Work w, GaussPtr
 
 // mode 1: one shared Gaussian set; one thread per Gaussian sums over all frames (grid-stride).
 // SPLINE: the time-parameterised form (g.n_ctrl > 0).
-template <bool CAM, bool SPLINE>
-__global__ void __launch_bounds__(128) project_bwd_shared_kernel(Work w, GaussPtrs g, GradPtrs gr) {
+template <bool CAM, bool SPLINE, bool SH>
+__global__ void __launch_bounds__(128, SH ? 3 : 1) project_bwd_shared_kernel(Work w, GaussPtrs g, GradPtrs gr) {
     __shared__ float s_cam[CAM ? kCamSmemFrames : 1][kCamGrad];
+    // each thread's coefficient-gradient sums over the frames, a column of its own
+    __shared__ float s_acc_sh[SH ? 3 * kShMax : 1][SH ? 128 : 1];
+    float *acc_sh = &s_acc_sh[0][SH ? threadIdx.x : 0];
+    const int Ksh = SH ? sh_terms(g.sh_degree) : 0;
     const int F = (int)w.L.F;
     if (CAM) cam_block_init(s_cam, F);
     const DevFrame &f0 = w.frames[0];
@@ -632,6 +831,8 @@ __global__ void __launch_bounds__(128) project_bwd_shared_kernel(Work w, GaussPt
         float acc[17];
 #pragma unroll
         for (int k = 0; k < 17; k++) acc[k] = 0.f;
+        if (SH)
+            for (int k = 0; k < 3 * kShMax; k++) acc_sh[k * 128] = 0.f;
         bool any_deferred = false;
         for (int f = 0; f < F; f++) {
             float cam[kCamGrad];
@@ -651,17 +852,26 @@ __global__ void __launch_bounds__(128) project_bwd_shared_kernel(Work w, GaussPt
                     float accf[17];
 #pragma unroll
                     for (int k = 0; k < 17; k++) accf[k] = 0.f;
-                    pair_backward(st, deferred, fr, w.g0[p], w.g1[p], w.g2[p], accf, CAM ? cam : nullptr);
-                    if (!deferred) store_grad_time(gr, g, fr, gi, accf, true);
+                    float shY[SH ? kShMax : 1];
+                    const float4 g1 = w.g1[p];
+                    const float g2 = w.g2[p];
+                    if (pair_backward<SH>(st, deferred, fr, w.g0[p], g1, g2, accf, CAM ? cam : nullptr, &g, gi, shY))
+                        sh_accumulate<SH>(shY, Ksh, g1, g2, acc_sh, 128);
+                    if (!deferred || SH) store_grad_time(gr, g, fr, gi, accf, true);
 #pragma unroll
                     for (int k = 6; k < 17; k++) acc[k] += accf[k];
                 } else {
-                    pair_backward(st, deferred, fr, w.g0[p], w.g1[p], w.g2[p], acc, CAM ? cam : nullptr);
+                    float shY[SH ? kShMax : 1];
+                    const float4 g1 = w.g1[p];
+                    const float g2 = w.g2[p];
+                    if (pair_backward<SH>(st, deferred, fr, w.g0[p], g1, g2, acc, CAM ? cam : nullptr, &g, gi, shY))
+                        sh_accumulate<SH>(shY, Ksh, g1, g2, acc_sh, 128);
                 }
             }
             if (CAM) cam_add(cam, f, s_cam, gr.cam);
         }
         if (in) store_grad(gr, g.N, gi, acc, false, any_deferred, false, SPLINE);
+        if (SH && in) store_grad_sh(gr, g, gi, nullptr, nullptr, acc_sh, false, 128);
     }
     if (CAM) cam_block_flush(s_cam, F, gr.cam);
 }
@@ -709,8 +919,12 @@ cudaError_t launch_project_fwd(const Work &w, const GaussPtrs &g, int tile_w, in
     if (w.L.P == 0) return cudaSuccess;
     int lw = __builtin_ctz(tile_w), lh = __builtin_ctz(tile_h);
     unsigned blocks = std::min((w.L.P + 255u) / 256u, (unsigned)num_sms * 8u);
-    if (g.n_ctrl > 0) project_fwd_kernel<true><<<blocks, 256, 0, s>>>(w, g, lw, lh, tile_sort_passes(w));
-    else project_fwd_kernel<false><<<blocks, 256, 0, s>>>(w, g, lw, lh, tile_sort_passes(w));
+    const int tp = tile_sort_passes(w);
+    const bool spline = g.n_ctrl > 0, sh = g.sh_degree > 0;
+    if (spline && sh) project_fwd_kernel<true, true><<<blocks, 256, 0, s>>>(w, g, lw, lh, tp);
+    else if (spline) project_fwd_kernel<true, false><<<blocks, 256, 0, s>>>(w, g, lw, lh, tp);
+    else if (sh) project_fwd_kernel<false, true><<<blocks, 256, 0, s>>>(w, g, lw, lh, tp);
+    else project_fwd_kernel<false, false><<<blocks, 256, 0, s>>>(w, g, lw, lh, tp);
     return cudaGetLastError();
 }
 
@@ -726,6 +940,21 @@ cudaError_t launch_bin_from_screen(const Work &w, long long n, const float *u, c
     return cudaGetLastError();
 }
 
+// Calls fn(CAM, SPLINE, SH) with the three flags as std::integral_constant<bool, .>.
+template <class Fn>
+void dispatch_bwd(bool cam, bool spline, bool sh, Fn &&fn) {
+    auto with_sh = [&](auto C, auto S) {
+        if (sh) fn(C, S, std::true_type{});
+        else fn(C, S, std::false_type{});
+    };
+    auto with_spline = [&](auto C) {
+        if (spline) with_sh(C, std::true_type{});
+        else with_sh(C, std::false_type{});
+    };
+    if (cam) with_spline(std::true_type{});
+    else with_spline(std::false_type{});
+}
+
 cudaError_t launch_project_bwd(const Work &w, const GaussPtrs &g, const GradPtrs &gr, int mode, int num_sms,
                                cudaStream_t s) {
     if (w.L.P == 0) return cudaSuccess;
@@ -733,19 +962,17 @@ cudaError_t launch_project_bwd(const Work &w, const GaussPtrs &g, const GradPtrs
         // all frames share one set; its size is the first frame's count
         unsigned n = w.L.P / w.L.F;
         unsigned blocks = std::min((n + 127) / 128, (unsigned)num_sms * 16u);
-        const bool spline = g.n_ctrl > 0;
-        if (gr.cam && spline) project_bwd_shared_kernel<true, true><<<blocks, 128, 0, s>>>(w, g, gr);
-        else if (gr.cam) project_bwd_shared_kernel<true, false><<<blocks, 128, 0, s>>>(w, g, gr);
-        else if (spline) project_bwd_shared_kernel<false, true><<<blocks, 128, 0, s>>>(w, g, gr);
-        else project_bwd_shared_kernel<false, false><<<blocks, 128, 0, s>>>(w, g, gr);
+        dispatch_bwd(gr.cam != nullptr, g.n_ctrl > 0, g.sh_degree > 0, [&](auto C, auto S, auto H) {
+            project_bwd_shared_kernel<decltype(C)::value, decltype(S)::value, decltype(H)::value>
+                <<<blocks, 128, 0, s>>>(w, g, gr);
+        });
     } else {
         unsigned blocks = std::min((w.L.P + 127) / 128, (unsigned)num_sms * 16u);
         const int at = mode == 2 ? 1 : 0;
-        const bool spline = g.n_ctrl > 0;
-        if (gr.cam && spline) project_bwd_pairs_kernel<true, true><<<blocks, 128, 0, s>>>(w, g, gr, at);
-        else if (gr.cam) project_bwd_pairs_kernel<true, false><<<blocks, 128, 0, s>>>(w, g, gr, at);
-        else if (spline) project_bwd_pairs_kernel<false, true><<<blocks, 128, 0, s>>>(w, g, gr, at);
-        else project_bwd_pairs_kernel<false, false><<<blocks, 128, 0, s>>>(w, g, gr, at);
+        dispatch_bwd(gr.cam != nullptr, g.n_ctrl > 0, g.sh_degree > 0, [&](auto C, auto S, auto H) {
+            project_bwd_pairs_kernel<decltype(C)::value, decltype(S)::value, decltype(H)::value>
+                <<<blocks, 128, 0, s>>>(w, g, gr, at);
+        });
     }
     return cudaGetLastError();
 }

@@ -54,12 +54,12 @@ class Gaussians(ctypes.Structure):
     _fields_ = [("N", ctypes.c_int64)] + [(k, ctypes.c_void_p) for k in
                                           ("mean", "vel", "log_scale", "quat", "opacity_logit", "rgb")] + \
                [("n_ctrl", ctypes.c_int32)] + [(k, ctypes.c_void_p) for k in ("ctrl", "log_scale_t", "quat_t")] + \
-               [("visible", ctypes.c_void_p)]
+               [("sh_degree", ctypes.c_int32), ("sh", ctypes.c_void_p), ("visible", ctypes.c_void_p)]
 
 
 class GaussiansGrad(ctypes.Structure):
     _fields_ = [(k, ctypes.c_void_p) for k in ("mean", "vel", "log_scale", "quat", "opacity_logit", "rgb",
-                                               "camera", "ctrl", "log_scale_t", "quat_t")]
+                                               "camera", "ctrl", "log_scale_t", "quat_t", "sh")]
 
 CAMERA_GRAD = 16  # per frame: dR (row-major, R as a general matrix), dt, dfx, dfy, dcx, dcy
 
@@ -217,10 +217,15 @@ TIME_KEYS = ("ctrl", "log_scale_t", "quat_t")  # time-parameterised form (Sec. 3
 def gaussians_struct(params: dict, visible=None) -> Gaussians:
     """params: the SoA planes; with "ctrl" ([3, n_ctrl, N]) the time-parameterised form
     (means on the cubic B-spline over ctrl; optional "log_scale_t" [3, 3, N] and "quat_t"
-    [3, 4, N] cubic terms), the camera time then in [0, 1].  visible: optional uint8 [N]
-    device tensor the forward sets to 1 for every Gaussian with a kept key (never cleared)."""
+    [3, 4, N] cubic terms), the camera time then in [0, 1]; with "sh" ([3, K, N],
+    K = (d + 1)^2 - 1 for d in 1..3) view-dependent colour rgb + sum_k Y_k(dir) sh[:, k].
+    visible: optional uint8 [N] device tensor the forward sets to 1 for every Gaussian with
+    a kept key (never cleared)."""
     g = Gaussians()
     g.visible = _ptr(visible) if visible is not None else None
+    sh = params.get("sh")
+    g.sh = _ptr(sh) if sh is not None else None
+    g.sh_degree = sh_degree_of(int(sh.shape[1])) if sh is not None else 0
     g.N = int(params["opacity_logit"].shape[-1])
     for k in PARAM_KEYS + TIME_KEYS:
         v = params.get(k)
@@ -230,11 +235,19 @@ def gaussians_struct(params: dict, visible=None) -> Gaussians:
     return g
 
 
+def sh_degree_of(K: int) -> int:
+    """Degree d of K = (d + 1)^2 - 1 spherical-harmonic terms above degree 0 (d <= 3)."""
+    for d in range(1, 4):
+        if (d + 1) ** 2 - 1 == K:
+            return d
+    raise ValueError(f"sh has {K} terms per channel; expected 3, 8 or 15 (degree 1, 2 or 3)")
+
+
 def grad_struct(grads: dict) -> GaussiansGrad:
-    """grads: the parameter planes, optionally "camera" ([F, 16] device tensor) and the
-    time-parameterised planes."""
+    """grads: the parameter planes, optionally "camera" ([F, 16] device tensor), the
+    time-parameterised planes and "sh"."""
     g = GaussiansGrad()
-    for k in PARAM_KEYS + ("camera",) + TIME_KEYS:
+    for k in PARAM_KEYS + ("camera",) + TIME_KEYS + ("sh",):
         v = grads.get(k)
         setattr(g, k, _ptr(v) if v is not None else None)
     return g

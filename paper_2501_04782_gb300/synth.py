@@ -94,6 +94,15 @@ def gaussians(rng: np.random.Generator, N: int, box=((-1.0, 1.0), (-1.0, 1.0), (
     return out
 
 
+def sh_coefficients(rng: np.random.Generator, N: int, degree: int, std: float = 0.15) -> np.ndarray:
+    """View-dependent colour terms above degree 0 (Sec. 3.1): [3, (degree + 1)^2 - 1, N],
+    N(0, std / l) for the terms of degree l (higher degrees smaller, as fitted colour
+    fields are)."""
+    K = (degree + 1) ** 2 - 1
+    l_of = np.array([int(np.floor(np.sqrt(k + 1))) for k in range(K)], np.float64)
+    return (rng.normal(size=(3, K, N)) * (std / l_of)[None, :, None]).astype(np.float32)
+
+
 def concat_gaussians(sets: list[dict]) -> dict:
     keys = sets[0].keys()
     return {k: np.concatenate([s[k] for s in sets], axis=-1) for k in keys}
