@@ -40,7 +40,7 @@ class Renderer:
 
     def forward(self, params: dict, frames: list[gv.Frame], total_pix: int, ws: torch.Tensor | None = None):
         """Returns (image [3*total_pix], final_T [total_pix], last_idx [total_pix], ws)."""
-        dev = params["mean"].device
+        dev = params["opacity_logit"].device
         if dev.type != "cuda":
             raise ValueError("libgv renders CUDA tensors only")
         image = torch.empty(3 * total_pix, device=dev)
@@ -68,17 +68,20 @@ class Renderer:
         return grads
 
 
+# every parameter plane the renderer reads: the static planes, the time-parameterised
+# form (Sec. 3.2) and the view-dependent colour terms (Sec. 3.1)
+ALL_KEYS = PARAM_KEYS + gv.TIME_KEYS + ("sh",)
+
+
 class _RenderFunction(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, renderer, frames, total_pix, mean, vel, log_scale, quat, opacity_logit, rgb):
-        params = dict(mean=mean.contiguous(), vel=vel.contiguous() if vel is not None else None,
-                      log_scale=log_scale.contiguous(), quat=quat.contiguous(),
-                      opacity_logit=opacity_logit.contiguous(), rgb=rgb.contiguous())
+    def forward(ctx, renderer, frames, total_pix, keys, *tensors):
+        params = {k: t.contiguous() for k, t in zip(keys, tensors) if t is not None}
         image, T, idx, ws = renderer.forward(params, frames, total_pix)
         ctx.renderer = renderer
         ctx.frames = frames
         ctx.params = params
-        ctx.has_vel = vel is not None
+        ctx.keys = keys
         ctx.save_for_backward(T, idx, ws)
         ctx.mark_non_differentiable(T, idx)
         return image, T, idx
@@ -87,8 +90,7 @@ class _RenderFunction(torch.autograd.Function):
     def backward(ctx, d_image, d_T, d_idx):
         T, idx, ws = ctx.saved_tensors
         grads = ctx.renderer.backward(ctx.params, ctx.frames, ws, T, idx, d_image)
-        return (None, None, None, grads["mean"], grads.get("vel") if ctx.has_vel else None, grads["log_scale"],
-                grads["quat"], grads["opacity_logit"], grads["rgb"])
+        return (None, None, None, None) + tuple(grads.get(k) for k in ctx.keys)
 
 
 def render(renderer: Renderer, params: dict, frames) -> tuple[torch.Tensor, torch.Tensor, torch.Tensor, list]:
@@ -98,9 +100,8 @@ def render(renderer: Renderer, params: dict, frames) -> tuple[torch.Tensor, torc
     are assigned in order.  Returns (image [3*P_total] planar per frame, final_T, last_idx,
     frames with offsets)."""
     fr, total = gv.layout_frames(frames)
-    image, T, idx = _RenderFunction.apply(renderer, fr, total, params["mean"], params.get("vel"),
-                                          params["log_scale"], params["quat"], params["opacity_logit"],
-                                          params["rgb"])
+    keys = tuple(k for k in ALL_KEYS if params.get(k) is not None)
+    image, T, idx = _RenderFunction.apply(renderer, fr, total, keys, *(params[k] for k in keys))
     return image, T, idx, fr
 
 
@@ -127,7 +128,7 @@ class Trainer:
     the graph is captured once; a step replaces the frames' cameras in the instantiated
     graph, copies their targets into the graph's target buffer, and launches."""
 
-    KEYS = ("mean", "vel", "log_scale", "quat", "opacity_logit", "rgb")
+    KEYS = ALL_KEYS
 
     def __init__(self, params: dict, cams: list, targets: torch.Tensor, batch: int = 8, lr: float = 0.01,
                  betas=None, eps: float = 1e-8, tile=(16, 16), stage_depth: int = 128,
@@ -139,7 +140,7 @@ class Trainer:
         lr * lr_decay^k (the paper decays 0.01 by 0.99995 per step)."""
         if optimizer not in ("adam", "adan"):
             raise ValueError("optimizer must be 'adam' or 'adan'")
-        dev = params["mean"].device
+        dev = params["opacity_logit"].device
         self.N = int(params["opacity_logit"].shape[-1])
         self.keys = [k for k in self.KEYS if params.get(k) is not None]
         sizes = [params[k].numel() for k in self.keys]

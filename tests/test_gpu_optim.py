@@ -87,9 +87,17 @@ def test_adan_matches_oracle_over_steps(wd, debias, offset):
     assert np.array_equal(gprev.cpu().numpy(), rg.astype(np.float32))
 
 
-def test_autograd_function_matches_direct_backward():
-    w = synth.workload_clip_shared(F=2, N=5000, W=160, H=96)
-    g = w["gaussians"]
+@pytest.mark.parametrize("form", ["static", "sh", "spline_sh"])
+def test_autograd_function_matches_direct_backward(form):
+    """torch.autograd through the renderer for every parameter plane it reads: the plain
+    set, with view-dependent colour, and with B-spline means and cubic terms as well."""
+    if form == "spline_sh":
+        w = synth.workload_spline_clip(F=2, N=5000, W=160, H=96, n_ctrl=5)
+    else:
+        w = synth.workload_clip_shared(F=2, N=5000, W=160, H=96)
+    g = dict(w["gaussians"])
+    if form != "static":
+        g["sh"] = synth.sh_coefficients(np.random.default_rng(4), 5000, 2)
     params = {k: torch.from_numpy(v).cuda().requires_grad_(True) for k, v in g.items()}
     rend = render.Renderer((16, 16), 128)
     image, T, idx, frames = render.render(rend, params, w["frames"])
@@ -102,4 +110,6 @@ def test_autograd_function_matches_direct_backward():
     gd = direct.backward(dL)
     for k, p in params.items():
         a = p.grad.cpu().numpy()
-        assert np.allclose(a, gd[k], rtol=1e-5, atol=1e-7 * (np.abs(gd[k]).max() + 1e-12)), k
+        # atomic sums (compositing backward, time-parameterised planes) differ in order
+        # between two runs: a few 1e-7 of the largest element
+        assert np.allclose(a, gd[k], rtol=1e-5, atol=5e-6 * (np.abs(gd[k]).max() + 1e-12)), k

@@ -21,8 +21,11 @@ def small_problem(F=10, N=3000, W=128, H=96):
     return w, cams, targets
 
 
-def test_step_gradient_and_update_match_direct_computation():
+@pytest.mark.parametrize("with_sh", [False, True])
+def test_step_gradient_and_update_match_direct_computation(with_sh):
     w, cams, targets = small_problem()
+    if with_sh:  # view-dependent colour terms join the flat parameter buffer
+        w["gaussians"]["sh"] = synth.sh_coefficients(np.random.default_rng(6), w["gaussians"]["rgb"].shape[-1], 3)
     params = {k: torch.from_numpy(v).cuda() for k, v in w["gaussians"].items()}
     theta0 = {k: v.clone() for k, v in params.items()}
     tr = render.Trainer(params, cams, targets, batch=4, lr=0.01)
