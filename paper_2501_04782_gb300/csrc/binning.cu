@@ -20,6 +20,7 @@ namespace {
 
 __global__ void setup_kernel(Work w, FrameChunk chunk, int first, int count, int zero_all,
                              long long spin_limit, int drop_signal) {
+    pdl_prologue();
     int tid = blockIdx.x * blockDim.x + threadIdx.x;
     int stride = gridDim.x * blockDim.x;
     for (int i = tid; i < count; i += stride) w.frames[first + i] = chunk.f[i];
@@ -40,6 +41,7 @@ __global__ void setup_kernel(Work w, FrameChunk chunk, int first, int count, int
 
 // Sum of the tile counts of each block of kEmitBlock pairs taken in depth order.
 __global__ void __launch_bounds__(kEmitThreads) count_reduce_kernel(Work w, const unsigned *order) {
+    pdl_prologue();
     __shared__ unsigned s_w[8];
     unsigned b = blockIdx.x;
     unsigned base = b * kEmitBlock;
@@ -67,6 +69,7 @@ __global__ void __launch_bounds__(kEmitThreads) count_reduce_kernel(Work w, cons
 // the cells against the chunk table.  On overflow keys_total reports the key capacity
 // the call needs.
 __global__ void __launch_bounds__(1024) count_scan_kernel(Work w) {
+    pdl_prologue();
     __shared__ unsigned long long s_w[32];
     __shared__ unsigned long long s_carry;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -122,6 +125,7 @@ __global__ void __launch_bounds__(1024) count_scan_kernel(Work w) {
 // the emission chunks whose first cell it owns.  Also clears look-back buffer 0 for the
 // emission chunks (the depth sort is finished with it).
 __global__ void __launch_bounds__(kEmitThreads) offsets_kernel(Work w, const unsigned *order) {
+    pdl_prologue();
     __shared__ unsigned s_w[8];
     const unsigned b = blockIdx.x, base = b * kEmitBlock;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
@@ -187,6 +191,7 @@ struct EmitSortArgs {
 };
 
 __global__ void __launch_bounds__(kEmitThreads, 4) emit_sort_kernel(Work w, EmitSortArgs a) {
+    pdl_prologue();
     __shared__ int s_owner[kEmitBlock];          // later: the chunk's keys, reordered by digit
     __shared__ unsigned s_off[kEmitBlock + 1];
     __shared__ unsigned s_pair[kEmitBlock];      // later: their pair ids
@@ -364,6 +369,7 @@ __global__ void __launch_bounds__(kEmitThreads, 4) emit_sort_kernel(Work w, Emit
 constexpr int kRangeItems = 8;
 
 __global__ void __launch_bounds__(256) ranges_kernel(Work w, const unsigned *keys) {
+    pdl_prologue();
     const unsigned n = w.hdr->keys_used;
     const int lane = threadIdx.x & 31;
     const unsigned warps = gridDim.x * (blockDim.x >> 5);
@@ -397,6 +403,7 @@ __global__ void __launch_bounds__(256) ranges_kernel(Work w, const unsigned *key
 
 __global__ void gather_debug_kernel(Work w, float *mean2d, float *conic, float *opacity, float *depth,
                                     int32_t *counts, int depth_buf) {
+    pdl_prologue();
     unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned P = w.L.P;
     if (p >= P) return;
@@ -423,16 +430,16 @@ cudaError_t launch_setup(const Work &w, const FrameChunk &chunk, int first, int 
                              : (unsigned)count;
     unsigned blocks = min((work + 255u) / 256u, 1024u);
     if (blocks == 0) blocks = 1;
-    setup_kernel<<<blocks, 256, 0, s>>>(w, chunk, first, count, zero_all ? 1 : 0, spin_limit, drop_signal);
+    launch_pdl(setup_kernel, blocks, 256, 0, s, w, chunk, first, count, zero_all ? 1 : 0, spin_limit, drop_signal);
     return cudaGetLastError();
 }
 
 cudaError_t launch_emit(const Work &w, int depth_buf, int tile_w, int tile_h, int num_sms, cudaStream_t s) {
     if (w.L.P == 0) return cudaSuccess;
     const unsigned *order = w.dval[depth_buf];
-    count_reduce_kernel<<<w.L.emit_blocks, kEmitThreads, 0, s>>>(w, order);
-    count_scan_kernel<<<1, 1024, 0, s>>>(w);
-    offsets_kernel<<<w.L.emit_blocks, kEmitThreads, 0, s>>>(w, order);
+    launch_pdl(count_reduce_kernel, w.L.emit_blocks, kEmitThreads, 0, s, w, order);
+    launch_pdl(count_scan_kernel, 1, 1024, 0, s, w);
+    launch_pdl(offsets_kernel, w.L.emit_blocks, kEmitThreads, 0, s, w, order);
     EmitSortArgs a;
     a.order = order;
     a.keys_out = w.tkey[1];
@@ -443,19 +450,19 @@ cudaError_t launch_emit(const Work &w, int depth_buf, int tile_w, int tile_h, in
     a.lw = __builtin_ctz(tile_w);
     a.lh = __builtin_ctz(tile_h);
     const unsigned grid = std::max(1u, std::min(w.L.chunk_cap, (unsigned)num_sms * 4u));
-    emit_sort_kernel<<<grid, kEmitThreads, 0, s>>>(w, a);
+    launch_pdl(emit_sort_kernel, grid, kEmitThreads, 0, s, w, a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ranges(const Work &w, int tile_buf, int num_sms, cudaStream_t s) {
-    ranges_kernel<<<num_sms * 8, 256, 0, s>>>(w, w.tkey[tile_buf]);
+    launch_pdl(ranges_kernel, num_sms * 8, 256, 0, s, w, w.tkey[tile_buf]);
     return cudaGetLastError();
 }
 
 cudaError_t launch_gather_debug(const Work &w, float *mean2d, float *conic, float *opacity, float *depth,
                                 int32_t *counts, int depth_buf, cudaStream_t s) {
     if (w.L.P == 0) return cudaSuccess;
-    gather_debug_kernel<<<(w.L.P + 255) / 256, 256, 0, s>>>(w, mean2d, conic, opacity, depth, counts, depth_buf);
+    launch_pdl(gather_debug_kernel, (w.L.P + 255) / 256, 256, 0, s, w, mean2d, conic, opacity, depth, counts, depth_buf);
     return cudaGetLastError();
 }
 

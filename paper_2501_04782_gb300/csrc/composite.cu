@@ -100,6 +100,7 @@ template <int TW, int TH, int DEPTH>
 __global__ void __launch_bounds__(TW *TH / 2) composite_fwd_kernel(Work w, const unsigned *ids, float bg0, float bg1,
                                                                    float bg2, float *image, float *final_T,
                                                                    int32_t *last_idx) {
+    pdl_prologue();
     constexpr int NT = TW * TH / 2;
     __shared__ float4 s_a[DEPTH + 1];
     __shared__ float4 s_b[DEPTH + 1];
@@ -210,6 +211,7 @@ template <int TW, int TH, int DEPTH>
 __global__ void __launch_bounds__(TW *TH / 2) composite_bwd_kernel(Work w, const unsigned *ids, float bg0, float bg1,
                                                                    float bg2, const float *final_T,
                                                                    const int32_t *last_idx, const float *dL) {
+    pdl_prologue();
     constexpr int NT = TW * TH / 2;
     __shared__ float4 s_a[DEPTH];
     __shared__ float4 s_b[DEPTH];
@@ -370,7 +372,7 @@ cudaError_t run_fwd(const Work &w, const unsigned *ids, float bg0, float bg1, fl
                     int32_t *idx, int num_sms, cudaStream_t s) {
     unsigned grid = min(w.L.tiles, (unsigned)(num_sms * occupancy_fwd<TW, TH, DEPTH>()));
     if (grid == 0) return cudaSuccess;
-    composite_fwd_kernel<TW, TH, DEPTH><<<grid, TW * TH / 2, 0, s>>>(w, ids, bg0, bg1, bg2, image, T, idx);
+    launch_pdl(composite_fwd_kernel<TW, TH, DEPTH>, grid, TW * TH / 2, 0, s, w, ids, bg0, bg1, bg2, image, T, idx);
     return cudaGetLastError();
 }
 
@@ -379,7 +381,7 @@ cudaError_t run_bwd(const Work &w, const unsigned *ids, float bg0, float bg1, fl
                     const int32_t *idx, const float *dL, int num_sms, cudaStream_t s) {
     unsigned grid = min(w.L.tiles, (unsigned)(num_sms * occupancy_bwd<TW, TH, DEPTH>()));
     if (grid == 0) return cudaSuccess;
-    composite_bwd_kernel<TW, TH, DEPTH><<<grid, TW * TH / 2, 0, s>>>(w, ids, bg0, bg1, bg2, T, idx, dL);
+    launch_pdl(composite_bwd_kernel<TW, TH, DEPTH>, grid, TW * TH / 2, 0, s, w, ids, bg0, bg1, bg2, T, idx, dL);
     return cudaGetLastError();
 }
 

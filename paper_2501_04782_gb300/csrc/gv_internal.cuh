@@ -20,6 +20,32 @@
 #include "gv.h"
 
 namespace gvk {
+// Programmatic dependent launch (every kernel of the library is launched with it): the
+// next kernel of the stream may be scheduled while this one runs, so launch latency and
+// the previous grid's tail overlap.  Every kernel starts with pdl_prologue(): it first
+// waits until the preceding grid has completed and its memory is visible (so nothing is
+// read or written early), then allows its own dependents to launch.
+__device__ __forceinline__ void pdl_prologue() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+// Launches kernel k with the programmatic-stream-serialisation attribute.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*k)(KArgs...), dim3 g, dim3 b, size_t smem, cudaStream_t st, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = g;
+    cfg.blockDim = b;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 
 // Rendering constants (Sec. 3.1 conventions; see include/gv.h).
 constexpr float kAlphaMin = 0.003921568859368563f;  // 1/255

@@ -14,6 +14,7 @@ namespace {
 
 __global__ void __launch_bounds__(256) l2_loss_kernel(const float *img, const float *tgt, long long n, float scale,
                                                       float *dL, float *loss) {
+    pdl_prologue();
     float acc = 0.f;
     const float two_s = 2.f * scale;
     long long stride = (long long)gridDim.x * blockDim.x;
@@ -149,6 +150,7 @@ struct AdanOp {
 
 template <class Op, bool VEC>
 __global__ void __launch_bounds__(256) optim_kernel(Op op, long long n) {
+    pdl_prologue();
     elementwise<Op, VEC>(op, n);
 }
 
@@ -159,6 +161,7 @@ bool aligned16(std::initializer_list<const void *> ptrs) {
 }
 
 __global__ void grad2d_debug_kernel(Work w, float *out) {
+    pdl_prologue();
     unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned P = w.L.P;
     if (p >= P) return;
@@ -180,7 +183,7 @@ int grid_for(long long n, int per_block = 256) {
 cudaError_t launch_l2_loss(const float *image, const float *target, long long n, float scale, float *dL, float *loss,
                            cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    l2_loss_kernel<<<grid_for(n), 256, 0, s>>>(image, target, n, scale, dL, loss);
+    launch_pdl(l2_loss_kernel, grid_for(n), 256, 0, s, image, target, n, scale, dL, loss);
     return cudaGetLastError();
 }
 
@@ -189,8 +192,8 @@ cudaError_t launch_adam(float *p, float *g, float *m, float *v, long long n, flo
     if (n <= 0) return cudaSuccess;
     AdamOp op{p, g, m, v, lr, b1, b2, 1.f - b1, 1.f - b2, eps, 1.f / bc1, 1.f / bc2, zero_grad};
     const int grid = grid_for((n + 3) / 4);
-    if (aligned16({p, g, m, v})) optim_kernel<AdamOp, true><<<grid, 256, 0, s>>>(op, n);
-    else optim_kernel<AdamOp, false><<<grid, 256, 0, s>>>(op, n);
+    if (aligned16({p, g, m, v})) launch_pdl(optim_kernel<AdamOp, true>, grid, 256, 0, s, op, n);
+    else launch_pdl(optim_kernel<AdamOp, false>, grid, 256, 0, s, op, n);
     return cudaGetLastError();
 }
 
@@ -210,14 +213,14 @@ cudaError_t launch_adan(float *p, float *g, float *m, float *v, float *nn, float
     AdanOp op{p, g, m, v, nn, g_prev, lr, b1, b2, b3, 1.f - b1, 1.f - b2, 1.f - b3, eps, 1.f / (1.f + wd * lr),
               c1, c2, c3, f1, f3, step == 1 ? 1 : 0, zero_grad};
     const int grid = grid_for((n + 3) / 4);
-    if (aligned16({p, g, m, v, nn, g_prev})) optim_kernel<AdanOp, true><<<grid, 256, 0, s>>>(op, n);
-    else optim_kernel<AdanOp, false><<<grid, 256, 0, s>>>(op, n);
+    if (aligned16({p, g, m, v, nn, g_prev})) launch_pdl(optim_kernel<AdanOp, true>, grid, 256, 0, s, op, n);
+    else launch_pdl(optim_kernel<AdanOp, false>, grid, 256, 0, s, op, n);
     return cudaGetLastError();
 }
 
 cudaError_t launch_grad2d_debug(const Work &w, float *out, cudaStream_t s) {
     if (w.L.P == 0) return cudaSuccess;
-    grad2d_debug_kernel<<<(w.L.P + 255) / 256, 256, 0, s>>>(w, out);
+    launch_pdl(grad2d_debug_kernel, (w.L.P + 255) / 256, 256, 0, s, w, out);
     return cudaGetLastError();
 }
 

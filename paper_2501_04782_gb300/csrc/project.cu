@@ -368,6 +368,7 @@ __device__ __forceinline__ bool ill_conditioned(const PairState<float> &st) {
 // Grid-stride over the pairs so each block flushes its counters once.
 template <bool SPLINE, bool SH>
 __global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, int lw, int lh, int tile_passes) {
+    pdl_prologue();
     __shared__ BinShared sb;
     bin_shared_init(sb);
     __syncthreads();
@@ -419,6 +420,7 @@ __global__ void __launch_bounds__(256) bin_from_screen_kernel(Work w, long long 
                                                               const float *tau, const float *depth,
                                                               const uint8_t *valid, int lw, int lh, int tile_passes,
                                                               int32_t *counts) {
+    pdl_prologue();
     __shared__ BinShared sb;
     __shared__ unsigned s_live[256];
     bin_shared_init(sb);
@@ -771,6 +773,7 @@ __device__ __forceinline__ void sh_accumulate(const float *Y, int K, float4 g1, 
 // time-parameterised form.
 template <bool CAM, bool SPLINE, bool SH>
 __global__ void __launch_bounds__(128) project_bwd_pairs_kernel(Work w, GaussPtrs g, GradPtrs gr, int atomic) {
+    pdl_prologue();
     __shared__ float s_cam[CAM ? kCamSmemFrames : 1][kCamGrad];
     const int F = (int)w.L.F;
     if (CAM) cam_block_init(s_cam, F);
@@ -816,6 +819,7 @@ __global__ void __launch_bounds__(128) project_bwd_pairs_kernel(Work w, GaussPtr
 // SPLINE: the time-parameterised form (g.n_ctrl > 0).
 template <bool CAM, bool SPLINE, bool SH>
 __global__ void __launch_bounds__(128, SH ? 3 : 1) project_bwd_shared_kernel(Work w, GaussPtrs g, GradPtrs gr) {
+    pdl_prologue();
     __shared__ float s_cam[CAM ? kCamSmemFrames : 1][kCamGrad];
     // each thread's coefficient-gradient sums over the frames, a column of its own
     __shared__ float s_acc_sh[SH ? 3 * kShMax : 1][SH ? 128 : 1];
@@ -881,6 +885,7 @@ __global__ void __launch_bounds__(128, SH ? 3 : 1) project_bwd_shared_kernel(Wor
 // pass runs concurrently.  The list lives until the next forward's setup clears it, so a
 // backward can be repeated.
 __global__ void __launch_bounds__(128) project_bwd_fp64_kernel(Work w, GaussPtrs g, GradPtrs gr) {
+    pdl_prologue();
     const unsigned n = min(w.hdr->fp64_count, w.L.P);
     for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const unsigned p = min(w.fp64_list[i], w.L.P - 1u);
@@ -921,10 +926,10 @@ cudaError_t launch_project_fwd(const Work &w, const GaussPtrs &g, int tile_w, in
     unsigned blocks = std::min((w.L.P + 255u) / 256u, (unsigned)num_sms * 8u);
     const int tp = tile_sort_passes(w);
     const bool spline = g.n_ctrl > 0, sh = g.sh_degree > 0;
-    if (spline && sh) project_fwd_kernel<true, true><<<blocks, 256, 0, s>>>(w, g, lw, lh, tp);
-    else if (spline) project_fwd_kernel<true, false><<<blocks, 256, 0, s>>>(w, g, lw, lh, tp);
-    else if (sh) project_fwd_kernel<false, true><<<blocks, 256, 0, s>>>(w, g, lw, lh, tp);
-    else project_fwd_kernel<false, false><<<blocks, 256, 0, s>>>(w, g, lw, lh, tp);
+    if (spline && sh) launch_pdl(project_fwd_kernel<true, true>, blocks, 256, 0, s, w, g, lw, lh, tp);
+    else if (spline) launch_pdl(project_fwd_kernel<true, false>, blocks, 256, 0, s, w, g, lw, lh, tp);
+    else if (sh) launch_pdl(project_fwd_kernel<false, true>, blocks, 256, 0, s, w, g, lw, lh, tp);
+    else launch_pdl(project_fwd_kernel<false, false>, blocks, 256, 0, s, w, g, lw, lh, tp);
     return cudaGetLastError();
 }
 
@@ -935,7 +940,7 @@ cudaError_t launch_bin_from_screen(const Work &w, long long n, const float *u, c
     if (n == 0) return cudaSuccess;
     int lw = __builtin_ctz(tile_w), lh = __builtin_ctz(tile_h);
     unsigned blocks = std::min((unsigned)((n + 255) / 256), (unsigned)num_sms * 8u);
-    bin_from_screen_kernel<<<blocks, 256, 0, s>>>(w, n, u, v, sxx, sxy, syy, tau, depth, valid, lw, lh,
+    launch_pdl(bin_from_screen_kernel, blocks, 256, 0, s, w, n, u, v, sxx, sxy, syy, tau, depth, valid, lw, lh,
                                                    tile_sort_passes(w), counts);
     return cudaGetLastError();
 }
@@ -963,15 +968,15 @@ cudaError_t launch_project_bwd(const Work &w, const GaussPtrs &g, const GradPtrs
         unsigned n = w.L.P / w.L.F;
         unsigned blocks = std::min((n + 127) / 128, (unsigned)num_sms * 16u);
         dispatch_bwd(gr.cam != nullptr, g.n_ctrl > 0, g.sh_degree > 0, [&](auto C, auto S, auto H) {
-            project_bwd_shared_kernel<decltype(C)::value, decltype(S)::value, decltype(H)::value>
-                <<<blocks, 128, 0, s>>>(w, g, gr);
+            launch_pdl(project_bwd_shared_kernel<decltype(C)::value, decltype(S)::value, decltype(H)::value>, blocks,
+                       128, 0, s, w, g, gr);
         });
     } else {
         unsigned blocks = std::min((w.L.P + 127) / 128, (unsigned)num_sms * 16u);
         const int at = mode == 2 ? 1 : 0;
         dispatch_bwd(gr.cam != nullptr, g.n_ctrl > 0, g.sh_degree > 0, [&](auto C, auto S, auto H) {
-            project_bwd_pairs_kernel<decltype(C)::value, decltype(S)::value, decltype(H)::value>
-                <<<blocks, 128, 0, s>>>(w, g, gr, at);
+            launch_pdl(project_bwd_pairs_kernel<decltype(C)::value, decltype(S)::value, decltype(H)::value>, blocks,
+                       128, 0, s, w, g, gr, at);
         });
     }
     return cudaGetLastError();
@@ -980,7 +985,7 @@ cudaError_t launch_project_bwd(const Work &w, const GaussPtrs &g, const GradPtrs
 cudaError_t launch_project_bwd_fp64(const Work &w, const GaussPtrs &g, const GradPtrs &gr, int num_sms,
                                     cudaStream_t s) {
     if (w.L.P == 0) return cudaSuccess;
-    project_bwd_fp64_kernel<<<num_sms, 128, 0, s>>>(w, g, gr);
+    launch_pdl(project_bwd_fp64_kernel, num_sms, 128, 0, s, w, g, gr);
     return cudaGetLastError();
 }
 

@@ -24,6 +24,7 @@ namespace {
 // passes == 0: the histograms were counted by the producer of the keys; only clear.
 __global__ void __launch_bounds__(256) sort_hist_kernel(const unsigned *keys, const unsigned *n_dev, unsigned n_cap,
                                                         int passes, unsigned *hist, unsigned *look0) {
+    pdl_prologue();
     __shared__ unsigned s_h[4][kRadix];
     for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0u;
     __syncthreads();
@@ -61,6 +62,7 @@ struct PassArgs {
 
 template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads, 4) sort_pass_kernel(PassArgs a) {
+    pdl_prologue();
     constexpr int TILE = kSortThreads * ITEMS;
     __shared__ unsigned s_keys[TILE];
     __shared__ unsigned s_vals[TILE];
@@ -181,7 +183,7 @@ cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2
     cudaError_t e;
     if (!prepared && first_pass == 0) {
         int hist_blocks = (int)std::min<unsigned>((n_cap + 255) / 256, (unsigned)num_sms * 4u);
-        sort_hist_kernel<<<hist_blocks, 256, 0, s>>>(keys[0], n_dev, n_cap, passes, hist, look[0]);
+        launch_pdl(sort_hist_kernel, hist_blocks, 256, 0, s, keys[0], n_dev, n_cap, passes, hist, look[0]);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -204,9 +206,9 @@ cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2
         a.ctr = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(w.hdr) + offsetof(DevHeader, sort_ctr)) +
                 ctr_slot + ps;
         a.hdr = w.hdr;
-        if (items == 8) sort_pass_kernel<8><<<grid, kSortThreads, 0, s>>>(a);
-        else if (items == 4) sort_pass_kernel<4><<<grid, kSortThreads, 0, s>>>(a);
-        else sort_pass_kernel<12><<<grid, kSortThreads, 0, s>>>(a);
+        if (items == 8) launch_pdl(sort_pass_kernel<8>, grid, kSortThreads, 0, s, a);
+        else if (items == 4) launch_pdl(sort_pass_kernel<4>, grid, kSortThreads, 0, s, a);
+        else launch_pdl(sort_pass_kernel<12>, grid, kSortThreads, 0, s, a);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         cur ^= 1;
