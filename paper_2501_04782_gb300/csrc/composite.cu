@@ -207,21 +207,36 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_fwd_kernel(Work w, const
     }
 }
 
-template <int TW, int TH, int DEPTH>
-__global__ void __launch_bounds__(TW *TH / 2) composite_bwd_kernel(Work w, const unsigned *ids, float bg0, float bg1,
-                                                                   float bg2, const float *final_T,
-                                                                   const int32_t *last_idx, const float *dL) {
+// Thread -> pixels of the backward: PX pixels per lane, all in one column, so the
+// Gaussian's dx and the terms that depend on it alone are shared.  A warp owns a block
+// WBW pixels wide: lane l takes column l % WBW and rows l / WBW + RS k (k < PX), RS = 32 /
+// WBW.  Four pixels per lane halve the warp reductions and atomics per pixel against two.
+template <int TW, int TH, int PX>
+struct BwdMap {
+    static constexpr int WBW = (PX == 4 && TH < 16) ? 16 : 8;
+    static constexpr int RS = 32 / WBW;
+    static constexpr int WBH = RS * PX;
+    static constexpr int WX = TW / WBW;
+    static constexpr int NT = TW * TH / PX;
+    static_assert(TW % WBW == 0 && TH % WBH == 0, "tile not covered by whole warps");
+};
+
+template <int TW, int TH, int DEPTH, int PX>
+__global__ void __launch_bounds__(TW *TH / PX) composite_bwd_kernel(Work w, const unsigned *ids, float bg0, float bg1,
+                                                                    float bg2, const float *final_T,
+                                                                    const int32_t *last_idx, const float *dL) {
     pdl_prologue();
-    constexpr int NT = TW * TH / 2;
+    using M = BwdMap<TW, TH, PX>;
+    constexpr int NT = M::NT, NP = PX / 2;
     __shared__ float4 s_a[DEPTH];
     __shared__ float4 s_b[DEPTH];
     __shared__ float s_c[DEPTH];
     __shared__ unsigned s_p[DEPTH];
     __shared__ unsigned s_tile;
     __shared__ int s_max;
-    int lx, ly;
-    pixels_of_thread<TW, TH>(threadIdx.x, lx, ly);
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const int lx = (wq % M::WX) * M::WBW + lane % M::WBW;
+    const int ly = (wq / M::WX) * M::WBH + lane / M::WBW;
     const unsigned ntiles = w.L.tiles;
     const int F = (int)w.L.F;
     const bool failed = w.hdr->err != 0u;  // lists incomplete: every tile renders empty
@@ -237,38 +252,47 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_bwd_kernel(Work w, const
         const int W = fr.W, H = fr.H;
         const unsigned lt = tile - fr.tile_offset;
         const int x = (int)(lt % fr.tiles_x) * TW + lx;
-        const int y0 = (int)(lt / fr.tiles_x) * TH + ly, y1 = y0 + 4;
+        const int ybase = (int)(lt / fr.tiles_x) * TH + ly;
         const float px = (float)x + 0.5f;
-        const float2 npy = make_float2(-((float)y0 + 0.5f), -((float)y1 + 0.5f));
         const uint2 rg = failed ? make_uint2(0u, 0u) : w.ranges[tile];
-        // per-pixel replay state, packed over the thread's two pixels
-        float2 T = make_float2(1.f, 1.f), g0 = make_float2(0.f, 0.f), g1 = g0, g2 = g0;
-        int last0 = -1, last1 = -1;
         const size_t plane = (size_t)W * H;
-        if (x < W && y0 < H) {
-            const size_t pix = (size_t)fr.pixel_offset + (size_t)y0 * W + x;
-            const size_t img = 3 * (size_t)fr.pixel_offset + (size_t)y0 * W + x;
-            T.x = final_T[pix];
-            last0 = min(last_idx[pix], (int)rg.y - 1);  // from the forward: in [rg.x, rg.y)
-            g0.x = dL[img];
-            g1.x = dL[img + plane];
-            g2.x = dL[img + 2 * plane];
-        }
-        if (x < W && y1 < H) {
-            const size_t pix = (size_t)fr.pixel_offset + (size_t)y1 * W + x;
-            const size_t img = 3 * (size_t)fr.pixel_offset + (size_t)y1 * W + x;
-            T.y = final_T[pix];
-            last1 = min(last_idx[pix], (int)rg.y - 1);
-            g0.y = dL[img];
-            g1.y = dL[img + plane];
-            g2.y = dL[img + 2 * plane];
+        // per-pixel replay state, packed over pixel pairs: pixel 2k + h is row ybase + RS (2k + h)
+        float2 npy[NP], T[NP], g0[NP], g1[NP], g2[NP], nS0[NP], nS1[NP], nS2[NP];
+        int last[PX];
+        unsigned n_comp = 0, n_eval = 0;
+        int lmax = -1;
+#pragma unroll
+        for (int q = 0; q < PX; q++) {
+            const int y = ybase + M::RS * q;
+            float Tq = 1.f, d0 = 0.f, d1 = 0.f, d2 = 0.f;
+            int lq = -1;
+            if (x < W && y < H) {
+                const size_t pix = (size_t)fr.pixel_offset + (size_t)y * W + x;
+                const size_t img = 3 * (size_t)fr.pixel_offset + (size_t)y * W + x;
+                Tq = final_T[pix];
+                lq = min(last_idx[pix], (int)rg.y - 1);  // from the forward: in [rg.x, rg.y)
+                d0 = dL[img];
+                d1 = dL[img + plane];
+                d2 = dL[img + 2 * plane];
+            }
+            last[q] = lq;
+            lmax = max(lmax, lq);
+            if (lq >= (int)rg.x) n_eval += (unsigned)(lq + 1 - (int)rg.x);
+            const float ny = -((float)y + 0.5f);
+            if (q & 1) {
+                npy[q >> 1].y = ny; T[q >> 1].y = Tq; g0[q >> 1].y = d0; g1[q >> 1].y = d1; g2[q >> 1].y = d2;
+            } else {
+                npy[q >> 1].x = ny; T[q >> 1].x = Tq; g0[q >> 1].x = d0; g1[q >> 1].x = d1; g2[q >> 1].x = d2;
+            }
         }
         // colour composited behind the current Gaussian, negated: nS = -(sum c w + T bg)
-        float2 nS0 = __fmul2_rn(T, dup2(-bg0)), nS1 = __fmul2_rn(T, dup2(-bg1)), nS2 = __fmul2_rn(T, dup2(-bg2));
-        unsigned n_comp = 0, n_eval = 0;
-        if (last0 >= (int)rg.x) n_eval += (unsigned)(last0 + 1 - (int)rg.x);
-        if (last1 >= (int)rg.x) n_eval += (unsigned)(last1 + 1 - (int)rg.x);
-        const int wmax = __reduce_max_sync(0xffffffffu, max(last0, last1));
+#pragma unroll
+        for (int k = 0; k < NP; k++) {
+            nS0[k] = __fmul2_rn(T[k], dup2(-bg0));
+            nS1[k] = __fmul2_rn(T[k], dup2(-bg1));
+            nS2[k] = __fmul2_rn(T[k], dup2(-bg2));
+        }
+        const int wmax = __reduce_max_sync(0xffffffffu, lmax);
         if (lane == 0) atomicMax(&s_max, wmax);
         __syncthreads();
         const int end = min(s_max + 1, (int)rg.y);
@@ -288,58 +312,76 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_bwd_kernel(Work w, const
             for (int j = jtop; j >= 0; j--) {
                 const float4 f0 = s_a[j], f1 = s_b[j];
                 const int pos = bstart + j;
-                float dx;
-                float2 dy;
-                const float2 e = splat_exponent2(f0, f1, px, npy, dx, dy);
-                const float r0 = ex2_approx(e.x), r1 = ex2_approx(e.y);  // o exp(-power), unclamped
-                float a0 = fminf(r0, kAlphaMax), a1 = fminf(r1, kAlphaMax);
-                const bool v0 = pos <= last0 && a0 >= kAlphaMin;
-                const bool v1 = pos <= last1 && a1 >= kAlphaMin;
-                const unsigned act = __ballot_sync(0xffffffffu, v0 || v1);
+                // exponents e = a' dx^2 + b' dx dy + c' dy^2 + log2 o, rounded exactly as the
+                // forward's (the replay divides its transmittance back)
+                const float dx = __fsub_rn(f0.x, px);
+                const float s0 = __fmaf_rn(__fmul_rn(f0.z, dx), dx, f1.y);
+                const float bdx = __fmul_rn(f0.w, dx);
+                float2 dy[NP], r[NP];
+                bool v[PX];
+                bool any = false;
+#pragma unroll
+                for (int k = 0; k < NP; k++) {
+                    dy[k] = __fadd2_rn(dup2(f0.y), npy[k]);
+                    const float2 t = __ffma2_rn(dup2(bdx), dy[k], dup2(s0));
+                    const float2 e = __ffma2_rn(__fmul2_rn(dup2(f1.x), dy[k]), dy[k], t);
+                    r[k] = make_float2(ex2_approx(e.x), ex2_approx(e.y));  // o exp(-power), unclamped
+                    v[2 * k] = pos <= last[2 * k] && fminf(r[k].x, kAlphaMax) >= kAlphaMin;
+                    v[2 * k + 1] = pos <= last[2 * k + 1] && fminf(r[k].y, kAlphaMax) >= kAlphaMin;
+                    any = any || v[2 * k] || v[2 * k + 1];
+                }
+                const unsigned act = __ballot_sync(0xffffffffu, any);
                 if (!act) continue;
-                n_comp += (unsigned)v0 + (unsigned)v1;
-                a0 = v0 ? a0 : 0.f;
-                a1 = v1 ? a1 : 0.f;
-                const float2 al = make_float2(a0, a1);
-                const float2 ra = make_float2(rcp_approx(1.f - a0), rcp_approx(1.f - a1));
-                float2 Tin = __fmul2_rn(T, ra);
-                Tin.x = v0 ? Tin.x : T.x;
-                Tin.y = v1 ? Tin.y : T.y;
-                const float2 wg = __fmul2_rn(al, Tin);
                 const float cb = s_c[j];
-                // dL/dalpha = sum_ch g_ch (c_ch Tin - S_ch / (1 - alpha))
-                const float2 x0 = __ffma2_rn(nS0, ra, __fmul2_rn(dup2(f1.z), Tin));
-                const float2 x1 = __ffma2_rn(nS1, ra, __fmul2_rn(dup2(f1.w), Tin));
-                const float2 x2 = __ffma2_rn(nS2, ra, __fmul2_rn(dup2(cb), Tin));
-                const float2 dal = __ffma2_rn(g2, x2, __ffma2_rn(g1, x1, __fmul2_rn(g0, x0)));
-                nS0 = __ffma2_rn(dup2(-f1.z), wg, nS0);
-                nS1 = __ffma2_rn(dup2(-f1.w), wg, nS1);
-                nS2 = __ffma2_rn(dup2(-cb), wg, nS2);
-                T = Tin;
-                // dL/de for the exponent e (alpha = 2^e unless clamped at 0.99)
-                const float2 k = make_float2((v0 && r0 < kAlphaMax) ? r0 * kLn2 : 0.f,
-                                             (v1 && r1 < kAlphaMax) ? r1 * kLn2 : 0.f);
-                const float2 de = __fmul2_rn(dal, k);
-                const float2 dxy = __fmul2_rn(dup2(dx), dy);
-                const float2 gu = __ffma2_rn(dup2(f0.w), dy, dup2(2.f * f0.z * dx));  // de/du = 2a'dx + b'dy
-                const float2 gv = __ffma2_rn(dup2(2.f * f1.x), dy, dup2(f0.w * dx));  // de/dv = b'dx + 2c'dy
-                const float2 cu = __fmul2_rn(de, gu), cv = __fmul2_rn(de, gv);
-                const float2 ca = __fmul2_rn(de, dup2(dx * dx)), cbb = __fmul2_rn(de, dxy);
-                const float2 cc = __fmul2_rn(de, __fmul2_rn(dy, dy));
-                const float2 dr = __fmul2_rn(wg, g0), dg = __fmul2_rn(wg, g1), db = __fmul2_rn(wg, g2);
-                float v[9] = {cu.x + cu.y, cv.x + cv.y, ca.x + ca.y, cbb.x + cbb.y, cc.x + cc.y,
-                              de.x + de.y, dr.x + dr.y, dg.x + dg.y, db.x + db.y};
+                const float gu0 = 2.f * f0.z * dx, gv0 = f0.w * dx, c2 = 2.f * f1.x, dxx = dx * dx;
+                float vs[9];
+#pragma unroll
+                for (int k = 0; k < NP; k++) {
+                    const bool va = v[2 * k], vb = v[2 * k + 1];
+                    n_comp += (unsigned)va + (unsigned)vb;
+                    const float a0 = va ? fminf(r[k].x, kAlphaMax) : 0.f, a1 = vb ? fminf(r[k].y, kAlphaMax) : 0.f;
+                    const float2 al = make_float2(a0, a1);
+                    const float2 ra = make_float2(rcp_approx(1.f - a0), rcp_approx(1.f - a1));
+                    float2 Tin = __fmul2_rn(T[k], ra);
+                    Tin.x = va ? Tin.x : T[k].x;
+                    Tin.y = vb ? Tin.y : T[k].y;
+                    const float2 wg = __fmul2_rn(al, Tin);
+                    // dL/dalpha = sum_ch g_ch (c_ch Tin - S_ch / (1 - alpha))
+                    const float2 x0 = __ffma2_rn(nS0[k], ra, __fmul2_rn(dup2(f1.z), Tin));
+                    const float2 x1 = __ffma2_rn(nS1[k], ra, __fmul2_rn(dup2(f1.w), Tin));
+                    const float2 x2 = __ffma2_rn(nS2[k], ra, __fmul2_rn(dup2(cb), Tin));
+                    const float2 dal = __ffma2_rn(g2[k], x2, __ffma2_rn(g1[k], x1, __fmul2_rn(g0[k], x0)));
+                    nS0[k] = __ffma2_rn(dup2(-f1.z), wg, nS0[k]);
+                    nS1[k] = __ffma2_rn(dup2(-f1.w), wg, nS1[k]);
+                    nS2[k] = __ffma2_rn(dup2(-cb), wg, nS2[k]);
+                    T[k] = Tin;
+                    // dL/de for the exponent e (alpha = 2^e unless clamped at 0.99)
+                    const float2 kk = make_float2((va && r[k].x < kAlphaMax) ? r[k].x * kLn2 : 0.f,
+                                                  (vb && r[k].y < kAlphaMax) ? r[k].y * kLn2 : 0.f);
+                    const float2 de = __fmul2_rn(dal, kk);
+                    const float2 dxy = __fmul2_rn(dup2(dx), dy[k]);
+                    const float2 gu = __ffma2_rn(dup2(f0.w), dy[k], dup2(gu0));  // de/du = 2a'dx + b'dy
+                    const float2 gv = __ffma2_rn(dup2(c2), dy[k], dup2(gv0));    // de/dv = b'dx + 2c'dy
+                    const float2 cu = __fmul2_rn(de, gu), cv = __fmul2_rn(de, gv);
+                    const float2 ca = __fmul2_rn(de, dup2(dxx)), cbb = __fmul2_rn(de, dxy);
+                    const float2 cc = __fmul2_rn(de, __fmul2_rn(dy[k], dy[k]));
+                    const float2 dr = __fmul2_rn(wg, g0[k]), dg = __fmul2_rn(wg, g1[k]), db = __fmul2_rn(wg, g2[k]);
+                    const float t9[9] = {cu.x + cu.y, cv.x + cv.y, ca.x + ca.y, cbb.x + cbb.y, cc.x + cc.y,
+                                         de.x + de.y, dr.x + dr.y, dg.x + dg.y, db.x + db.y};
+#pragma unroll
+                    for (int q = 0; q < 9; q++) vs[q] = k ? vs[q] + t9[q] : t9[q];
+                }
                 if (__popc(act) <= kSparseLanes) {
-                    if (v0 || v1) {
+                    if (any) {
                         const unsigned p = s_p[j];
                         float *a = &w.g0[p].x, *b = &w.g1[p].x;
-                        atomicAdd(a, v[0]); atomicAdd(a + 1, v[1]); atomicAdd(a + 2, v[2]); atomicAdd(a + 3, v[3]);
-                        atomicAdd(b, v[4]); atomicAdd(b + 1, v[5]); atomicAdd(b + 2, v[6]); atomicAdd(b + 3, v[7]);
-                        atomicAdd(w.g2 + p, v[8]);
+                        atomicAdd(a, vs[0]); atomicAdd(a + 1, vs[1]); atomicAdd(a + 2, vs[2]); atomicAdd(a + 3, vs[3]);
+                        atomicAdd(b, vs[4]); atomicAdd(b + 1, vs[5]); atomicAdd(b + 2, vs[6]); atomicAdd(b + 3, vs[7]);
+                        atomicAdd(w.g2 + p, vs[8]);
                     }
                 } else {
                     int slot;
-                    const float sum = warp_reduce9(v, lane, slot);
+                    const float sum = warp_reduce9(vs, lane, slot);
                     if (slot < 9 && !(lane & 1)) {
                         const unsigned p = s_p[j];
                         float *dst = slot < 4 ? &w.g0[p].x + slot : (slot < 8 ? &w.g1[p].x + (slot - 4) : w.g2 + p);
@@ -353,6 +395,11 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_bwd_kernel(Work w, const
     }
 }
 
+// Pixels per lane of the backward for a tile shape: four where a warp still covers whole
+// rows of the tile (16-wide tiles), else two.
+template <int TW, int TH>
+constexpr int bwd_px() { return TW >= 16 ? 4 : 2; }
+
 template <int TW, int TH, int DEPTH>
 int occupancy_fwd() {
     static int blocks = 0;
@@ -362,8 +409,10 @@ int occupancy_fwd() {
 
 template <int TW, int TH, int DEPTH>
 int occupancy_bwd() {
+    constexpr int PX = bwd_px<TW, TH>();
     static int blocks = 0;
-    if (!blocks) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, composite_bwd_kernel<TW, TH, DEPTH>, TW * TH / 2, 0);
+    if (!blocks)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, composite_bwd_kernel<TW, TH, DEPTH, PX>, TW * TH / PX, 0);
     return blocks > 0 ? blocks : 1;
 }
 
@@ -381,7 +430,8 @@ cudaError_t run_bwd(const Work &w, const unsigned *ids, float bg0, float bg1, fl
                     const int32_t *idx, const float *dL, int num_sms, cudaStream_t s) {
     unsigned grid = min(w.L.tiles, (unsigned)(num_sms * occupancy_bwd<TW, TH, DEPTH>()));
     if (grid == 0) return cudaSuccess;
-    launch_pdl(composite_bwd_kernel<TW, TH, DEPTH>, grid, TW * TH / 2, 0, s, w, ids, bg0, bg1, bg2, T, idx, dL);
+    constexpr int PX = bwd_px<TW, TH>();
+    launch_pdl(composite_bwd_kernel<TW, TH, DEPTH, PX>, grid, TW * TH / PX, 0, s, w, ids, bg0, bg1, bg2, T, idx, dL);
     return cudaGetLastError();
 }
 
