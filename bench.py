@@ -68,6 +68,8 @@ def parse_args():
                          "clip1080p: --frames frames of the 1920x1080 / 1M-Gaussian training clip, batched")
     ap.add_argument("--frames", type=int, default=2, help="frames per step for --workload clip1080p")
     ap.add_argument("--no-autotune", action="store_true", help="keep 16x16 tiles, stage depth 128 (profiling runs)")
+    ap.add_argument("--tile-config", default=None, help="WxHxDEPTH, e.g. 16x8x64: this launch configuration "
+                    "instead of the autotuner's (profiling runs)")
     return ap.parse_args()
 
 
@@ -236,7 +238,10 @@ def run_gv(args):
         ctx.render_bwd(params, frames, ws, T, idx, dL, grads)
 
     # ---- autotune tile shape and stage depth on this workload (untimed) ----------------
-    if args.no_autotune:
+    if args.tile_config:
+        tw, th, dp = (int(v) for v in args.tile_config.lower().split("x"))
+        ctx.set_options(tile=(tw, th), stage_depth=dp)
+    elif args.no_autotune:
         ctx.set_options(tile=(16, 16), stage_depth=128)
     else:
         best, tune_ms = ctx.autotune(params, frames, ws, image, T, idx, dL, grads, reps=3)
@@ -331,12 +336,15 @@ def run_gv(args):
     for s in ("setup", "ranges"):
         stages[s] = {"ms": round(mean_stage[s], 4)}
     d = stages.get(dom, {"bound": "alu", "achieved": None, "unit": "Gop/s", "frac": None})
-    # DRAM bytes per launch (read + write) of the dominant kernel, from one ncu capture of the
-    # kernel as it is (the first timed backward of this 960x540 workload); unknown otherwise
-    ncu_traffic = {"composite_bwd": 15.475968e6}
+    # DRAM bytes per launch (read + write) of the dominant kernel in this launch configuration,
+    # from one ncu capture of the kernel as it is (the first timed backward of this 960x540
+    # workload); unknown (null) for other kernels or configurations
+    o = ctx.options
+    cfg_key = (dom, f"{o.tile_w}x{o.tile_h}", o.stage_depth)
+    ncu_traffic = {("composite_bwd", "16x16", 128): 15.465984e6, ("composite_bwd", "16x8", 64): 16.432128e6}
     roofline = {"kernel": dom, "bound": d.get("bound"), "achieved": d.get("achieved"),
                 "peak": round(alu_peak_gops, 1) if d.get("bound") == "alu" else hbm_peak, "unit": d.get("unit"),
-                "frac": d.get("frac"), "traffic": ncu_traffic.get(dom),
+                "frac": d.get("frac"), "traffic": ncu_traffic.get(cfg_key),
                 "peak_source": ("152 SMs x 128 FP32 lanes x median SM clock sampled during the timed region"
                                 if d.get("bound") == "alu" else "MEASURED_PEAKS.json hbm_gbs (of measured)")}
 
