@@ -1,9 +1,9 @@
 // sort.cu -- stable LSD radix sort of (32-bit key, 32-bit value) pairs, 8 bits per pass.
 //
-// One pass is a single "onesweep" kernel: each block takes the next 3072-key tile from an
-// atomic counter, ranks its keys stably per digit (warp match + per-warp histograms),
-// publishes its per-digit counts, obtains the exclusive prefix of all earlier tiles by
-// decoupled look-back, and scatters.  The per-digit global offsets come from one
+// One pass is a single "onesweep" kernel: each block takes the next tile (256 x 4, 8 or 12
+// keys by the key count) from an atomic counter, ranks its keys stably per digit (warp
+// match or bit ballots + per-warp histograms), publishes its per-digit counts, obtains the
+// exclusive prefix of all earlier tiles by decoupled look-back, and scatters.  The per-digit global offsets come from one
 // histogram kernel that counts every pass's digits up front.  Keys and values are read
 // once and written once per pass (the HBM roofline of the sort).
 //
@@ -60,7 +60,7 @@ struct PassArgs {
     DevHeader *hdr;
 };
 
-template <int ITEMS>
+template <int ITEMS, bool BALLOT>
 __global__ void __launch_bounds__(kSortThreads, 4) sort_pass_kernel(PassArgs a) {
     pdl_prologue();
     constexpr int TILE = kSortThreads * ITEMS;
@@ -103,11 +103,24 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_pass_kernel(PassArgs a) 
                 v[i] = 0u;
             }
         }
-        // stable rank inside the warp: by item, then by lane
+        // stable rank inside the warp: by item, then by lane.  The lanes holding the same
+        // digit come from a warp match or (BALLOT, faster on sorts of many millions of keys)
+        // from eight ballots, one per digit bit.
 #pragma unroll
         for (int i = 0; i < ITEMS; i++) {
             unsigned d = (k[i] >> a.shift) & 255u;
-            unsigned peers = __match_any_sync(0xffffffffu, d);
+            unsigned peers;
+            if (BALLOT) {
+                peers = 0xffffffffu;
+#pragma unroll
+                for (int b = 0; b < 8; b++) {
+                    const bool bit = (d >> b) & 1u;
+                    const unsigned m = __ballot_sync(0xffffffffu, bit);
+                    peers &= bit ? m : ~m;
+                }
+            } else {
+                peers = __match_any_sync(0xffffffffu, d);
+            }
             unsigned before = s_whist[wid][d];
             r[i] = before + __popc(peers & lanemask_lt());
             __syncwarp();
@@ -163,6 +176,10 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_pass_kernel(PassArgs a) 
 
 int sort_passes(int bits) { return bits <= 0 ? 0 : (bits + 7) / 8; }
 
+// Key capacity from which the passes rank by ballots (measured: 15 % faster on 34M keys,
+// slower on 1M).
+constexpr unsigned kSortBallotN = 1u << 22;
+
 // Sorts keys[0]/vals[0] by their low `bits` bits.  *result_buf receives the buffer index
 // (0 or 1) that holds the sorted output.  hist_slot selects 4 histogram rows of the
 // workspace (0 or 4), ctr_slot 4 tile counters (both zero on entry: the setup kernel
@@ -206,9 +223,10 @@ cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2
         a.ctr = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(w.hdr) + offsetof(DevHeader, sort_ctr)) +
                 ctr_slot + ps;
         a.hdr = w.hdr;
-        if (items == 8) launch_pdl(sort_pass_kernel<8>, grid, kSortThreads, 0, s, a);
-        else if (items == 4) launch_pdl(sort_pass_kernel<4>, grid, kSortThreads, 0, s, a);
-        else launch_pdl(sort_pass_kernel<12>, grid, kSortThreads, 0, s, a);
+        if (items == 8) launch_pdl(sort_pass_kernel<8, false>, grid, kSortThreads, 0, s, a);
+        else if (items == 4) launch_pdl(sort_pass_kernel<4, false>, grid, kSortThreads, 0, s, a);
+        else if (n_cap < kSortBallotN) launch_pdl(sort_pass_kernel<12, false>, grid, kSortThreads, 0, s, a);
+        else launch_pdl(sort_pass_kernel<12, true>, grid, kSortThreads, 0, s, a);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         cur ^= 1;
