@@ -817,8 +817,10 @@ __global__ void __launch_bounds__(128) project_bwd_pairs_kernel(Work w, GaussPtr
 
 // mode 1: one shared Gaussian set; one thread per Gaussian sums over all frames (grid-stride).
 // SPLINE: the time-parameterised form (g.n_ctrl > 0).
+// The SH variants cap their registers at three blocks per SM; the others take no minimum
+// (a minimum of one block made the compiler's code 30 % slower on 1M-Gaussian sets).
 template <bool CAM, bool SPLINE, bool SH>
-__global__ void __launch_bounds__(128, SH ? 3 : 1) project_bwd_shared_kernel(Work w, GaussPtrs g, GradPtrs gr) {
+__global__ void __launch_bounds__(128, SH ? 3 : 0) project_bwd_shared_kernel(Work w, GaussPtrs g, GradPtrs gr) {
     pdl_prologue();
     __shared__ float s_cam[CAM ? kCamSmemFrames : 1][kCamGrad];
     // each thread's coefficient-gradient sums over the frames, a column of its own
