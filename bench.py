@@ -592,7 +592,6 @@ def run_training(torch, gv, synth, dev, steps, hbm_peak, alu_peak_gops):
     w = synth.workload_training()
     cams = [c for c, _, _ in w["frames"]]
     N = w["gaussians"]["opacity_logit"].shape[-1]
-    gctx = gv.Context((16, 16), 128)
     gt = {k: torch.from_numpy(v).to(dev) for k, v in w["gt"].items()}
     targets = torch.empty(F, 3 * TW * TH, device=dev)
     for c0 in range(0, F, 10):
@@ -602,7 +601,11 @@ def run_training(torch, gv, synth, dev, steps, hbm_peak, alu_peak_gops):
         targets[c0:c0 + len(fr)] = img.view(len(fr), -1)
     del gt
     params = {k: torch.from_numpy(v).to(dev) for k, v in w["gaussians"].items()}
-    tr = render.Trainer(params, cams, targets, batch=B, lr=0.01, seed=7, optimizer="adan", lr_decay=0.99995)
+    tr = render.Trainer(params, cams, targets, batch=B, lr=0.01, seed=7, optimizer="adan", lr_decay=0.99995,
+                        tile="auto")
+    to = tr.ctx.options
+    tile, depth = (to.tile_w, to.tile_h), to.stage_depth
+    gctx = gv.Context(tile, depth)
 
     def clip_psnr(ids):
         fr, total = gv.layout_frames([(cams[i], 0, N) for i in ids])
@@ -653,7 +656,7 @@ def run_training(torch, gv, synth, dev, steps, hbm_peak, alu_peak_gops):
     adan_ms = a.elapsed_time(b) / 20
     adan_gbs = 48 * nflat / (adan_ms / 1000) / 1e9
     # per-stage rates at this size (plain batched calls with per-stage events)
-    pctx = gv.Context((16, 16), 128)
+    pctx = gv.Context(tile, depth)
     pctx.profile_enable(True)
     fr, total = gv.layout_frames([(cams[i], 0, N) for i in range(B)])
     pimg = torch.empty(3 * total, device=dev)
@@ -680,14 +683,15 @@ def run_training(torch, gv, synth, dev, steps, hbm_peak, alu_peak_gops):
     pctx.read_status(pws)  # raises unless the profiled calls fitted
     cnt = pctx.read_counters(pws)
     P, K = cnt["pairs"], cnt["keys"]
-    tiles = B * math.ceil(TW / 16) * math.ceil(TH / 16)
+    tiles = B * math.ceil(TW / tile[0]) * math.ceil(TH / tile[1])
     tpass = math.ceil(math.ceil(math.log2(tiles)) / 8)
     amounts = {"project": ("hbm", 112 * P), "depth_sort": ("hbm", P * (4 + 4 * 16)),
                "tile_sort": ("hbm", K * (tpass - 1) * 16), "emit": ("hbm", P * (12 + 4 + 48) + K * 8),
                "project_bwd": ("hbm", N * 56 * 2 + P * (56 + 36)),
                "composite_fwd": ("alu", OPS_EVAL * cnt["fwd_eval"] + OPS_COMP_FWD * cnt["bwd_replayed"]),
                "composite_bwd": ("alu", OPS_EVAL * cnt["bwd_eval"] + OPS_COMP_BWD * cnt["bwd_replayed"])}
-    large = {"workload": f"{B} frames 1920x1080 sharing 1M Gaussians (pairs {P}, keys {K})"}
+    large = {"workload": f"{B} frames 1920x1080 sharing 1M Gaussians (pairs {P}, keys {K})",
+             "tile": f"{tile[0]}x{tile[1]}", "stage_depth": depth}
     for k, (kind, amount) in amounts.items():
         m = statistics.median(ms_acc.get(k, [0.0]))
         if m <= 0:
@@ -699,6 +703,7 @@ def run_training(torch, gv, synth, dev, steps, hbm_peak, alu_peak_gops):
     large["adan"] = {"ms": round(adan_ms, 3), "bound": "hbm", "achieved": round(adan_gbs, 1), "unit": "GB/s",
                      "frac": round(adan_gbs / hbm_peak, 4), "params": nflat}
     training = {"frames_per_s": round(steps * B / t, 2), "steps_per_s": round(steps / t, 3), "steps": steps,
+                "tile": f"{tile[0]}x{tile[1]}", "stage_depth": depth,
                 "frames_per_step": B, "render_fps_1080p": round(fps, 1),
                 "psnr_before": round(psnr0, 2), "psnr_after": round(psnr1, 2),
                 "workload": "50-frame 1920x1080 clip, targets from 1M ground-truth Gaussians drifting linearly, "

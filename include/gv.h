@@ -148,7 +148,7 @@ typedef struct {
     int64_t pixel_offset;
 } gv_frame_desc;
 
-/* Launch configuration: tile shape (8x8, 16x8 or 16x16) and the number of Gaussians
+/* Launch configuration: tile shape (8x8, 16x8, 16x16, 32x16 or 32x32) and the number of Gaussians
  * staged through shared memory per batch (32, 64, 128 or 256); background colour. */
 typedef struct {
     int32_t tile_w, tile_h;
@@ -261,11 +261,14 @@ GV_API gv_status gv_adan_step(gv_ctx *ctx, float *param, float *grad, float *m, 
 
 /* ---- autotuner -------------------------------------------------------------------- */
 
-/* Time forward + backward of this batch for every tile shape {8x8, 16x8, 16x16} and stage
- * depth {64, 128, 256} (reps timed runs each after one warm-up, CUDA events on `stream`)
- * and store the fastest in *best (and in the context).  The buffers are the caller's and
- * are overwritten; grad may be any scratch of the right size.  ms_out (HOST, may be NULL)
- * receives 9 timings in the order tiles x depths.  Synchronises the stream. */
+/* Time forward + backward of this batch for every tile shape {8x8, 16x8, 16x16, 32x16,
+ * 32x32} and stage depth {64, 128, 256} (reps timed runs each after one warm-up, CUDA
+ * events on `stream`) and store the fastest in *best (and in the context).  The buffers
+ * are the caller's and are overwritten; grad may be any scratch of the right size.  A
+ * configuration whose keys do not fit the workspace is skipped (timing INFINITY).  ms_out
+ * (HOST, may be NULL) receives GV_AUTOTUNE_CONFIGS = 15 timings in the order tiles x
+ * depths.  Synchronises the stream. */
+#define GV_AUTOTUNE_CONFIGS 15
 GV_API gv_status gv_autotune(gv_ctx *ctx, const gv_gaussians *g, const gv_frame_desc *frames, int32_t F,
                       void *workspace, size_t ws_bytes, float *image, float *final_T,
                       int32_t *last_idx, const float *dL_dimage, gv_gaussians_grad *grad,

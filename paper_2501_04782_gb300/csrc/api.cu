@@ -80,7 +80,8 @@ gv_status fail(gv_ctx *c, gv_status s, const char *fmt, ...) {
 
 bool valid_options(const gv_options &o) {
     bool tile_ok = (o.tile_w == 8 && o.tile_h == 8) || (o.tile_w == 16 && o.tile_h == 8) ||
-                   (o.tile_w == 16 && o.tile_h == 16);
+                   (o.tile_w == 16 && o.tile_h == 16) || (o.tile_w == 32 && o.tile_h == 16) ||
+                   (o.tile_w == 32 && o.tile_h == 32);
     bool depth_ok = o.stage_depth == 32 || o.stage_depth == 64 || o.stage_depth == 128 || o.stage_depth == 256;
     return tile_ok && depth_ok && std::isfinite(o.bg[0]) && std::isfinite(o.bg[1]) && std::isfinite(o.bg[2]);
 }
@@ -736,7 +737,8 @@ gv_status gv_autotune(gv_ctx *ctx, const gv_gaussians *g, const gv_frame_desc *f
                       gv_gaussians_grad *grad, int32_t reps, gv_options *best, float *ms_out, gv_stream stream) {
     if (!ctx) return GV_ERR_INVALID_ARG;
     if (reps < 1) reps = 1;
-    const int shapes[3][2] = {{8, 8}, {16, 8}, {16, 16}};
+    constexpr int kShapes = 5;
+    const int shapes[kShapes][2] = {{8, 8}, {16, 8}, {16, 16}, {32, 16}, {32, 32}};
     const int depths[3] = {64, 128, 256};
     gv_options keep = ctx->opt, found = ctx->opt;
     float best_ms = INFINITY;
@@ -746,7 +748,7 @@ gv_status gv_autotune(gv_ctx *ctx, const gv_gaussians *g, const gv_frame_desc *f
     GV_CUDA(cudaEventCreate(&e1));
     gv_status result = GV_OK;
     int k = 0;
-    for (int si = 0; si < 3 && result == GV_OK; si++) {
+    for (int si = 0; si < kShapes && result == GV_OK; si++) {
         for (int di = 0; di < 3 && result == GV_OK; di++, k++) {
             gv_options o = keep;
             o.tile_w = shapes[si][0];

@@ -453,6 +453,22 @@ cudaError_t run_bwd(const Work &w, const unsigned *ids, float bg0, float bg1, fl
                 case 256: return FN<16, 8, 256>(__VA_ARGS__);                                    \
             }                                                                                    \
             break;                                                                               \
+        case 32016:                                                                              \
+            switch (depth) {                                                                     \
+                case 32: return FN<32, 16, 32>(__VA_ARGS__);                                     \
+                case 64: return FN<32, 16, 64>(__VA_ARGS__);                                     \
+                case 128: return FN<32, 16, 128>(__VA_ARGS__);                                   \
+                case 256: return FN<32, 16, 256>(__VA_ARGS__);                                   \
+            }                                                                                    \
+            break;                                                                               \
+        case 32032:                                                                              \
+            switch (depth) {                                                                     \
+                case 32: return FN<32, 32, 32>(__VA_ARGS__);                                     \
+                case 64: return FN<32, 32, 64>(__VA_ARGS__);                                     \
+                case 128: return FN<32, 32, 128>(__VA_ARGS__);                                   \
+                case 256: return FN<32, 32, 256>(__VA_ARGS__);                                   \
+            }                                                                                    \
+            break;                                                                               \
         case 16016:                                                                              \
             switch (depth) {                                                                     \
                 case 32: return FN<16, 16, 32>(__VA_ARGS__);                                     \

@@ -62,6 +62,9 @@ class GaussiansGrad(ctypes.Structure):
                                                "camera", "ctrl", "log_scale_t", "quat_t", "sh")]
 
 CAMERA_GRAD = 16  # per frame: dR (row-major, R as a general matrix), dt, dfx, dfy, dcx, dcy
+TILE_SHAPES = ((8, 8), (16, 8), (16, 16), (32, 16), (32, 32))  # the autotuner's order
+STAGE_DEPTHS = (64, 128, 256)
+AUTOTUNE_CONFIGS = len(TILE_SHAPES) * len(STAGE_DEPTHS)
 
 
 class FrameDesc(ctypes.Structure):
@@ -377,7 +380,7 @@ class Context:
         g = gaussians_struct(params)
         gr = grad_struct(grads)
         best = Options()
-        ms = (ctypes.c_float * 9)()
+        ms = (ctypes.c_float * AUTOTUNE_CONFIGS)()
         self.check(self.lib.gv_autotune(self.h, ctypes.byref(g), arr, len(frames), _ptr(ws), ws.numel(),
                                         _ptr(image), _ptr(final_T), _ptr(last_idx), _ptr(dL_dimage),
                                         ctypes.byref(gr), int(reps), ctypes.byref(best), ms, _stream_handle(stream)))

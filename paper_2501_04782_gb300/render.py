@@ -137,7 +137,8 @@ class Trainer:
         """optimizer: "adam" (betas default (0.9, 0.999)) or "adan" (the paper's, Sec. 4.1;
         betas default (0.02, 0.08, 0.01); adan_bias_correction selects the debiased form
         over Algorithm 1's first-gradient start); the learning rate of step k is
-        lr * lr_decay^k (the paper decays 0.01 by 0.99995 per step)."""
+        lr * lr_decay^k (the paper decays 0.01 by 0.99995 per step).  tile: a tile shape, or
+        "auto" to let the autotuner pick tile shape and stage depth on the first batch."""
         if optimizer not in ("adam", "adan"):
             raise ValueError("optimizer must be 'adam' or 'adan'")
         dev = params["opacity_logit"].device
@@ -165,7 +166,8 @@ class Trainer:
         self.betas = betas if betas is not None else ((0.9, 0.999) if optimizer == "adam" else (0.02, 0.08, 0.01))
         self.step_count = 0
         self.rng = torch.Generator().manual_seed(seed)
-        self.ctx = gv.Context(tile, stage_depth)
+        auto = tile == "auto"
+        self.ctx = gv.Context((16, 16) if auto else tile, stage_depth)
         W, H = int(cams[0].W), int(cams[0].H)
         self.frames, self.total = gv.layout_frames([(c, 0, self.N) for c in cams[:batch]])
         cap = key_capacity if key_capacity else 0
@@ -185,6 +187,10 @@ class Trainer:
             st, keys = self.ctx.read_status(self.ws, raise_on_error=False)
             self.ws = torch.empty(self.ctx.workspace_size(self.frames, int(keys * 1.5) + 65536),
                                   dtype=torch.uint8, device=dev)
+        if auto:  # tile shape and stage depth timed on the first batch (fwd + bwd)
+            self.dL.normal_(0.0, 1e-3)
+            self.ctx.autotune(self.params, self.frames, self.ws, self.image, self.T, self.idx, self.dL, self.grads)
+            self.grad.zero_()
         self.scale = 1.0 / (3 * self.total)
         torch.cuda.synchronize()
         with torch.cuda.stream(self.stream):

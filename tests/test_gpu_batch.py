@@ -127,9 +127,10 @@ def test_autotune_picks_a_valid_configuration():
     grads = {k: torch.zeros_like(v) for k, v in run.params.items()}
     best, ms = ctx.autotune(run.params, run.frames, run.ws, run.image, run.T, run.idx, dL, grads, reps=2)
     print(f"[autotune] best {best.tile_w}x{best.tile_h} depth {best.stage_depth}; ms {ms}")
-    assert (best.tile_w, best.tile_h) in ((8, 8), (16, 8), (16, 16))
-    assert best.stage_depth in (64, 128, 256)
-    assert all(np.isfinite(ms))
-    assert ms[[(8, 8), (16, 8), (16, 16)].index((best.tile_w, best.tile_h)) * 3 + (64, 128, 256).index(best.stage_depth)] == min(ms)
+    assert (best.tile_w, best.tile_h) in gv.TILE_SHAPES
+    assert best.stage_depth in gv.STAGE_DEPTHS
+    assert len(ms) == gv.AUTOTUNE_CONFIGS and all(np.isfinite(ms))
+    k = gv.TILE_SHAPES.index((best.tile_w, best.tile_h)) * len(gv.STAGE_DEPTHS) + gv.STAGE_DEPTHS.index(best.stage_depth)
+    assert ms[k] == min(ms)
     o = ctx.options
     assert (o.tile_w, o.tile_h, o.stage_depth) == (best.tile_w, best.tile_h, best.stage_depth)

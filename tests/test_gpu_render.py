@@ -11,7 +11,7 @@ from paper_2501_04782_gb300 import gv, synth
 
 pytestmark = pytest.mark.gpu
 
-CONFIGS = [((8, 8), 64), ((16, 8), 128), ((16, 16), 256), ((16, 16), 32)]
+CONFIGS = [((8, 8), 64), ((16, 8), 128), ((16, 16), 256), ((16, 16), 32), ((32, 16), 128), ((32, 32), 64)]
 
 
 def full_frame_check(g, cam, ctx, label):
@@ -51,7 +51,7 @@ def test_forward_with_background_and_ragged_tiles():
     compare_pixels(run.frame_image(0).reshape(3, -1).T, ref["rgb"].reshape(3, -1).T, ref["amb"].ravel(), "bg+ragged")
 
 
-@pytest.mark.parametrize("tile,depth", [((16, 16), 256), ((8, 8), 64)])
+@pytest.mark.parametrize("tile,depth", [((16, 16), 256), ((8, 8), 64), ((32, 16), 128), ((32, 32), 256)])
 def test_backward_128x128_2k(tile, depth):
     w = synth.workload_single_128()
     g = w["gaussians"]

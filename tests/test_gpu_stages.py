@@ -10,7 +10,7 @@ from paper_2501_04782_gb300 import gv, synth
 
 pytestmark = pytest.mark.gpu
 
-TILES = [(8, 8), (16, 8), (16, 16)]
+TILES = [(8, 8), (16, 8), (16, 16), (32, 16), (32, 32)]
 
 
 def screen_inputs(seed, n, W, H, tie_depths=False, frac_invalid=0.05):

@@ -12,7 +12,7 @@ import numpy as np
 import oracle
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "binning_cull_cases.txt")
-TILES = ((8, 8), (16, 16), (16, 8))
+TILES = ((8, 8), (16, 16), (16, 8), (32, 16), (32, 32))
 
 
 def load_cases():
