@@ -793,11 +793,17 @@ def cpu_baseline(g, cam, tgt, seconds: float) -> dict:
     import oracle
     from paper_2501_04782_gb300 import synth
     oracle.lib()
-    px, py = synth.pixel_sample(4242, W, H, 64)
-    t0 = time.perf_counter()
-    oracle_step(oracle, g, cam, tgt, px, py)
-    t64 = time.perf_counter() - t0
-    n = int(min(W * H, max(64, 64 * seconds / max(t64, 1e-3))))
+    # two pilot runs separate the per-call cost (projection of every Gaussian, threads) from
+    # the per-pixel cost, so the sample fills about `seconds`
+    times = []
+    for m, seed in ((64, 4242), (512, 4244)):
+        px, py = synth.pixel_sample(seed, W, H, m)
+        t0 = time.perf_counter()
+        oracle_step(oracle, g, cam, tgt, px, py)
+        times.append(time.perf_counter() - t0)
+    per_px = max((times[1] - times[0]) / 448, 1e-7)
+    fixed = max(times[0] - 64 * per_px, 0.0)
+    n = int(min(W * H, max(64, (seconds - fixed) / per_px)))
     px, py = synth.pixel_sample(4243, W, H, n)
     t0 = time.perf_counter()
     oracle_step(oracle, g, cam, tgt, px, py)
