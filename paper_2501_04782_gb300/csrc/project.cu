@@ -684,16 +684,28 @@ __device__ __forceinline__ void store_grad_sh(const GradPtrs &gr, const GaussPtr
     if (!gr.sh) return;
     const long long N = g.N;
     const int K = sh_terms(g.sh_degree);
+    if (atomic) {
 #pragma unroll
-    for (int k = 0; k < kShMax; k++) {
-        if (k >= K) break;
+        for (int k = 0; k < kShMax; k++) {
+            if (k >= K) break;
 #pragma unroll
-        for (int ch = 0; ch < 3; ch++) {
-            float *dst = gr.sh + ((long long)ch * K + k) * N + gi;
-            const float v = Y ? Y[k] * c[ch] : acc[(ch * kShMax + k) * stride];
-            if (atomic) atomicAdd(dst, v);
-            else *dst += v;
+            for (int ch = 0; ch < 3; ch++)
+                atomicAdd(gr.sh + ((long long)ch * K + k) * N + gi, Y ? Y[k] * c[ch] : acc[(ch * kShMax + k) * stride]);
         }
+        return;
+    }
+    // read-modify-write one channel at a time in two phases: the channel's old values are
+    // all loaded before any is stored, so those loads are in flight together
+#pragma unroll
+    for (int ch = 0; ch < 3; ch++) {
+        float *row = gr.sh + (long long)ch * K * N + gi;
+        float old[kShMax];
+#pragma unroll
+        for (int k = 0; k < kShMax; k++)
+            if (k < K) old[k] = row[(long long)k * N];
+#pragma unroll
+        for (int k = 0; k < kShMax; k++)
+            if (k < K) row[(long long)k * N] = old[k] + (Y ? Y[k] * c[ch] : acc[(ch * kShMax + k) * stride]);
     }
 }
 
