@@ -714,68 +714,87 @@ def run_training(torch, gv, synth, dev, steps, hbm_peak, alu_peak_gops):
 
 
 def run_e2e(torch, gv, ctx, params, target, frames, ws, dev, flush, steps, scale, world):
-    """Same step through the C ABI with HOST inputs: the parameter planes and the target
-    copied from pinned host memory, gradients and loss copied back, every step.  The planes
-    live in one flat buffer on each side (one copy per direction for the parameters, one
-    for the gradients and the loss); the target, needed only by the loss, is copied on a
-    second stream while the forward runs."""
+    """Same step through the C ABI with HOST inputs: every step copies the parameter planes
+    and the target in from pinned host memory and the gradients and loss back out.  The
+    planes live in one flat buffer on each side (one copy per direction), and the loop is
+    pipelined like a data loader's: inputs and outputs are double-buffered, copies run on
+    their own streams, so step k+1's inputs arrive and step k-1's gradients leave while
+    step k computes.  The whole loop is timed, the 512 MB L2 flush before every step's
+    compute included (it only lengthens the measured time)."""
     keys = list(params)
     sizes = [params[k].numel() for k in keys]
     n_par = sum(sizes)
-    host_in = torch.empty(n_par, dtype=torch.float32).pin_memory()
+    n_tgt = target.numel()
+    host_in = torch.empty(n_par + n_tgt, dtype=torch.float32).pin_memory()  # parameters, then target
     off = 0
     for k, n in zip(keys, sizes):
         host_in[off:off + n].copy_(params[k].reshape(-1).cpu())
         off += n
-    host_target = target.cpu().pin_memory()
-    dev_in = torch.empty(n_par, device=dev)
-    dtarget = torch.empty_like(target)
-    dev_out = torch.zeros(n_par + 1, device=dev)  # gradients, then the loss
-    host_out = torch.empty(n_par + 1, dtype=torch.float32).pin_memory()
-    dparams, grads, off = {}, {}, 0
-    for k, n in zip(keys, sizes):
-        dparams[k] = dev_in[off:off + n].view(params[k].shape)
-        grads[k] = dev_out[off:off + n].view(params[k].shape)
-        off += n
-    loss = dev_out[n_par:]
+    host_in[n_par:].copy_(target.reshape(-1).cpu())
+    dev_in = [torch.empty(n_par + n_tgt, device=dev) for _ in range(2)]
+    dev_out = [torch.zeros(n_par + 1, device=dev) for _ in range(2)]  # gradients, then the loss
+    host_out = [torch.empty(n_par + 1, dtype=torch.float32).pin_memory() for _ in range(2)]
+    views = []
+    for b in range(2):
+        dp, gr, off = {}, {}, 0
+        for k, n in zip(keys, sizes):
+            dp[k] = dev_in[b][off:off + n].view(params[k].shape)
+            gr[k] = dev_out[b][off:off + n].view(params[k].shape)
+            off += n
+        views.append((dp, dev_in[b][n_par:], gr, dev_out[b][n_par:]))
     P = W * H
     image = torch.empty(3 * P, device=dev)
     T = torch.empty(P, device=dev)
     idx = torch.empty(P, dtype=torch.int32, device=dev)
     dL = torch.empty(3 * P, device=dev)
-    h2d = n_par * 4 + host_target.numel() * 4
+    h2d = (n_par + n_tgt) * 4
     d2h = (n_par + 1) * 4
-    side = torch.cuda.Stream(device=dev)
     main = torch.cuda.current_stream()
+    s_in, s_out = torch.cuda.Stream(device=dev), torch.cuda.Stream(device=dev)
+    ev = lambda: torch.cuda.Event()
+    in_ready, in_free = [ev(), ev()], [ev(), ev()]
+    out_ready, out_free = [ev(), ev()], [ev(), ev()]
+    for b in range(2):  # both buffers start free
+        in_free[b].record(main)
+        out_free[b].record(main)
 
-    def step():
-        side.wait_stream(main)  # the previous step's loss has read the target buffer
-        with torch.cuda.stream(side):
-            dtarget.copy_(host_target, non_blocking=True)
-        dev_in.copy_(host_in, non_blocking=True)
-        ctx.render_fwd(dparams, frames, ws, image, T, idx)
-        dev_out.zero_()
-        main.wait_stream(side)
-        ctx.l2_loss_grad(image, dtarget, scale, dL, loss)
-        ctx.render_bwd(dparams, frames, ws, T, idx, dL, grads)
-        host_out.copy_(dev_out, non_blocking=True)
-
-    for _ in range(3):
-        step()
-    torch.cuda.synchronize()
-    total_ms = 0.0
-    for _ in range(steps):
+    def step(k):
+        b = k & 1
+        dp, dtarget, grads, loss = views[b]
+        s_in.wait_event(in_free[b])  # step k - 2 has finished reading this buffer
+        with torch.cuda.stream(s_in):
+            dev_in[b].copy_(host_in, non_blocking=True)
+        in_ready[b].record(s_in)
         flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        a.record()
-        step()
-        b.record()
-        b.synchronize()
-        total_ms += a.elapsed_time(b)
+        main.wait_event(in_ready[b])
+        main.wait_event(out_free[b])  # step k - 2's gradients have left this buffer
+        ctx.render_fwd(dp, frames, ws, image, T, idx)
+        dev_out[b].zero_()
+        ctx.l2_loss_grad(image, dtarget, scale, dL, loss)
+        ctx.render_bwd(dp, frames, ws, T, idx, dL, grads)
+        in_free[b].record(main)  # the backward read the parameters last
+        out_ready[b].record(main)
+        s_out.wait_event(out_ready[b])
+        with torch.cuda.stream(s_out):
+            host_out[b].copy_(dev_out[b], non_blocking=True)
+        out_free[b].record(s_out)
+
+    for k in range(4):
+        step(k)
+    torch.cuda.synchronize()
+    a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(main)
+    for k in range(steps):
+        step(k)
+    main.wait_stream(s_out)
+    e.record(main)
+    e.synchronize()
+    total_ms = a.elapsed_time(e)
     value, _ = aggregate(steps * P / 1e6, total_ms / 1000, world, dev)
     return {"value": round(value, 2), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "copies_per_step": {"h2d": 2, "d2h": 1},
+            "ms_per_step": round(total_ms / steps, 4), "copies_per_step": {"h2d": 1, "d2h": 1},
+            "pipelined": "double-buffered inputs and outputs, copy streams beside the compute stream; "
+                         "L2 flush inside the timed loop",
             "api": "gv_render_fwd / gv_l2_loss_grad / gv_render_bwd with pinned host buffers copied in and out"}
 
 

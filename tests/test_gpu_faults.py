@@ -58,3 +58,32 @@ def test_invalid_arguments_are_rejected():
     zero = [gv.Frame(synth.Camera(0, 10, 1, 1, 0, 0), 0, 10, 0)]
     with pytest.raises(gv.GVError):
         ctx.workspace_size(zero)
+
+
+def test_invalid_parameterisations_are_rejected():
+    """Time-parameterised and view-dependent forms outside their ranges: n_ctrl outside
+    [4, 64], a spherical-harmonic degree outside [0, 3] or with no coefficients, Adan's
+    debiased form with a zero beta; a coefficient count that is no (d + 1)^2 - 1 is
+    refused by the binding."""
+    import ctypes
+    ctx = gv.Context((16, 16), 64)
+    w = synth.workload_single_128(N=10)
+    run = GpuRun(ctx, w["gaussians"], w["frames"])
+    g = gv.gaussians_struct(run.params)
+    arr = gv.frame_array(run.frames)
+
+    def fwd(st):
+        return ctx.lib.gv_render_batch_fwd(ctx.h, ctypes.byref(st), arr, 1, gv._ptr(run.ws), run.ws.numel(),
+                                           gv._ptr(run.image), gv._ptr(run.T), gv._ptr(run.idx), None)
+
+    assert fwd(g) == gv.GV_OK
+    for field, value in (("sh_degree", 4), ("sh_degree", -1), ("sh_degree", 2), ("n_ctrl", 3), ("n_ctrl", 65)):
+        bad = gv.gaussians_struct(run.params)
+        setattr(bad, field, value)  # sh_degree 2 with no coefficient planes, n_ctrl with no control points
+        assert fwd(bad) == gv.GV_ERR_INVALID_ARG, (field, value)
+    with pytest.raises(ValueError):
+        gv.gaussians_struct(dict(run.params, sh=torch.zeros(3, 5, 10, device="cuda")))
+    p = torch.zeros(8, device="cuda")
+    with pytest.raises(gv.GVError):
+        ctx.adan_step(p, p.clone(), p.clone(), p.clone(), p.clone(), p.clone(), 1, 0.01, betas=(0.0, 0.08, 0.01),
+                      bias_correction=True)
