@@ -62,6 +62,7 @@ class GaussiansGrad(ctypes.Structure):
                                                "camera", "ctrl", "log_scale_t", "quat_t", "sh")]
 
 CAMERA_GRAD = 16  # per frame: dR (row-major, R as a general matrix), dt, dfx, dfy, dcx, dcy
+MAX_FRAMES = 1024  # GV_MAX_FRAMES: frames per call
 TILE_SHAPES = ((8, 8), (16, 8), (16, 16), (32, 16), (32, 32))  # the autotuner's order
 STAGE_DEPTHS = (64, 128, 256)
 AUTOTUNE_CONFIGS = len(TILE_SHAPES) * len(STAGE_DEPTHS)

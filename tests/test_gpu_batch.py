@@ -134,3 +134,43 @@ def test_autotune_picks_a_valid_configuration():
     assert ms[k] == min(ms)
     o = ctx.options
     assert (o.tile_w, o.tile_h, o.stage_depth) == (best.tile_w, best.tile_h, best.stage_depth)
+
+
+@pytest.mark.parametrize("kind", ["shared", "own"])
+def test_maximum_frame_count(kind):
+    """GV_MAX_FRAMES (1024) small frames in one call: frame tables beyond one setup launch
+    (96 frames each) and beyond the emission's shared-memory frame cache (64), frame
+    lookups by pair and by tile across all of them; forward equal to per-frame calls on a
+    sample of frames, backward equal to the sum of per-frame backwards."""
+    rng = np.random.default_rng(21)
+    F = gv.MAX_FRAMES
+    n_per = 6 if kind == "own" else 300
+    sets, frames = [], []
+    for f in range(F):
+        W, H = (24, 16) if f % 3 else (17, 11)  # ragged tiles, two sizes
+        R, t = synth.random_pose(rng, 10.0, 0.1)
+        cam = synth.centred_camera(W, H, float(W), R, t)
+        if kind == "own":
+            sets.append(synth.gaussians(rng, n_per, box=((-1, 1), (-1, 1), (2.0, 5.0))))
+            frames.append((cam, f * n_per, n_per))
+        else:
+            frames.append((cam, 0, n_per))
+    g = synth.concat_gaussians(sets) if kind == "own" else synth.gaussians(rng, n_per,
+                                                                             box=((-1, 1), (-1, 1), (2.0, 5.0)))
+    ctx = gv.Context((16, 8), 64)
+    batch = GpuRun(ctx, g, frames).forward()
+    dL = np.random.default_rng(22).normal(size=3 * batch.total)
+    gb = batch.backward(dL)
+    acc = {k: np.zeros_like(v) for k, v in gb.items()}
+    for f in range(F):
+        single = GpuRun(ctx, g, [frames[f]]).forward()
+        if f % 97 == 0 or f == F - 1:
+            assert np.array_equal(single.frame_image(0), batch.frame_image(f)), f
+        off = 3 * batch.frames[f].pixel_offset
+        npx = 3 * frames[f][0].W * frames[f][0].H
+        part = np.zeros(3 * single.total)
+        part[:] = dL[off:off + npx]
+        for k, v in single.backward(part).items():
+            acc[k] += v
+    for k in gb:
+        assert np.allclose(gb[k], acc[k], rtol=1e-4, atol=1e-5 * (np.abs(acc[k]).max() + 1e-12)), k
