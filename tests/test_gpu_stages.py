@@ -57,11 +57,13 @@ def ctx_tile(ctx):
 
 
 @pytest.mark.parametrize("tile", TILES)
-@pytest.mark.parametrize("case", ["random", "ties", "ragged_small", "one", "many_keys"])
+@pytest.mark.parametrize("case", ["random", "ties", "ragged_small", "one", "many_keys", "uhd"])
 def test_binning_and_sort_bit_exact(tile, case):
+    """uhd: a 3840x2160 frame, whose 8x8 tiling has 129,600 tiles (17 tile-id bits: the
+    emission's pass and two more)."""
     W, H = {"random": (300, 200), "ties": (256, 128), "ragged_small": (37, 21), "one": (64, 64),
-            "many_keys": (1000, 700)}[case]
-    n = {"random": 20000, "ties": 9001, "ragged_small": 57, "one": 1, "many_keys": 60000}[case]
+            "many_keys": (1000, 700), "uhd": (3840, 2160)}[case]
+    n = {"random": 20000, "ties": 9001, "ragged_small": 57, "one": 1, "many_keys": 60000, "uhd": 80000}[case]
     u, v, sxx, sxy, syy, tau, depth, valid = screen_inputs(hash((case, tile)) % 2**31, n, W, H,
                                                            tie_depths=(case == "ties"))
     if case == "one":
@@ -82,6 +84,8 @@ def test_binning_and_sort_bit_exact(tile, case):
         assert cnt_ref.sum() < cells_ref.sum()  # the cull removed cells
     if case == "many_keys":
         assert K > 3 * 3072  # several sort tiles and a ragged tail
+    if case == "uhd" and tile == (8, 8):
+        assert int(s_tile.max()) >= 1 << 16  # tile ids past 16 bits: a third pass sorted them
 
 
 def test_binning_empty_input():
