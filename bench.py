@@ -656,6 +656,17 @@ def run_training(torch, gv, synth, dev, steps, hbm_peak, alu_peak_gops):
     b.synchronize()
     adan_ms = a.elapsed_time(b) / 20
     adan_gbs = 48 * nflat / (adan_ms / 1000) / 1e9
+    # the fused Adam step on the same planes (four planes read, four written: 32 B; its
+    # moments borrow the Adan state buffers)
+    for k in range(3):
+        tr.ctx.adam_step(tr.flat, tr.grad, tr.m, tr.nsq, 10_000 + k, 1e-9, stream=tr.stream)
+    a.record(tr.stream)
+    for k in range(20):
+        tr.ctx.adam_step(tr.flat, tr.grad, tr.m, tr.nsq, 10_003 + k, 1e-9, stream=tr.stream)
+    b.record(tr.stream)
+    b.synchronize()
+    adam_ms = a.elapsed_time(b) / 20
+    adam_gbs = 32 * nflat / (adam_ms / 1000) / 1e9
     # per-stage rates at this size (plain batched calls with per-stage events)
     pctx = gv.Context(tile, depth)
     pctx.profile_enable(True)
@@ -703,6 +714,8 @@ def run_training(torch, gv, synth, dev, steps, hbm_peak, alu_peak_gops):
                     "unit": "GB/s" if kind == "hbm" else "Gop/s", "frac": round(r / peak, 4)}
     large["adan"] = {"ms": round(adan_ms, 3), "bound": "hbm", "achieved": round(adan_gbs, 1), "unit": "GB/s",
                      "frac": round(adan_gbs / hbm_peak, 4), "params": nflat}
+    large["adam"] = {"ms": round(adam_ms, 3), "bound": "hbm", "achieved": round(adam_gbs, 1), "unit": "GB/s",
+                     "frac": round(adam_gbs / hbm_peak, 4), "params": nflat}
     training = {"frames_per_s": round(steps * B / t, 2), "steps_per_s": round(steps / t, 3), "steps": steps,
                 "tile": f"{tile[0]}x{tile[1]}", "stage_depth": depth,
                 "frames_per_step": B, "render_fps_1080p": round(fps, 1),

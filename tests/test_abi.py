@@ -54,9 +54,11 @@ def test_struct_layouts_match_c(tmp_path):
 #include <stddef.h>
 #include "gv.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gv_camera), sizeof(gv_gaussians), sizeof(gv_gaussians_grad),
-         sizeof(gv_frame_desc), sizeof(gv_options), offsetof(gv_frame_desc, gauss_offset),
-         offsetof(gv_camera, time), offsetof(gv_options, bg));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(gv_camera), sizeof(gv_gaussians),
+         sizeof(gv_gaussians_grad), sizeof(gv_frame_desc), sizeof(gv_options), offsetof(gv_frame_desc, gauss_offset),
+         offsetof(gv_camera, time), offsetof(gv_options, bg), offsetof(gv_gaussians, n_ctrl),
+         offsetof(gv_gaussians, sh_degree), offsetof(gv_gaussians, sh), offsetof(gv_gaussians, visible),
+         offsetof(gv_gaussians_grad, camera), offsetof(gv_gaussians_grad, sh));
   return 0;
 }
 """)
@@ -65,7 +67,9 @@ int main(void) {
     got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     want = [ctypes.sizeof(gv.Camera), ctypes.sizeof(gv.Gaussians), ctypes.sizeof(gv.GaussiansGrad),
             ctypes.sizeof(gv.FrameDesc), ctypes.sizeof(gv.Options), gv.FrameDesc.gauss_offset.offset,
-            gv.Camera.time.offset, gv.Options.bg.offset]
+            gv.Camera.time.offset, gv.Options.bg.offset, gv.Gaussians.n_ctrl.offset, gv.Gaussians.sh_degree.offset,
+            gv.Gaussians.sh.offset, gv.Gaussians.visible.offset, gv.GaussiansGrad.camera.offset,
+            gv.GaussiansGrad.sh.offset]
     assert got == want
 
 
