@@ -486,8 +486,12 @@ __global__ void __launch_bounds__(TW *TH / PX) composite_bwd_kernel(Work w, cons
                 const unsigned act = __ballot_sync(0xffffffffu, any);
                 if (!act) continue;
                 const float cb = s_c[j];
-                const float gu0 = 2.f * f0.z * dx, gv0 = f0.w * dx, c2 = 2.f * f1.x, dxx = dx * dx;
-                float vs[9];
+                // Per-lane sums over the thread's pixels (one column: dx is the lane's):
+                // S0 = sum dL/de, S1 = sum dL/de dy, S2 = sum dL/de dy^2 and the colour terms;
+                // the screen-space gradients follow by the chain rule of e: du = (2a'dx) S0 +
+                // b' S1, dv = (b'dx) S0 + 2c' S1, da' = dx^2 S0, db' = dx S1, dc' = S2, and
+                // dlog2o = S0 (alpha = 2^e, so dL/de carries the factor ln 2, applied to the sums).
+                float2 A0, A1, A2, Cr, Cg, Cb;
 #pragma unroll
                 for (int k = 0; k < NP; k++) {
                     const bool va = v[2 * k], vb = v[2 * k + 1];
@@ -508,22 +512,23 @@ __global__ void __launch_bounds__(TW *TH / PX) composite_bwd_kernel(Work w, cons
                     nS1[k] = __ffma2_rn(dup2(-f1.w), wg, nS1[k]);
                     nS2[k] = __ffma2_rn(dup2(-cb), wg, nS2[k]);
                     T[k] = Tin;
-                    // dL/de for the exponent e (alpha = 2^e unless clamped at 0.99)
-                    const float2 kk = make_float2((va && r[k].x < kAlphaMax) ? r[k].x * kLn2 : 0.f,
-                                                  (vb && r[k].y < kAlphaMax) ? r[k].y * kLn2 : 0.f);
+                    // dL/de / ln 2 for the exponent e (alpha = 2^e unless clamped at 0.99)
+                    const float2 kk = make_float2((va && r[k].x < kAlphaMax) ? r[k].x : 0.f,
+                                                  (vb && r[k].y < kAlphaMax) ? r[k].y : 0.f);
                     const float2 de = __fmul2_rn(dal, kk);
-                    const float2 dxy = __fmul2_rn(dup2(dx), dy[k]);
-                    const float2 gu = __ffma2_rn(dup2(f0.w), dy[k], dup2(gu0));  // de/du = 2a'dx + b'dy
-                    const float2 gv = __ffma2_rn(dup2(c2), dy[k], dup2(gv0));    // de/dv = b'dx + 2c'dy
-                    const float2 cu = __fmul2_rn(de, gu), cv = __fmul2_rn(de, gv);
-                    const float2 ca = __fmul2_rn(de, dup2(dxx)), cbb = __fmul2_rn(de, dxy);
-                    const float2 cc = __fmul2_rn(de, __fmul2_rn(dy[k], dy[k]));
+                    const float2 ddy = __fmul2_rn(de, dy[k]);
+                    const float2 ddy2 = __fmul2_rn(ddy, dy[k]);
                     const float2 dr = __fmul2_rn(wg, g0[k]), dg = __fmul2_rn(wg, g1[k]), db = __fmul2_rn(wg, g2[k]);
-                    const float t9[9] = {cu.x + cu.y, cv.x + cv.y, ca.x + ca.y, cbb.x + cbb.y, cc.x + cc.y,
-                                         de.x + de.y, dr.x + dr.y, dg.x + dg.y, db.x + db.y};
-#pragma unroll
-                    for (int q = 0; q < 9; q++) vs[q] = k ? vs[q] + t9[q] : t9[q];
+                    if (k == 0) {
+                        A0 = de; A1 = ddy; A2 = ddy2; Cr = dr; Cg = dg; Cb = db;
+                    } else {
+                        A0 = __fadd2_rn(A0, de); A1 = __fadd2_rn(A1, ddy); A2 = __fadd2_rn(A2, ddy2);
+                        Cr = __fadd2_rn(Cr, dr); Cg = __fadd2_rn(Cg, dg); Cb = __fadd2_rn(Cb, db);
+                    }
                 }
+                const float S0 = (A0.x + A0.y) * kLn2, S1 = (A1.x + A1.y) * kLn2, S2 = (A2.x + A2.y) * kLn2;
+                const float vs[9] = {fmaf(f0.w, S1, 2.f * f0.z * dx * S0), fmaf(2.f * f1.x, S1, f0.w * dx * S0),
+                                     dx * dx * S0, dx * S1, S2, S0, Cr.x + Cr.y, Cg.x + Cg.y, Cb.x + Cb.y};
                 if (__popc(act) <= kSparseLanes) {
                     if (any) {
                         const unsigned p = s_p[j];
