@@ -410,7 +410,7 @@ __global__ void __launch_bounds__(TW *TH / PX) composite_bwd_kernel(Work w, cons
         const uint2 rg = failed ? make_uint2(0u, 0u) : w.ranges[tile];
         const size_t plane = (size_t)W * H;
         // per-pixel replay state, packed over pixel pairs: pixel 2k + h is row ybase + RS (2k + h)
-        float2 npy[NP], T[NP], g0[NP], g1[NP], g2[NP], nS0[NP], nS1[NP], nS2[NP];
+        float2 npy[NP], T[NP], g0[NP], g1[NP], g2[NP], gS[NP];
         int last[PX];
         unsigned n_comp = 0, n_eval = 0;
         int lmax = -1;
@@ -438,12 +438,13 @@ __global__ void __launch_bounds__(TW *TH / PX) composite_bwd_kernel(Work w, cons
                 npy[q >> 1].x = ny; T[q >> 1].x = Tq; g0[q >> 1].x = d0; g1[q >> 1].x = d1; g2[q >> 1].x = d2;
             }
         }
-        // colour composited behind the current Gaussian, negated: nS = -(sum c w + T bg)
 #pragma unroll
         for (int k = 0; k < NP; k++) {
-            nS0[k] = __fmul2_rn(T[k], dup2(-bg0));
-            nS1[k] = __fmul2_rn(T[k], dup2(-bg1));
-            nS2[k] = __fmul2_rn(T[k], dup2(-bg2));
+            // gS = -(sum_ch g_ch S_ch), S_ch the colour composited behind the current
+            // Gaussian (the background term to start with): only its dot product with the
+            // pixel's upstream gradient g enters dL/dalpha
+            const float2 gbg = __ffma2_rn(g2[k], dup2(bg2), __ffma2_rn(g1[k], dup2(bg1), __fmul2_rn(g0[k], dup2(bg0))));
+            gS[k] = __fmul2_rn(T[k], make_float2(-gbg.x, -gbg.y));
         }
         const int wmax = __reduce_max_sync(0xffffffffu, lmax);
         if (lane == 0) atomicMax(&s_max, wmax);
@@ -503,14 +504,10 @@ __global__ void __launch_bounds__(TW *TH / PX) composite_bwd_kernel(Work w, cons
                     Tin.x = va ? Tin.x : T[k].x;
                     Tin.y = vb ? Tin.y : T[k].y;
                     const float2 wg = __fmul2_rn(al, Tin);
-                    // dL/dalpha = sum_ch g_ch (c_ch Tin - S_ch / (1 - alpha))
-                    const float2 x0 = __ffma2_rn(nS0[k], ra, __fmul2_rn(dup2(f1.z), Tin));
-                    const float2 x1 = __ffma2_rn(nS1[k], ra, __fmul2_rn(dup2(f1.w), Tin));
-                    const float2 x2 = __ffma2_rn(nS2[k], ra, __fmul2_rn(dup2(cb), Tin));
-                    const float2 dal = __ffma2_rn(g2[k], x2, __ffma2_rn(g1[k], x1, __fmul2_rn(g0[k], x0)));
-                    nS0[k] = __ffma2_rn(dup2(-f1.z), wg, nS0[k]);
-                    nS1[k] = __ffma2_rn(dup2(-f1.w), wg, nS1[k]);
-                    nS2[k] = __ffma2_rn(dup2(-cb), wg, nS2[k]);
+                    // dL/dalpha = sum_ch g_ch (c_ch Tin - S_ch / (1 - alpha)) = gc Tin + gS / (1 - alpha)
+                    const float2 gc = __ffma2_rn(g2[k], dup2(cb), __ffma2_rn(g1[k], dup2(f1.w), __fmul2_rn(g0[k], dup2(f1.z))));
+                    const float2 dal = __ffma2_rn(gS[k], ra, __fmul2_rn(gc, Tin));
+                    gS[k] = __ffma2_rn(make_float2(-gc.x, -gc.y), wg, gS[k]);
                     T[k] = Tin;
                     // dL/de / ln 2 for the exponent e (alpha = 2^e unless clamped at 0.99)
                     const float2 kk = make_float2((va && r[k].x < kAlphaMax) ? r[k].x : 0.f,
