@@ -13,7 +13,8 @@
 // runs four pixels of one column per thread on tiles 16 or 32 wide (8x16 or 16x8 per
 // warp), two on 8x8 tiles.
 // Gaussians are staged through shared memory in batches of DEPTH (the stage depth); every
-// lane then reads the same staged Gaussian (broadcast).  The forward takes two Gaussians
+// lane then reads the same staged Gaussian (broadcast).  The backward double-buffers its
+// stages: the next stage's records arrive by cp.async while one is replayed.  The forward takes two Gaussians
 // per round; a pixel's cutoff test compares alpha with a per-pixel threshold (1/255, or 2
 // once the pixel is done), so the stop rule costs no extra test per Gaussian; a warp
 // leaves the tile once all its pixels are done and a block once every pixel is
@@ -112,6 +113,28 @@ struct PixMap {
     static constexpr int NT = TW * TH / PX;
     static_assert(TW % WBW == 0 && TH % WBH == 0, "tile not covered by whole warps");
 };
+
+// Double-buffered stages of a tile's list (the backward's).  The ids of a stage are
+// copied two stages ahead and its Gaussians' records one stage ahead (cp.async), so the
+// replay of one stage overlaps the loads of the next two.  Thread t copies entries t,
+// t + NT, ... of both, so it reads back only id slots it copied itself (its own cp.async
+// wait suffices); the records need the block barrier.
+template <int NT>
+__device__ __forceinline__ void stage_copy_ids(unsigned *slot, const unsigned *ids, unsigned first, int n) {
+    for (int i = threadIdx.x; i < n; i += NT) cp_async4(slot + i, ids + first + i);
+}
+
+template <int NT>
+__device__ __forceinline__ void stage_copy_records(const Work &w, const unsigned *slot, int n, float4 *a, float4 *b,
+                                                   float *c, unsigned *pair) {
+    for (int i = threadIdx.x; i < n; i += NT) {
+        const unsigned p = min(slot[i], w.L.P - 1u);  // in range unless a wait gave up
+        if (pair) pair[i] = p;
+        cp_async16(a + i, w.feat0 + p);
+        cp_async16(b + i, w.feat1 + p);
+        cp_async4(c + i, w.feat2 + p);
+    }
+}
 
 template <int TW, int TH, int DEPTH>
 __global__ void __launch_bounds__(TW *TH / 2) composite_fwd_kernel(Work w, const unsigned *ids, float bg0, float bg1,
@@ -381,10 +404,12 @@ __global__ void __launch_bounds__(TW *TH / PX) composite_bwd_kernel(Work w, cons
     pdl_prologue();
     using M = PixMap<TW, TH, PX>;
     constexpr int NT = M::NT, NP = PX / 2;
-    __shared__ float4 s_a[DEPTH];
-    __shared__ float4 s_b[DEPTH];
-    __shared__ float s_c[DEPTH];
-    __shared__ unsigned s_p[DEPTH];
+    // two stage buffers: the copies of the next stage land while this one is replayed
+    __shared__ float4 s_a[2][DEPTH];
+    __shared__ float4 s_b[2][DEPTH];
+    __shared__ float s_c[2][DEPTH];
+    __shared__ unsigned s_p[2][DEPTH];
+    __shared__ unsigned s_id[2][DEPTH];
     __shared__ unsigned s_tile;
     __shared__ int s_max;
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
@@ -449,22 +474,33 @@ __global__ void __launch_bounds__(TW *TH / PX) composite_bwd_kernel(Work w, cons
         const int wmax = __reduce_max_sync(0xffffffffu, lmax);
         if (lane == 0) atomicMax(&s_max, wmax);
         __syncthreads();
-        const int end = min(s_max + 1, (int)rg.y);
-        for (int bend = end; bend > (int)rg.x; bend -= DEPTH) {
-            const int bstart = max((int)rg.x, bend - DEPTH);
+        const int end = min(s_max + 1, (int)rg.y), lo = (int)rg.x;
+        // stage s holds the Gaussians [max(lo, end - (s + 1) DEPTH), end - s DEPTH), replayed
+        // back to front from buffer s & 1
+        auto stage_n = [&](int bend) { return bend > lo ? bend - max(lo, bend - DEPTH) : 0; };
+        auto stage_first = [&](int bend) { return (unsigned)max(lo, bend - DEPTH); };
+        stage_copy_ids<NT>(s_id[0], ids, stage_first(end), stage_n(end));
+        cp_async_commit();
+        cp_async_wait_all();
+        stage_copy_records<NT>(w, s_id[0], stage_n(end), s_a[0], s_b[0], s_c[0], s_p[0]);
+        stage_copy_ids<NT>(s_id[1], ids, stage_first(end - DEPTH), stage_n(end - DEPTH));
+        cp_async_commit();
+        int buf = 0;
+        for (int bend = end; bend > lo; bend -= DEPTH, buf ^= 1) {
+            const int bstart = max(lo, bend - DEPTH);
             const int n = bend - bstart;
-            __syncthreads();
-            for (int i = threadIdx.x; i < n; i += NT) {
-                const unsigned p = min(ids[bstart + i], w.L.P - 1u);
-                s_p[i] = p;
-                s_a[i] = w.feat0[p];
-                s_b[i] = w.feat1[p];
-                s_c[i] = w.feat2[p];
-            }
-            __syncthreads();
+            cp_async_wait_all();
+            __syncthreads();  // stage in buffer buf complete; the other buffer's stage replayed
+            stage_copy_records<NT>(w, s_id[buf ^ 1], stage_n(bend - DEPTH), s_a[buf ^ 1], s_b[buf ^ 1], s_c[buf ^ 1],
+                                   s_p[buf ^ 1]);
+            stage_copy_ids<NT>(s_id[buf], ids, stage_first(bend - 2 * DEPTH), stage_n(bend - 2 * DEPTH));
+            cp_async_commit();
+            const float4 *sa = s_a[buf], *sb = s_b[buf];
+            const float *sc = s_c[buf];
+            const unsigned *sp = s_p[buf];
             const int jtop = min(n - 1, wmax - bstart);  // this warp's pixels stop before the rest
             for (int j = jtop; j >= 0; j--) {
-                const float4 f0 = s_a[j], f1 = s_b[j];
+                const float4 f0 = sa[j], f1 = sb[j];
                 const int pos = bstart + j;
                 // exponents e = a' dx^2 + b' dx dy + c' dy^2 + log2 o, rounded exactly as the
                 // forward's (the replay divides its transmittance back)
@@ -486,7 +522,7 @@ __global__ void __launch_bounds__(TW *TH / PX) composite_bwd_kernel(Work w, cons
                 }
                 const unsigned act = __ballot_sync(0xffffffffu, any);
                 if (!act) continue;
-                const float cb = s_c[j];
+                const float cb = sc[j];
                 // Per-lane sums over the thread's pixels (one column: dx is the lane's):
                 // S0 = sum dL/de, S1 = sum dL/de dy, S2 = sum dL/de dy^2 and the colour terms;
                 // the screen-space gradients follow by the chain rule of e: du = (2a'dx) S0 +
@@ -528,7 +564,7 @@ __global__ void __launch_bounds__(TW *TH / PX) composite_bwd_kernel(Work w, cons
                                      dx * dx * S0, dx * S1, S2, S0, Cr.x + Cr.y, Cg.x + Cg.y, Cb.x + Cb.y};
                 if (__popc(act) <= kSparseLanes) {
                     if (any) {
-                        const unsigned p = s_p[j];
+                        const unsigned p = sp[j];
                         float *a = &w.g0[p].x, *b = &w.g1[p].x;
                         atomicAdd(a, vs[0]); atomicAdd(a + 1, vs[1]); atomicAdd(a + 2, vs[2]); atomicAdd(a + 3, vs[3]);
                         atomicAdd(b, vs[4]); atomicAdd(b + 1, vs[5]); atomicAdd(b + 2, vs[6]); atomicAdd(b + 3, vs[7]);
@@ -538,7 +574,7 @@ __global__ void __launch_bounds__(TW *TH / PX) composite_bwd_kernel(Work w, cons
                     int slot;
                     const float sum = warp_reduce9(vs, lane, slot);
                     if (slot < 9 && !(lane & 1)) {
-                        const unsigned p = s_p[j];
+                        const unsigned p = sp[j];
                         float *dst = slot < 4 ? &w.g0[p].x + slot : (slot < 8 ? &w.g1[p].x + (slot - 4) : w.g2 + p);
                         atomicAdd(dst, sum);
                     }

@@ -289,6 +289,19 @@ __device__ __forceinline__ float rcp_approx(float x) {  // hardware 1/x (MUFU), 
 
 __device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
 
+// Asynchronous global -> shared copies (cp.async): the copy needs no register and lands
+// while the thread computes; cp_async_wait_all() then a block barrier make it visible.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {  // both 16-byte aligned
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // Exponents of one staged Gaussian at the two pixels (px, py.x) and (px, py.y) a thread
 // owns: e = a' dx^2 + b' dx dy + c' dy^2 + log2 o, with dx shared.  Written with explicit
 // round-to-nearest (packed) operations so the forward and the backward compute
