@@ -32,7 +32,7 @@ def dev_params(g: dict) -> dict:
     return {k: torch.from_numpy(np.ascontiguousarray(v, np.float32)).cuda() for k, v in g.items()}
 
 
-class GpuRun:
+class CudaRun:
     """Forward (and optionally backward) of a batch of frames through the C ABI."""
 
     def __init__(self, ctx: gv.Context, g: dict, frames, key_capacity: int = 0):

@@ -7,7 +7,7 @@ import pytest
 import torch
 
 import oracle
-from gvtest import GpuRun, compare_grads, compare_pixels, frame_gaussians
+from gvtest import CudaRun, compare_grads, compare_pixels, frame_gaussians
 from paper_2501_04782_gb300 import gv, synth
 
 pytestmark = pytest.mark.gpu
@@ -25,7 +25,7 @@ def per_frame_runs(ctx, g, frames):
     runs = []
     for cam, off, cnt in frames:
         sub = frame_gaussians(g, off, cnt)
-        runs.append(GpuRun(ctx, sub, [(cam, 0, cnt)]).forward())
+        runs.append(CudaRun(ctx, sub, [(cam, 0, cnt)]).forward())
     return runs
 
 
@@ -33,7 +33,7 @@ def per_frame_runs(ctx, g, frames):
 def test_batched_forward_equals_per_frame(kind):
     w = small_clip() if kind == "shared" else small_uneven()
     ctx = gv.Context((16, 16), 128)
-    batch = GpuRun(ctx, w["gaussians"], w["frames"]).forward()
+    batch = CudaRun(ctx, w["gaussians"], w["frames"]).forward()
     singles = per_frame_runs(ctx, w["gaussians"], w["frames"])
     for f, run in enumerate(singles):
         assert np.array_equal(batch.frame_image(f), run.frame_image(0))
@@ -45,13 +45,13 @@ def test_batched_backward_equals_sum_of_per_frame(kind):
     w = small_clip() if kind == "shared" else small_uneven()
     g = w["gaussians"]
     ctx = gv.Context((16, 16), 128)
-    batch = GpuRun(ctx, g, w["frames"]).forward()
+    batch = CudaRun(ctx, g, w["frames"]).forward()
     rng = np.random.default_rng(3)
     dLs = [rng.normal(size=3 * cam.W * cam.H) for cam, _, _ in w["frames"]]
     gb = batch.backward(np.concatenate(dLs))
     acc = {k: np.zeros_like(v) for k, v in gb.items()}
     for (cam, off, cnt), dL in zip(w["frames"], dLs):
-        run = GpuRun(ctx, frame_gaussians(g, off, cnt), [(cam, 0, cnt)]).forward()
+        run = CudaRun(ctx, frame_gaussians(g, off, cnt), [(cam, 0, cnt)]).forward()
         gr = run.backward(dL)
         for k in acc:
             acc[k][..., off:off + cnt] += gr[k]
@@ -66,7 +66,7 @@ def test_shared_clip_matches_oracle_sampled():
     w = small_clip(F=3, N=8000, W=200, H=120)
     g = w["gaussians"]
     ctx = gv.Context((16, 16), 128)
-    run = GpuRun(ctx, g, w["frames"]).forward()
+    run = CudaRun(ctx, g, w["frames"]).forward()
     grad_ref, gabs_ref, dL = None, None, []
     for f, (cam, off, cnt) in enumerate(w["frames"]):
         px, py = synth.pixel_sample(50 + f, cam.W, cam.H, 600)
@@ -89,11 +89,11 @@ def test_graph_capture_launch_and_set_frames():
     w = small_clip(F=3)
     g = w["gaussians"]
     ctx = gv.Context((16, 16), 128)
-    direct = GpuRun(ctx, g, w["frames"]).forward()
+    direct = CudaRun(ctx, g, w["frames"]).forward()
     rng = np.random.default_rng(0)
     dL = torch.from_numpy(rng.normal(size=3 * direct.total).astype(np.float32)).cuda()
     grads_direct = direct.backward(dL.cpu().numpy())
-    run = GpuRun(ctx, g, w["frames"])
+    run = CudaRun(ctx, g, w["frames"])
     grads = {k: torch.zeros_like(v) for k, v in run.params.items()}
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
@@ -114,7 +114,7 @@ def test_graph_capture_launch_and_set_frames():
     with torch.cuda.stream(stream):
         graph.launch(stream)
     stream.synchronize()
-    ref = GpuRun(ctx, g, moved).forward()
+    ref = CudaRun(ctx, g, moved).forward()
     assert torch.equal(run.image, ref.image)
     graph.close()
 
@@ -122,7 +122,7 @@ def test_graph_capture_launch_and_set_frames():
 def test_autotune_picks_a_valid_configuration():
     w = small_clip(F=2)
     ctx = gv.Context((16, 16), 256)
-    run = GpuRun(ctx, w["gaussians"], w["frames"])
+    run = CudaRun(ctx, w["gaussians"], w["frames"])
     dL = torch.randn(3 * run.total, device="cuda")
     grads = {k: torch.zeros_like(v) for k, v in run.params.items()}
     best, ms = ctx.autotune(run.params, run.frames, run.ws, run.image, run.T, run.idx, dL, grads, reps=2)
@@ -158,12 +158,12 @@ def test_maximum_frame_count(kind):
     g = synth.concat_gaussians(sets) if kind == "own" else synth.gaussians(rng, n_per,
                                                                              box=((-1, 1), (-1, 1), (2.0, 5.0)))
     ctx = gv.Context((16, 8), 64)
-    batch = GpuRun(ctx, g, frames).forward()
+    batch = CudaRun(ctx, g, frames).forward()
     dL = np.random.default_rng(22).normal(size=3 * batch.total)
     gb = batch.backward(dL)
     acc = {k: np.zeros_like(v) for k, v in gb.items()}
     for f in range(F):
-        single = GpuRun(ctx, g, [frames[f]]).forward()
+        single = CudaRun(ctx, g, [frames[f]]).forward()
         if f % 97 == 0 or f == F - 1:
             assert np.array_equal(single.frame_image(0), batch.frame_image(f)), f
         off = 3 * batch.frames[f].pixel_offset

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gvtest import GpuRun, compare_camera, compare_grads, frame_gaussians
+from gvtest import CudaRun, compare_camera, compare_grads, frame_gaussians
 from paper_2501_04782_gb300 import gv, synth
 
 pytestmark = pytest.mark.gpu
@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 
 def camera_parity(w, frames, n_pix, label, seed, shared=True, tile=(16, 16)):
     g = w["gaussians"]
-    run = GpuRun(gv.Context(tile, 128), g, frames).forward()
+    run = CudaRun(gv.Context(tile, 128), g, frames).forward()
     dL, refs = [], []
     for f, (cam, off, cnt) in enumerate(frames):
         sub = g if shared else frame_gaussians(g, off, cnt)
@@ -63,7 +63,7 @@ def test_camera_gradient_own_sets():
 def test_camera_gradient_accumulates():
     """Two backward calls into the same buffer give twice the camera gradient."""
     w = synth.workload_single_128()
-    run = GpuRun(gv.Context((16, 16), 128), w["gaussians"], w["frames"]).forward()
+    run = CudaRun(gv.Context((16, 16), 128), w["gaussians"], w["frames"]).forward()
     cam = w["frames"][0][0]
     dL = np.random.default_rng(5).normal(size=3 * cam.W * cam.H)
     import torch

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gvtest import GpuRun, compare_grads, compare_pixels, frame_gaussians
+from gvtest import CudaRun, compare_grads, compare_pixels, frame_gaussians
 from paper_2501_04782_gb300 import gv, synth
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
@@ -19,7 +19,7 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 def batched_parity(w, frames, n_pix, label, seed=0, tile=(16, 16), depth=128, shared=True):
     g = w["gaussians"]
     ctx = gv.Context(tile, depth)
-    run = GpuRun(ctx, g, frames).forward()
+    run = CudaRun(ctx, g, frames).forward()
     N = g["opacity_logit"].shape[-1]
     grad_ref = np.zeros((oracle.NGRAD, N))
     gabs_ref = np.zeros((oracle.NGRAD, N))

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 import torch
 
-from gvtest import GpuRun
+from gvtest import CudaRun
 from paper_2501_04782_gb300 import gv, synth
 
 pytestmark = pytest.mark.gpu
@@ -15,7 +15,7 @@ pytestmark = pytest.mark.gpu
 def test_capacity_overflow_is_reported_and_retry_succeeds():
     w = synth.workload_single_128()
     ctx = gv.Context((8, 8), 64)
-    small = GpuRun(ctx, w["gaussians"], w["frames"], key_capacity=500)
+    small = CudaRun(ctx, w["gaussians"], w["frames"], key_capacity=500)
     guard = torch.full((1 << 16,), 7, dtype=torch.uint8, device="cuda")
     ws = torch.cat([small.ws, guard])  # bytes after the workspace must stay untouched
     small.ws = ws[:small.ws.numel()]
@@ -24,21 +24,21 @@ def test_capacity_overflow_is_reported_and_retry_succeeds():
     assert st == gv.GV_ERR_CAPACITY
     assert needed > 500
     assert torch.all(ws[small.ws.numel():] == 7)
-    big = GpuRun(ctx, w["gaussians"], w["frames"], key_capacity=needed).forward()
+    big = CudaRun(ctx, w["gaussians"], w["frames"], key_capacity=needed).forward()
     assert big.K == needed
 
 
 def test_bounded_wait_times_out_and_context_recovers():
     w = synth.workload_single_540p(N=40000)
     ctx = gv.Context((16, 16), 128)
-    ref = GpuRun(ctx, w["gaussians"], w["frames"]).forward()
+    ref = CudaRun(ctx, w["gaussians"], w["frames"]).forward()
     ctx.debug_set_wait(spin_limit=64, drop_signal=True)
-    run = GpuRun(ctx, w["gaussians"], w["frames"])
+    run = CudaRun(ctx, w["gaussians"], w["frames"])
     ctx.render_fwd(run.params, run.frames, run.ws, run.image, run.T, run.idx)
     st, _ = ctx.read_status(run.ws, raise_on_error=False)
     assert st == gv.GV_ERR_TIMEOUT
     ctx.debug_set_wait(0, False)
-    again = GpuRun(ctx, w["gaussians"], w["frames"]).forward()
+    again = CudaRun(ctx, w["gaussians"], w["frames"]).forward()
     assert torch.equal(again.image, ref.image)
 
 
@@ -49,7 +49,7 @@ def test_invalid_arguments_are_rejected():
         gv.Context((16, 16), 100)
     ctx = gv.Context((16, 16), 64)
     w = synth.workload_single_128(N=10)
-    run = GpuRun(ctx, w["gaussians"], w["frames"])
+    run = CudaRun(ctx, w["gaussians"], w["frames"])
     bad = [gv.Frame(w["frames"][0][0], 5, 10, 0)]  # range beyond N
     with pytest.raises(gv.GVError):
         ctx.render_fwd(run.params, bad, run.ws, run.image, run.T, run.idx)
@@ -68,7 +68,7 @@ def test_invalid_parameterisations_are_rejected():
     import ctypes
     ctx = gv.Context((16, 16), 64)
     w = synth.workload_single_128(N=10)
-    run = GpuRun(ctx, w["gaussians"], w["frames"])
+    run = CudaRun(ctx, w["gaussians"], w["frames"])
     g = gv.gaussians_struct(run.params)
     arr = gv.frame_array(run.frames)
 

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gvtest import GpuRun, compare_grads, compare_pixels, compare_split, frame_gaussians
+from gvtest import CudaRun, compare_grads, compare_pixels, compare_split, frame_gaussians
 from paper_2501_04782_gb300 import gv, synth
 
 pytestmark = pytest.mark.gpu
@@ -24,7 +24,7 @@ CANCEL_REL_SPLINE = 6e-4
 
 
 def motion_parity(g, frames, n_pix, label, seed, shared=True, tile=(16, 16)):
-    run = GpuRun(gv.Context(tile, 128), g, frames).forward()
+    run = CudaRun(gv.Context(tile, 128), g, frames).forward()
     N = g["opacity_logit"].shape[-1]
     C = g["ctrl"].shape[1]
     grad = np.zeros((oracle.NGRAD, N))
@@ -82,6 +82,6 @@ def test_constant_spline_renders_like_static():
     gs = {k: g[k] for k in ("log_scale", "quat", "opacity_logit", "rgb")}
     gs["ctrl"] = np.repeat(g["mean"][:, None, :], C, axis=1)
     cam = synth.centred_camera(256, 160, 256.0, time=0.42)
-    a = GpuRun(gv.Context((16, 16), 128), gs, [(cam, 0, 5000)]).forward()
-    b = GpuRun(gv.Context((16, 16), 128), g, [(cam, 0, 5000)]).forward()
+    a = CudaRun(gv.Context((16, 16), 128), gs, [(cam, 0, 5000)]).forward()
+    b = CudaRun(gv.Context((16, 16), 128), g, [(cam, 0, 5000)]).forward()
     assert np.max(np.abs(a.frame_image(0) - b.frame_image(0))) < 2e-5

@@ -4,7 +4,7 @@ import pytest
 import torch
 
 import oracle
-from gvtest import GpuRun
+from gvtest import CudaRun
 from paper_2501_04782_gb300 import gv, render, synth
 
 pytestmark = pytest.mark.gpu
@@ -104,7 +104,7 @@ def test_autograd_function_matches_direct_backward(form):
     tgt = torch.from_numpy(np.concatenate([t.reshape(-1) for t in w["targets"]])).cuda()
     loss = ((image - tgt) ** 2).sum()
     loss.backward()
-    direct = GpuRun(gv.Context((16, 16), 128), g, w["frames"]).forward()
+    direct = CudaRun(gv.Context((16, 16), 128), g, w["frames"]).forward()
     assert torch.equal(direct.image, image.detach())
     dL = (2 * (direct.image - tgt)).cpu().numpy()
     gd = direct.backward(dL)

@@ -6,7 +6,7 @@ import pytest
 import torch
 
 import oracle
-from gvtest import GpuRun, compare_grads, compare_pixels, frame_gaussians
+from gvtest import CudaRun, compare_grads, compare_pixels, frame_gaussians
 from paper_2501_04782_gb300 import gv, synth
 
 pytestmark = pytest.mark.gpu
@@ -15,7 +15,7 @@ CONFIGS = [((8, 8), 64), ((16, 8), 128), ((16, 16), 256), ((16, 16), 32), ((32, 
 
 
 def full_frame_check(g, cam, ctx, label):
-    run = GpuRun(ctx, g, [(cam, 0, g["opacity_logit"].shape[-1])]).forward()
+    run = CudaRun(ctx, g, [(cam, 0, g["opacity_logit"].shape[-1])]).forward()
     ref = oracle.render_image(g, cam)
     W, H = cam.W, cam.H
     img = run.frame_image(0)
@@ -46,7 +46,7 @@ def test_forward_with_background_and_ragged_tiles():
     R, t = synth.random_pose(rng, 10, 0.1)
     cam = synth.Camera(101, 67, 90.0, 95.0, 50.3, 33.9, R, t)
     ctx = gv.Context((16, 16), 64, bg=(0.2, 0.5, 0.9))
-    run = GpuRun(ctx, g, [(cam, 0, 700)]).forward()
+    run = CudaRun(ctx, g, [(cam, 0, 700)]).forward()
     ref = oracle.render_image(g, cam, oracle.Params(bg=(0.2, 0.5, 0.9)))
     compare_pixels(run.frame_image(0).reshape(3, -1).T, ref["rgb"].reshape(3, -1).T, ref["amb"].ravel(), "bg+ragged")
 
@@ -57,7 +57,7 @@ def test_backward_128x128_2k(tile, depth):
     g = w["gaussians"]
     cam = w["frames"][0][0]
     ctx = gv.Context(tile, depth)
-    run = GpuRun(ctx, g, w["frames"]).forward()
+    run = CudaRun(ctx, g, w["frames"]).forward()
     ref = oracle.render_image(g, cam)
     tgt = w["targets"][0].astype(np.float64)
     # gradient of the sum-reduced L2 loss, upstream gradient from the oracle's image,
@@ -77,7 +77,7 @@ def test_forward_backward_540p_200k_sampled():
     g = w["gaussians"]
     cam = w["frames"][0][0]
     ctx = gv.Context((16, 16), 256)
-    run = GpuRun(ctx, g, w["frames"]).forward()
+    run = CudaRun(ctx, g, w["frames"]).forward()
     px, py = synth.pixel_sample(777, cam.W, cam.H, 1500)
     ref = oracle.render_pixels(g, cam, px, py)
     img = run.frame_image(0)
@@ -99,7 +99,7 @@ def test_image_is_independent_of_tile_shape_and_stage_depth():
     w = synth.workload_single_540p(N=30000)
     imgs = []
     for tile, depth in CONFIGS:
-        run = GpuRun(gv.Context(tile, depth), w["gaussians"], w["frames"]).forward()
+        run = CudaRun(gv.Context(tile, depth), w["gaussians"], w["frames"]).forward()
         imgs.append((run.image.cpu().numpy(), run.T.cpu().numpy()))
     for im, T in imgs[1:]:
         assert np.array_equal(im, imgs[0][0])
@@ -112,18 +112,18 @@ def test_degenerate_inputs():
     # every Gaussian behind the near plane
     g = synth.gaussians(rng, 100, box=((-1, 1), (-1, 1), (-3.0, 0.19)))
     cam = synth.centred_camera(40, 30, 40.0)
-    run = GpuRun(ctx, g, [(cam, 0, 100)]).forward()
+    run = CudaRun(ctx, g, [(cam, 0, 100)]).forward()
     img = run.frame_image(0)
     assert np.allclose(img[0], 0.1) and np.allclose(img[1], 0.2) and np.allclose(img[2], 0.3)
     assert np.all(run.frame_T(0) == 1.0) and np.all(run.frame_idx(0) == -1)
     # empty Gaussian set
     e = {k: v[..., :0] for k, v in g.items()}
-    run = GpuRun(ctx, e, [(cam, 0, 0)]).forward()
+    run = CudaRun(ctx, e, [(cam, 0, 0)]).forward()
     assert np.allclose(run.frame_image(0)[2], 0.3)
     # 1x1 image
     g2 = synth.gaussians(rng, 50, box=((-0.1, 0.1), (-0.1, 0.1), (2.0, 4.0)))
     cam1 = synth.centred_camera(1, 1, 1.0)
-    run = GpuRun(gv.Context((8, 8), 32), g2, [(cam1, 0, 50)]).forward()
+    run = CudaRun(gv.Context((8, 8), 32), g2, [(cam1, 0, 50)]).forward()
     ref = oracle.render_image(g2, cam1)
     if ref["amb"][0, 0] == 0:
         assert np.max(np.abs(run.frame_image(0).ravel() - ref["rgb"].ravel())) <= 1e-4

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gvtest import GpuRun, compare_camera, compare_grads, compare_pixels, compare_split, frame_gaussians
+from gvtest import CudaRun, compare_camera, compare_grads, compare_pixels, compare_split, frame_gaussians
 from paper_2501_04782_gb300 import gv, synth
 
 pytestmark = pytest.mark.gpu
@@ -17,7 +17,7 @@ BASE_KEYS = ("mean", "vel", "log_scale", "quat", "opacity_logit", "rgb")
 
 
 def sh_parity(g, frames, n_pix, label, seed, shared=True, tile=(16, 16), cancel_rel=None):
-    run = GpuRun(gv.Context(tile, 128), g, frames).forward()
+    run = CudaRun(gv.Context(tile, 128), g, frames).forward()
     N = g["opacity_logit"].shape[-1]
     K = g["sh"].shape[1]
     C = g["ctrl"].shape[1] if "ctrl" in g else 0
@@ -90,9 +90,9 @@ def test_sh_with_time_parameterised_means():
 def test_zero_coefficients_render_exactly_like_plain_colour():
     w = synth.workload_clip_shared(F=2, N=20000, W=240, H=136)
     g = w["gaussians"]
-    a = GpuRun(gv.Context((16, 16), 128), g, w["frames"]).forward()
+    a = CudaRun(gv.Context((16, 16), 128), g, w["frames"]).forward()
     z = dict(g, sh=np.zeros((3, 15, 20000), np.float32))
-    b = GpuRun(gv.Context((16, 16), 128), z, w["frames"]).forward()
+    b = CudaRun(gv.Context((16, 16), 128), z, w["frames"]).forward()
     diff = float((a.image - b.image).abs().max())
     print(f"[sh zero] max image difference {diff:.3e}")
     assert diff <= 1e-6

@@ -5,7 +5,7 @@ import pytest
 import torch
 
 import oracle
-from gvtest import GpuRun
+from gvtest import CudaRun
 from paper_2501_04782_gb300 import gv, synth
 
 pytestmark = pytest.mark.gpu
@@ -101,7 +101,7 @@ def test_projection_matches_fp64(wl):
     g = w["gaussians"]
     cam, off, cnt = w["frames"][0]
     ctx = gv.Context((16, 16), 128)
-    run = GpuRun(ctx, g, w["frames"]).forward()
+    run = CudaRun(ctx, g, w["frames"]).forward()
     d = run.debug()
     ref = oracle.project(g, cam)
     valid = ref["valid"] > 0

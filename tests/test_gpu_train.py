@@ -7,7 +7,7 @@ import pytest
 import torch
 
 import oracle
-from gvtest import GpuRun
+from gvtest import CudaRun
 from paper_2501_04782_gb300 import gv, render, synth
 
 pytestmark = pytest.mark.gpu
@@ -16,7 +16,7 @@ pytestmark = pytest.mark.gpu
 def small_problem(F=10, N=3000, W=128, H=96):
     w = synth.workload_training(F=F, N=N, W=W, H=H)
     cams = [c for c, _, _ in w["frames"]]
-    gt = GpuRun(gv.Context((16, 16), 128), w["gt"], w["frames"]).forward()
+    gt = CudaRun(gv.Context((16, 16), 128), w["gt"], w["frames"]).forward()
     targets = gt.image.view(F, -1).clone()
     return w, cams, targets
 
@@ -35,7 +35,7 @@ def test_step_gradient_and_update_match_direct_computation(with_sh):
     assert tr.status()[0] == gv.GV_OK
     # direct: forward, loss gradient, backward on the same frames
     frames = [(cams[i], 0, tr.N) for i in ids]
-    run = GpuRun(gv.Context((16, 16), 128), {k: v.cpu().numpy() for k, v in theta0.items()}, frames).forward()
+    run = CudaRun(gv.Context((16, 16), 128), {k: v.cpu().numpy() for k, v in theta0.items()}, frames).forward()
     tgt = torch.cat([targets[i] for i in ids])
     dL = (2.0 * tr.scale * (run.image - tgt)).cpu().numpy()
     g = run.backward(dL)
@@ -71,7 +71,7 @@ def test_training_fits_the_clip():
     frames = [(c, 0, tr.N) for c in cams]
 
     def clip_psnr():
-        run = GpuRun(gv.Context((16, 16), 128), {k: v.detach().cpu().numpy() for k, v in tr.params.items()},
+        run = CudaRun(gv.Context((16, 16), 128), {k: v.detach().cpu().numpy() for k, v in tr.params.items()},
                      frames).forward()
         return render.psnr(run.image, targets.reshape(-1))
 
@@ -97,7 +97,7 @@ def test_training_with_adan_fits_the_clip(debias):
     frames = [(c, 0, tr.N) for c in cams]
 
     def clip_psnr():
-        run = GpuRun(gv.Context((16, 16), 128), {k: v.detach().cpu().numpy() for k, v in tr.params.items()},
+        run = CudaRun(gv.Context((16, 16), 128), {k: v.detach().cpu().numpy() for k, v in tr.params.items()},
                      frames).forward()
         return render.psnr(run.image, targets.reshape(-1))
 

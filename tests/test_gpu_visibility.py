@@ -8,7 +8,7 @@ import pytest
 import torch
 
 import oracle
-from gvtest import GpuRun
+from gvtest import CudaRun
 from paper_2501_04782_gb300 import gv, synth
 
 pytestmark = pytest.mark.gpu
@@ -28,7 +28,7 @@ def oracle_kept(g: dict, cam, tile) -> np.ndarray:
 
 def run_visible(g, frames, tile=(16, 16), visible=None):
     ctx = gv.Context(tile, 128)
-    run = GpuRun(ctx, g, frames)
+    run = CudaRun(ctx, g, frames)
     N = len(g["opacity_logit"])
     if visible is None:
         visible = torch.zeros(N, dtype=torch.uint8, device="cuda")

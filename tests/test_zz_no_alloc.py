@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 import torch
 
-from gvtest import PIX_TOL, GpuRun
+from gvtest import PIX_TOL, CudaRun
 from paper_2501_04782_gb300 import gv, synth
 
 pytestmark = pytest.mark.gpu
@@ -29,7 +29,7 @@ def call_noalloc(ctx, params, cam, image, T, idx):
 def test_noalloc_forward_equals_workspace_forward_on_two_calls(workload):
     w = synth.workload_single_128() if workload == "128x128_2k" else synth.workload_single_540p(N=20000)
     ctx = gv.Context((16, 16), 128)
-    ref = GpuRun(ctx, w["gaussians"], w["frames"]).forward()  # caller-allocated workspace
+    ref = CudaRun(ctx, w["gaussians"], w["frames"]).forward()  # caller-allocated workspace
     cam = w["frames"][0][0]
     for call in range(2):
         image = torch.full_like(ref.image, float("nan"))
