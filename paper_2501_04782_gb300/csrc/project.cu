@@ -5,8 +5,15 @@
 // projected onto the image plane of the frame's pinhole camera (Sec. 3.4: intrinsics
 // fx, fy, cx, cy; extrinsics R, t).  The 2D covariance is the local-affine (EWA)
 // approximation J W Sigma W^T J^T plus a 0.3 px^2 low-pass, its inverse the conic.
-// Sec. 3.2 / Eq. 3: the mean moves with time (mu_t = mu_0 + t vel), colour and opacity
-// do not.  Both kernels are HBM-bound: one thread per pair, coalesced SoA plane reads.
+// Sec. 3.2: the mean moves with time, colour and opacity do not -- a linear drift
+// mu_t = mu_0 + t vel, or Eq. 2's clamped cubic B-spline over control points with Eq. 3's
+// cubic log-scale and quaternion terms (SPLINE).  Sec. 3.1's view-dependent colour adds
+// real spherical harmonics of degree 1-3 at the direction from the camera centre (SH).
+// The forward also culls each pair's extent box per tile row against the ellipse, counts
+// the digits of the depth sort and of the tile sort's kept keys, and sets the "drawn on
+// some frame" flag (Sec. 4.1); the backward also accumulates the camera adjoint
+// (Sec. 3.4, CAM) and runs ill-conditioned pairs' geometry in FP64.  The kernels are
+// HBM-bound: one thread per pair, coalesced SoA plane reads.
 #include <algorithm>
 
 #include <type_traits>
