@@ -82,3 +82,33 @@ def test_product_path_does_not_import_the_oracle():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "oracle.c" not in src, f
+
+
+def test_options_are_validated_on_the_host(lib):
+    """gv_create checks tile shape, stage depth and background before any CUDA call, so an
+    invalid option set is refused without a GPU; a valid one reaches the device query
+    (GV_OK with a GPU, GV_ERR_CUDA without one)."""
+    from paper_2501_04782_gb300 import gv
+    lib.gv_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(gv.Options)]
+    lib.gv_destroy.argtypes = [ctypes.c_void_p]
+
+    def create(tw, th, depth, bg=(0.0, 0.0, 0.0)):
+        o = gv.Options(tw, th, depth, (ctypes.c_float * 3)(*bg))
+        h = ctypes.c_void_p()
+        st = lib.gv_create(ctypes.byref(h), ctypes.byref(o))
+        if st == 0:
+            lib.gv_destroy(h)
+        else:
+            assert not h.value  # nothing handed out on failure
+        return st
+
+    for tw, th in ((12, 12), (8, 16), (16, 32), (64, 64), (0, 0), (-8, 8)):
+        assert create(tw, th, 128) == 1, (tw, th)
+    for depth in (0, 16, 48, 100, 512):
+        assert create(16, 16, depth) == 1, depth
+    assert create(16, 16, 128, (float("nan"), 0.0, 0.0)) == 1
+    assert create(16, 16, 128, (0.0, float("inf"), 0.0)) == 1
+    assert lib.gv_create(None, None) == 1
+    for tw, th in ((8, 8), (16, 8), (16, 16), (32, 16), (32, 32)):
+        for depth in (32, 64, 128, 256):
+            assert create(tw, th, depth) in (0, 4), (tw, th, depth)
