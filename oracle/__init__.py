@@ -56,7 +56,7 @@ class _Params(ctypes.Structure):
                 ("znear", ctypes.c_double), ("ext_k", ctypes.c_double),
                 ("bg", ctypes.c_double * 3),
                 ("amb_alpha_rel", ctypes.c_double), ("amb_T_rel", ctypes.c_double),
-                ("amb_depth_rel", ctypes.c_double)]
+                ("amb_depth_ulps", ctypes.c_double)]
 
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -79,12 +79,12 @@ class Params:
     ext_k: float = EXT_K
     bg: tuple = (0.0, 0.0, 0.0)
     # ambiguity windows (decisions within FP32 reach of a threshold): alpha within 1e-5
-    # (relative) of 1/255; T within 1e-3 (relative) of the stop value -- a flipped stop
-    # changes a pixel by at most T_stop * max colour, inside the pixel tolerance anyway;
-    # consecutive contributor depths within 1e-6 (relative, ~8 FP32 ulps)
+    # (relative) of 1/255; T within T_stop * (1e-5 + the running FP32 error bound of the
+    # transmittance product) of the stop value; consecutive contributor depths within 4
+    # FP32 ulps of the larger
     amb_alpha_rel: float = 1e-5
-    amb_T_rel: float = 1e-3
-    amb_depth_rel: float = 1e-6
+    amb_T_rel: float = 1e-5
+    amb_depth_ulps: float = 4.0
 
     @staticmethod
     def smooth(**kw) -> "Params":
@@ -97,7 +97,7 @@ class Params:
         p.eps2d, p.znear, p.ext_k = self.eps2d, self.znear, self.ext_k
         for i in range(3):
             p.bg[i] = float(self.bg[i])
-        p.amb_alpha_rel, p.amb_T_rel, p.amb_depth_rel = self.amb_alpha_rel, self.amb_T_rel, self.amb_depth_rel
+        p.amb_alpha_rel, p.amb_T_rel, p.amb_depth_ulps = self.amb_alpha_rel, self.amb_T_rel, self.amb_depth_ulps
         return p
 
 
@@ -113,6 +113,9 @@ def lib():
         L.orc_render.argtypes = [ctypes.POINTER(_Gaussians), ctypes.POINTER(_Camera), ctypes.POINTER(_Params),
                                  ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
                                  _dp, _dp, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
+        L.orc_render_alts.argtypes = [ctypes.POINTER(_Gaussians), ctypes.POINTER(_Camera), ctypes.POINTER(_Params),
+                                      ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int32,
+                                      _dp, _dp] + [ctypes.c_void_p] * 5 + [ctypes.c_int]
         L.orc_render_bwd.argtypes = [ctypes.POINTER(_Gaussians), ctypes.POINTER(_Camera), ctypes.POINTER(_Params),
                                      ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, _dp,
                                      _dp, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -128,7 +131,7 @@ def lib():
                                         [ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_int64])
         L.orc_emit_cull_f32.restype = ctypes.c_int64
-        for f in (L.orc_project, L.orc_render, L.orc_render_bwd, L.orc_bin_f32, L.orc_bin_f64, L.orc_cull_f32):
+        for f in (L.orc_project, L.orc_render, L.orc_render_alts, L.orc_render_bwd, L.orc_bin_f32, L.orc_bin_f64, L.orc_cull_f32):
             f.restype = ctypes.c_int
         _LIB = L
     return _LIB
@@ -211,6 +214,35 @@ def render_pixels(g: dict, cam, px, py, params: Params | None = None, nthreads: 
     if rc:
         raise MemoryError("oracle render failed")
     return dict(rgb=rgb, T=T, last=last, amb=amb, n=cnt)
+
+
+def render_pixels_alts(g: dict, cam, px, py, params: Params | None = None, cap: int = 32,
+                       nthreads: int | None = None) -> dict:
+    """Every correct outcome of the listed pixels: where a pixel's decisions (alpha at the
+    1/255 cutoff, the stop at T < 1e-4, the order of two near-equal depths) sit within
+    FP32 reach of their threshold, each combination of their sides is a leaf.  Returns
+    rgb [n,cap,3], T [n,cap], last [n,cap], n_contrib [n,cap], dev [n,cap] (choices against
+    the FP64 one; the leaf with dev 0 is render_pixels' result), nleaves [n], overflow [n]
+    (more than cap leaves: only the first cap are listed), amb [n] (render_pixels' bits)."""
+    params = params or Params()
+    px = np.ascontiguousarray(px, np.int32)
+    py = np.ascontiguousarray(py, np.int32)
+    n = px.shape[0]
+    h = _GaussHolder(g)
+    rgb = np.zeros((n, cap, 3), np.float64)
+    T = np.zeros((n, cap), np.float64)
+    last = np.full((n, cap), -2, np.int64)
+    cnt = np.zeros((n, cap), np.int32)
+    dev = np.full((n, cap), -1, np.int32)
+    nl = np.zeros(n, np.int32)
+    amb = np.zeros(n, np.int32)
+    rc = lib().orc_render_alts(ctypes.byref(h.c), ctypes.byref(_camera(cam)), ctypes.byref(params._c()), n,
+                               px.ctypes.data, py.ctypes.data, int(cap), rgb.ctypes.data_as(_dp),
+                               T.ctypes.data_as(_dp), last.ctypes.data, cnt.ctypes.data, dev.ctypes.data,
+                               nl.ctypes.data, amb.ctypes.data, nthreads or default_threads())
+    if rc:
+        raise MemoryError("oracle render failed")
+    return dict(rgb=rgb, T=T, last=last, n_contrib=cnt, dev=dev, nleaves=np.abs(nl), overflow=nl < 0, amb=amb)
 
 
 def render_image(g: dict, cam, params: Params | None = None, nthreads: int | None = None) -> dict:

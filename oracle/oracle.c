@@ -35,12 +35,19 @@
  *   function of the parameters so central finite differences apply.
  *
  * Ambiguity flags: where the CUDA path (FP32) may legitimately take the other side of a
- * hard threshold, the pixel is flagged: bit 0 an alpha within amb_alpha_rel of
- * alpha_min, bit 1 a transmittance within amb_T_rel of T_stop, bit 2 two consecutive
- * contributors whose depths differ by less than amb_depth_rel (relative), bit 3 a
- * composited o exp(-power) within amb_alpha_rel of alpha_max (the clamp is continuous in
- * the image but switches the opacity/conic/mean gradient of that pixel on or off, so
- * this bit concerns the backward only).
+ * hard threshold, the pixel is flagged: bit 0 an alpha within amb_alpha_rel (relative) of
+ * alpha_min, bit 1 a transmittance within T_stop * tw of T_stop, bit 2 two consecutive
+ * contributors whose depths differ by at most amb_depth_ulps FP32 ulps of the larger,
+ * bit 3 a composited o exp(-power) within amb_alpha_rel of alpha_max (the clamp is
+ * continuous in the image but switches the opacity/conic/mean gradient of that pixel on
+ * or off, so this bit concerns the backward only).  tw is the running relative error
+ * bound of an FP32 transmittance product: amb_T_rel, plus per composited Gaussian two
+ * unit roundoffs (the subtraction and the product) and the relative error of its
+ * 1 - alpha (t_err_step).
+ *
+ * Where a pixel has such decisions, every combination of their two sides is a correct
+ * result of the method in FP32; orc_render_alts enumerates them (the outcome set the
+ * CUDA path's pixel must fall in), leaf by leaf, with the FP64 choices marked.
  */
 #include <math.h>
 #include <pthread.h>
@@ -59,7 +66,7 @@ typedef struct {
 typedef struct {
     double alpha_min, alpha_max, T_stop, eps2d, znear, ext_k;
     double bg[3];
-    double amb_alpha_rel, amb_T_rel, amb_depth_rel;
+    double amb_alpha_rel, amb_T_rel, amb_depth_ulps;
 } orc_params;
 
 typedef struct {
@@ -368,11 +375,14 @@ typedef struct {
     int64_t last;
     int32_t amb;
     int32_t n;        /* number of contributors */
+    int64_t nc;       /* candidates left sorted in the caller's scratch */
 } orc_pixel_result;
 
-/* Walk one pixel.  cand/contrib are caller scratch of capacity N. */
-static void render_pixel(const orc_proj *pr, int64_t N, const orc_params *p, double px, double py,
-                         orc_cand *cand, orc_contrib *contrib, orc_pixel_result *res) {
+/* Candidates of one pixel: every projected Gaussian whose alpha at the pixel centre
+ * reaches the low end of the alpha window, sorted by depth (ties by index).  Returns the
+ * count; cand is caller scratch of capacity N. */
+static int64_t gather_candidates(const orc_proj *pr, int64_t N, const orc_params *p, double px, double py,
+                                 orc_cand *cand) {
     int64_t nc = 0;
     double a_lo = p->alpha_min * (1.0 - p->amb_alpha_rel);
     for (int64_t i = 0; i < N; i++) {
@@ -388,7 +398,39 @@ static void render_pixel(const orc_proj *pr, int64_t N, const orc_params *p, dou
         c->power = power; c->dx = dx; c->dy = dy;
     }
     qsort(cand, (size_t)nc, sizeof(orc_cand), cand_cmp);
-    double T = 1.0, C[3] = {0, 0, 0};
+    return nc;
+}
+
+/* One FP32 unit in the last place at |x| (the spacing of FP32 numbers there). */
+static double f32_ulp(double x) {
+    int e;
+    frexp(fabs(x), &e);
+    return ldexp(1.0, e - 24);
+}
+
+/* Two depths an FP32 computation may order either way. */
+static int depth_close(const orc_params *p, double d0, double d1) {
+    return fabs(d1 - d0) <= p->amb_depth_ulps * f32_ulp(fmax(fabs(d0), fabs(d1)));
+}
+
+/* Relative error bound added to the FP32 transmittance product by one composited alpha:
+ * the subtraction and the product (one unit roundoff each) and the error of alpha carried
+ * into 1 - alpha.  Alpha's relative error is that of its exponent, which grows with the
+ * exponent's magnitude: amb_alpha_rel at the cutoff (power = ln 255), in proportion below
+ * it, plus four unit roundoffs for the hardware 2^x; a clamped alpha is 0.99 rounded to
+ * FP32. */
+static double t_err_step(const orc_params *p, double alpha, double power) {
+    const double u = ldexp(1.0, -24);
+    const double rel = p->amb_alpha_rel * fmin(1.0, fabs(power) / log(255.0)) + 4.0 * u;
+    const double da = alpha >= p->alpha_max ? u * alpha : rel * alpha;
+    return 2.0 * u + da / (1.0 - alpha);
+}
+
+/* Walk one pixel.  cand/contrib are caller scratch of capacity N. */
+static void render_pixel(const orc_proj *pr, int64_t N, const orc_params *p, double px, double py,
+                         orc_cand *cand, orc_contrib *contrib, orc_pixel_result *res) {
+    const int64_t nc = gather_candidates(pr, N, p, px, py, cand);
+    double T = 1.0, C[3] = {0, 0, 0}, tw = p->amb_T_rel;
     int64_t last = -1;
     int32_t amb = 0, n = 0;
     double prev_depth = -1.0;
@@ -396,7 +438,7 @@ static void render_pixel(const orc_proj *pr, int64_t N, const orc_params *p, dou
         const orc_cand *c = &cand[k];
         if (p->alpha_min > 0 && fabs(c->alpha - p->alpha_min) <= p->amb_alpha_rel * p->alpha_min) amb |= 1;
         if (c->alpha < p->alpha_min) continue;
-        if (n > 0 && fabs(c->depth - prev_depth) <= p->amb_depth_rel * fabs(c->depth)) amb |= 4;
+        if (n > 0 && depth_close(p, prev_depth, c->depth)) amb |= 4;
         prev_depth = c->depth;
         if (p->alpha_max < INFINITY && fabs(c->araw - p->alpha_max) <= p->amb_alpha_rel * p->alpha_max) amb |= 8;
         const orc_proj *q = &pr[c->idx];
@@ -408,12 +450,98 @@ static void render_pixel(const orc_proj *pr, int64_t N, const orc_params *p, dou
         n++;
         for (int ch = 0; ch < 3; ch++) C[ch] += q->c[ch] * c->alpha * T;
         T *= (1.0 - c->alpha);
+        tw += t_err_step(p, c->alpha, c->power);
         last = c->idx;
-        if (p->T_stop > 0 && fabs(T - p->T_stop) <= p->amb_T_rel * p->T_stop) amb |= 2;
+        if (p->T_stop > 0 && fabs(T - p->T_stop) <= tw * p->T_stop) amb |= 2;
         if (T < p->T_stop) break;
     }
     for (int ch = 0; ch < 3; ch++) res->C[ch] = C[ch] + T * p->bg[ch];
-    res->T = T; res->last = last; res->amb = amb; res->n = n;
+    res->T = T; res->last = last; res->amb = amb; res->n = n; res->nc = nc;
+}
+
+/* ---- every correct outcome of a pixel --------------------------------------------- */
+/* Sec. 3.1's rasterizer takes hard decisions (alpha >= 1/255, stop once T < 1e-4, depth
+ * order).  Where FP32 arithmetic can take a decision either way (the windows above), both
+ * sides are correct results; the walk below follows both, so the leaves are every correct
+ * (colour, T, last, contributor count) of the pixel.  dev counts the choices a leaf takes
+ * against the FP64 one: the leaf with dev = 0 is render_pixel's result.  Decisions:
+ *   alpha  |alpha - alpha_min| <= amb_alpha_rel alpha_min: composited or skipped;
+ *   stop   |T - T_stop| <= tw T_stop after a composited Gaussian: stop or go on;
+ *   order  two consecutive candidates within amb_depth_ulps FP32 ulps: either order (one
+ *          adjacent swap per pair; longer runs of near-equal depths get those swaps only). */
+typedef struct {
+    double C[3], T, tw;
+    int64_t last;
+    int32_t n, dev;
+} alt_state;
+
+typedef struct {
+    const orc_proj *pr;
+    const orc_params *p;
+    const orc_cand *cand;
+    int64_t nc;
+    int cap, n, overflow;
+    double *rgb, *T;  /* [cap][3], [cap] */
+    int64_t *last;    /* [cap] */
+    int32_t *cnt, *dev;
+} alt_set;
+
+static void alt_emit(alt_set *a, const alt_state *s) {
+    if (a->n >= a->cap) { a->overflow = 1; return; }
+    for (int ch = 0; ch < 3; ch++) a->rgb[a->n * 3 + ch] = s->C[ch] + s->T * a->p->bg[ch];
+    a->T[a->n] = s->T;
+    a->last[a->n] = s->last;
+    a->cnt[a->n] = s->n;
+    a->dev[a->n] = s->dev;
+    a->n++;
+}
+
+/* Continues the walk of state s: the pending candidates (pend0, then pend1) first, then
+ * cand[k..].  Every branch point recurses on one side and goes on with the other. */
+static void alt_walk(alt_set *a, const orc_cand *pend0, const orc_cand *pend1, int64_t k, alt_state s) {
+    const orc_params *p = a->p;
+    for (;;) {
+        if (a->overflow) return;
+        const orc_cand *c;
+        if (pend0) {
+            c = pend0;
+            pend0 = pend1;
+            pend1 = NULL;
+        } else {
+            if (k >= a->nc) { alt_emit(a, &s); return; }
+            if (k + 1 < a->nc && depth_close(p, a->cand[k].depth, a->cand[k + 1].depth)) {
+                alt_state sw = s;  /* the other order of the pair */
+                sw.dev++;
+                alt_walk(a, &a->cand[k + 1], &a->cand[k], k + 2, sw);
+            }
+            c = &a->cand[k++];
+        }
+        const int keep64 = c->alpha >= p->alpha_min;
+        const int either = p->alpha_min > 0 && fabs(c->alpha - p->alpha_min) <= p->amb_alpha_rel * p->alpha_min;
+        if (!keep64 && !either) continue;
+        if (either) {  /* c skipped (recursion) or composited (below); one side is FP64's */
+            alt_state skip = s;
+            if (keep64) skip.dev++; else s.dev++;
+            alt_walk(a, pend0, pend1, k, skip);
+        }
+        const orc_proj *q = &a->pr[c->idx];
+        for (int ch = 0; ch < 3; ch++) s.C[ch] += q->c[ch] * c->alpha * s.T;
+        s.T *= (1.0 - c->alpha);
+        s.tw += t_err_step(p, c->alpha, c->power);
+        s.last = c->idx;
+        s.n++;
+        if (p->T_stop > 0) {
+            const int stop64 = s.T < p->T_stop;
+            const int either_t = fabs(s.T - p->T_stop) <= s.tw * p->T_stop;
+            if (stop64 || either_t) {
+                alt_state st = s;
+                if (!stop64) st.dev++;
+                alt_emit(a, &st);
+                if (!either_t) return;
+                if (stop64) s.dev++;  /* going on past a stop FP64 takes */
+            }
+        }
+    }
 }
 
 typedef struct {
@@ -470,6 +598,67 @@ int orc_render(const orc_gaussians *g, const orc_camera *cam, const orc_params *
         render_job jb = {pr, g->N, p, npix, px, py, out_rgb, out_T, out_last, out_amb, out_n, t, nthreads, 0};
         jobs[t] = jb;
         pthread_create(&th[t], NULL, render_worker, &jobs[t]);
+    }
+    int err = 0;
+    for (int t = 0; t < nthreads; t++) { pthread_join(th[t], NULL); err |= jobs[t].err; }
+    free(th); free(jobs); free(pr);
+    return err;
+}
+
+typedef struct {
+    const orc_proj *pr;
+    int64_t N;
+    const orc_params *p;
+    int64_t npix;
+    const int32_t *px, *py;
+    int cap;
+    double *rgb, *T;
+    int64_t *last;
+    int32_t *cnt, *dev, *nleaves, *amb;
+    int tid, nthreads;
+    int err;
+} alts_job;
+
+static void *alts_worker(void *arg) {
+    alts_job *j = (alts_job *)arg;
+    orc_cand *cand = (orc_cand *)malloc(sizeof(orc_cand) * (size_t)(j->N > 0 ? j->N : 1));
+    if (!cand) { j->err = 1; return NULL; }
+    for (int64_t k = j->tid; k < j->npix; k += j->nthreads) {
+        orc_pixel_result r;
+        render_pixel(j->pr, j->N, j->p, j->px[k] + 0.5, j->py[k] + 0.5, cand, NULL, &r);
+        const int64_t o = k * j->cap;
+        alt_set a = {j->pr, j->p, cand, r.nc, j->cap, 0, 0, j->rgb + 3 * o, j->T + o, j->last + o, j->cnt + o,
+                     j->dev + o};
+        alt_state s = {{0.0, 0.0, 0.0}, 1.0, j->p->amb_T_rel, -1, 0, 0};
+        alt_walk(&a, NULL, NULL, 0, s);
+        j->nleaves[k] = a.overflow ? -a.n : a.n;
+        j->amb[k] = r.amb;
+    }
+    free(cand);
+    return NULL;
+}
+
+/* Exported: every correct outcome of the listed pixels (see alt_walk), up to cap leaves a
+ * pixel.  out_rgb [npix][cap][3], out_T / out_last / out_n / out_dev [npix][cap] (colour
+ * with background, final T, last contributor or -1, contributor count, choices against
+ * FP64), out_nleaves [npix] (leaves written; negative when the pixel has more than cap),
+ * out_amb [npix] (the flag bits of render_pixel). */
+int orc_render_alts(const orc_gaussians *g, const orc_camera *cam, const orc_params *p, int64_t npix,
+                    const int32_t *px, const int32_t *py, int32_t cap, double *out_rgb, double *out_T,
+                    int64_t *out_last, int32_t *out_n, int32_t *out_dev, int32_t *out_nleaves, int32_t *out_amb,
+                    int nthreads) {
+    if (nthreads < 1) nthreads = 1;
+    if (cap < 1) return 1;
+    if (g->sh_degree < 0 || g->sh_degree > 3 || (g->sh_degree > 0 && !g->sh)) return 1;
+    orc_proj *pr = project_all(g, cam, p);
+    if (!pr) return 1;
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nthreads);
+    alts_job *jobs = (alts_job *)malloc(sizeof(alts_job) * (size_t)nthreads);
+    for (int t = 0; t < nthreads; t++) {
+        alts_job jb = {pr, g->N, p, npix, px, py, cap, out_rgb, out_T, out_last, out_n, out_dev, out_nleaves,
+                       out_amb, t, nthreads, 0};
+        jobs[t] = jb;
+        pthread_create(&th[t], NULL, alts_worker, &jobs[t]);
     }
     int err = 0;
     for (int t = 0; t < nthreads; t++) { pthread_join(th[t], NULL); err |= jobs[t].err; }
