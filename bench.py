@@ -34,6 +34,13 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd megapixels/s at 960×540, 200k Gaussians (batched vs per-frame)"
+
+# The GPU parity test (against the FP64 oracle, at this workload's full size) that covers
+# each launch configuration the autotuner can pick; a pick outside it is flagged in the line.
+_EVERY = [(w, h, d) for (w, h) in ((8, 8), (16, 8), (16, 16), (32, 16), (32, 32)) for d in (64, 128, 256)]
+PARITY_TESTS = {
+    "frame540p": {c: "tests/test_gpu_render.py::test_540p_200k_every_autotuner_configuration" for c in _EVERY},
+}
 UNIT = "Mpix/s"
 W, H, N_GAUSS = 960, 540, 200_000
 BATCH_FRAMES = 8
@@ -362,6 +369,8 @@ def run_gv(args):
                    "frames_per_step": len(frames),
                    "tile": f"{o.tile_w}x{o.tile_h}", "stage_depth": o.stage_depth, "autotuned": not args.no_autotune,
                    "keys": counters["keys"], "l2": "512 MB write between timed steps (L2 flushed)",
+                   "parity_test": (PARITY_TESTS.get(args.workload, {}).get((o.tile_w, o.tile_h, o.stage_depth))
+                                   or "NONE: no parity test covers this launch configuration"),
                    "parallelism": "replicas" if world > 1 else "single"},
         "roofline": roofline,
         "stages": stages,
@@ -629,6 +638,8 @@ def run_training(torch, gv, synth, dev, steps, hbm_peak, alu_peak_gops):
     b.synchronize()
     t = a.elapsed_time(b) / 1000.0
     st, keys = tr.status()
+    if st != gv.GV_OK:  # a step since construction overflowed its keys or timed out
+        raise RuntimeError(f"training: a step failed with gv status {st} (key capacity or device wait)")
     psnr1 = clip_psnr(probe)
     # steady-state render rate: forward of one 1080p frame of the model
     one = [gv.Frame(cams[0], 0, N, 0)]

@@ -220,6 +220,14 @@ GV_API gv_status gv_render_bwd(gv_ctx *ctx, const gv_gaussians *g, const gv_came
 GV_API gv_status gv_read_status(gv_ctx *ctx, const void *workspace, size_t ws_bytes, gv_stream stream,
                          int64_t *keys_needed);
 
+/* OR the device-side failure bits the last render call recorded in `workspace` into *acc
+ * (a DEVICE int32 the caller zeroes), stream-ordered and without host synchronisation, so
+ * a failure in any of many launches (steps of a captured graph, say) stays visible until
+ * the caller reads *acc: bit 0 key capacity exceeded (gv_read_status's GV_ERR_CAPACITY),
+ * bit 1 a device-side wait gave up (GV_ERR_TIMEOUT).  Not part of the paper's method: a
+ * record for callers that launch many steps before they synchronise. */
+GV_API gv_status gv_status_accumulate(gv_ctx *ctx, const void *workspace, int32_t *acc, gv_stream stream);
+
 /* Synchronise `stream` and read the work counters of the last forward / backward on this
  * workspace (HOST out[6]): [0] keys emitted, [1] (frame, Gaussian) pairs, [2] (pixel,
  * Gaussian) pairs the forward evaluated, [3] always 0 (the forward does not count the pairs
@@ -366,14 +374,17 @@ GV_API gv_status gv_debug_read_grad2d(gv_ctx *ctx, const gv_frame_desc *frames, 
  * call allocates nothing (no cudaMalloc, no cudaFree, no allocating library routine);
  * image, final_T and last_idx are the caller's device buffers as for gv_render_fwd, and
  * the results are the same.
- *  - The first call on a device looks up that device's address of the array (with the
- *    device current); make that first call before any stream capture.
+ *  - Each call looks up the array's device address in the current context (the current
+ *    device's); the first call on a device also loads the library's module there, so make
+ *    that first call before any stream capture.
  *  - Every call on a device shares the one array and leaves the last call's contents in
  *    it; each call clears what must start at zero.  Calls that overlap on the GPU (two
  *    streams, two threads, two contexts of one process) race on the array: serialise them.
- *  - A frame whose Gaussian count or key count does not fit returns GV_ERR_INVALID_ARG or
- *    GV_ERR_CAPACITY with a message naming the limit.  The call synchronises `stream`
- *    before it returns, to report a key-capacity overflow. */
+ *  - A frame whose Gaussian count does not fit returns GV_ERR_INVALID_ARG, one whose keys
+ *    do not fit GV_ERR_CAPACITY (every tile then renders empty: background, T = 1, last
+ *    index -1), each with a message naming the limit; an invalid frame (size, counts)
+ *    returns GV_ERR_INVALID_ARG with gv_render_fwd's message.  The call synchronises
+ *    `stream` before it returns, to report a key-capacity overflow. */
 GV_API gv_status gv_render_fwd_noalloc(gv_ctx *ctx, const gv_gaussians *g, const gv_camera *cam,
                                        float *image, float *final_T, int32_t *last_idx,
                                        gv_stream stream);

@@ -8,7 +8,6 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
-#include <mutex>
 #include <string>
 #include <vector>
 
@@ -452,26 +451,22 @@ gv_frame_desc single_frame(const gv_camera *cam, long long N) {
 }  // namespace
 
 // Scratch of gv_render_fwd_noalloc: one device array per GPU that loads the library, held
-// until exit.  Host code needs the array's device address, looked up once per device.
+// until exit.  Host code needs the array's device address: the name is only a host-side
+// stand-in for it.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[GV_NOALLOC_SCRATCH_BYTES];
 
 namespace {
 
-constexpr int kMaxDevices = 256;
-std::mutex g_noalloc_mu;
-void *g_noalloc_addr[kMaxDevices] = {};
-
-// Device address of g_noalloc_scratch on the current device (looked up on first use).
-cudaError_t noalloc_scratch(int device, void **out) {
-    if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[device]) {
-        void *p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_addr[device] = p;
-    }
-    *out = g_noalloc_addr[device];
+// Device address of g_noalloc_scratch in the current context (the current device's), looked
+// up on every call: an address kept from an earlier call would belong to whatever context
+// was current then (a cudaDeviceReset, or another context made current on the device,
+// makes it stale).  The lookup does not allocate; the first one on a device also loads the
+// library's module there.
+cudaError_t noalloc_scratch(void **out) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    *out = p;
     return cudaSuccess;
 }
 
@@ -479,6 +474,7 @@ cudaError_t noalloc_scratch(int device, void **out) {
 
 struct gv_graph {
     gv_ctx *ctx = nullptr;
+    gv_options opt{};  // the context's options at capture (tile shape of the captured kernels)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     std::vector<cudaGraphNode_t> setup_nodes;  // in launch order, one per frame chunk
@@ -652,17 +648,19 @@ gv_status gv_render_fwd_noalloc(gv_ctx *ctx, const gv_gaussians *g, const gv_cam
     gv_status st = check_gaussians(ctx, g);
     if (st != GV_OK) return st;
     if (!image || !final_T || !last_idx) return fail(ctx, GV_ERR_INVALID_ARG, "NULL buffer");
-    int device = 0;
-    GV_CUDA(cudaGetDevice(&device));
     void *scratch = nullptr;
-    GV_CUDA(noalloc_scratch(device, &scratch));
+    GV_CUDA(noalloc_scratch(&scratch));
     gv_frame_desc d = single_frame(cam, g->N);
     Plan pl;
-    st = make_plan(ctx, ctx->opt, g->N, &d, 1, 0, GV_NOALLOC_SCRATCH_BYTES, pl, g->n_ctrl);
-    if (st != GV_OK)
+    // the frame itself first (sizes, ranges: errors passed through), then its fit
+    st = make_plan(ctx, ctx->opt, g->N, &d, 1, 1, 0, pl, g->n_ctrl);
+    if (st != GV_OK) return st;
+    if (pl.L.total > GV_NOALLOC_SCRATCH_BYTES)
         return fail(ctx, GV_ERR_INVALID_ARG,
-                    "%d Gaussians on a %dx%d frame need more than the %u-byte static scratch (%s)", (int)g->N,
-                    cam->W, cam->H, (unsigned)GV_NOALLOC_SCRATCH_BYTES, ctx->err.c_str());
+                    "%lld Gaussians on a %dx%d frame need %zu bytes before any key, more than the %u-byte static "
+                    "scratch", (long long)g->N, cam->W, cam->H, pl.L.total, (unsigned)GV_NOALLOC_SCRATCH_BYTES);
+    st = make_plan(ctx, ctx->opt, g->N, &d, 1, 0, GV_NOALLOC_SCRATCH_BYTES, pl, g->n_ctrl);
+    if (st != GV_OK) return st;
     Work w = make_work(scratch, pl.L);
     cudaStream_t s = (cudaStream_t)stream;
     // the array keeps the previous call's contents: the forward's own setup kernel clears
@@ -692,6 +690,12 @@ gv_status gv_read_status(gv_ctx *ctx, const void *workspace, size_t ws_bytes, gv
     if (h.err & ERR_CAPACITY)
         return fail(ctx, GV_ERR_CAPACITY, "the call needed %llu keys, more than the workspace holds",
                     (unsigned long long)h.keys_total);
+    return GV_OK;
+}
+
+gv_status gv_status_accumulate(gv_ctx *ctx, const void *workspace, int32_t *acc, gv_stream stream) {
+    if (!ctx || !workspace || !acc) return GV_ERR_INVALID_ARG;
+    GV_CUDA(launch_status_or(workspace, acc, (cudaStream_t)stream));
     return GV_OK;
 }
 
@@ -806,6 +810,7 @@ gv_status gv_graph_capture(gv_ctx *ctx, const gv_gaussians *g, const gv_frame_de
     gv_graph *G = new (std::nothrow) gv_graph();
     if (!G) return fail(ctx, GV_ERR_INVALID_ARG, "out of host memory");
     G->ctx = ctx;
+    G->opt = ctx->opt;
     st = make_plan(ctx, ctx->opt, g->N, frames, F, 0, ws_bytes, G->plan, g->n_ctrl);
     G->n_ctrl = g->n_ctrl;
     if (st != GV_OK) { delete G; return st; }
@@ -873,7 +878,7 @@ gv_status gv_graph_set_frames(gv_graph *G, const gv_frame_desc *frames, int32_t 
     Plan pl;
     long long N = 0;
     for (int f = 0; f < F; f++) N = std::max<long long>(N, frames[f].gauss_offset + frames[f].gauss_count);
-    gv_status st = make_plan(ctx, ctx->opt, N, frames, F, G->plan.L.key_cap, 0, pl, G->n_ctrl);
+    gv_status st = make_plan(ctx, G->opt, N, frames, F, G->plan.L.key_cap, 0, pl, G->n_ctrl);
     if (st != GV_OK) return st;
     int ci = 0;
     for (int first = 0; first < F; first += kMaxFramesPerSetup, ci++) {

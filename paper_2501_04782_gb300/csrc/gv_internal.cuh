@@ -243,6 +243,8 @@ cudaError_t launch_adam(float *p, float *g, float *m, float *v, long long n, flo
 cudaError_t launch_adan(float *p, float *g, float *m, float *v, float *nn, float *g_prev, long long n, float lr,
                         float b1, float b2, float b3, float eps, float wd, long long step, bool debias, int zero_grad,
                         cudaStream_t s);
+// acc |= the error word of the render call that last used `workspace` (header at offset 0)
+cudaError_t launch_status_or(const void *workspace, int *acc, cudaStream_t s);
 cudaError_t launch_gather_debug(const Work &w, float *mean2d, float *conic, float *opacity,
                                 float *depth, int32_t *counts, int depth_buf, cudaStream_t s);
 cudaError_t launch_grad2d_debug(const Work &w, float *out, cudaStream_t s);

@@ -173,6 +173,13 @@ __global__ void grad2d_debug_kernel(Work w, float *out) {
     for (int k = 0; k < 9; k++) out[(size_t)k * P + p] = vals[k];
 }
 
+// acc |= the device error word of the workspace's last render call (one thread).
+__global__ void status_or_kernel(const DevHeader *hdr, int *acc) {
+    pdl_prologue();
+    const unsigned e = *(volatile const unsigned *)&hdr->err;
+    if (e) atomicOr(acc, (int)e);
+}
+
 int grid_for(long long n, int per_block = 256) {
     long long b = (n + per_block - 1) / per_block;
     return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
@@ -215,6 +222,11 @@ cudaError_t launch_adan(float *p, float *g, float *m, float *v, float *nn, float
     const int grid = grid_for((n + 3) / 4);
     if (aligned16({p, g, m, v, nn, g_prev})) launch_pdl(optim_kernel<AdanOp, true>, grid, 256, 0, s, op, n);
     else launch_pdl(optim_kernel<AdanOp, false>, grid, 256, 0, s, op, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_status_or(const void *workspace, int *acc, cudaStream_t s) {
+    launch_pdl(status_or_kernel, 1, 1, 0, s, reinterpret_cast<const DevHeader *>(workspace), acc);
     return cudaGetLastError();
 }
 

@@ -23,7 +23,7 @@ EXPORTS = [
     "gv_read_status", "gv_l2_loss_grad", "gv_adam_step", "gv_adan_step", "gv_autotune", "gv_graph_capture",
     "gv_graph_set_frames", "gv_graph_launch", "gv_graph_destroy", "gv_debug_bin_sort", "gv_debug_read",
     "gv_debug_set_wait", "gv_debug_read_grad2d", "gv_profile_enable", "gv_profile_read",
-    "gv_read_counters", "gv_render_fwd_noalloc",
+    "gv_read_counters", "gv_status_accumulate", "gv_render_fwd_noalloc",
 ]
 
 STAGES = ["setup", "project", "depth_sort", "emit", "tile_sort", "ranges", "composite_fwd", "composite_bwd",
@@ -93,6 +93,7 @@ _SIGS = {
     "gv_render_bwd": [_vp, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), _vp, ctypes.c_size_t, _vp, _vp, _vp,
                       ctypes.POINTER(GaussiansGrad), _vp],
     "gv_read_status": [_vp, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(ctypes.c_int64)],
+    "gv_status_accumulate": [_vp, _vp, _vp, _vp],
     "gv_l2_loss_grad": [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_float, _vp, _vp, _vp],
     "gv_adam_step": [_vp, _vp, _vp, _vp, _vp, ctypes.c_int64, ctypes.c_int64, ctypes.c_float, ctypes.c_float,
                      ctypes.c_float, ctypes.c_float, ctypes.c_int32, _vp],
@@ -350,6 +351,13 @@ class Context:
         if raise_on_error and st != GV_OK:
             self.check(st)
         return st, k.value
+
+    def status_accumulate(self, ws: torch.Tensor, acc: torch.Tensor, stream=None):
+        """acc (device int32 [1]) |= the failure bits of the last render call on ws, on the
+        stream, without synchronising (1: key capacity exceeded, 2: a device wait gave up)."""
+        if acc.dtype != torch.int32 or acc.numel() < 1:
+            raise ValueError("acc must be a device int32 tensor")
+        self.check(self.lib.gv_status_accumulate(self.h, _ptr(ws), _ptr(acc), _stream_handle(stream)))
 
     def read_counters(self, ws: torch.Tensor, stream=None) -> dict:
         out = (ctypes.c_int64 * 6)()

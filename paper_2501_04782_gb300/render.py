@@ -177,6 +177,8 @@ class Trainer:
         self.idx = torch.empty(self.total, dtype=torch.int32, device=dev)
         self.dL = torch.empty(3 * self.total, device=dev)
         self.loss = torch.zeros(1, device=dev)
+        # failure bits of every step since construction (sticky: a failed step is never lost)
+        self.failures = torch.zeros(1, dtype=torch.int32, device=dev)
         self.target_buf = torch.empty(3 * self.total, device=dev)
         # Gaussians drawn (a kept tile key) on some frame since the last take_invisible()
         self.visible = torch.zeros(self.N, dtype=torch.uint8, device=dev)
@@ -220,6 +222,7 @@ class Trainer:
         with torch.cuda.stream(self.stream):
             self.target_buf.view(self.batch, -1).copy_(self.targets[ids])
             self.graph.launch(self.stream)
+            self.ctx.status_accumulate(self.ws, self.failures, stream=self.stream)
             self.step_count += 1
             lr = self.lr * self.lr_decay ** (self.step_count - 1)
             if self.optimizer == "adan":
@@ -233,7 +236,15 @@ class Trainer:
         return self.loss
 
     def status(self):
+        """(status of the last step, its keys): GV_ERR_CAPACITY / GV_ERR_TIMEOUT when any step
+        since construction recorded that failure (its gradients covered incomplete tile
+        lists), else GV_OK.  Synchronises the trainer's stream."""
         st, keys = self.ctx.read_status(self.ws, stream=self.stream, raise_on_error=False)
+        bits = int(self.failures.item())
+        if bits & 2:
+            st = gv.GV_ERR_TIMEOUT
+        elif bits & 1:
+            st = gv.GV_ERR_CAPACITY
         return st, keys
 
 

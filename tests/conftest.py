@@ -17,3 +17,14 @@ def pytest_configure(config):
 def oracle_lib():
     import oracle
     return oracle.lib()
+
+
+@pytest.fixture(autouse=True)
+def several_outcomes_share():
+    """After each test that compared GPU pixels with the oracle's correct outcomes: the share
+    of checked pixels with several correct outcomes, over all the frames the test checked,
+    stays under gvtest.MULTI_CAP."""
+    yield
+    gt = sys.modules.get("gvtest")
+    if gt is not None:
+        gt.check_multi_share()

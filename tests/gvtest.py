@@ -3,11 +3,21 @@ FP64 oracle on the same seeded inputs, and compare with the stated tolerances.
 
 Tolerances (from the task's accuracy bar): tile counts and sorted key lists bit-exact;
 pixel values within max-abs 1e-4; gradients within 1e-3 relative or 1e-6 absolute.
-Pixels the oracle flags as ambiguous (a decision within FP32 reach of a threshold)
-are compared at 1e-2 and counted; their upstream gradient is set to zero on both sides.
-Their share grows with the number of candidate Gaussians behind a pixel (~400 at 540p /
-200k, ~2000 at 1080p / 1M put 2-8 % of pixels within 1e-5 of the 1/255 cutoff); the cap of
-20 % only guards against a vacuous comparison.
+
+Every checked pixel is compared at 1e-4.  Where a pixel's decisions (alpha at the 1/255
+cutoff, the stop at T < 1e-4, the order of near-equal depths) sit within FP32 reach of their
+threshold, the oracle lists every correct outcome (oracle.render_pixels_alts) and the GPU
+pixel must equal one of them within 1e-4 (colour and T).  A pixel keeps its upstream
+gradient in the backward check when the GPU took the FP64 decisions: it matches the FP64
+outcome, with the same last contributor and T within 1e-3 relative (any flipped alpha moves
+T by at least 1/255 relative; FP32 rounding moves it by far less).  Pixels where the GPU
+took another correct outcome, whose FP64 outcome is not the only one consistent with the
+GPU's (two depth orders can agree in colour within 1e-4), or whose alpha sits within FP32
+reach of the 0.99 clamp (continuous in the image, not in the gradient), have their upstream
+gradient set to zero on both sides.  Only pixels the oracle lists with several outcomes (or
+the clamp) may leave the gradient check; their share is printed per test and bounded by
+MULTI_CAP (measured: 0-2 %, most of it depth pairs within 4 FP32 ulps among the ~2000
+candidates per pixel of 1080p frames of 1M Gaussians).
 A gradient element failing both bounds but within CANCEL_REL of the sum of absolute
 per-pixel contributions is counted as cancellation-limited, not hidden: each FP32
 contribution carries a relative error up to about half an ulp of the pixel coordinate
@@ -22,10 +32,25 @@ import oracle
 from paper_2501_04782_gb300 import gv, synth
 
 PIX_TOL = 1e-4
-AMB_TOL = 1e-2
+T_SAME_REL = 1e-3
+MULTI_CAP = 0.05
 GRAD_REL = 1e-3
 GRAD_ABS = 1e-6
 CANCEL_REL = 2e-4
+
+
+# pixels checked / with several correct outcomes (or the clamp) since the last check_multi_share
+_TALLY = {"n": 0, "multi": 0}
+
+
+def check_multi_share() -> None:
+    """The share of checked pixels with several correct outcomes, over everything a test
+    checked (one frame's sample is too small for a share), stays under MULTI_CAP.  Called
+    after every test (tests/conftest.py); resets the tally."""
+    n, m = _TALLY["n"], _TALLY["multi"]
+    _TALLY["n"] = _TALLY["multi"] = 0
+    print(f"[outcomes] {m} of {n} checked pixels with several correct outcomes")
+    assert m <= max(2, MULTI_CAP * n), f"{m} of {n} checked pixels have several correct outcomes"
 
 
 def dev_params(g: dict) -> dict:
@@ -40,12 +65,15 @@ class CudaRun:
         self.g = g
         self.params = dev_params(g)
         self.frames, self.total = gv.layout_frames(frames)
+        self.pair_offset = np.cumsum([0] + [f.gauss_count for f in self.frames])[:-1]
+        self._sorted_id = None
         self.ws = torch.empty(ctx.workspace_size(self.frames, key_capacity), dtype=torch.uint8, device="cuda")
         self.image = torch.full((3 * self.total,), float("nan"), device="cuda")
         self.T = torch.full((self.total,), float("nan"), device="cuda")
         self.idx = torch.full((self.total,), -7, dtype=torch.int32, device="cuda")
 
     def forward(self, grow: bool = True):
+        self._sorted_id = None
         self.ctx.render_fwd(self.params, self.frames, self.ws, self.image, self.T, self.idx)
         st, self.K = self.ctx.read_status(self.ws, raise_on_error=not grow)
         if st == gv.GV_ERR_CAPACITY:
@@ -81,6 +109,16 @@ class CudaRun:
         fr = self.frames[f]
         return self.idx[fr.pixel_offset:fr.pixel_offset + fr.cam.W * fr.cam.H].view(fr.cam.H, fr.cam.W).cpu().numpy()
 
+    def frame_last_id(self, f: int) -> np.ndarray:
+        """Last contributor of each pixel of frame f as an index into the frame's own
+        Gaussian set (-1: none): the GPU stores a position in the sorted key list."""
+        if self._sorted_id is None:
+            self._sorted_id = self.debug()["sorted_id"].cpu().numpy().view(np.uint32).astype(np.int64)
+        sid = self._sorted_id
+        idx = self.frame_idx(f)
+        pair = np.where(idx >= 0, sid[np.clip(idx, 0, max(len(sid) - 1, 0))], -1)
+        return np.where(pair >= 0, pair - self.pair_offset[f], -1)
+
     def debug(self) -> dict:
         P = sum(f.gauss_count for f in self.frames)
         tiles = sum(((f.cam.W + 7) // 8) * ((f.cam.H + 7) // 8) for f in self.frames)
@@ -91,17 +129,68 @@ def frame_gaussians(g: dict, off: int, cnt: int) -> dict:
     return {k: v[..., off:off + cnt] for k, v in g.items()}
 
 
-def compare_pixels(gpu_rgb: np.ndarray, ref_rgb: np.ndarray, amb: np.ndarray, label: str = "") -> dict:
-    """gpu_rgb, ref_rgb: [n,3]; amb: [n] ambiguity bits."""
-    err = np.abs(gpu_rgb.astype(np.float64) - ref_rgb).max(axis=1)
-    clean = (amb & oracle.AMB_IMAGE) == 0
-    st = dict(n=len(err), n_amb=int((~clean).sum()), max_clean=float(err[clean].max()) if clean.any() else 0.0,
-              max_amb=float(err[~clean].max()) if (~clean).any() else 0.0)
-    assert st["max_clean"] <= PIX_TOL, f"{label} max-abs {st['max_clean']:.3e} > {PIX_TOL} ({st})"
-    assert st["max_amb"] <= AMB_TOL, f"{label} ambiguous pixel error {st['max_amb']:.3e} > {AMB_TOL}"
-    assert st["n_amb"] <= max(3, 0.2 * st["n"]), f"{label} too many ambiguous pixels {st}"
+def compare_outcomes(gpu_rgb: np.ndarray, gpu_T: np.ndarray, gpu_last: np.ndarray, ref: dict,
+                     label: str = "") -> np.ndarray:
+    """gpu_rgb [n,3], gpu_T [n], gpu_last [n] (index into the frame's Gaussian set, -1 none);
+    ref from oracle.render_pixels_alts on the same pixels.  Asserts that every pixel equals
+    one correct outcome within PIX_TOL; returns the mask of pixels that keep their upstream
+    gradient (the GPU took the FP64 decisions, no clamp ambiguity)."""
+    n, L = ref["rgb"].shape[:2]
+    valid = np.arange(L)[None, :] < ref["nleaves"][:, None]
+    e_img = np.abs(gpu_rgb.astype(np.float64)[:, None, :] - ref["rgb"]).max(axis=2)
+    e_T = np.abs(gpu_T.astype(np.float64)[:, None] - ref["T"])
+    close = valid & (e_img <= PIX_TOL) & (e_T <= PIX_TOL)
+    matched = close.any(axis=1)
+    b = np.argmax(valid & (ref["dev"] == 0), axis=1)
+    r = np.arange(n)
+    # outcomes consistent with the GPU's decisions: colour and T within tolerance, the same
+    # last contributor, T within T_SAME_REL (a flipped alpha or stop moves T by far more)
+    full = close & (gpu_last[:, None] == ref["last"]) & (
+        np.abs(gpu_T.astype(np.float64)[:, None] - ref["T"]) <= T_SAME_REL * ref["T"] + 1e-12)
+    # the GPU took the FP64 decisions when the FP64 outcome is the only consistent one (two
+    # depth orders can agree in colour within tolerance while their gradients differ)
+    same = full[r, b] & (full.sum(axis=1) == 1)
+    clamp = (ref["amb"] & 8) != 0
+    keep = same & ~clamp
+    best = np.where(valid, np.maximum(e_img, e_T), np.inf).min(axis=1)
+    st = dict(n=n, multi=int((ref["nleaves"] > 1).sum()), no_grad=int((~keep).sum()),
+              other_outcome=int((matched & ~full[r, b]).sum()),
+              clamp=int(clamp.sum()), overflow=int(ref["overflow"].sum()), max_err=float(best.max()) if n else 0.0,
+              max_err_fp64=float(np.maximum(e_img[r, b], e_T[r, b])[same].max()) if same.any() else 0.0)
+    if not matched.all():
+        i = int(np.argmax(~matched))
+        raise AssertionError(f"{label}: {int((~matched).sum())} pixels match no correct outcome within {PIX_TOL}; "
+                             f"first: pixel {i}, gpu rgb {gpu_rgb[i]}, T {gpu_T[i]}, last {gpu_last[i]}; "
+                             f"oracle leaves rgb {ref['rgb'][i, :ref['nleaves'][i]].tolist()}, "
+                             f"T {ref['T'][i, :ref['nleaves'][i]].tolist()}, last {ref['last'][i, :ref['nleaves'][i]]} "
+                             f"({st})")
+    # a pixel leaves the gradient check only where the oracle lists more than one correct
+    # outcome (or a clamp ambiguity): a single-outcome pixel must match it in every decision
+    multi = ref["nleaves"] > 1
+    assert not (~keep & ~multi & ~clamp).any(), f"{label}: a pixel with one correct outcome took other decisions {st}"
+    _TALLY["n"] += n
+    _TALLY["multi"] += int((multi | clamp).sum())
     print(f"[pixels {label}] {st}")
-    return st
+    return keep
+
+
+def check_frame(run: "CudaRun", f: int, g_frame: dict, cam, px, py, label: str, params=None,
+                ref: dict | None = None) -> tuple[np.ndarray, dict]:
+    """Frame f of a forward run against the oracle's outcomes on pixels (px, py) (computed
+    here unless given as ref): asserts the match (compare_outcomes) and returns the mask of
+    pixels that keep their gradient, and the oracle's outcomes."""
+    if ref is None:
+        ref = oracle.render_pixels_alts(g_frame, cam, px, py, params)
+    img = run.frame_image(f)
+    assert np.all(np.isfinite(img))
+    keep = compare_outcomes(img[:, py, px].T, run.frame_T(f)[py, px], run.frame_last_id(f)[py, px], ref, label)
+    return keep, ref
+
+
+def fp64_rgb(ref: dict) -> np.ndarray:
+    """The FP64 outcome's colour [n,3] of oracle.render_pixels_alts' result."""
+    b = np.argmax((ref["dev"] == 0) & (np.arange(ref["dev"].shape[1])[None, :] < ref["nleaves"][:, None]), axis=1)
+    return ref["rgb"][np.arange(len(b)), b]
 
 
 def compare_grads(gpu: dict, ref: np.ndarray, gabs: np.ndarray, label: str = "", keys=None,

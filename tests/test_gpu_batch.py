@@ -7,7 +7,7 @@ import pytest
 import torch
 
 import oracle
-from gvtest import CudaRun, compare_grads, compare_pixels, frame_gaussians
+from gvtest import CudaRun, check_frame, compare_grads, frame_gaussians
 from paper_2501_04782_gb300 import gv, synth
 
 pytestmark = pytest.mark.gpu
@@ -70,11 +70,9 @@ def test_shared_clip_matches_oracle_sampled():
     grad_ref, gabs_ref, dL = None, None, []
     for f, (cam, off, cnt) in enumerate(w["frames"]):
         px, py = synth.pixel_sample(50 + f, cam.W, cam.H, 600)
-        ref = oracle.render_pixels(g, cam, px, py)
-        img = run.frame_image(f)
-        compare_pixels(img[:, py, px].T, ref["rgb"], ref["amb"], f"clip frame {f}")
+        keep, _ = check_frame(run, f, g, cam, px, py, f"clip frame {f}")
         d = np.random.default_rng(f).normal(size=(len(px), 3))
-        d[ref["amb"] != 0] = 0
+        d[~keep] = 0
         full = np.zeros((3, cam.H, cam.W))
         full[:, py, px] = d.T
         dL.append(full.reshape(-1))

@@ -7,7 +7,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gvtest import CudaRun, compare_camera, compare_grads, frame_gaussians
+from gvtest import CudaRun, check_frame, compare_camera, compare_grads, frame_gaussians
 from paper_2501_04782_gb300 import gv, synth
 
 pytestmark = pytest.mark.gpu
@@ -23,9 +23,9 @@ def camera_parity(w, frames, n_pix, label, seed, shared=True, tile=(16, 16)):
             px, py = synth.pixel_sample(1000 * seed + f, cam.W, cam.H, n_pix)
         else:
             py, px = (a.ravel().astype(np.int32) for a in np.mgrid[0:cam.H, 0:cam.W])
-        amb = oracle.render_pixels(sub, cam, px, py)["amb"]
+        keep, _ = check_frame(run, f, sub, cam, px, py, f"{label} frame {f}")
         d = np.random.default_rng(seed * 31 + f).normal(size=(len(px), 3))
-        d[amb != 0] = 0
+        d[~keep] = 0
         full = np.zeros((3, cam.H, cam.W))
         full[:, py, px] = d.T
         dL.append(full.reshape(-1))

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
-from gvtest import CudaRun, compare_camera, compare_grads, compare_pixels, compare_split, frame_gaussians
+from gvtest import CudaRun, check_frame, compare_camera, compare_grads, compare_split, frame_gaussians
 from paper_2501_04782_gb300 import gv, synth
 
 pytestmark = pytest.mark.gpu
@@ -28,12 +28,9 @@ def sh_parity(g, frames, n_pix, label, seed, shared=True, tile=(16, 16), cancel_
     for f, (cam, off, cnt) in enumerate(frames):
         sub = g if shared else frame_gaussians(g, off, cnt)
         px, py = synth.pixel_sample(1000 * seed + f, cam.W, cam.H, n_pix)
-        ref = oracle.render_pixels(sub, cam, px, py)
-        img = run.frame_image(f)
-        assert np.all(np.isfinite(img))
-        compare_pixels(img[:, py, px].T, ref["rgb"], ref["amb"], f"{label} frame {f}")
+        keep, _ = check_frame(run, f, sub, cam, px, py, f"{label} frame {f}")
         d = np.random.default_rng(seed * 7919 + f).normal(size=(len(px), 3))
-        d[ref["amb"] != 0] = 0
+        d[~keep] = 0
         full = np.zeros((3, cam.H, cam.W))
         full[:, py, px] = d.T
         dL.append(full.reshape(-1))

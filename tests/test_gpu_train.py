@@ -107,3 +107,25 @@ def test_training_with_adan_fits_the_clip(debias):
     print(f"[train adan debias={debias}] PSNR {p0:.2f} -> {p1:.2f} dB; loss {losses[0]:.3e} -> {losses[-1]:.3e}")
     assert p1 > p0 + 3.0
     assert np.mean(losses[-10:]) < 0.5 * np.mean(losses[:5])
+
+
+def test_failure_record_is_sticky_across_calls_and_steps():
+    """gv_status_accumulate ORs a call's failure bits into a device word without a host
+    synchronisation, so an overflowing call is not hidden by a later one that fits; the
+    trainer keeps that record over all its steps and reports it."""
+    w = synth.workload_single_128()
+    ctx = gv.Context((16, 16), 128)
+    small = CudaRun(ctx, w["gaussians"], w["frames"], key_capacity=64)  # far too few keys
+    acc = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ctx.render_fwd(small.params, small.frames, small.ws, small.image, small.T, small.idx)
+    ctx.status_accumulate(small.ws, acc)
+    ok = CudaRun(ctx, w["gaussians"], w["frames"]).forward()
+    ctx.status_accumulate(ok.ws, acc)
+    torch.cuda.synchronize()
+    assert int(acc.item()) == 1  # the capacity bit of the first call survives the second
+    wp, cams, targets = small_problem(F=6)
+    params = {k: torch.from_numpy(v).cuda() for k, v in wp["gaussians"].items()}
+    tr = render.Trainer(params, cams, targets, batch=2, lr=0.01, key_capacity=64)
+    tr.step([0, 1])
+    tr.step([2, 3])
+    assert tr.status()[0] == gv.GV_ERR_CAPACITY
