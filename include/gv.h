@@ -230,9 +230,10 @@ GV_API gv_status gv_status_accumulate(gv_ctx *ctx, const void *workspace, int32_
 
 /* Synchronise `stream` and read the work counters of the last forward / backward on this
  * workspace (HOST out[6]): [0] keys emitted, [1] (frame, Gaussian) pairs, [2] (pixel,
- * Gaussian) pairs the forward evaluated, [3] always 0 (the forward does not count the pairs
- * it composites: they are exactly the pairs the backward replays, [5]), [4] pairs the
- * backward evaluated, [5] of those the pairs replayed (alpha >= 1/255).  "Evaluated" counts,
+ * Gaussian) pairs the forward evaluated, [3] pairs with a non-empty extent box (the pairs
+ * the depth sort orders after its first pass drops the others), [4] pairs the backward
+ * evaluated, [5] of those the pairs replayed (alpha >= 1/255; exactly the pairs the
+ * forward composited).  "Evaluated" counts,
  * per pixel, the list entries up to the pixel's stop (the algorithmic work of compositing). */
 GV_API gv_status gv_read_counters(gv_ctx *ctx, const void *workspace, gv_stream stream, int64_t *out);
 

@@ -357,8 +357,12 @@ gv_status forward_stages(gv_ctx *ctx, const gv_gaussians *g, const Plan &pl, con
             StageTimer tm(ctx, GV_STAGE_DEPTH_SORT, s, sort_passes(32));
             const unsigned *n_pairs = reinterpret_cast<const unsigned *>(reinterpret_cast<const char *>(w.hdr) +
                                                                            offsetof(DevHeader, n_pairs));
+            const unsigned *n_drawn = reinterpret_cast<const unsigned *>(reinterpret_cast<const char *>(w.hdr) +
+                                                                           offsetof(DevHeader, n_drawn));
             unsigned *dk[2] = {w.dkey[0], w.dkey[1]}, *dv[2] = {w.dval[0], w.dval[1]};
-            GV_CUDA(launch_radix_sort(w, dk, dv, n_pairs, w.L.P, 32, true, true, 0, 0, ctx->num_sms, s, &dres));
+            // the first pass drops the culled pairs (no depth key); the others sort the rest
+            GV_CUDA(launch_radix_sort(w, dk, dv, n_pairs, w.L.P, 32, true, true, 0, 0, ctx->num_sms, s, &dres, 0,
+                                      n_drawn));
         }
         {
             StageTimer tm(ctx, GV_STAGE_EMIT, s, 4);
@@ -707,6 +711,7 @@ gv_status gv_read_counters(gv_ctx *ctx, const void *workspace, gv_stream stream,
     out[0] = (int64_t)h.keys_used;
     out[1] = (int64_t)h.n_pairs;
     for (int i = 0; i < 4; i++) out[2 + i] = (int64_t)h.work[i];
+    out[3] = (int64_t)h.n_drawn;  // the forward does not count composited pairs (work[1] is 0)
     return GV_OK;
 }
 
@@ -942,8 +947,11 @@ gv_status gv_debug_bin_sort(gv_ctx *ctx, int64_t n, const float *u, const float 
         int dres = 0;
         const unsigned *n_pairs = reinterpret_cast<const unsigned *>(reinterpret_cast<const char *>(w.hdr) +
                                                                        offsetof(DevHeader, n_pairs));
+        const unsigned *n_drawn = reinterpret_cast<const unsigned *>(reinterpret_cast<const char *>(w.hdr) +
+                                                                       offsetof(DevHeader, n_drawn));
         unsigned *dk[2] = {w.dkey[0], w.dkey[1]}, *dv[2] = {w.dval[0], w.dval[1]};
-        GV_CUDA(launch_radix_sort(w, dk, dv, n_pairs, w.L.P, 32, true, true, 0, 0, ctx->num_sms, s, &dres));
+        GV_CUDA(launch_radix_sort(w, dk, dv, n_pairs, w.L.P, 32, true, true, 0, 0, ctx->num_sms, s, &dres, 0,
+                                  n_drawn));
         GV_CUDA(launch_emit(w, dres, ctx->opt.tile_w, ctx->opt.tile_h, ctx->num_sms, s));
         GV_CUDA(tile_sort_rest(ctx, w, s, &tres));
     }

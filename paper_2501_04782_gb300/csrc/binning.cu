@@ -39,16 +39,18 @@ __global__ void setup_kernel(Work w, FrameChunk chunk, int first, int count, int
     for (unsigned i = tid; i < nlook; i += stride) w.look[i] = 0u;
 }
 
-// Sum of the tile counts of each block of kEmitBlock pairs taken in depth order.
+// Sum of the tile counts of each block of kEmitBlock pairs taken in depth order (the
+// n_drawn pairs with a depth key; blocks past them sum to 0).
 __global__ void __launch_bounds__(kEmitThreads) count_reduce_kernel(Work w, const unsigned *order) {
     pdl_prologue();
     __shared__ unsigned s_w[8];
     unsigned b = blockIdx.x;
     unsigned base = b * kEmitBlock;
+    const unsigned nd = min(w.hdr->n_drawn, w.L.P);
     unsigned sum = 0;
     for (int i = 0; i < kEmitItems; i++) {
         unsigned idx = base + i * kEmitThreads + threadIdx.x;
-        if (idx < w.L.P) {
+        if (idx < nd) {
             unsigned p = order[idx];
             if (p < w.L.P) sum += w.rect[p].z;  // ids are in range unless a bounded wait gave up
         }
@@ -120,7 +122,8 @@ __global__ void __launch_bounds__(1024) count_scan_kernel(Work w) {
     }
 }
 
-// Exclusive cell offsets of every pair in depth order: off[i] for i < P, off[P] = cells.
+// Exclusive cell offsets of every pair in depth order: off[i] for i < n_drawn,
+// off[n_drawn] = cells.
 // Block b scans its kEmitBlock pairs and adds the block prefix.  Each pair also records
 // the emission chunks whose first cell it owns.  Also clears look-back buffer 0 for the
 // emission chunks (the depth sort is finished with it).
@@ -130,15 +133,16 @@ __global__ void __launch_bounds__(kEmitThreads) offsets_kernel(Work w, const uns
     const unsigned b = blockIdx.x, base = b * kEmitBlock;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const unsigned nchunks = w.hdr->n_chunks;
+    const unsigned nd = min(w.hdr->n_drawn, w.L.P);
     for (unsigned i = b * kEmitThreads + t; i < nchunks * kRadix; i += gridDim.x * kEmitThreads) w.look[i] = 0u;
     // blocked: thread t owns pairs base + t*8 .. +7
     unsigned c[kEmitItems], sum = 0;
 #pragma unroll
     for (int i = 0; i < kEmitItems; i++) {
         unsigned idx = base + t * kEmitItems + i;
-        unsigned p = idx < w.L.P ? order[idx] : 0u;
+        unsigned p = idx < nd ? order[idx] : 0u;
         if (p >= w.L.P) p = 0u;  // ids are in range unless a bounded wait gave up
-        c[i] = idx < w.L.P ? w.rect[p].z : 0u;
+        c[i] = idx < nd ? w.rect[p].z : 0u;
         sum += c[i];
     }
     unsigned inc = sum;
@@ -154,7 +158,7 @@ __global__ void __launch_bounds__(kEmitThreads) offsets_kernel(Work w, const uns
 #pragma unroll
     for (int i = 0; i < kEmitItems; i++) {
         unsigned idx = base + t * kEmitItems + i;
-        if (idx < w.L.P) {
+        if (idx < nd) {
             const unsigned lo = run, hi = run + c[i];
             w.offsets[idx] = lo;
             // this pair owns the first cell of every emission chunk starting in [lo, hi)
@@ -163,7 +167,7 @@ __global__ void __launch_bounds__(kEmitThreads) offsets_kernel(Work w, const uns
         }
         run += c[i];
     }
-    if (b == 0 && t == 0) w.offsets[w.L.P] = (unsigned)min(w.hdr->cells, 0xFFFFFFFFull);
+    if (b == 0 && t == 0) w.offsets[nd] = (unsigned)min(w.hdr->cells, 0xFFFFFFFFull);
 }
 
 // Key emission fused with the first pass of the tile sort, balanced over cells.  Each
@@ -205,7 +209,7 @@ __global__ void __launch_bounds__(kEmitThreads, 4) emit_sort_kernel(Work w, Emit
     unsigned *s_keys = reinterpret_cast<unsigned *>(s_owner);
     unsigned *s_vals = s_pair;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const unsigned P = w.L.P, nchunks = w.hdr->n_chunks;
+    const unsigned P = w.L.P, nchunks = w.hdr->n_chunks, nd = min(w.hdr->n_drawn, P);
     const unsigned cells = (unsigned)min(w.hdr->cells, 0xFFFFFFFFull);
     const unsigned *off = w.offsets;
     const long long limit = w.hdr->spin_limit;
@@ -231,15 +235,15 @@ __global__ void __launch_bounds__(kEmitThreads, 4) emit_sort_kernel(Work w, Emit
         if (t == 0) {
             // the pairs owning this chunk's cells run from the owner of its first cell to the
             // owner of the next chunk's first cell (pairs after the last cell own nothing here)
-            const unsigned lo = min(w.chunk_first[chunk], P - 1u);
-            const unsigned hi = chunk + 1 < nchunks ? min(w.chunk_first[chunk + 1], P - 1u) : P - 1u;
+            const unsigned lo = min(w.chunk_first[chunk], nd - 1u);  // chunks exist only when nd > 0
+            const unsigned hi = chunk + 1 < nchunks ? min(w.chunk_first[chunk + 1], nd - 1u) : nd - 1u;
             s_lo = lo;
             s_n = min(hi >= lo ? hi - lo + 1 : 1u, (unsigned)kEmitBlock);
         }
         __syncthreads();
         const unsigned plo = s_lo, np = s_n;
         for (unsigned i = t; i <= np; i += kEmitThreads) {
-            const unsigned o = off[plo + i];  // plo + np <= P: off[P] = cells
+            const unsigned o = off[plo + i];  // plo + np <= nd: off[nd] = cells
             s_off[i] = o;
             if (i == np) break;
             const unsigned p = a.order[plo + i];
@@ -407,6 +411,7 @@ __global__ void gather_debug_kernel(Work w, float *mean2d, float *conic, float *
     unsigned p = blockIdx.x * blockDim.x + threadIdx.x;
     unsigned P = w.L.P;
     if (p >= P) return;
+    const unsigned nd = min(w.hdr->n_drawn, P);
     float4 a = w.feat0[p], b = w.feat1[p];
     if (mean2d) { mean2d[p] = a.x; mean2d[P + p] = a.y; }
     if (conic) {  // the staged record holds -log2(e) (A/2, B, C/2)
@@ -416,8 +421,9 @@ __global__ void gather_debug_kernel(Work w, float *mean2d, float *conic, float *
     }
     if (opacity) opacity[p] = exp2f(b.y);
     if (counts) counts[p] = (int32_t)w.rect[p].z;
-    // position p of the depth-sorted list holds (depth key, pair id); culled pairs: NaN
-    if (depth) depth[w.dval[depth_buf][p]] = __uint_as_float(w.dkey[depth_buf][p]);
+    // position p < n_drawn of the depth-sorted list holds (depth key, pair id); culled pairs
+    // are not in it (the caller's initial value stays)
+    if (depth && p < nd) depth[min(w.dval[depth_buf][p], P - 1u)] = __uint_as_float(w.dkey[depth_buf][p]);
 }
 
 }  // namespace

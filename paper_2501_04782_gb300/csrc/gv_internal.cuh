@@ -83,8 +83,9 @@ struct DevHeader {
     unsigned keys_used;             // min(keys_total, capacity)
     unsigned long long keys_total;  // keys (after culling) the call emits; on a capacity error,
                                     // the key capacity it needs
-    unsigned n_pairs;               // P, read by the depth sort
-    unsigned pad0;
+    unsigned n_pairs;               // P, read by the depth sort's first pass
+    unsigned n_drawn;               // pairs with a depth key (a non-empty extent box): the
+                                    // depth-sorted list holds only these, in its first n_drawn slots
     unsigned sort_ctr[16];          // tile-acquisition counters of the sort passes
     unsigned queue[4];              // persistent work-queue counters
     long long spin_limit;           // iteration limit of every device-side wait
@@ -213,10 +214,16 @@ cudaError_t launch_project_bwd(const Work &w, const GaussPtrs &g, const GradPtrs
 cudaError_t launch_project_bwd_fp64(const Work &w, const GaussPtrs &g, const GradPtrs &gr, int num_sms,
                                     cudaStream_t s);
 // sort.cu
+// Key 0xFFFFFFFF means "no key": every pass drops it (neither ranked, counted nor written),
+// so a pass writes only the live keys, compacted; digit histograms count live keys only.
+constexpr unsigned kNoKey = 0xFFFFFFFFu;
 int sort_passes(int bits);
+// n_dev: keys read by the first pass; n_dev_later (or n_dev when NULL): by the later passes
+// (the live keys the first pass kept).
 cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2], const unsigned *n_dev,
                               unsigned n_cap, int bits, bool vals_identity, bool prepared, int hist_slot,
-                              int ctr_slot, int num_sms, cudaStream_t s, int *result_buf, int first_pass = 0);
+                              int ctr_slot, int num_sms, cudaStream_t s, int *result_buf, int first_pass = 0,
+                              const unsigned *n_dev_later = nullptr);
 // Warp-aggregated count of one 8-bit digit per lane into a shared histogram row.
 __device__ __forceinline__ void count_digit(unsigned *row, unsigned d, unsigned active) {
     const unsigned peers = __match_any_sync(active, d);

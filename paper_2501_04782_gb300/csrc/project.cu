@@ -155,6 +155,7 @@ struct BinShared {
     unsigned tile[4][kRadix];
     int diff[257];
     unsigned full;
+    unsigned drawn;  // pairs with a depth key
     unsigned long long live;
 };
 
@@ -164,7 +165,7 @@ __device__ __forceinline__ void bin_shared_init(BinShared &sb) {
         (&sb.tile[0][0])[i] = 0u;
     }
     for (int i = threadIdx.x; i < 257; i += blockDim.x) sb.diff[i] = 0;
-    if (threadIdx.x == 0) { sb.full = 0u; sb.live = 0ull; }
+    if (threadIdx.x == 0) { sb.full = 0u; sb.drawn = 0u; sb.live = 0ull; }
 }
 
 // View-dependent colour (Sec. 3.1: colour as spherical harmonics of order d_c <= 3; the
@@ -356,6 +357,7 @@ __device__ __forceinline__ void bin_shared_flush(const Work &w, BinShared &sb, u
         if (c) atomicAdd(w.hist + i, c);
     }
     if (threadIdx.x == 0 && sb.live) atomicAdd(&w.hdr->keys_total, sb.live);
+    if (threadIdx.x == 0 && sb.drawn) atomicAdd(&w.hdr->n_drawn, sb.drawn);
     flush_tile_hist(tile_passes, sb.diff, sb.full, sb.tile, w.hist + 4 * kRadix);
 }
 
@@ -413,8 +415,10 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, i
         unsigned kept_lanes;
         live_sum += warp_cull_rows<false>(pb, lw, lh, tile_passes, sb, nullptr, kept_lanes);
         if (g.visible && ((kept_lanes >> (threadIdx.x & 31)) & 1u)) g.visible[gi] = 1;  // benign same-value race
-        const unsigned active = __ballot_sync(0xffffffffu, in);
-        if (in)
+        // depth digits of the pairs with a key (the sort drops the others)
+        const unsigned active = __ballot_sync(0xffffffffu, in && key != kNoKey);
+        if ((threadIdx.x & 31) == 0 && active) atomicAdd(&sb.drawn, (unsigned)__popc(active));
+        if (in && key != kNoKey)
             for (int ps = 0; ps < 4; ps++) count_digit(sb.depth[ps], (key >> (8 * ps)) & 255u, active);
     }
     bin_shared_flush(w, sb, live_sum, tile_passes);
@@ -456,8 +460,10 @@ __global__ void __launch_bounds__(256) bin_from_screen_kernel(Work w, long long 
         live_sum += warp_cull_rows<true>(pb, lw, lh, tile_passes, sb, s_warp_live, kept_lanes);
         __syncwarp();
         if (in && counts) counts[p] = (int32_t)s_live[threadIdx.x];
-        const unsigned active = __ballot_sync(0xffffffffu, in);
-        if (in)
+        // depth digits of the pairs with a key (the sort drops the others)
+        const unsigned active = __ballot_sync(0xffffffffu, in && key != kNoKey);
+        if ((threadIdx.x & 31) == 0 && active) atomicAdd(&sb.drawn, (unsigned)__popc(active));
+        if (in && key != kNoKey)
             for (int ps = 0; ps < 4; ps++) count_digit(sb.depth[ps], (key >> (8 * ps)) & 255u, active);
     }
     bin_shared_flush(w, sb, live_sum, tile_passes);

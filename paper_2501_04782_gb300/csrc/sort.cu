@@ -19,8 +19,8 @@ namespace gvk {
 
 namespace {
 
-// Per-pass digit histograms of n keys (passes of 8 bits starting at bit 0); also clears
-// look-back buffer 0 for the tiles this sort will use.
+// Per-pass digit histograms of the live keys among n (passes of 8 bits starting at bit 0);
+// also clears look-back buffer 0 for the tiles this sort will use.
 // passes == 0: the histograms were counted by the producer of the keys; only clear.
 __global__ void __launch_bounds__(256) sort_hist_kernel(const unsigned *keys, const unsigned *n_dev, unsigned n_cap,
                                                         int passes, unsigned *hist, unsigned *look0) {
@@ -32,8 +32,8 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(const unsigned *keys, co
     unsigned stride = gridDim.x * blockDim.x;
     for (unsigned base = blockIdx.x * blockDim.x; base < n; base += stride) {
         unsigned i = base + threadIdx.x;
-        bool ok = i < n;
-        unsigned k = ok ? keys[i] : 0u;
+        unsigned k = i < n ? keys[i] : kNoKey;
+        bool ok = k != kNoKey;
         unsigned active = __ballot_sync(0xffffffffu, ok);
         if (!ok) continue;
         for (int ps = 0; ps < passes; ps++) count_digit(s_h[ps], (k >> (8 * ps)) & 255u, active);
@@ -50,7 +50,7 @@ __global__ void __launch_bounds__(256) sort_hist_kernel(const unsigned *keys, co
 struct PassArgs {
     const unsigned *keys_in, *vals_in;  // vals_in == nullptr: value = input position
     unsigned *keys_out, *vals_out;
-    const unsigned *n_dev;
+    const unsigned *n_dev;  // keys this pass reads
     unsigned n_cap;
     int shift;
     const unsigned *hist;   // this pass's 256 digit counts
@@ -99,19 +99,20 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_pass_kernel(PassArgs a) 
                 k[i] = a.keys_in[idx];
                 v[i] = a.vals_in ? a.vals_in[idx] : idx;
             } else {
-                k[i] = 0xFFFFFFFFu;  // tail sentinel: ranks after every real key of digit 255
+                k[i] = kNoKey;  // past the end: dropped like any absent key
                 v[i] = 0u;
             }
         }
-        // stable rank inside the warp: by item, then by lane.  The lanes holding the same
-        // digit come from a warp match or (BALLOT, faster on sorts of many millions of keys)
-        // from eight ballots, one per digit bit.
+        // stable rank of the live keys inside the warp: by item, then by lane.  The lanes
+        // holding the same digit come from a warp match or (BALLOT, faster on sorts of many
+        // millions of keys) from eight ballots, one per digit bit; absent keys match nothing.
 #pragma unroll
         for (int i = 0; i < ITEMS; i++) {
+            const bool live = k[i] != kNoKey;
             unsigned d = (k[i] >> a.shift) & 255u;
             unsigned peers;
             if (BALLOT) {
-                peers = 0xffffffffu;
+                peers = __ballot_sync(0xffffffffu, live);
 #pragma unroll
                 for (int b = 0; b < 8; b++) {
                     const bool bit = (d >> b) & 1u;
@@ -119,12 +120,12 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_pass_kernel(PassArgs a) 
                     peers &= bit ? m : ~m;
                 }
             } else {
-                peers = __match_any_sync(0xffffffffu, d);
+                peers = __match_any_sync(0xffffffffu, live ? d : 0x100u + (unsigned)lane);
             }
-            unsigned before = s_whist[wid][d];
+            unsigned before = live ? s_whist[wid][d] : 0u;
             r[i] = before + __popc(peers & lanemask_lt());
             __syncwarp();
-            if (lane == __ffs(peers) - 1) s_whist[wid][d] = before + __popc(peers);
+            if (live && lane == __ffs(peers) - 1) s_whist[wid][d] = before + __popc(peers);
             __syncwarp();
         }
         __syncthreads();
@@ -136,21 +137,19 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_pass_kernel(PassArgs a) 
             s_whist[q][t] = total;
             total += c;
         }
-        unsigned tail = 0;  // sentinels counted in digit 255 of the last tile
-        if (t == 255 && base + TILE > n) tail = base + TILE - n;
-        const unsigned mine = total - tail;
         // decoupled look-back for digit t
         bool gave_up = false;
-        const unsigned excl = lookback_digit(a.look_cur, tile, mine, a.hdr, limit, drop, gave_up);
+        const unsigned excl = lookback_digit(a.look_cur, tile, total, a.hdr, limit, drop, gave_up);
         if (gave_up) s_abort = 1;
         unsigned dex;
-        block_excl_scan_256(total, s_scan, dex);
+        const unsigned nlive = block_excl_scan_256(total, s_scan, dex);
         s_dstart[t] = dex;
         s_gbase[t] = s_gexcl[t] + excl;
         a.look_next[(size_t)tile * kRadix + t] = 0u;
         __syncthreads();
 #pragma unroll
         for (int i = 0; i < ITEMS; i++) {
+            if (k[i] == kNoKey) continue;
             unsigned d = (k[i] >> a.shift) & 255u;
             unsigned pos = s_dstart[d] + s_whist[wid][d] + r[i];
             s_keys[pos] = k[i];
@@ -158,7 +157,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_pass_kernel(PassArgs a) 
         }
         __syncthreads();
         if (!s_abort) {
-            for (int pos = t; pos < TILE; pos += kSortThreads) {
+            for (int pos = t; pos < (int)nlive; pos += kSortThreads) {
                 unsigned key = s_keys[pos];
                 unsigned d = (key >> a.shift) & 255u;
                 unsigned gpos = s_gbase[d] + (unsigned)pos - s_dstart[d];
@@ -190,7 +189,8 @@ constexpr unsigned kSortBallotN = 1u << 22;
 // first_pass & 1, and the look-back buffer of pass first_pass is cleared).
 cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2], const unsigned *n_dev,
                               unsigned n_cap, int bits, bool vals_identity, bool prepared, int hist_slot,
-                              int ctr_slot, int num_sms, cudaStream_t s, int *result_buf, int first_pass) {
+                              int ctr_slot, int num_sms, cudaStream_t s, int *result_buf, int first_pass,
+                              const unsigned *n_dev_later) {
     int passes = sort_passes(bits);
     *result_buf = first_pass & 1;
     if (passes <= first_pass || n_cap == 0) return cudaSuccess;
@@ -214,7 +214,7 @@ cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2
         a.vals_in = (ps == 0 && vals_identity) ? nullptr : vals[cur];
         a.keys_out = keys[cur ^ 1];
         a.vals_out = vals[cur ^ 1];
-        a.n_dev = n_dev;
+        a.n_dev = ps > 0 && n_dev_later ? n_dev_later : n_dev;
         a.n_cap = n_cap;
         a.shift = 8 * ps;
         a.hist = hist + (size_t)ps * kRadix;

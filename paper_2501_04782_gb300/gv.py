@@ -362,7 +362,7 @@ class Context:
     def read_counters(self, ws: torch.Tensor, stream=None) -> dict:
         out = (ctypes.c_int64 * 6)()
         self.check(self.lib.gv_read_counters(self.h, _ptr(ws), _stream_handle(stream), out))
-        keys = ("keys", "pairs", "fwd_eval", None, "bwd_eval", "bwd_replayed")  # slot 3 is always 0
+        keys = ("keys", "pairs", "fwd_eval", "drawn", "bwd_eval", "bwd_replayed")
         return {k: v for k, v in zip(keys, list(out)) if k is not None}
 
     def l2_loss_grad(self, image, target, scale: float, dL_dimage, loss, stream=None):
