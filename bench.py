@@ -57,6 +57,61 @@ BATCH_FRAMES = 8
 #                   plus the warp reduction of 9 values over 5 levels amortised
 #                   per lane (2 * 9 * 5 / 32 ~ 3)                               = 38
 OPS_EVAL, OPS_COMP_FWD, OPS_COMP_BWD = 14, 7, 38
+# The algorithmic work of the hot-path scope table: FP32 operations per evaluated pair of the
+# compositing forward (20) and backward (45), an FMA counting as two, against the FP32 peak
+# SMs x 128 lanes x 2 x clock; bytes per unit of the HBM-bound stages.
+SPEC_OPS_FWD, SPEC_OPS_BWD = 20, 45
+
+
+def stage_work(cnt: dict, tile_passes: int, vel: bool, n_gauss: int) -> dict:
+    """stage -> (bound, algorithmic amount, amount the kernels here move) for one
+    forward + backward with the work counters cnt.  Bytes: projection 44 B read (56 with the
+    velocity) + 40 B written per drawn (frame, Gaussian) pair, 44 (56) + 4 per culled pair;
+    these kernels read 56 (68) B of parameters and write 72 B per pair (staged record 36,
+    pixel box 16, cull record 16, depth key 4).  Depth sort: key + value read and written
+    per pass (16 B), the first pass reading every pair and writing the drawn ones, the other
+    three over the drawn pairs.  Emission: 16 B per drawn pair + 8 B per key written (tile
+    id, pair id; the first tile-sort pass is fused).  Tile sort: 16 B per key per remaining
+    pass.  Projection backward: parameters (56 / 68 B) and the 36 B screen-space gradient
+    read per pair, parameter gradients read and written per Gaussian.  Compositing:
+    evaluated pairs x operations (the lane-operation form: FMA as one op, against lanes x
+    clock, beside it)."""
+    P, D, K = cnt["pairs"], cnt["drawn"], cnt["keys"]
+    rd = 56 if vel else 44
+    par = 68 if vel else 56
+    planes = 17 if vel else 14
+    return {
+        "composite_fwd": ("alu", SPEC_OPS_FWD * cnt["fwd_eval"],
+                          OPS_EVAL * cnt["fwd_eval"] + OPS_COMP_FWD * cnt["bwd_replayed"]),
+        "composite_bwd": ("alu", SPEC_OPS_BWD * cnt["bwd_eval"],
+                          OPS_EVAL * cnt["bwd_eval"] + OPS_COMP_BWD * cnt["bwd_replayed"]),
+        "project": ("hbm", D * (rd + 40) + (P - D) * (rd + 4), P * (par + 72)),
+        "depth_sort": ("hbm", 8 * P + 8 * D + 3 * 16 * D, 8 * P + 8 * D + 3 * 16 * D),
+        "emit": ("hbm", 16 * D + 8 * K, 16 * D + 8 * K),
+        "tile_sort": ("hbm", 16 * K * (tile_passes - 1), 16 * K * (tile_passes - 1)),
+        "project_bwd": ("hbm", P * (par + 36) + n_gauss * 4 * planes * 2, P * (par + 36) + n_gauss * 4 * planes * 2),
+    }
+
+
+def stage_rates(work: dict, ms: dict, hbm_peak: float, fp32_peak_gflops: float) -> dict:
+    """Per stage: achieved rate and fraction of its roofline (HBM GB/s of measured, or FP32
+    GFLOP/s against SMs x 128 x 2 x clock), from the stage's event time in ms."""
+    out = {}
+    for s, (kind, amount, moved) in work.items():
+        t_s = ms.get(s, 0.0) / 1000.0
+        if t_s <= 0:
+            continue
+        if kind == "alu":
+            a = amount / t_s / 1e9
+            lane = moved / t_s / 1e9
+            out[s] = {"ms": round(ms[s], 4), "bound": "alu", "achieved": round(a, 1), "unit": "GFLOP/s",
+                      "frac": round(a / fp32_peak_gflops, 4), "lane_ops_frac": round(lane / (fp32_peak_gflops / 2), 4)}
+        else:
+            a = amount / t_s / 1e9
+            out[s] = {"ms": round(ms[s], 4), "bound": "hbm", "achieved": round(a, 1), "unit": "GB/s",
+                      "frac": round(a / hbm_peak, 4), "moved_gbs": round(moved / t_s / 1e9, 1),
+                      "l2_resident": moved < 100e6}
+    return out
 
 
 def parse_args():
@@ -69,8 +124,12 @@ def parse_args():
     ap.add_argument("--ref-seconds", type=float, default=150.0,
                     help="oracle time budget of the whole --impl reference run (warm-up and timed steps)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-plan", action="store_true",
+                    help="also time the oracle on every configuration of the plan (minutes of host time)")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched, e2e and training legs")
     ap.add_argument("--no-training", action="store_true", help="skip the 1080p / 1M-Gaussian training leg")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 16-frame clip and the 32-frame uneven batch (one CUDA graph each)")
     ap.add_argument("--train-steps", type=int, default=20)
     ap.add_argument("--workload", default="frame540p", choices=["frame540p", "clip1080p"],
                     help="frame540p: one 960x540 frame, 200k Gaussians (the metric's configuration); "
@@ -310,38 +369,14 @@ def run_gv(args):
     mean_stage = {s: (sum(v) / len(v) if v else 0.0) for s, v in stage_ms.items()}
     dom = max(mean_stage, key=mean_stage.get)
     sm_mhz = clk.get("sm_mhz") or peaks.get("clocks_under_load", {}).get("sm_mhz_median", 1485.0)
-    alu_peak_gops = num_sms * 128 * sm_mhz / 1e3  # FP32 lanes x clock
+    alu_peak_gops = num_sms * 128 * sm_mhz / 1e3  # FP32 lanes x clock (the lane-operation form)
+    fp32_peak = 2 * alu_peak_gops                  # FP32 FLOP/s: lanes x 2 (FMA) x clock
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     o = ctx.options
     tiles = sum(math.ceil(f.cam.W / o.tile_w) * math.ceil(f.cam.H / o.tile_h) for f in frames)
     tile_passes = math.ceil(max(1, math.ceil(math.log2(tiles))) / 8)
-    npairs = counters["pairs"]
-    pbytes = 56 + (12 if "vel" in params else 0)  # parameter bytes read per pair
-    work = {
-        # the backward replays exactly the pairs the forward composited
-        "composite_fwd": ("alu", OPS_EVAL * counters["fwd_eval"] + OPS_COMP_FWD * counters["bwd_replayed"]),
-        "composite_bwd": ("alu", OPS_EVAL * counters["bwd_eval"] + OPS_COMP_BWD * counters["bwd_replayed"]),
-        "project": ("hbm", (pbytes + 56) * npairs),
-        "depth_sort": ("hbm", npairs * (4 + 4 * 16)),
-        # the first tile-sort pass is fused into the emission (cells enumerated in depth
-        # order from the pairs' offsets, rect, cull record and mean; kept keys scattered)
-        "tile_sort": ("hbm", counters["keys"] * (tile_passes - 1) * 16),
-        "emit": ("hbm", npairs * (12 + 4 + 48) + counters["keys"] * 8),
-        "project_bwd": ("hbm", npairs * (pbytes + 36) + n_gauss * 4 * (14 + (3 if "vel" in params else 0))),
-    }
-    stages = {}
-    for s, (kind, amount) in work.items():
-        t_s = mean_stage.get(s, 0.0) / 1000.0
-        if t_s <= 0:
-            continue
-        if kind == "alu":
-            a = amount / t_s / 1e9
-            stages[s] = {"ms": round(mean_stage[s], 4), "bound": "alu", "achieved": round(a, 1),
-                         "unit": "Gop/s", "frac": round(a / alu_peak_gops, 4)}
-        else:
-            a = amount / t_s / 1e9
-            stages[s] = {"ms": round(mean_stage[s], 4), "bound": "hbm", "achieved": round(a, 1), "unit": "GB/s",
-                         "frac": round(a / hbm_peak, 4), "l2_resident": amount < 100e6}
+    stages = stage_rates(stage_work(counters, tile_passes, "vel" in params, n_gauss), mean_stage, hbm_peak,
+                         fp32_peak)
     for s in ("setup", "ranges"):
         stages[s] = {"ms": round(mean_stage[s], 4)}
     d = stages.get(dom, {"bound": "alu", "achieved": None, "unit": "Gop/s", "frac": None})
@@ -354,10 +389,14 @@ def run_gv(args):
                    ("composite_bwd", "32x16", 256): 15.057664e6, ("composite_bwd", "16x16", 128): 15.471872e6,
                    ("composite_bwd", "16x8", 64): 16.441088e6}
     roofline = {"kernel": dom, "bound": d.get("bound"), "achieved": d.get("achieved"),
-                "peak": round(alu_peak_gops, 1) if d.get("bound") == "alu" else hbm_peak, "unit": d.get("unit"),
+                "peak": round(fp32_peak, 1) if d.get("bound") == "alu" else hbm_peak, "unit": d.get("unit"),
                 "frac": d.get("frac"), "traffic": ncu_traffic.get(cfg_key),
-                "peak_source": ("152 SMs x 128 FP32 lanes x median SM clock sampled during the timed region"
-                                if d.get("bound") == "alu" else "MEASURED_PEAKS.json hbm_gbs (of measured)")}
+                "peak_source": ("152 SMs x 128 FP32 lanes x 2 (FMA) x median SM clock sampled during the timed "
+                                "region; work = evaluated (pixel, Gaussian) pairs x 45 FP32 operations (x 20 for "
+                                "the forward)" if d.get("bound") == "alu" else
+                                "MEASURED_PEAKS.json hbm_gbs (of measured)")}
+    if d.get("bound") == "alu":
+        roofline["lane_ops_frac"] = d.get("lane_ops_frac")
 
     per_step_launches = sum(launches.values()) + 1  # + the loss kernel
     out = {
@@ -385,6 +424,19 @@ def run_gv(args):
         out["sh3"] = run_sh(torch, gv, synth, ctx, dev, flush, params, frames, target, max(50, args.steps // 4),
                             hbm_peak)
         out["batched"] = run_batched(torch, gv, synth, ctx, dev, flush, max(20, args.steps // 4))
+        if not args.no_configs:
+            wc = synth.workload_clip_shared()
+            out["clip16"] = run_graph_workload(
+                torch, gv, dev, flush, wc["gaussians"], wc["frames"], 20, "clip_16x960x540_300k",
+                "16 frames 960x540 sharing 300,000 Gaussians moving as mu_t = mu_0 + t v, smooth camera "
+                "trajectory; fwd + L2 + bwd, shared gradients summed over frames", autotune=True)
+            del wc
+            wu = synth.workload_uneven()
+            out["uneven32"] = run_graph_workload(
+                torch, gv, dev, flush, wu["gaussians"], wu["frames"], 10, "uneven_32_frames",
+                "32 frames of 480x270 / 960x540 / 1920x1080, each its own set of 50k-1M Gaussians "
+                "(log-uniform) and random pose; fwd + L2 + bwd", autotune=True)
+            del wu
         out["e2e"] = run_e2e(torch, gv, ctx, params, target, frames, ws, dev, flush, max(20, args.steps // 4), scale,
                              world)
         if not args.no_training:
@@ -394,6 +446,8 @@ def run_gv(args):
         out["e2e"] = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.workload == "frame540p":
         out["cpu_baseline"] = cpu_baseline(g, cam, wl["targets"][0], args.cpu_seconds)
+        if args.cpu_plan:
+            out["cpu_baseline"]["plan"] = cpu_baseline_plan()
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
@@ -592,6 +646,122 @@ def run_batched(torch, gv, synth, ctx, dev, flush, steps):
                         "graph per step (forward, L2 loss, backward) vs the plain renderer once per frame"}
 
 
+def run_graph_workload(torch, gv, dev, flush, g, frames_in, steps, name, workload, autotune):
+    """One batch of frames as one CUDA graph per step (setup, projection, sorts, emission,
+    compositing forward, L2 loss, compositing backward, projection backward), beside the
+    same launch sequence issued directly and beside the plain renderer called once per
+    frame on the same frames.  Also the sum of the per-stage event times of the direct
+    sequence, so the time between stages inside the graph is visible (graph time minus
+    that sum).  autotune: tile shape and stage depth picked by gv_autotune on this batch."""
+    params = {k: torch.from_numpy(np.ascontiguousarray(v)).to(dev) for k, v in g.items()}
+    frames, total = gv.layout_frames(frames_in)
+    ctx = gv.Context((16, 16), 128)
+    image = torch.empty(3 * total, device=dev)
+    T = torch.empty(total, device=dev)
+    idx = torch.empty(total, dtype=torch.int32, device=dev)
+    dL = torch.empty(3 * total, device=dev)
+    loss = torch.zeros(1, device=dev)
+    grads = {k: torch.zeros_like(v) for k, v in params.items()}
+    rng = np.random.default_rng(31)
+    target = torch.from_numpy(rng.uniform(0.0, 1.0, 3 * total).astype(np.float32)).to(dev)
+
+    def sized_workspace(c, fr):
+        ws = torch.empty(c.workspace_size(fr, 0), dtype=torch.uint8, device=dev)
+        c.render_fwd(params, fr, ws, image, T, idx)
+        _, keys = c.read_status(ws, raise_on_error=False)
+        del ws
+        return torch.empty(c.workspace_size(fr, int(keys * 1.1) + 65536), dtype=torch.uint8, device=dev)
+
+    # the 8x8 tilings need the most keys: size for them before the autotuner tries every shape
+    ctx.set_options(tile=(8, 8), stage_depth=64)
+    ws = sized_workspace(ctx, frames)
+    if autotune:
+        dL.normal_(0.0, 1e-3)
+        best, _ = ctx.autotune(params, frames, ws, image, T, idx, dL, grads, reps=2)
+        for v in grads.values():
+            v.zero_()
+    else:
+        ctx.set_options(tile=(16, 16), stage_depth=128)
+    o = ctx.options
+    scale = 1.0 / (3 * total)
+    stream = torch.cuda.Stream(device=dev)
+    with torch.cuda.stream(stream):
+        graph = gv.Graph(ctx, params, frames, ws, image, T, idx, dL, grads, stream, target=target,
+                         loss_scale=scale, loss=loss)
+    # the plain renderer, one frame per call (its workspace sized for the largest frame)
+    one = [[gv.Frame(f.cam, f.gauss_offset, f.gauss_count, 0)] for f in frames]
+    big = max(range(len(frames)), key=lambda i: frames[i].gauss_count * frames[i].cam.W * frames[i].cam.H)
+    ws1 = sized_workspace(ctx, one[big])
+    cap1 = 0
+    for fr1 in one:  # grow it until every frame fits
+        ctx.render_fwd(params, fr1, ws1, image, T, idx)
+        st, k1 = ctx.read_status(ws1, raise_on_error=False)
+        cap1 = max(cap1, k1)
+    ws1 = torch.empty(ctx.workspace_size(one[big], int(cap1 * 1.05) + 65536), dtype=torch.uint8, device=dev)
+
+    def graph_step():
+        graph.launch(stream)
+
+    def direct_step():
+        ctx.render_fwd(params, frames, ws, image, T, idx)
+        ctx.l2_loss_grad(image, target, scale, dL, loss)
+        ctx.render_bwd(params, frames, ws, T, idx, dL, grads)
+
+    def per_frame_step():
+        for f, fr in enumerate(frames):
+            n = fr.cam.W * fr.cam.H
+            sl = slice(3 * fr.pixel_offset, 3 * (fr.pixel_offset + n))
+            pl = slice(fr.pixel_offset, fr.pixel_offset + n)
+            ctx.render_fwd(params, one[f], ws1, image[sl], T[pl], idx[pl])
+            ctx.l2_loss_grad(image[sl], target[sl], scale, dL[sl], loss)
+            ctx.render_bwd(params, one[f], ws1, T[pl], idx[pl], dL[sl], grads)
+
+    res = {}
+    for key, fn, strm in (("graph", graph_step, stream), ("direct", direct_step, torch.cuda.current_stream()),
+                          ("per_frame", per_frame_step, torch.cuda.current_stream())):
+        with torch.cuda.stream(strm):
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            ms = []
+            for _ in range(steps):
+                flush.zero_()
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fn()
+                b.record()
+                b.synchronize()
+                ms.append(a.elapsed_time(b))
+        res[key] = statistics.median(ms)
+    st, keys = ctx.read_status(ws)
+    st1, _ = ctx.read_status(ws1)
+    # per-stage event times of the direct sequence (forward stages, then backward stages)
+    ctx.profile_enable(True)
+    sums = []
+    for _ in range(max(5, steps // 4)):
+        flush.zero_()
+        ctx.render_fwd(params, frames, ws, image, T, idx)
+        fwd_ms, _ = ctx.profile_read()
+        ctx.l2_loss_grad(image, target, scale, dL, loss)
+        ctx.render_bwd(params, frames, ws, T, idx, dL, grads)
+        bwd_ms, _ = ctx.profile_read()
+        stage = {k: v for k, v in fwd_ms.items() if v >= 0 and k not in ("composite_bwd", "project_bwd")}
+        stage.update({k: v for k, v in bwd_ms.items() if k in ("composite_bwd", "project_bwd") and v >= 0})
+        sums.append(sum(stage.values()))
+    ctx.profile_enable(False)
+    graph.close()
+    mpix = total / 1e6
+    kernel_sum = statistics.median(sums)
+    return {"value": round(mpix / (res["graph"] / 1000), 2), "unit": UNIT, "frames_per_step": len(frames),
+            "steps": steps, "ms_per_step": round(res["graph"], 4),
+            "direct_launches": round(mpix / (res["direct"] / 1000), 2),
+            "per_frame_same_frames": round(mpix / (res["per_frame"] / 1000), 2),
+            "stage_sum_ms": round(kernel_sum, 4),
+            "between_stages_frac": round((res["graph"] - kernel_sum) / res["graph"], 4),
+            "tile": f"{o.tile_w}x{o.tile_h}", "stage_depth": o.stage_depth, "autotuned": autotune,
+            "keys": int(keys), "megapixels_per_step": round(mpix, 3), "workload": workload, "name": name}
+
+
 def run_training(torch, gv, synth, dev, steps, hbm_peak, alu_peak_gops):
     """Training-step throughput on the 50-frame 1920x1080 clip: targets rendered from the
     seeded 1M-Gaussian ground truth, a perturbed 1M-Gaussian model, 8 random frames per step
@@ -711,21 +881,11 @@ def run_training(torch, gv, synth, dev, steps, hbm_peak, alu_peak_gops):
     P, K = cnt["pairs"], cnt["keys"]
     tiles = B * math.ceil(TW / tile[0]) * math.ceil(TH / tile[1])
     tpass = math.ceil(math.ceil(math.log2(tiles)) / 8)
-    amounts = {"project": ("hbm", 112 * P), "depth_sort": ("hbm", P * (4 + 4 * 16)),
-               "tile_sort": ("hbm", K * (tpass - 1) * 16), "emit": ("hbm", P * (12 + 4 + 48) + K * 8),
-               "project_bwd": ("hbm", N * 56 * 2 + P * (56 + 36)),
-               "composite_fwd": ("alu", OPS_EVAL * cnt["fwd_eval"] + OPS_COMP_FWD * cnt["bwd_replayed"]),
-               "composite_bwd": ("alu", OPS_EVAL * cnt["bwd_eval"] + OPS_COMP_BWD * cnt["bwd_replayed"])}
-    large = {"workload": f"{B} frames 1920x1080 sharing 1M Gaussians (pairs {P}, keys {K})",
+    large = {"workload": f"{B} frames 1920x1080 sharing 1M Gaussians (pairs {P}, drawn {cnt['drawn']}, keys {K})",
              "tile": f"{tile[0]}x{tile[1]}", "stage_depth": depth}
-    for k, (kind, amount) in amounts.items():
-        m = statistics.median(ms_acc.get(k, [0.0]))
-        if m <= 0:
-            continue
-        r = amount / (m / 1000) / 1e9
-        peak = hbm_peak if kind == "hbm" else alu_peak_gops
-        large[k] = {"ms": round(m, 3), "bound": kind, "achieved": round(r, 1),
-                    "unit": "GB/s" if kind == "hbm" else "Gop/s", "frac": round(r / peak, 4)}
+    med = {k: statistics.median(v) for k, v in ms_acc.items() if v}
+    for k, v in stage_rates(stage_work(cnt, tpass, "vel" in tr.params, N), med, hbm_peak, 2 * alu_peak_gops).items():
+        large[k] = v
     large["adan"] = {"ms": round(adan_ms, 3), "bound": "hbm", "achieved": round(adan_gbs, 1), "unit": "GB/s",
                      "frac": round(adan_gbs / hbm_peak, 4), "params": nflat}
     large["adam"] = {"ms": round(adam_ms, 3), "bound": "hbm", "achieved": round(adam_gbs, 1), "unit": "GB/s",
@@ -857,6 +1017,58 @@ def cpu_baseline(g, cam, tgt, seconds: float) -> dict:
     return {"value": round(n / t / 1e6, 6), "unit": UNIT, "cores": oracle.default_threads(), "kind": "oracle",
             "sample": f"{n} seeded pixels of the 960x540 / 200k-Gaussian frame, FP64 forward + analytic "
                       f"backward over all Gaussians per pixel, {t:.1f} s"}
+
+
+def cpu_baseline_plan() -> dict:
+    """The FP64 oracle (forward + analytic backward, all host cores) on each configuration of
+    the benchmark's plan: the 128x128 / 2k and 960x540 / 200k frames in full; the 16-frame
+    clip on every frame, each on a seeded 1 % pixel sample; the uneven batch and the
+    training clip on a seeded subset of 2 frames, 1 % of their pixels.  Mpix/s = pixels
+    rendered and differentiated / wall time; sampled entries are labelled extrapolated (the
+    rate of the sample, which covers the per-call projection of every Gaussian too)."""
+    import oracle
+    from paper_2501_04782_gb300 import synth
+    oracle.lib()
+
+    def timed(g, frames, frac, seed):
+        npx, t = 0, 0.0
+        for f, (cam, off, cnt) in enumerate(frames):
+            sub = {k: v[..., off:off + cnt] for k, v in g.items()}
+            n = cam.W * cam.H if frac >= 1.0 else max(64, int(frac * cam.W * cam.H))
+            if frac >= 1.0:
+                yy, xx = np.mgrid[0:cam.H, 0:cam.W]
+                px, py = xx.ravel().astype(np.int32), yy.ravel().astype(np.int32)
+            else:
+                px, py = synth.pixel_sample(seed + f, cam.W, cam.H, n)
+            t0 = time.perf_counter()
+            r = oracle.render_pixels(sub, cam, px, py)
+            d = np.random.default_rng(seed + f).normal(size=(len(px), 3)) * 1e-3
+            oracle.render_bwd_pixels(sub, cam, px, py, d, want_abs=False, want_2d=False)
+            t += time.perf_counter() - t0
+            npx += len(px)
+        return npx, t
+
+    plan = {}
+    w1 = synth.workload_single_128()
+    w2 = synth.workload_single_540p()
+    w3 = synth.workload_clip_shared()
+    w4 = synth.workload_uneven()
+    w5 = synth.workload_training()
+    rng = np.random.default_rng(5)
+    sub4 = [w4["frames"][i] for i in sorted(rng.choice(len(w4["frames"]), 2, replace=False))]
+    sub5 = [w5["frames"][i] for i in sorted(rng.choice(len(w5["frames"]), 2, replace=False))]
+    for key, g, frames, frac, label in (
+            ("config1_128x128_2k", w1["gaussians"], w1["frames"], 1.0, "full frame"),
+            ("config2_960x540_200k", w2["gaussians"], w2["frames"], 1.0, "full frame"),
+            ("config3_clip_16x960x540_300k", w3["gaussians"], w3["frames"], 0.01,
+             "all 16 frames, 1 % seeded pixel sample each (extrapolated)"),
+            ("config4_uneven_32", w4["gaussians"], sub4, 0.01,
+             "seeded 2-frame subset, 1 % pixel sample (extrapolated)"),
+            ("config5_training_1080p_1m", w5["gaussians"], sub5, 0.01,
+             "seeded 2-frame subset, 1 % pixel sample (extrapolated)")):
+        npx, t = timed(g, frames, frac, 777)
+        plan[key] = {"mpix_s": round(npx / t / 1e6, 6), "pixels": npx, "seconds": round(t, 2), "sample": label}
+    return plan
 
 
 def run_reference(args):
