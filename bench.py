@@ -425,6 +425,10 @@ def run_gv(args):
                             hbm_peak)
         out["batched"] = run_batched(torch, gv, synth, ctx, dev, flush, max(20, args.steps // 4))
         if not args.no_configs:
+            w1 = synth.workload_single_128()
+            out["frame128"] = run_graph_workload(
+                torch, gv, dev, flush, w1["gaussians"], w1["frames"], 50, "frame_128x128_2k",
+                "one 128x128 frame, 2,000 Gaussians, identity pose; fwd + L2 + bwd", autotune=True)
             wc = synth.workload_clip_shared()
             out["clip16"] = run_graph_workload(
                 torch, gv, dev, flush, wc["gaussians"], wc["frames"], 20, "clip_16x960x540_300k",

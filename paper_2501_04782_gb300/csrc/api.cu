@@ -201,8 +201,7 @@ gv_status make_plan(gv_ctx *ctx, const gv_options &o, long long N, const gv_fram
     L.dkey[1] = take(4 * Pn);
     L.dval[0] = take(4 * Pn);
     L.dval[1] = take(4 * Pn);
-    L.blocksum = take(4 * std::max<size_t>(L.emit_blocks, 1));
-    L.blockprefix = take(4 * std::max<size_t>(L.emit_blocks, 1));
+    L.scan_look = take(8 * std::max<size_t>(L.emit_blocks, 1));
     L.offsets = take(4 * (Pn + 1));
     L.g0 = take(16 * Pn);
     L.g1 = take(16 * Pn);
@@ -270,8 +269,7 @@ Work make_work(void *ws, const Layout &L) {
         w.tkey[i] = (unsigned *)(b + L.tkey[i]);
         w.tval[i] = (unsigned *)(b + L.tval[i]);
     }
-    w.blocksum = (unsigned *)(b + L.blocksum);
-    w.blockprefix = (unsigned *)(b + L.blockprefix);
+    w.scan_look = (unsigned long long *)(b + L.scan_look);
     w.offsets = (unsigned *)(b + L.offsets);
     w.chunk_first = (unsigned *)(b + L.chunk_first);
     w.g0 = (float4 *)(b + L.g0);
@@ -365,7 +363,7 @@ gv_status forward_stages(gv_ctx *ctx, const gv_gaussians *g, const Plan &pl, con
                                       n_drawn));
         }
         {
-            StageTimer tm(ctx, GV_STAGE_EMIT, s, 4);
+            StageTimer tm(ctx, GV_STAGE_EMIT, s, 2);
             GV_CUDA(launch_emit(w, dres, o.tile_w, o.tile_h, ctx->num_sms, s));
         }
         int tres = 0;

@@ -34,140 +34,138 @@ __global__ void setup_kernel(Work w, FrameChunk chunk, int first, int count, int
     }
     for (int i = tid; i < 8 * kRadix; i += stride) w.hist[i] = 0u;
     for (unsigned i = tid; i < w.L.tiles; i += stride) w.ranges[i] = make_uint2(0u, 0u);
+    for (unsigned i = tid; i < w.L.emit_blocks; i += stride) w.scan_look[i] = 0ull;
     // look-back buffer 0 of the depth sort (its digits are counted by the projection)
     const unsigned nlook = sort_tiles(w.L.P, w.L.P) * kRadix;
     for (unsigned i = tid; i < nlook; i += stride) w.look[i] = 0u;
 }
 
-// Sum of the tile counts of each block of kEmitBlock pairs taken in depth order (the
-// n_drawn pairs with a depth key; blocks past them sum to 0).
-__global__ void __launch_bounds__(kEmitThreads) count_reduce_kernel(Work w, const unsigned *order) {
-    pdl_prologue();
-    __shared__ unsigned s_w[8];
-    unsigned b = blockIdx.x;
-    unsigned base = b * kEmitBlock;
-    const unsigned nd = min(w.hdr->n_drawn, w.L.P);
-    unsigned sum = 0;
-    for (int i = 0; i < kEmitItems; i++) {
-        unsigned idx = base + i * kEmitThreads + threadIdx.x;
-        if (idx < nd) {
-            unsigned p = order[idx];
-            if (p < w.L.P) sum += w.rect[p].z;  // ids are in range unless a bounded wait gave up
-        }
+// Cell offsets in one pass.  Each block takes the next run of kEmitBlock depth-ordered
+// drawn pairs from a ticket counter, scans their cell counts (the tiles of their extent
+// boxes), gets the cells of all earlier runs by decoupled look-back over 64-bit status words
+// (flag in the top two bits), and writes every pair's exclusive offset: off[i] for
+// i < n_drawn, off[n_drawn] = cells.  Each pair records the emission chunks whose first cell
+// it owns, and each block clears the emission's look-back words of the chunks that start in
+// its cells.  The block holding the last run checks the capacities: the kept keys (counted
+// by the projection) against the key capacity, the cells against the chunk table; on
+// overflow keys_total reports the key capacity the call needs.  Every wait is bounded: a
+// look-back that gives up sets ERR_TIMEOUT (the offsets are then wrong but every write
+// stays in bounds).
+constexpr unsigned long long kScanAgg = 1ull << 62, kScanInc = 2ull << 62, kScanVal = (1ull << 62) - 1ull;
+constexpr int kScanCtr = 12;
+
+__device__ __forceinline__ void finish_cells(Work &w, unsigned long long cells) {
+    const unsigned long long K = w.hdr->keys_total;
+    const unsigned long long chunks = (cells + kEmitBlock - 1) / kEmitBlock;
+    bool over = K > w.L.key_cap;
+    const bool table = chunks > w.L.chunk_cap || cells > 0xFFFFFFFFull;
+    if (table) {
+        over = true;
+        const unsigned long long need = (cells + kCellsPerKey - 1) / kCellsPerKey + kEmitBlock;
+        w.hdr->keys_total = max(K, need);
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if ((threadIdx.x & 31) == 0) s_w[threadIdx.x >> 5] = sum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned tot = 0;
-        for (int i = 0; i < kEmitThreads / 32; i++) tot += s_w[i];
-        w.blocksum[b] = tot;
-    }
+    w.hdr->cells = cells;
+    w.hdr->keys_used = (unsigned)min(K, (unsigned long long)w.L.key_cap);
+    w.hdr->n_chunks = table ? 0u : (unsigned)chunks;
+    if (over) atomicOr(&w.hdr->err, ERR_CAPACITY);
 }
 
-// Exclusive scan of the block cell sums (single block), cell total, chunk count and the
-// capacity checks: the kept keys (counted by the projection) against the key capacity,
-// the cells against the chunk table.  On overflow keys_total reports the key capacity
-// the call needs.
-__global__ void __launch_bounds__(1024) count_scan_kernel(Work w) {
+__global__ void __launch_bounds__(kEmitThreads) cell_offsets_kernel(Work w, const unsigned *order) {
     pdl_prologue();
-    __shared__ unsigned long long s_w[32];
-    __shared__ unsigned long long s_carry;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    const unsigned nb = w.L.emit_blocks;
-    for (unsigned base = 0; base < nb; base += 1024) {
-        unsigned i = base + threadIdx.x;
-        unsigned long long x = i < nb ? w.blocksum[i] : 0ull;
-        unsigned long long inc = x;
+    __shared__ unsigned long long s_w[kEmitThreads / 32];
+    __shared__ unsigned long long s_excl;
+    __shared__ unsigned s_blk;
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const unsigned P = w.L.P, nd = min(w.hdr->n_drawn, P);
+    const unsigned nblk = (nd + kEmitBlock - 1) / kEmitBlock;
+    const long long limit = w.hdr->spin_limit;
+    unsigned *look0 = w.look;  // the emission's look-back words (buffer 0)
+    if (nblk == 0) {
+        if (blockIdx.x == 0 && t == 0) {
+            w.offsets[0] = 0u;
+            finish_cells(w, 0ull);
+        }
+        return;
+    }
+    for (;;) {
+        if (t == 0) s_blk = atomicAdd(&w.hdr->sort_ctr[kScanCtr], 1u);
+        __syncthreads();
+        const unsigned b = s_blk;
+        if (b >= nblk) break;
+        const unsigned base = b * kEmitBlock;
+        // blocked: thread t owns the pairs base + 8t .. base + 8t + 7
+        unsigned c[kEmitItems];
+        unsigned long long sum = 0;
+#pragma unroll
+        for (int i = 0; i < kEmitItems; i++) {
+            const unsigned idx = base + t * kEmitItems + i;
+            unsigned p = idx < nd ? order[idx] : 0u;
+            if (p >= P) p = 0u;  // ids are in range unless a bounded wait gave up
+            c[i] = idx < nd ? w.rect[p].z : 0u;
+            sum += c[i];
+        }
+        unsigned long long inc = sum;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
-            unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += y;
         }
         if (lane == 31) s_w[wid] = inc;
         __syncthreads();
-        if (wid == 0) {
-            unsigned long long t = s_w[lane], ti = t;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                unsigned long long y = __shfl_up_sync(0xffffffffu, ti, o);
-                if (lane >= o) ti += y;
+        if (t == 0) {
+            unsigned long long total = 0;
+            for (int q = 0; q < kEmitThreads / 32; q++) total += s_w[q];
+            unsigned long long excl = 0;
+            if (b == 0) {
+                atomicExch(&w.scan_look[0], kScanInc | (total & kScanVal));
+            } else {
+                atomicExch(&w.scan_look[b], kScanAgg | (total & kScanVal));
+                long long spins = 0;
+                int j = (int)b - 1;
+                for (;;) {
+                    const unsigned long long st = *((volatile unsigned long long *)&w.scan_look[j]);
+                    const unsigned long long fl = st & ~kScanVal;
+                    if (fl == kScanInc) { excl += st & kScanVal; break; }
+                    if (fl == kScanAgg) { excl += st & kScanVal; j--; spins = 0; continue; }
+                    if (++spins > limit || (*((volatile unsigned *)&w.hdr->err) & ERR_TIMEOUT)) {
+                        atomicOr(&w.hdr->err, ERR_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(32);
+                }
+                atomicExch(&w.scan_look[b], kScanInc | ((excl + total) & kScanVal));
             }
-            s_w[lane] = ti - t;
+            s_excl = excl;
+            if (b == nblk - 1) {
+                w.offsets[nd] = (unsigned)min(excl + total, 0xFFFFFFFFull);
+                finish_cells(w, excl + total);
+            }
         }
         __syncthreads();
-        unsigned long long ex = s_carry + s_w[wid] + inc - x;
-        // prefixes past 2^32 - 1 cells are clamped (the call fails the capacity check)
-        if (i < nb) w.blockprefix[i] = (unsigned)min(ex, 0xFFFFFFFFull);
-        __syncthreads();
-        if (threadIdx.x == 1023) s_carry = ex + x;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        const unsigned long long cells = s_carry, K = w.hdr->keys_total;
-        const unsigned long long chunks = (cells + kEmitBlock - 1) / kEmitBlock;
-        bool over = K > w.L.key_cap;
-        if (chunks > w.L.chunk_cap || cells > 0xFFFFFFFFull) {
-            over = true;
-            const unsigned long long need = (cells + kCellsPerKey - 1) / kCellsPerKey + kEmitBlock;
-            w.hdr->keys_total = max(K, need);
+        unsigned long long run = s_excl + inc - sum;
+        for (int q = 0; q < wid; q++) run += s_w[q];
+        const unsigned long long blk_lo = s_excl;
+        unsigned long long blk_hi = s_excl;
+        for (int q = 0; q < kEmitThreads / 32; q++) blk_hi += s_w[q];
+#pragma unroll
+        for (int i = 0; i < kEmitItems; i++) {
+            const unsigned idx = base + t * kEmitItems + i;
+            if (idx < nd) {
+                const unsigned long long lo = run, hi = run + c[i];
+                w.offsets[idx] = (unsigned)min(lo, 0xFFFFFFFFull);
+                // this pair owns the first cell of every emission chunk starting in [lo, hi)
+                for (unsigned long long ch = (lo + kEmitBlock - 1) / kEmitBlock;
+                     ch < w.L.chunk_cap && ch * kEmitBlock < hi; ch++)
+                    w.chunk_first[ch] = idx;
+            }
+            run += c[i];
         }
-        w.hdr->cells = cells;
-        w.hdr->keys_used = (unsigned)min(K, (unsigned long long)w.L.key_cap);
-        w.hdr->n_chunks = over && (chunks > w.L.chunk_cap || cells > 0xFFFFFFFFull) ? 0u : (unsigned)chunks;
-        if (over) atomicOr(&w.hdr->err, ERR_CAPACITY);
+        // the emission chunks starting in this block's cells: clear their look-back words
+        const unsigned long long ch0 = (blk_lo + kEmitBlock - 1) / kEmitBlock;
+        const unsigned long long ch1 = min((blk_hi + kEmitBlock - 1) / kEmitBlock, (unsigned long long)w.L.chunk_cap);
+        for (unsigned long long i = ch0 * kRadix + t; i < ch1 * kRadix; i += kEmitThreads) look0[i] = 0u;
+        __syncthreads();
     }
-}
-
-// Exclusive cell offsets of every pair in depth order: off[i] for i < n_drawn,
-// off[n_drawn] = cells.
-// Block b scans its kEmitBlock pairs and adds the block prefix.  Each pair also records
-// the emission chunks whose first cell it owns.  Also clears look-back buffer 0 for the
-// emission chunks (the depth sort is finished with it).
-__global__ void __launch_bounds__(kEmitThreads) offsets_kernel(Work w, const unsigned *order) {
-    pdl_prologue();
-    __shared__ unsigned s_w[8];
-    const unsigned b = blockIdx.x, base = b * kEmitBlock;
-    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-    const unsigned nchunks = w.hdr->n_chunks;
-    const unsigned nd = min(w.hdr->n_drawn, w.L.P);
-    for (unsigned i = b * kEmitThreads + t; i < nchunks * kRadix; i += gridDim.x * kEmitThreads) w.look[i] = 0u;
-    // blocked: thread t owns pairs base + t*8 .. +7
-    unsigned c[kEmitItems], sum = 0;
-#pragma unroll
-    for (int i = 0; i < kEmitItems; i++) {
-        unsigned idx = base + t * kEmitItems + i;
-        unsigned p = idx < nd ? order[idx] : 0u;
-        if (p >= w.L.P) p = 0u;  // ids are in range unless a bounded wait gave up
-        c[i] = idx < nd ? w.rect[p].z : 0u;
-        sum += c[i];
-    }
-    unsigned inc = sum;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (lane >= o) inc += y;
-    }
-    if (lane == 31) s_w[wid] = inc;
-    __syncthreads();
-    unsigned run = w.blockprefix[b] + inc - sum;
-    for (int q = 0; q < wid; q++) run += s_w[q];
-#pragma unroll
-    for (int i = 0; i < kEmitItems; i++) {
-        unsigned idx = base + t * kEmitItems + i;
-        if (idx < nd) {
-            const unsigned lo = run, hi = run + c[i];
-            w.offsets[idx] = lo;
-            // this pair owns the first cell of every emission chunk starting in [lo, hi)
-            for (unsigned ch = (lo + kEmitBlock - 1) / kEmitBlock; ch < nchunks && ch * kEmitBlock < hi; ch++)
-                w.chunk_first[ch] = idx;
-        }
-        run += c[i];
-    }
-    if (b == 0 && t == 0) w.offsets[nd] = (unsigned)min(w.hdr->cells, 0xFFFFFFFFull);
 }
 
 // Key emission fused with the first pass of the tile sort, balanced over cells.  Each
@@ -175,7 +173,7 @@ __global__ void __launch_bounds__(kEmitThreads) offsets_kernel(Work w, const uns
 // offsets define: pairs by depth, each pair's extent-box tiles row-major) from an atomic
 // counter and finds the pair owning every cell with a load-balancing search: the pairs
 // whose cells fall in the chunk (a window of the depth-ordered offsets starting at the
-// chunk's owner recorded by offsets_kernel) mark their first cell, and an inclusive max
+// chunk's owner recorded by cell_offsets_kernel) mark their first cell, and an inclusive max
 // scan over the chunk carries each mark forward.  A cell is a key when the cull keeps its
 // tile (cull_tiles, as the projection counted).  The keys are ranked stably by their low
 // tile digit inside the chunk (warp match + per-warp histograms, in cell order), the
@@ -443,9 +441,8 @@ cudaError_t launch_setup(const Work &w, const FrameChunk &chunk, int first, int 
 cudaError_t launch_emit(const Work &w, int depth_buf, int tile_w, int tile_h, int num_sms, cudaStream_t s) {
     if (w.L.P == 0) return cudaSuccess;
     const unsigned *order = w.dval[depth_buf];
-    launch_pdl(count_reduce_kernel, w.L.emit_blocks, kEmitThreads, 0, s, w, order);
-    launch_pdl(count_scan_kernel, 1, 1024, 0, s, w);
-    launch_pdl(offsets_kernel, w.L.emit_blocks, kEmitThreads, 0, s, w, order);
+    launch_pdl(cell_offsets_kernel, std::max(1u, std::min(w.L.emit_blocks, (unsigned)num_sms * 4u)), kEmitThreads,
+               0, s, w, order);
     EmitSortArgs a;
     a.order = order;
     a.keys_out = w.tkey[1];

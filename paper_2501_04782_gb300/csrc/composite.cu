@@ -516,8 +516,10 @@ __global__ void __launch_bounds__(TW *TH / PX) composite_bwd_kernel(Work w, cons
                     const float2 t = __ffma2_rn(dup2(bdx), dy[k], dup2(s0));
                     const float2 e = __ffma2_rn(__fmul2_rn(dup2(f1.x), dy[k]), dy[k], t);
                     r[k] = make_float2(ex2_approx(e.x), ex2_approx(e.y));  // o exp(-power), unclamped
-                    v[2 * k] = pos <= last[2 * k] && fminf(r[k].x, kAlphaMax) >= kAlphaMin;
-                    v[2 * k + 1] = pos <= last[2 * k + 1] && fminf(r[k].y, kAlphaMax) >= kAlphaMin;
+                    // the forward's cutoff test min(r, 0.99) >= 1/255 is r >= 1/255 (r = 2^e is
+                    // finite and non-negative): the same decision without the clamp
+                    v[2 * k] = pos <= last[2 * k] && r[k].x >= kAlphaMin;
+                    v[2 * k + 1] = pos <= last[2 * k + 1] && r[k].y >= kAlphaMin;
                     any = any || v[2 * k] || v[2 * k + 1];
                 }
                 const unsigned act = __ballot_sync(0xffffffffu, any);
@@ -535,10 +537,10 @@ __global__ void __launch_bounds__(TW *TH / PX) composite_bwd_kernel(Work w, cons
                     n_comp += (unsigned)va + (unsigned)vb;
                     const float a0 = va ? fminf(r[k].x, kAlphaMax) : 0.f, a1 = vb ? fminf(r[k].y, kAlphaMax) : 0.f;
                     const float2 al = make_float2(a0, a1);
+                    // a pixel that does not composite this Gaussian has alpha 0: 1 / (1 - 0) is
+                    // exactly 1 (the hardware reciprocal is exact on powers of two), so T stays
                     const float2 ra = make_float2(rcp_approx(1.f - a0), rcp_approx(1.f - a1));
-                    float2 Tin = __fmul2_rn(T[k], ra);
-                    Tin.x = va ? Tin.x : T[k].x;
-                    Tin.y = vb ? Tin.y : T[k].y;
+                    const float2 Tin = __fmul2_rn(T[k], ra);
                     const float2 wg = __fmul2_rn(al, Tin);
                     // dL/dalpha = sum_ch g_ch (c_ch Tin - S_ch / (1 - alpha)) = gc Tin + gS / (1 - alpha)
                     const float2 gc = __ffma2_rn(g2[k], dup2(cb), __ffma2_rn(g1[k], dup2(f1.w), __fmul2_rn(g0[k], dup2(f1.z))));

@@ -86,7 +86,7 @@ struct DevHeader {
     unsigned n_pairs;               // P, read by the depth sort's first pass
     unsigned n_drawn;               // pairs with a depth key (a non-empty extent box): the
                                     // depth-sorted list holds only these, in its first n_drawn slots
-    unsigned sort_ctr[16];          // tile-acquisition counters of the sort passes
+    unsigned sort_ctr[16];          // tile-acquisition counters: sort passes 0-7, cell-offset scan 12
     unsigned queue[4];              // persistent work-queue counters
     long long spin_limit;           // iteration limit of every device-side wait
     int drop_signal;                // test hook: first look-back block never publishes
@@ -133,7 +133,7 @@ __host__ __device__ constexpr unsigned emit_chunk_cap(unsigned key_cap) {
 struct Layout {
     size_t hdr, frames;
     size_t feat0, feat1, feat2, rect, ell, dkey[2], dval[2];
-    size_t blocksum, blockprefix, offsets, chunk_first;
+    size_t scan_look, offsets, chunk_first;
     size_t g0, g1, g2;
     size_t fp64_list;
     size_t ranges;
@@ -158,7 +158,7 @@ struct Work {
     uint4 *rect;   // (x0 | y0 << 16, x1 | y1 << 16, cells, frame | kRectFp64): pixel box of the extent
     float4 *ell;   // culling record (kx, ds, tc, dn), see cull_record
     unsigned *dkey[2], *dval[2];
-    unsigned *blocksum, *blockprefix;
+    unsigned long long *scan_look;  // [emit_blocks] status words of the cell-offset scan
     unsigned *offsets;      // [P + 1] exclusive cell offsets of the pairs in depth order
     unsigned *chunk_first;  // [chunk_cap] depth-ordered pair owning a chunk's first cell
     float4 *g0, *g1;

@@ -950,7 +950,9 @@ cudaError_t launch_project_fwd(const Work &w, const GaussPtrs &g, int tile_w, in
                                cudaStream_t s) {
     if (w.L.P == 0) return cudaSuccess;
     int lw = __builtin_ctz(tile_w), lh = __builtin_ctz(tile_h);
-    unsigned blocks = std::min((w.L.P + 255u) / 256u, (unsigned)num_sms * 8u);
+    // four blocks per SM: fewer per-block histogram flushes (measured at 960x540 / 200k: 24.7 -> 20.7 us;
+    // unchanged on 8 x 1920x1080 / 1M)
+    unsigned blocks = std::min((w.L.P + 255u) / 256u, (unsigned)num_sms * 4u);
     const int tp = tile_sort_passes(w);
     const bool spline = g.n_ctrl > 0, sh = g.sh_degree > 0;
     if (spline && sh) launch_pdl(project_fwd_kernel<true, true>, blocks, 256, 0, s, w, g, lw, lh, tp);
