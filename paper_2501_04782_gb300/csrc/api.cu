@@ -348,7 +348,7 @@ gv_status forward_stages(gv_ctx *ctx, const gv_gaussians *g, const Plan &pl, con
     if (w.L.P > 0) {
         {
             StageTimer tm(ctx, GV_STAGE_PROJECT, s, 1);
-            GV_CUDA(launch_project_fwd(w, gauss_ptrs(g), o.tile_w, o.tile_h, ctx->num_sms, s));
+            GV_CUDA(launch_project_fwd(w, gauss_ptrs(g), o.tile_w, o.tile_h, pl.bwd_mode == 1, ctx->num_sms, s));
         }
         int dres = 0;
         {

@@ -202,8 +202,10 @@ cudaError_t launch_setup(const Work &w, const FrameChunk &chunk, int first, int 
                          long long spin_limit, int drop_signal, cudaStream_t s);
 const void *setup_kernel_ptr();
 // project.cu
-cudaError_t launch_project_fwd(const Work &w, const GaussPtrs &g, int tile_w, int tile_h, int num_sms,
-                               cudaStream_t s);
+// shared_set: every frame draws the same Gaussian range (one thread per Gaussian then loops
+// over the frames, for the plain form)
+cudaError_t launch_project_fwd(const Work &w, const GaussPtrs &g, int tile_w, int tile_h, bool shared_set,
+                               int num_sms, cudaStream_t s);
 cudaError_t launch_bin_from_screen(const Work &w, long long n, const float *u, const float *v,
                                    const float *sxx, const float *sxy, const float *syy, const float *tau,
                                    const float *depth, const uint8_t *valid, int tile_w, int tile_h,

@@ -50,11 +50,13 @@ struct PairState {
     bool valid;
 };
 
+// The projection of one (frame, Gaussian) pair in three parts: the mean at the frame's time
+// (load_mean), the Gaussian's own shape -- scales, rotation, 3D covariance, opacity --
+// (load_shape: frame-independent unless SPLINE), and the camera part (project_camera).
 // SPLINE: the time-parameterised form (g.n_ctrl > 0: B-spline means, cubic log-scale and
 // quaternion); otherwise mean + t vel and constant log-scale and quaternion.
 template <typename F, bool SPLINE = false>
-__device__ __forceinline__ void load_and_project(const GaussPtrs &g, long long gi, const DevFrame &fr,
-                                                 PairState<F> &st) {
+__device__ __forceinline__ void load_mean(const GaussPtrs &g, long long gi, const DevFrame &fr, PairState<F> &st) {
     const long long N = g.N;
     const F time = (F)fr.time;
     if constexpr (SPLINE) {  // Eq. 2: mu(t) = sum_i N_{i,3}(t) P_i over the four non-zero weights
@@ -78,6 +80,12 @@ __device__ __forceinline__ void load_and_project(const GaussPtrs &g, long long g
             st.mz = fma_(time, (F)g.vel[2 * N + gi], st.mz);
         }
     }
+}
+
+template <typename F, bool SPLINE = false>
+__device__ __forceinline__ void load_shape(const GaussPtrs &g, long long gi, const DevFrame &fr, PairState<F> &st) {
+    const long long N = g.N;
+    const F time = (F)fr.time;
     // Eq. 3: log-scale and quaternion as cubic polynomials of t (t^0 term: the plain plane)
     auto cubic = [&](const float *base, const float *terms, int rows, int k) -> F {
         F v = (F)base[k * N + gi];
@@ -110,12 +118,19 @@ __device__ __forceinline__ void load_and_project(const GaussPtrs &g, long long g
     st.S3[3] = R[3] * R[3] * s0q + R[4] * R[4] * s1q + R[5] * R[5] * s2q;
     st.S3[4] = R[3] * R[6] * s0q + R[4] * R[7] * s1q + R[5] * R[8] * s2q;
     st.S3[5] = R[6] * R[6] * s0q + R[7] * R[7] * s1q + R[8] * R[8] * s2q;
+    st.o = one / (one + exp_(-(F)g.logit[gi]));
+}
+
+// The camera part: camera-space mean, near cull, J W, Sigma2 (with the low-pass), conic,
+// screen mean; st.valid false when culled.
+template <typename F>
+__device__ __forceinline__ void project_camera(const DevFrame &fr, PairState<F> &st) {
+    const F one = (F)1;
     F W[9];
     for (int i = 0; i < 9; i++) W[i] = (F)fr.R[i];
     st.xc = W[0] * st.mx + W[1] * st.my + W[2] * st.mz + (F)fr.t[0];
     st.yc = W[3] * st.mx + W[4] * st.my + W[5] * st.mz + (F)fr.t[1];
     st.zc = W[6] * st.mx + W[7] * st.my + W[8] * st.mz + (F)fr.t[2];
-    st.o = one / (one + exp_(-(F)g.logit[gi]));
     st.valid = st.zc > (F)kZNear;
     if (!st.valid) return;
     F iz = one / st.zc;
@@ -146,6 +161,14 @@ __device__ __forceinline__ void load_and_project(const GaussPtrs &g, long long g
     st.v = fma_((F)fr.fy, ry, (F)fr.cy);
     if (!(isfinite(st.u) && isfinite(st.v) && isfinite(st.A) && isfinite(st.B) && isfinite(st.C)))
         st.valid = false;
+}
+
+template <typename F, bool SPLINE = false>
+__device__ __forceinline__ void load_and_project(const GaussPtrs &g, long long gi, const DevFrame &fr,
+                                                 PairState<F> &st) {
+    load_mean<F, SPLINE>(g, gi, fr, st);
+    load_shape<F, SPLINE>(g, gi, fr, st);
+    project_camera<F>(fr, st);
 }
 
 // Per-block binning counters of the projection: depth-sort digits (4 passes), tile-sort
@@ -374,6 +397,45 @@ __device__ __forceinline__ bool ill_conditioned(const PairState<float> &st) {
     return st.a * st.c > kFp64Condition * det;
 }
 
+// alpha >= 1/255 needs d^T conic d <= tau = 2 ln(255 o) (capped at 2 ln 255 by the clamp)
+__device__ __forceinline__ float tau_of(float o) { return fminf(2.f * (kLn255 + logf(o)), kExtK * kExtK); }
+
+// The records of one projected pair: binning box and cull record (bin_pair; nothing binned
+// when the pair is culled), the FP64 list entry of an ill-conditioned binned pair, the
+// staged compositing record and the depth key.  Returns the key (kNoKey: bins nothing).
+__device__ __forceinline__ unsigned write_pair(const Work &w, unsigned p, int f, const DevFrame &fr,
+                                               const PairState<float> &st, float tau, float log2o, const float col[3],
+                                               int lw, int lh, PairBin &pb) {
+    const unsigned cells =
+        bin_pair(w, p, st.u, st.v, st.a, st.b, st.c, st.valid ? tau : 0.f, fr, (unsigned)f, lw, lh, pb);
+    if (cells && ill_conditioned(st)) {  // only binned pairs get a gradient
+        w.fp64_list[atomicAdd(&w.hdr->fp64_count, 1u)] = p;
+        w.rect[p].w = (unsigned)f | kRectFp64;
+    }
+    w.feat0[p] = make_float4(st.u, st.v, -0.5f * kLog2e * st.A, -kLog2e * st.B);
+    w.feat1[p] = make_float4(-0.5f * kLog2e * st.C, log2o, col[0], col[1]);
+    w.feat2[p] = col[2];
+    const unsigned key = cells ? __float_as_uint(st.zc) : kNoKey;
+    w.dkey[0][p] = key;
+    return key;
+}
+
+// Counters of one round of pairs (every lane of the warp calls it): the kept keys' tile
+// digits (warp_cull_rows), the drawn flag, the drawn pairs and their depth digits (the sort
+// drops the others).  Returns the round's kept keys of this lane's rows.
+__device__ __forceinline__ unsigned count_round(const GaussPtrs &g, long long gi, bool in, unsigned key,
+                                                const PairBin &pb, int lw, int lh, int tile_passes, BinShared &sb,
+                                                unsigned &kept) {
+    unsigned kept_lanes;
+    const unsigned live = warp_cull_rows<false>(pb, lw, lh, tile_passes, sb, nullptr, kept_lanes);
+    kept = (kept_lanes >> (threadIdx.x & 31)) & 1u;
+    const unsigned active = __ballot_sync(0xffffffffu, in && key != kNoKey);
+    if ((threadIdx.x & 31) == 0 && active) atomicAdd(&sb.drawn, (unsigned)__popc(active));
+    if (in && key != kNoKey)
+        for (int ps = 0; ps < 4; ps++) count_digit(sb.depth[ps], (key >> (8 * ps)) & 255u, active);
+    return live;
+}
+
 // Grid-stride over the pairs so each block flushes its counters once.
 template <bool SPLINE, bool SH>
 __global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, int lw, int lh, int tile_passes) {
@@ -397,29 +459,77 @@ __global__ void __launch_bounds__(256) project_fwd_kernel(Work w, GaussPtrs g, i
             gi = fr.gauss_offset + (long long)(p - fr.pair_offset);
             PairState<float> st;
             load_and_project<float, SPLINE>(g, gi, fr, st);
-            // alpha >= 1/255 needs d^T conic d <= tau = 2 ln(255 o)
-            const float tau = st.valid ? fminf(2.f * (kLn255 + logf(st.o)), kExtK * kExtK) : 0.f;
-            const unsigned cells = bin_pair(w, p, st.u, st.v, st.a, st.b, st.c, tau, fr, (unsigned)f, lw, lh, pb);
-            if (cells && ill_conditioned(st)) {  // only binned pairs get a gradient
-                w.fp64_list[atomicAdd(&w.hdr->fp64_count, 1u)] = p;
-                w.rect[p].w = (unsigned)f | kRectFp64;
-            }
             float col[3];
             pair_colour<SH>(g, gi, st, fr, col);
-            w.feat0[p] = make_float4(st.u, st.v, -0.5f * kLog2e * st.A, -kLog2e * st.B);
-            w.feat1[p] = make_float4(-0.5f * kLog2e * st.C, log2f(st.o), col[0], col[1]);
-            w.feat2[p] = col[2];
-            key = cells ? __float_as_uint(st.zc) : 0xFFFFFFFFu;
-            w.dkey[0][p] = key;
+            key = write_pair(w, p, f, fr, st, tau_of(st.o), log2f(st.o), col, lw, lh, pb);
         }
-        unsigned kept_lanes;
-        live_sum += warp_cull_rows<false>(pb, lw, lh, tile_passes, sb, nullptr, kept_lanes);
-        if (g.visible && ((kept_lanes >> (threadIdx.x & 31)) & 1u)) g.visible[gi] = 1;  // benign same-value race
-        // depth digits of the pairs with a key (the sort drops the others)
-        const unsigned active = __ballot_sync(0xffffffffu, in && key != kNoKey);
-        if ((threadIdx.x & 31) == 0 && active) atomicAdd(&sb.drawn, (unsigned)__popc(active));
-        if (in && key != kNoKey)
-            for (int ps = 0; ps < 4; ps++) count_digit(sb.depth[ps], (key >> (8 * ps)) & 255u, active);
+        unsigned kept;
+        live_sum += count_round(g, gi, in, key, pb, lw, lh, tile_passes, sb, kept);
+        if (g.visible && kept) g.visible[gi] = 1;  // benign same-value race
+    }
+    bin_shared_flush(w, sb, live_sum, tile_passes);
+}
+
+// A shared set (every frame of the call draws the same Gaussian range; plain colour, means
+// constant or drifting linearly): one thread per Gaussian loops over the frames, so its
+// parameters are read once and the frame-independent part of the projection (scales,
+// rotation, 3D covariance, opacity, colour, the cutoff level tau) is computed once instead
+// of once per frame.  Records and counters are project_fwd_kernel's, pair by pair (the
+// same expressions on the same values).
+__global__ void __launch_bounds__(256, 4) project_fwd_shared_kernel(Work w, GaussPtrs g, int lw, int lh,
+                                                                 int tile_passes) {
+    pdl_prologue();
+    __shared__ BinShared sb;
+    bin_shared_init(sb);
+    __syncthreads();
+    const DevFrame &f0 = w.frames[0];
+    const unsigned n = f0.gauss_count;
+    const int F = (int)w.L.F;
+    const long long N = g.N;
+    const unsigned stride = gridDim.x * blockDim.x;
+    unsigned live_sum = 0;
+    // every thread of a block runs the same rounds (the warp votes see full warps)
+    for (unsigned base = blockIdx.x * blockDim.x; base < n; base += stride) {
+        const unsigned j = base + threadIdx.x;
+        const bool in = j < n;
+        const long long gi = f0.gauss_offset + (long long)(in ? j : 0u);
+        PairState<float> st;
+        float m[3] = {0.f, 0.f, 0.f}, vel[3] = {0.f, 0.f, 0.f}, col[3] = {0.f, 0.f, 0.f};
+        float tau = 0.f, log2o = 0.f;
+        if (in) {
+            for (int k = 0; k < 3; k++) {
+                m[k] = g.mean[k * N + gi];
+                if (g.vel) vel[k] = g.vel[k * N + gi];
+                col[k] = g.rgb[k * N + gi];
+            }
+            load_shape<float, false>(g, gi, f0, st);
+            tau = tau_of(st.o);
+            log2o = log2f(st.o);
+        }
+        unsigned drawn = 0;
+        for (int f = 0; f < F; f++) {
+            const DevFrame &fr = w.frames[f];
+            const unsigned p = fr.pair_offset + j;
+            unsigned key = kNoKey;
+            PairBin pb;
+            pb.rows = 0;
+            if (in) {
+                if (g.vel) {
+                    const float time = fr.time;
+                    st.mx = fmaf(time, vel[0], m[0]);
+                    st.my = fmaf(time, vel[1], m[1]);
+                    st.mz = fmaf(time, vel[2], m[2]);
+                } else {
+                    st.mx = m[0]; st.my = m[1]; st.mz = m[2];
+                }
+                project_camera<float>(fr, st);
+                key = write_pair(w, p, f, fr, st, tau, log2o, col, lw, lh, pb);
+            }
+            unsigned kept;
+            live_sum += count_round(g, gi, in, key, pb, lw, lh, tile_passes, sb, kept);
+            drawn |= kept;
+        }
+        if (g.visible && in && drawn) g.visible[gi] = 1;
     }
     bin_shared_flush(w, sb, live_sum, tile_passes);
 }
@@ -946,10 +1056,16 @@ __global__ void __launch_bounds__(128) project_bwd_fp64_kernel(Work w, GaussPtrs
 
 int tile_sort_passes(const Work &w) { return std::max(1, (w.L.tile_bits + 7) / 8); }
 
-cudaError_t launch_project_fwd(const Work &w, const GaussPtrs &g, int tile_w, int tile_h, int num_sms,
-                               cudaStream_t s) {
+cudaError_t launch_project_fwd(const Work &w, const GaussPtrs &g, int tile_w, int tile_h, bool shared_set,
+                               int num_sms, cudaStream_t s) {
     if (w.L.P == 0) return cudaSuccess;
     int lw = __builtin_ctz(tile_w), lh = __builtin_ctz(tile_h);
+    if (shared_set && w.L.F > 1 && g.n_ctrl == 0 && g.sh_degree == 0) {
+        const unsigned n = w.L.P / w.L.F;
+        const unsigned blocks = std::max(1u, std::min((n + 255u) / 256u, (unsigned)num_sms * 4u));
+        launch_pdl(project_fwd_shared_kernel, blocks, 256, 0, s, w, g, lw, lh, tile_sort_passes(w));
+        return cudaGetLastError();
+    }
     // four blocks per SM: fewer per-block histogram flushes (measured at 960x540 / 200k: 24.7 -> 20.7 us;
     // unchanged on 8 x 1920x1080 / 1M)
     unsigned blocks = std::min((w.L.P + 255u) / 256u, (unsigned)num_sms * 4u);
