@@ -385,9 +385,8 @@ def run_gv(args):
     # workload); unknown (null) for other kernels or configurations
     o = ctx.options
     cfg_key = (dom, f"{o.tile_w}x{o.tile_h}", o.stage_depth)
-    ncu_traffic = {("composite_bwd", "32x16", 64): 15.058688e6, ("composite_bwd", "32x16", 128): 15.051264e6,
-                   ("composite_bwd", "32x16", 256): 15.057664e6, ("composite_bwd", "16x16", 128): 15.471872e6,
-                   ("composite_bwd", "16x8", 64): 16.441088e6}
+    ncu_traffic = {("composite_bwd", "32x16", 64): 15.068672e6, ("composite_bwd", "32x16", 128): 15.063808e6,
+                   ("composite_bwd", "32x16", 256): 15.050496e6}
     roofline = {"kernel": dom, "bound": d.get("bound"), "achieved": d.get("achieved"),
                 "peak": round(fp32_peak, 1) if d.get("bound") == "alu" else hbm_peak, "unit": d.get("unit"),
                 "frac": d.get("frac"), "traffic": ncu_traffic.get(cfg_key),
