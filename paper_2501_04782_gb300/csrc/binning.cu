@@ -334,7 +334,10 @@ __global__ void __launch_bounds__(kEmitThreads, 4) emit_sort_kernel(Work w, Emit
             total += c;
         }
         bool gave_up = false;
-        const unsigned excl = lookback_digit(w.look, chunk, total, w.hdr, limit, false, gave_up);
+        // digits above the tile ids' live bits hold no key: no look-back for them
+        const unsigned excl = t < (1 << min(8, w.L.tile_bits))
+                                  ? lookback_digit(w.look, chunk, total, w.hdr, limit, false, gave_up)
+                                  : 0u;
         if (gave_up) s_abort = 1;
         unsigned dex;
         const unsigned nkeys = block_excl_scan_256(total, s_scan, dex);

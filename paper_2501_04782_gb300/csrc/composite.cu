@@ -548,8 +548,8 @@ __global__ void __launch_bounds__(TW *TH / PX) composite_bwd_kernel(Work w, cons
                     gS[k] = __ffma2_rn(make_float2(-gc.x, -gc.y), wg, gS[k]);
                     T[k] = Tin;
                     // dL/de / ln 2 for the exponent e (alpha = 2^e unless clamped at 0.99)
-                    const float2 kk = make_float2((va && r[k].x < kAlphaMax) ? r[k].x : 0.f,
-                                                  (vb && r[k].y < kAlphaMax) ? r[k].y : 0.f);
+                    // (a < 0.99 ? a : 0) is r where composited below the clamp, else 0
+                    const float2 kk = make_float2(a0 < kAlphaMax ? a0 : 0.f, a1 < kAlphaMax ? a1 : 0.f);
                     const float2 de = __fmul2_rn(dal, kk);
                     const float2 ddy = __fmul2_rn(de, dy[k]);
                     const float2 ddy2 = __fmul2_rn(ddy, dy[k]);

@@ -53,6 +53,7 @@ struct PassArgs {
     const unsigned *n_dev;  // keys this pass reads
     unsigned n_cap;
     int shift;
+    int dbits;              // live bits of this pass's digit (the last pass of a sort may have fewer than 8)
     const unsigned *hist;   // this pass's 256 digit counts
     unsigned *look_cur;     // [tiles][256] status words of this pass
     unsigned *look_next;    // cleared for the next pass
@@ -115,6 +116,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_pass_kernel(PassArgs a) 
                 peers = __ballot_sync(0xffffffffu, live);
 #pragma unroll
                 for (int b = 0; b < 8; b++) {
+                    if (b >= a.dbits) break;  // the digit's bits above dbits are zero
                     const bool bit = (d >> b) & 1u;
                     const unsigned m = __ballot_sync(0xffffffffu, bit);
                     peers &= bit ? m : ~m;
@@ -137,9 +139,10 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_pass_kernel(PassArgs a) 
             s_whist[q][t] = total;
             total += c;
         }
-        // decoupled look-back for digit t
+        // decoupled look-back for digit t (digits above the pass's live bits hold no key)
         bool gave_up = false;
-        const unsigned excl = lookback_digit(a.look_cur, tile, total, a.hdr, limit, drop, gave_up);
+        const unsigned excl =
+            t < (1 << a.dbits) ? lookback_digit(a.look_cur, tile, total, a.hdr, limit, drop, gave_up) : 0u;
         if (gave_up) s_abort = 1;
         unsigned dex;
         const unsigned nlive = block_excl_scan_256(total, s_scan, dex);
@@ -217,6 +220,7 @@ cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2
         a.n_dev = ps > 0 && n_dev_later ? n_dev_later : n_dev;
         a.n_cap = n_cap;
         a.shift = 8 * ps;
+        a.dbits = std::min(8, bits - 8 * ps);
         a.hist = hist + (size_t)ps * kRadix;
         a.look_cur = look[ps & 1];
         a.look_next = look[(ps & 1) ^ 1];
