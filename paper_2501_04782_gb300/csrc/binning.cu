@@ -206,6 +206,9 @@ __global__ void __launch_bounds__(kEmitThreads, 4) emit_sort_kernel(Work w, Emit
     __shared__ uint2 s_frames[kEmitSmemFrames];  // (tile_offset, tiles_x) of the first frames
     unsigned *s_keys = reinterpret_cast<unsigned *>(s_owner);
     unsigned *s_vals = s_pair;
+    // a call whose capacity check failed keeps no list: nothing to emit (the decision is the
+    // block's, as a wait of another block may set a timeout meanwhile)
+    if (__syncthreads_or(*((volatile unsigned *)&w.hdr->err) != 0u)) return;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const unsigned P = w.L.P, nchunks = w.hdr->n_chunks, nd = min(w.hdr->n_drawn, P);
     const unsigned cells = (unsigned)min(w.hdr->cells, 0xFFFFFFFFull);
@@ -375,7 +378,7 @@ constexpr int kRangeItems = 8;
 
 __global__ void __launch_bounds__(256) ranges_kernel(Work w, const unsigned *keys) {
     pdl_prologue();
-    const unsigned n = w.hdr->keys_used;
+    const unsigned n = w.hdr->err != 0u ? 0u : w.hdr->keys_used;  // a failed call's tiles stay empty
     const int lane = threadIdx.x & 31;
     const unsigned warps = gridDim.x * (blockDim.x >> 5);
     const unsigned span = 32u * kRangeItems;

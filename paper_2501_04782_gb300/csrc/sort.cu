@@ -78,8 +78,17 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_pass_kernel(PassArgs a) 
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const unsigned n = min(*a.n_dev, a.n_cap);
     const unsigned ntiles = (n + TILE - 1) / TILE;
+    // every key's digit is taken to the pass's live bits, so ranking, histogram, offsets and
+    // scatter agree on it for any key (a key with bits above them cannot index past a digit)
+    const unsigned dmask = (1u << a.dbits) - 1u;
     const long long limit = a.hdr->spin_limit;
     const bool drop = a.hdr->drop_signal != 0;
+    // A call that already failed (key capacity exceeded, or a wait that gave up) has
+    // incomplete input here -- the emission kept only the first key_cap keys while the
+    // digit counts cover all of them, and a block that gave up wrote nothing -- and its
+    // lists are discarded: the pass does nothing (the block takes no tile; the decision is
+    // the block's, as a wait of another block may set the error meanwhile).
+    if (__syncthreads_or(*((volatile unsigned *)&a.hdr->err) != 0u)) return;
     {
         unsigned ex;
         block_excl_scan_256(a.hist[t], s_scan, ex);
@@ -110,13 +119,13 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_pass_kernel(PassArgs a) 
 #pragma unroll
         for (int i = 0; i < ITEMS; i++) {
             const bool live = k[i] != kNoKey;
-            unsigned d = (k[i] >> a.shift) & 255u;
+            unsigned d = (k[i] >> a.shift) & dmask;
             unsigned peers;
             if (BALLOT) {
                 peers = __ballot_sync(0xffffffffu, live);
 #pragma unroll
                 for (int b = 0; b < 8; b++) {
-                    if (b >= a.dbits) break;  // the digit's bits above dbits are zero
+                    if (b >= a.dbits) break;  // the digit has dbits bits
                     const bool bit = (d >> b) & 1u;
                     const unsigned m = __ballot_sync(0xffffffffu, bit);
                     peers &= bit ? m : ~m;
@@ -153,7 +162,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_pass_kernel(PassArgs a) 
 #pragma unroll
         for (int i = 0; i < ITEMS; i++) {
             if (k[i] == kNoKey) continue;
-            unsigned d = (k[i] >> a.shift) & 255u;
+            unsigned d = (k[i] >> a.shift) & dmask;
             unsigned pos = s_dstart[d] + s_whist[wid][d] + r[i];
             s_keys[pos] = k[i];
             s_vals[pos] = v[i];
@@ -162,7 +171,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_pass_kernel(PassArgs a) 
         if (!s_abort) {
             for (int pos = t; pos < (int)nlive; pos += kSortThreads) {
                 unsigned key = s_keys[pos];
-                unsigned d = (key >> a.shift) & 255u;
+                unsigned d = (key >> a.shift) & dmask;
                 unsigned gpos = s_gbase[d] + (unsigned)pos - s_dstart[d];
                 if (gpos < n) {
                     a.keys_out[gpos] = key;

@@ -28,6 +28,41 @@ def test_capacity_overflow_is_reported_and_retry_succeeds():
     assert big.K == needed
 
 
+def test_capacity_overflow_of_a_three_pass_tile_sort_on_a_stale_workspace():
+    """Tile ids of 17 bits (16 frames of 960x540 sharing 300,000 Gaussians, 8x8 tiles:
+    130,560 tiles), so the tile sort takes three passes, and a key capacity 5 % short, on a
+    workspace whose every byte is 0x7F (a stale key there has bits far above the tile ids').
+    The emission keeps only the first key_cap keys while the digit counts cover all of them,
+    so the passes after it must not sort the slots it left unwritten: the call reports
+    GV_ERR_CAPACITY with at least the keys it needs, renders every pixel empty, writes
+    nothing after the workspace, and the batch then renders as on a clean workspace."""
+    wc = synth.workload_clip_shared()
+    tiles = sum(-(-c.W // 8) * -(-c.H // 8) for c, _, _ in wc["frames"])
+    assert tiles > 1 << 16  # three 8-bit passes
+    bg = (0.25, 0.5, 0.75)
+    ctx = gv.Context((8, 8), 64, bg=bg)
+    ref = CudaRun(ctx, wc["gaussians"], wc["frames"]).forward()
+    cap = int(ref.K * 0.95)
+    small = CudaRun(ctx, wc["gaussians"], wc["frames"], key_capacity=cap)
+    guard = torch.full((1 << 16,), 7, dtype=torch.uint8, device="cuda")
+    ws = torch.cat([torch.full_like(small.ws, 0x7F), guard])
+    small.ws = ws[:small.ws.numel()]
+    ctx.render_fwd(small.params, small.frames, small.ws, small.image, small.T, small.idx)
+    st, needed = ctx.read_status(small.ws, raise_on_error=False)
+    assert st == gv.GV_ERR_CAPACITY
+    assert needed >= ref.K
+    assert torch.all(ws[small.ws.numel():] == 7)
+    img = small.image.view(len(small.frames), 3, -1)  # frame by frame, each [3][H*W]
+    for ch, b in enumerate(bg):
+        assert torch.all(img[:, ch] == b)
+    assert torch.all(small.T == 1.0) and torch.all(small.idx == -1)
+    again = CudaRun(ctx, wc["gaussians"], wc["frames"], key_capacity=needed)
+    again.ws.fill_(0x7F)
+    again.forward(grow=False)
+    assert again.K == ref.K
+    assert torch.equal(again.image, ref.image) and torch.equal(again.T, ref.T) and torch.equal(again.idx, ref.idx)
+
+
 def test_bounded_wait_times_out_and_context_recovers():
     w = synth.workload_single_540p(N=40000)
     ctx = gv.Context((16, 16), 128)
