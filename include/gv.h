@@ -233,7 +233,8 @@ GV_API gv_status gv_status_accumulate(gv_ctx *ctx, const void *workspace, int32_
  * Gaussian) pairs the forward evaluated, [3] pairs with a non-empty extent box (the pairs
  * the depth sort orders after its first pass drops the others), [4] pairs the backward
  * evaluated, [5] of those the pairs replayed (alpha >= 1/255; exactly the pairs the
- * forward composited).  "Evaluated" counts,
+ * forward composited; counted only by a backward run in profile mode 2 of
+ * gv_profile_enable, else 0: the count costs inner-loop instructions).  "Evaluated" counts,
  * per pixel, the list entries up to the pixel's stop (the algorithmic work of compositing). */
 GV_API gv_status gv_read_counters(gv_ctx *ctx, const void *workspace, gv_stream stream, int64_t *out);
 
@@ -320,7 +321,9 @@ typedef enum {
 } gv_stage;
 
 /* Record a CUDA event pair around every stage of later render calls on this context
- * (on the call's stream; not inside graph capture).  on = 0 stops recording. */
+ * (on the call's stream; not inside graph capture).  on = 0 stops recording; on = 2 also
+ * makes the backward count the pairs it replays (gv_read_counters out[5]), which costs it
+ * a few per cent. */
 GV_API gv_status gv_profile_enable(gv_ctx *ctx, int32_t on);
 
 /* Synchronise the recorded events and write, per stage, the milliseconds of the most

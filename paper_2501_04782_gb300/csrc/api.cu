@@ -25,6 +25,7 @@ struct gv_ctx {
     // per-stage timing (gv_profile_enable): an event pair per stage, recorded on the
     // call's stream, and the kernels the stage launched
     bool profile = false;
+    bool count_replayed = false;  // the backward counts its replayed pairs (profile mode 2)
     bool capturing = false;
     cudaEvent_t ev[GV_NUM_STAGES][2] = {};
     bool ev_used[GV_NUM_STAGES] = {};
@@ -395,8 +396,9 @@ gv_status backward_stages(gv_ctx *ctx, const gv_gaussians *g, const Plan &pl, co
                             s));
     {
         StageTimer tm(ctx, GV_STAGE_COMPOSITE_BWD, s, 1);
+        // the replayed pairs are counted only in profile mode 2
         GV_CUDA(launch_composite_bwd(w, o.tile_w, o.tile_h, o.stage_depth, tile_result_buf(w.L), o.bg[0], o.bg[1],
-                                     o.bg[2], final_T, last_idx, dL, ctx->num_sms, s));
+                                     o.bg[2], final_T, last_idx, dL, ctx->count_replayed, ctx->num_sms, s));
     }
     GradPtrs gp;
     gp.mean = grad->mean; gp.vel = grad->vel; gp.log_scale = grad->log_scale;
@@ -547,6 +549,7 @@ gv_status gv_profile_enable(gv_ctx *ctx, int32_t on) {
             for (int j = 0; j < 2; j++) GV_CUDA(cudaEventCreate(&ctx->ev[i][j]));
     }
     ctx->profile = on != 0;
+    ctx->count_replayed = on == 2;
     for (int i = 0; i < GV_NUM_STAGES; i++) ctx->ev_used[i] = false;
     return GV_OK;
 }

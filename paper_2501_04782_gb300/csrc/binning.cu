@@ -174,7 +174,10 @@ __global__ void __launch_bounds__(kEmitThreads) cell_offsets_kernel(Work w, cons
 // counter and finds the pair owning every cell with a load-balancing search: the pairs
 // whose cells fall in the chunk (a window of the depth-ordered offsets starting at the
 // chunk's owner recorded by cell_offsets_kernel) mark their first cell, and an inclusive max
-// scan over the chunk carries each mark forward.  A cell is a key when the cull keeps its
+// scan over the chunk carries each mark forward.  While the window is read, the records of
+// its first kEmitStage pairs (pixel box, frame, screen mean, cull record) are staged in
+// shared memory, so the cells read them there instead of gathering them from L2 cell by
+// cell (8 x 1920x1080 / 1M: emission 1.22 -> 1.09 ms).  A cell is a key when the cull keeps its
 // tile (cull_tiles, as the projection counted).  The keys are ranked stably by their low
 // tile digit inside the chunk (warp match + per-warp histograms, in cell order), the
 // per-digit counts of all earlier chunks come from decoupled look-back, and (tile id, pair
@@ -182,6 +185,7 @@ __global__ void __launch_bounds__(kEmitThreads) cell_offsets_kernel(Work w, cons
 // compacted and sorted by the low tile digit, in depth order within a digit.  The global
 // digit offsets come from the projection's counts of the kept keys.
 constexpr int kEmitSmemFrames = 64;
+constexpr int kEmitStage = 128;  // pairs of a chunk whose records are staged in shared memory
 
 struct EmitSortArgs {
     const unsigned *order;  // depth-sorted pair ids
@@ -204,6 +208,11 @@ __global__ void __launch_bounds__(kEmitThreads, 4) emit_sort_kernel(Work w, Emit
     __shared__ unsigned s_chunk, s_lo, s_n;
     __shared__ int s_abort;
     __shared__ uint2 s_frames[kEmitSmemFrames];  // (tile_offset, tiles_x) of the first frames
+    // records of the chunk's first kEmitStage pairs: pixel box, frame (tile_offset, tiles_x),
+    // screen mean, cull record (the cells of later pairs read them from global memory)
+    __shared__ uint2 s_pbox[kEmitStage], s_pfg[kEmitStage];
+    __shared__ float2 s_puv[kEmitStage];
+    __shared__ float4 s_pell[kEmitStage];
     unsigned *s_keys = reinterpret_cast<unsigned *>(s_owner);
     unsigned *s_vals = s_pair;
     // a call whose capacity check failed keeps no list: nothing to emit (the decision is the
@@ -247,10 +256,20 @@ __global__ void __launch_bounds__(kEmitThreads, 4) emit_sort_kernel(Work w, Emit
             const unsigned o = off[plo + i];  // plo + np <= nd: off[nd] = cells
             s_off[i] = o;
             if (i == np) break;
-            const unsigned p = a.order[plo + i];
-            s_pair[i] = p < P ? p : 0u;  // in range unless a bounded wait gave up
+            const unsigned p = min(a.order[plo + i], P - 1u);  // in range unless a bounded wait gave up
+            s_pair[i] = p;
             const unsigned first = o > k0 ? o - k0 : 0u;
             if (first < kb) s_owner[first] = (int)i;
+            if (i < (unsigned)kEmitStage) {
+                const uint4 r = w.rect[p];
+                const float4 f0 = w.feat0[p];
+                const unsigned fi = min(r.w & kRectFrame, w.L.F - 1u);
+                s_pbox[i] = make_uint2(r.x, r.y);
+                s_pfg[i] = fi < (unsigned)kEmitSmemFrames ? s_frames[fi]
+                                                          : make_uint2(w.frames[fi].tile_offset, w.frames[fi].tiles_x);
+                s_puv[i] = make_float2(f0.x, f0.y);
+                s_pell[i] = w.ell[p];
+            }
         }
         __syncthreads();
         {   // inclusive max scan of s_owner: thread t owns entries t*8 .. t*8+7
@@ -291,11 +310,25 @@ __global__ void __launch_bounds__(kEmitThreads, 4) emit_sort_kernel(Work w, Emit
                 const int oi = max(s_owner[e], 0);
                 const unsigned j = k0 + e - s_off[oi];
                 const unsigned p = s_pair[oi];
-                const uint4 r = w.rect[p];  // consecutive cells mostly share a pair: L1 hits
-                const unsigned fi = min(r.w & kRectFrame, w.L.F - 1u);
-                const uint2 fg =
-                    fi < (unsigned)kEmitSmemFrames ? s_frames[fi] : make_uint2(w.frames[fi].tile_offset, w.frames[fi].tiles_x);
-                const PixBox bx = unpack_box(r);
+                uint2 box, fg;
+                float2 uv;
+                float4 el;
+                if (oi < kEmitStage) {
+                    box = s_pbox[oi];
+                    fg = s_pfg[oi];
+                    uv = s_puv[oi];
+                    el = s_pell[oi];
+                } else {
+                    const uint4 r = w.rect[p];
+                    const unsigned fi = min(r.w & kRectFrame, w.L.F - 1u);
+                    box = make_uint2(r.x, r.y);
+                    fg = fi < (unsigned)kEmitSmemFrames ? s_frames[fi]
+                                                        : make_uint2(w.frames[fi].tile_offset, w.frames[fi].tiles_x);
+                    const float4 f0 = w.feat0[p];
+                    uv = make_float2(f0.x, f0.y);
+                    el = w.ell[p];
+                }
+                const PixBox bx = unpack_box(make_uint4(box.x, box.y, 0u, 0u));
                 const unsigned tx0 = (unsigned)bx.x0 >> a.lw, ty0 = (unsigned)bx.y0 >> a.lh;
                 const unsigned wr = ((unsigned)bx.x1 >> a.lw) - tx0 + 1u;
                 // j / wr through the FP32 reciprocal, corrected to the exact quotient (j < 2^24)
@@ -304,9 +337,8 @@ __global__ void __launch_bounds__(kEmitThreads, 4) emit_sort_kernel(Work w, Emit
                 if (rem < 0) { q--; rem += (int)wr; }
                 else if (rem >= (int)wr) { q++; rem -= (int)wr; }
                 const int tx = (int)tx0 + rem, ty = (int)(ty0 + q);
-                const float4 f0 = w.feat0[p];
                 int t0, t1;
-                if (cull_tiles(f0.x, f0.y, w.ell[p], bx, ty, a.lw, a.lh, t0, t1) && tx >= t0 && tx <= t1) {
+                if (cull_tiles(uv.x, uv.y, el, bx, ty, a.lw, a.lh, t0, t1) && tx >= t0 && tx <= t1) {
                     key[i] = min(fg.x + (unsigned)ty * fg.y + (unsigned)tx, w.L.tiles - 1u);
                     val[i] = p;
                     kept |= 1u << i;

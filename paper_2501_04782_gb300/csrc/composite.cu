@@ -397,7 +397,9 @@ __global__ void __launch_bounds__(TW *TH / PX) composite_fwd4_kernel(Work w, con
 template <int TW, int TH>
 constexpr int fwd_px() { return TH >= 32 ? 4 : 2; }
 
-template <int TW, int TH, int DEPTH, int PX>
+// COUNT: also count the replayed (composited) pairs into work[3] (only while per-stage
+// profiling is on: the count costs instructions in the inner loop).
+template <int TW, int TH, int DEPTH, int PX, bool COUNT>
 __global__ void __launch_bounds__(TW *TH / PX) composite_bwd_kernel(Work w, const unsigned *ids, float bg0, float bg1,
                                                                     float bg2, const float *final_T,
                                                                     const int32_t *last_idx, const float *dL) {
@@ -534,7 +536,7 @@ __global__ void __launch_bounds__(TW *TH / PX) composite_bwd_kernel(Work w, cons
 #pragma unroll
                 for (int k = 0; k < NP; k++) {
                     const bool va = v[2 * k], vb = v[2 * k + 1];
-                    n_comp += (unsigned)va + (unsigned)vb;
+                    if (COUNT) n_comp += (unsigned)va + (unsigned)vb;
                     const float a0 = va ? fminf(r[k].x, kAlphaMax) : 0.f, a1 = vb ? fminf(r[k].y, kAlphaMax) : 0.f;
                     const float2 al = make_float2(a0, a1);
                     // a pixel that does not composite this Gaussian has alpha 0: 1 / (1 - 0) is
@@ -611,7 +613,8 @@ int occupancy_bwd() {
     constexpr int PX = bwd_px<TW, TH>();
     static int blocks = 0;
     if (!blocks)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, composite_bwd_kernel<TW, TH, DEPTH, PX>, TW * TH / PX, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, composite_bwd_kernel<TW, TH, DEPTH, PX, false>,
+                                                      TW * TH / PX, 0);
     return blocks > 0 ? blocks : 1;
 }
 
@@ -629,11 +632,16 @@ cudaError_t run_fwd(const Work &w, const unsigned *ids, float bg0, float bg1, fl
 
 template <int TW, int TH, int DEPTH>
 cudaError_t run_bwd(const Work &w, const unsigned *ids, float bg0, float bg1, float bg2, const float *T,
-                    const int32_t *idx, const float *dL, int num_sms, cudaStream_t s) {
+                    const int32_t *idx, const float *dL, bool count, int num_sms, cudaStream_t s) {
     unsigned grid = min(w.L.tiles, (unsigned)(num_sms * occupancy_bwd<TW, TH, DEPTH>()));
     if (grid == 0) return cudaSuccess;
     constexpr int PX = bwd_px<TW, TH>();
-    launch_pdl(composite_bwd_kernel<TW, TH, DEPTH, PX>, grid, TW * TH / PX, 0, s, w, ids, bg0, bg1, bg2, T, idx, dL);
+    if (count)
+        launch_pdl(composite_bwd_kernel<TW, TH, DEPTH, PX, true>, grid, TW * TH / PX, 0, s, w, ids, bg0, bg1, bg2, T,
+                   idx, dL);
+    else
+        launch_pdl(composite_bwd_kernel<TW, TH, DEPTH, PX, false>, grid, TW * TH / PX, 0, s, w, ids, bg0, bg1, bg2, T,
+                   idx, dL);
     return cudaGetLastError();
 }
 
@@ -693,9 +701,9 @@ cudaError_t launch_composite_fwd(const Work &w, int tile_w, int tile_h, int dept
 
 cudaError_t launch_composite_bwd(const Work &w, int tile_w, int tile_h, int depth, int tile_buf, float bg0,
                                  float bg1, float bg2, const float *final_T, const int32_t *last_idx,
-                                 const float *dL_dimage, int num_sms, cudaStream_t s) {
+                                 const float *dL_dimage, bool count_replayed, int num_sms, cudaStream_t s) {
     const unsigned *ids = w.tval[tile_buf];
-    GV_DISPATCH(run_bwd, w, ids, bg0, bg1, bg2, final_T, last_idx, dL_dimage, num_sms, s)
+    GV_DISPATCH(run_bwd, w, ids, bg0, bg1, bg2, final_T, last_idx, dL_dimage, count_replayed, num_sms, s)
 }
 
 }  // namespace gvk

@@ -240,10 +240,11 @@ cudaError_t launch_ranges(const Work &w, int tile_buf, int num_sms, cudaStream_t
 cudaError_t launch_composite_fwd(const Work &w, int tile_w, int tile_h, int depth, int tile_buf,
                                  float bg0, float bg1, float bg2, float *image, float *final_T,
                                  int32_t *last_idx, int num_sms, cudaStream_t s);
+// count_replayed: also count the replayed pairs (work[3]; costs inner-loop instructions)
 cudaError_t launch_composite_bwd(const Work &w, int tile_w, int tile_h, int depth, int tile_buf,
                                  float bg0, float bg1, float bg2, const float *final_T,
-                                 const int32_t *last_idx, const float *dL_dimage, int num_sms,
-                                 cudaStream_t s);
+                                 const int32_t *last_idx, const float *dL_dimage, bool count_replayed,
+                                 int num_sms, cudaStream_t s);
 // optim.cu
 cudaError_t launch_l2_loss(const float *image, const float *target, long long n, float scale,
                            float *dL, float *loss, cudaStream_t s);

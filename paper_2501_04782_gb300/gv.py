@@ -395,8 +395,10 @@ class Context:
                                         ctypes.byref(gr), int(reps), ctypes.byref(best), ms, _stream_handle(stream)))
         return best, list(ms)
 
-    def profile_enable(self, on: bool = True):
-        self.check(self.lib.gv_profile_enable(self.h, 1 if on else 0))
+    def profile_enable(self, on: bool | int = True):
+        """Per-stage events on later calls (on = 2: the backward also counts the pairs it
+        replays, read by read_counters as "bwd_replayed")."""
+        self.check(self.lib.gv_profile_enable(self.h, int(on)))
 
     def profile_read(self) -> tuple[dict, dict]:
         """(ms per stage of the most recent call, kernel launches per stage)."""

@@ -137,3 +137,28 @@ def test_degenerate_inputs():
     # backward of all-zero upstream gradient is exactly zero
     gr = run.backward(np.zeros(3))
     assert all(np.all(v == 0) for v in gr.values())
+
+
+def test_replayed_pair_count_only_in_profile_mode_2():
+    """The backward's replayed pairs (read_counters "bwd_replayed") are counted only in
+    profile mode 2, where they equal the oracle's composited (pixel, Gaussian) pairs over the
+    whole 128x128 frame, up to one per pixel whose outcome is ambiguous; otherwise 0."""
+    w = synth.workload_single_128()
+    cam = w["frames"][0][0]
+    ctx = gv.Context((16, 16), 64)
+    run = CudaRun(ctx, w["gaussians"], w["frames"]).forward()
+    dL = np.full(3 * run.total, 1e-3, np.float32)
+    run.backward(dL)
+    c0 = ctx.read_counters(run.ws)
+    # the forward evaluates a pixel's whole list unless it saturates; the backward replays
+    # up to the pixel's last contributor
+    assert c0["bwd_replayed"] == 0 and 0 < c0["bwd_eval"] <= c0["fwd_eval"]
+    ctx.profile_enable(2)
+    run.forward()
+    run.backward(dL)
+    ctx.profile_enable(False)
+    c2 = ctx.read_counters(run.ws)
+    px, py = np.meshgrid(np.arange(cam.W), np.arange(cam.H))
+    ref = oracle.render_pixels(w["gaussians"], cam, px.ravel(), py.ravel())
+    assert abs(c2["bwd_replayed"] - int(ref["n"].sum())) <= int(np.count_nonzero(ref["amb"] & 7))
+    assert 0 < c2["bwd_replayed"] <= c2["bwd_eval"] == c0["bwd_eval"]
