@@ -210,6 +210,22 @@ GV_API gv_status gv_render_bwd(gv_ctx *ctx, const gv_gaussians *g, const gv_came
                         size_t ws_bytes, const float *final_T, const int32_t *last_idx,
                         const float *dL_dimage, gv_gaussians_grad *grad, gv_stream stream);
 
+/* The forward with the L2 reconstruction loss of Sec. 4.1 fused into its compositing
+ * pass: besides image, final_T and last_idx it writes dL_dimage = 2 scale (image -
+ * target) (if not NULL) and adds scale * sum (image - target)^2 to *loss (if not NULL;
+ * one device float, accumulated: zero it first), the same values gv_l2_loss_grad computes
+ * from the image (the loss up to the order of the float additions).  target: device
+ * array in the image's layout, required.  Saves the loss kernel and its re-read of the
+ * image. */
+GV_API gv_status gv_render_batch_fwd_l2(gv_ctx *ctx, const gv_gaussians *g, const gv_frame_desc *frames,
+                                 int32_t F, void *workspace, size_t ws_bytes, float *image,
+                                 float *final_T, int32_t *last_idx, const float *target, float scale,
+                                 float *dL_dimage, float *loss, gv_stream stream);
+GV_API gv_status gv_render_fwd_l2(gv_ctx *ctx, const gv_gaussians *g, const gv_camera *cam, void *workspace,
+                           size_t ws_bytes, float *image, float *final_T, int32_t *last_idx,
+                           const float *target, float scale, float *dL_dimage, float *loss,
+                           gv_stream stream);
+
 /* Synchronise `stream` and report device-side failures recorded in the workspace by the
  * last render call: GV_ERR_CAPACITY (then *keys_needed, if not NULL, is the key capacity
  * the call needs: its kept keys, or more when its cells -- the tiles of the Gaussians'
@@ -294,6 +310,7 @@ typedef struct gv_graph gv_graph;
  * loss = loss_scale * sum (image - target)^2 and dL_dimage = 2 loss_scale (image -
  * target) (dL_dimage is then an output).  gv_graph_set_frames replaces the frame
  * cameras of an instantiated graph (same sizes, offsets and counts) without recapture.
+ * The loss is fused into the forward's compositing pass (gv_render_batch_fwd_l2).
  * Launch with gv_graph_launch. */
 GV_API gv_status gv_graph_capture(gv_ctx *ctx, const gv_gaussians *g, const gv_frame_desc *frames,
                            int32_t F, void *workspace, size_t ws_bytes, float *image,

@@ -337,8 +337,9 @@ cudaError_t tile_sort_rest(gv_ctx *ctx, const Work &w, cudaStream_t s, int *tres
                              1);
 }
 
+// loss: the L2 loss fused into the compositing forward (target == nullptr: none)
 gv_status forward_stages(gv_ctx *ctx, const gv_gaussians *g, const Plan &pl, const Work &w, float *image,
-                         float *final_T, int32_t *last_idx, cudaStream_t s) {
+                         float *final_T, int32_t *last_idx, cudaStream_t s, const LossArgs &loss = LossArgs()) {
     const gv_options &o = ctx->opt;
     for (int i = 0; i < GV_NUM_STAGES; i++) ctx->launches[i] = 0;
     {
@@ -380,7 +381,7 @@ gv_status forward_stages(gv_ctx *ctx, const gv_gaussians *g, const Plan &pl, con
     {
         StageTimer tm(ctx, GV_STAGE_COMPOSITE_FWD, s, 1);
         GV_CUDA(launch_composite_fwd(w, o.tile_w, o.tile_h, o.stage_depth, tile_result_buf(w.L), o.bg[0], o.bg[1],
-                                     o.bg[2], image, final_T, last_idx, ctx->num_sms, s));
+                                     o.bg[2], image, final_T, last_idx, loss, ctx->num_sms, s));
     }
     return GV_OK;
 }
@@ -615,6 +616,25 @@ gv_status gv_render_batch_fwd(gv_ctx *ctx, const gv_gaussians *g, const gv_frame
     return forward_stages(ctx, g, pl, w, image, final_T, last_idx, (cudaStream_t)stream);
 }
 
+gv_status gv_render_batch_fwd_l2(gv_ctx *ctx, const gv_gaussians *g, const gv_frame_desc *frames, int32_t F,
+                                 void *workspace, size_t ws_bytes, float *image, float *final_T, int32_t *last_idx,
+                                 const float *target, float scale, float *dL_dimage, float *loss, gv_stream stream) {
+    if (!ctx) return GV_ERR_INVALID_ARG;
+    gv_status st = check_gaussians(ctx, g);
+    if (st != GV_OK) return st;
+    if (!workspace || !image || !final_T || !last_idx || !target) return fail(ctx, GV_ERR_INVALID_ARG, "NULL buffer");
+    Plan pl;
+    st = make_plan(ctx, ctx->opt, g->N, frames, F, 0, ws_bytes, pl, g->n_ctrl);
+    if (st != GV_OK) return st;
+    Work w = make_work(workspace, pl.L);
+    LossArgs la;
+    la.target = target;
+    la.dL = dL_dimage;
+    la.loss = loss;
+    la.scale = scale;
+    return forward_stages(ctx, g, pl, w, image, final_T, last_idx, (cudaStream_t)stream, la);
+}
+
 gv_status gv_render_batch_bwd(gv_ctx *ctx, const gv_gaussians *g, const gv_frame_desc *frames, int32_t F,
                               void *workspace, size_t ws_bytes, const float *final_T, const int32_t *last_idx,
                               const float *dL_dimage, gv_gaussians_grad *grad, gv_stream stream) {
@@ -636,6 +656,15 @@ gv_status gv_render_fwd(gv_ctx *ctx, const gv_gaussians *g, const gv_camera *cam
     if (!ctx || !g || !cam) return ctx ? fail(ctx, GV_ERR_INVALID_ARG, "NULL argument") : GV_ERR_INVALID_ARG;
     gv_frame_desc d = single_frame(cam, g->N);
     return gv_render_batch_fwd(ctx, g, &d, 1, workspace, ws_bytes, image, final_T, last_idx, stream);
+}
+
+gv_status gv_render_fwd_l2(gv_ctx *ctx, const gv_gaussians *g, const gv_camera *cam, void *workspace,
+                           size_t ws_bytes, float *image, float *final_T, int32_t *last_idx, const float *target,
+                           float scale, float *dL_dimage, float *loss, gv_stream stream) {
+    if (!ctx || !g || !cam) return ctx ? fail(ctx, GV_ERR_INVALID_ARG, "NULL argument") : GV_ERR_INVALID_ARG;
+    gv_frame_desc d = single_frame(cam, g->N);
+    return gv_render_batch_fwd_l2(ctx, g, &d, 1, workspace, ws_bytes, image, final_T, last_idx, target, scale,
+                                  dL_dimage, loss, stream);
 }
 
 gv_status gv_render_bwd(gv_ctx *ctx, const gv_gaussians *g, const gv_camera *cam, void *workspace, size_t ws_bytes,
@@ -826,13 +855,19 @@ gv_status gv_graph_capture(gv_ctx *ctx, const gv_gaussians *g, const gv_frame_de
     cudaError_t e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { delete G; return fail(ctx, GV_ERR_CUDA, "begin capture: %s", cudaGetErrorString(e)); }
     ctx->capturing = true;
-    st = forward_stages(ctx, g, G->plan, G->work, image, final_T, last_idx, s);
-    if (st == GV_OK && target) {
-        long long n = 3ll * total_pixels(G->plan);
-        cudaError_t e2 = loss ? cudaMemsetAsync(loss, 0, sizeof(float), s) : cudaSuccess;
-        if (e2 == cudaSuccess) e2 = launch_l2_loss(image, target, n, loss_scale, dL_dimage, loss, s);
-        if (e2 != cudaSuccess) st = fail(ctx, GV_ERR_CUDA, "loss in capture: %s", cudaGetErrorString(e2));
+    // with a target, the L2 loss is fused into the compositing forward
+    LossArgs la;
+    if (target) {
+        la.target = target;
+        la.dL = dL_dimage;
+        la.loss = loss;
+        la.scale = loss_scale;
+        if (loss) {
+            const cudaError_t e2 = cudaMemsetAsync(loss, 0, sizeof(float), s);
+            if (e2 != cudaSuccess) st = fail(ctx, GV_ERR_CUDA, "loss in capture: %s", cudaGetErrorString(e2));
+        }
     }
+    if (st == GV_OK) st = forward_stages(ctx, g, G->plan, G->work, image, final_T, last_idx, s, la);
     if (st == GV_OK && dL_dimage)
         st = backward_stages(ctx, g, G->plan, G->work, final_T, last_idx, dL_dimage, grad, s);
     ctx->capturing = false;

@@ -136,10 +136,47 @@ __device__ __forceinline__ void stage_copy_records(const Work &w, const unsigned
     }
 }
 
+// One pixel's colour out of the forward, and with a loss target its L2 terms: dL =
+// 2 scale (c - target) per channel, the squared differences added to acc.
+__device__ __forceinline__ void write_pixel(float *image, size_t img, size_t plane, float c0, float c1, float c2,
+                                            const LossArgs &ls, float &acc) {
+    image[img] = c0;
+    image[img + plane] = c1;
+    image[img + 2 * plane] = c2;
+    if (ls.target) {
+        const float d0 = c0 - ls.target[img], d1 = c1 - ls.target[img + plane], d2 = c2 - ls.target[img + 2 * plane];
+        if (ls.dL) {
+            const float two_s = 2.f * ls.scale;
+            ls.dL[img] = two_s * d0;
+            ls.dL[img + plane] = two_s * d1;
+            ls.dL[img + 2 * plane] = two_s * d2;
+        }
+        acc = fmaf(d0, d0, acc);
+        acc = fmaf(d1, d1, acc);
+        acc = fmaf(d2, d2, acc);
+    }
+}
+
+// The block's loss terms into *loss (scaled), one atomic per block; every thread calls it.
+template <int NT>
+__device__ __forceinline__ void flush_loss(const LossArgs &ls, float acc) {
+    if (!ls.target || !ls.loss) return;
+    __shared__ float s_l[NT / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) s_l[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int i = 0; i < NT / 32; i++) t += s_l[i];
+        atomicAdd(ls.loss, ls.scale * t);
+    }
+}
+
 template <int TW, int TH, int DEPTH>
 __global__ void __launch_bounds__(TW *TH / 2) composite_fwd_kernel(Work w, const unsigned *ids, float bg0, float bg1,
                                                                    float bg2, float *image, float *final_T,
-                                                                   int32_t *last_idx) {
+                                                                   int32_t *last_idx, LossArgs ls) {
     pdl_prologue();
     constexpr int NT = TW * TH / 2;
     __shared__ float4 s_a[DEPTH + 1];
@@ -151,6 +188,7 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_fwd_kernel(Work w, const
     const unsigned ntiles = w.L.tiles;
     const int F = (int)w.L.F;
     const bool failed = w.hdr->err != 0u;  // lists incomplete: every tile renders empty
+    float lacc = 0.f;  // this thread's squared loss terms
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&w.hdr->queue[0], 1u);
         __syncthreads();
@@ -228,23 +266,22 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_fwd_kernel(Work w, const
         if (in0) {
             const size_t pix = (size_t)fr.pixel_offset + (size_t)y0 * W + x;
             const size_t img = 3 * (size_t)fr.pixel_offset + (size_t)y0 * W + x;
-            image[img] = fmaf(T.x, bg0, cr.x);
-            image[img + plane] = fmaf(T.x, bg1, cg.x);
-            image[img + 2 * plane] = fmaf(T.x, bg2, cb.x);
+            write_pixel(image, img, plane, fmaf(T.x, bg0, cr.x), fmaf(T.x, bg1, cg.x), fmaf(T.x, bg2, cb.x), ls,
+                        lacc);
             final_T[pix] = T.x;
             last_idx[pix] = last0;
         }
         if (in1) {
             const size_t pix = (size_t)fr.pixel_offset + (size_t)y1 * W + x;
             const size_t img = 3 * (size_t)fr.pixel_offset + (size_t)y1 * W + x;
-            image[img] = fmaf(T.y, bg0, cr.y);
-            image[img + plane] = fmaf(T.y, bg1, cg.y);
-            image[img + 2 * plane] = fmaf(T.y, bg2, cb.y);
+            write_pixel(image, img, plane, fmaf(T.y, bg0, cr.y), fmaf(T.y, bg1, cg.y), fmaf(T.y, bg2, cb.y), ls,
+                        lacc);
             final_T[pix] = T.y;
             last_idx[pix] = last1;
         }
         __syncthreads();
     }
+    flush_loss<NT>(ls, lacc);
 }
 
 // The forward with PX (four) pixels per lane; same arithmetic and decisions as
@@ -252,7 +289,7 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_fwd_kernel(Work w, const
 template <int TW, int TH, int DEPTH, int PX>
 __global__ void __launch_bounds__(TW *TH / PX) composite_fwd4_kernel(Work w, const unsigned *ids, float bg0, float bg1,
                                                                      float bg2, float *image, float *final_T,
-                                                                     int32_t *last_idx) {
+                                                                     int32_t *last_idx, LossArgs ls) {
     pdl_prologue();
     using M = PixMap<TW, TH, PX>;
     constexpr int NT = M::NT, NP = PX / 2;
@@ -266,6 +303,7 @@ __global__ void __launch_bounds__(TW *TH / PX) composite_fwd4_kernel(Work w, con
     const unsigned ntiles = w.L.tiles;
     const int F = (int)w.L.F;
     const bool failed = w.hdr->err != 0u;  // lists incomplete: every tile renders empty
+    float lacc = 0.f;  // this thread's squared loss terms
     for (;;) {
         if (threadIdx.x == 0) s_tile = atomicAdd(&w.hdr->queue[0], 1u);
         __syncthreads();
@@ -380,15 +418,14 @@ __global__ void __launch_bounds__(TW *TH / PX) composite_fwd4_kernel(Work w, con
             n_eval += (Tq < kTStop) ? (unsigned)(last[q] + 1 - (int)rg.x) : rg.y - rg.x;
             const size_t pix = (size_t)fr.pixel_offset + (size_t)y * W + x;
             const size_t img = 3 * (size_t)fr.pixel_offset + (size_t)y * W + x;
-            image[img] = fmaf(Tq, bg0, rq);
-            image[img + plane] = fmaf(Tq, bg1, gq);
-            image[img + 2 * plane] = fmaf(Tq, bg2, bq);
+            write_pixel(image, img, plane, fmaf(Tq, bg0, rq), fmaf(Tq, bg1, gq), fmaf(Tq, bg2, bq), ls, lacc);
             final_T[pix] = Tq;
             last_idx[pix] = last[q];
         }
         add_work(w.hdr->work, n_eval, 0u);
         __syncthreads();
     }
+    flush_loss<NT>(ls, lacc);
 }
 
 // Pixels per lane of the forward for a tile shape (measured: four on 32x32 tiles, 17 %
@@ -620,13 +657,15 @@ int occupancy_bwd() {
 
 template <int TW, int TH, int DEPTH>
 cudaError_t run_fwd(const Work &w, const unsigned *ids, float bg0, float bg1, float bg2, float *image, float *T,
-                    int32_t *idx, int num_sms, cudaStream_t s) {
+                    int32_t *idx, const LossArgs &ls, int num_sms, cudaStream_t s) {
     unsigned grid = min(w.L.tiles, (unsigned)(num_sms * occupancy_fwd<TW, TH, DEPTH>()));
     if (grid == 0) return cudaSuccess;
     if constexpr (fwd_px<TW, TH>() == 4)
-        launch_pdl(composite_fwd4_kernel<TW, TH, DEPTH, 4>, grid, TW * TH / 4, 0, s, w, ids, bg0, bg1, bg2, image, T, idx);
+        launch_pdl(composite_fwd4_kernel<TW, TH, DEPTH, 4>, grid, TW * TH / 4, 0, s, w, ids, bg0, bg1, bg2, image, T, idx,
+                   ls);
     else
-        launch_pdl(composite_fwd_kernel<TW, TH, DEPTH>, grid, TW * TH / 2, 0, s, w, ids, bg0, bg1, bg2, image, T, idx);
+        launch_pdl(composite_fwd_kernel<TW, TH, DEPTH>, grid, TW * TH / 2, 0, s, w, ids, bg0, bg1, bg2, image, T, idx,
+                   ls);
     return cudaGetLastError();
 }
 
@@ -694,9 +733,9 @@ cudaError_t run_bwd(const Work &w, const unsigned *ids, float bg0, float bg1, fl
 
 cudaError_t launch_composite_fwd(const Work &w, int tile_w, int tile_h, int depth, int tile_buf, float bg0,
                                  float bg1, float bg2, float *image, float *final_T, int32_t *last_idx,
-                                 int num_sms, cudaStream_t s) {
+                                 const LossArgs &loss, int num_sms, cudaStream_t s) {
     const unsigned *ids = w.tval[tile_buf];
-    GV_DISPATCH(run_fwd, w, ids, bg0, bg1, bg2, image, final_T, last_idx, num_sms, s)
+    GV_DISPATCH(run_fwd, w, ids, bg0, bg1, bg2, image, final_T, last_idx, loss, num_sms, s)
 }
 
 cudaError_t launch_composite_bwd(const Work &w, int tile_w, int tile_h, int depth, int tile_buf, float bg0,

@@ -237,9 +237,18 @@ __device__ __forceinline__ void count_digit(unsigned *row, unsigned d, unsigned 
 cudaError_t launch_emit(const Work &w, int depth_buf, int tile_w, int tile_h, int num_sms, cudaStream_t s);
 cudaError_t launch_ranges(const Work &w, int tile_buf, int num_sms, cudaStream_t s);
 // composite.cu
+// The L2 loss fused into the compositing forward (Sec. 4.1); target == nullptr: none.
+// dL (if not null) = 2 scale (image - target), loss (if not null) += scale sum (image -
+// target)^2 -- the same expressions as the separate loss kernel.
+struct LossArgs {
+    const float *target = nullptr;
+    float *dL = nullptr;
+    float *loss = nullptr;
+    float scale = 0.f;
+};
 cudaError_t launch_composite_fwd(const Work &w, int tile_w, int tile_h, int depth, int tile_buf,
                                  float bg0, float bg1, float bg2, float *image, float *final_T,
-                                 int32_t *last_idx, int num_sms, cudaStream_t s);
+                                 int32_t *last_idx, const LossArgs &loss, int num_sms, cudaStream_t s);
 // count_replayed: also count the replayed pairs (work[3]; costs inner-loop instructions)
 cudaError_t launch_composite_bwd(const Work &w, int tile_w, int tile_h, int depth, int tile_buf,
                                  float bg0, float bg1, float bg2, const float *final_T,

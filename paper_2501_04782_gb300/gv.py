@@ -23,7 +23,8 @@ EXPORTS = [
     "gv_read_status", "gv_l2_loss_grad", "gv_adam_step", "gv_adan_step", "gv_autotune", "gv_graph_capture",
     "gv_graph_set_frames", "gv_graph_launch", "gv_graph_destroy", "gv_debug_bin_sort", "gv_debug_read",
     "gv_debug_set_wait", "gv_debug_read_grad2d", "gv_profile_enable", "gv_profile_read",
-    "gv_read_counters", "gv_status_accumulate", "gv_render_fwd_noalloc",
+    "gv_read_counters", "gv_status_accumulate", "gv_render_fwd_noalloc", "gv_render_batch_fwd_l2",
+    "gv_render_fwd_l2",
 ]
 
 STAGES = ["setup", "project", "depth_sort", "emit", "tile_sort", "ranges", "composite_fwd", "composite_bwd",
@@ -90,6 +91,10 @@ _SIGS = {
     "gv_render_batch_bwd": [_vp, ctypes.POINTER(Gaussians), ctypes.POINTER(FrameDesc), ctypes.c_int32, _vp,
                             ctypes.c_size_t, _vp, _vp, _vp, ctypes.POINTER(GaussiansGrad), _vp],
     "gv_render_fwd": [_vp, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), _vp, ctypes.c_size_t, _vp, _vp, _vp, _vp],
+    "gv_render_batch_fwd_l2": [_vp, ctypes.POINTER(Gaussians), ctypes.POINTER(FrameDesc), ctypes.c_int32, _vp,
+                               ctypes.c_size_t, _vp, _vp, _vp, _vp, ctypes.c_float, _vp, _vp, _vp],
+    "gv_render_fwd_l2": [_vp, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), _vp, ctypes.c_size_t, _vp, _vp,
+                         _vp, _vp, ctypes.c_float, _vp, _vp, _vp],
     "gv_render_bwd": [_vp, ctypes.POINTER(Gaussians), ctypes.POINTER(Camera), _vp, ctypes.c_size_t, _vp, _vp, _vp,
                       ctypes.POINTER(GaussiansGrad), _vp],
     "gv_read_status": [_vp, _vp, ctypes.c_size_t, _vp, ctypes.POINTER(ctypes.c_int64)],
@@ -321,6 +326,16 @@ class Context:
         g = gaussians_struct(params, visible)
         self.check(self.lib.gv_render_batch_fwd(self.h, ctypes.byref(g), arr, len(frames), _ptr(ws), ws.numel(),
                                                 _ptr(image), _ptr(final_T), _ptr(last_idx), _stream_handle(stream)))
+
+    def render_fwd_l2(self, params: dict, frames: list[Frame], ws: torch.Tensor, image, final_T, last_idx, target,
+                      scale: float, dL_dimage, loss, stream=None):
+        """render_fwd with the L2 loss fused into compositing: also dL_dimage = 2 scale
+        (image - target) and loss += scale sum (image - target)^2 (dL_dimage or loss may be None)."""
+        arr = frame_array(frames)
+        g = gaussians_struct(params)
+        self.check(self.lib.gv_render_batch_fwd_l2(self.h, ctypes.byref(g), arr, len(frames), _ptr(ws), ws.numel(),
+                                                   _ptr(image), _ptr(final_T), _ptr(last_idx), _ptr(target),
+                                                   float(scale), _ptr(dL_dimage), _ptr(loss), _stream_handle(stream)))
 
     def render_bwd(self, params: dict, frames: list[Frame], ws: torch.Tensor, final_T, last_idx, dL_dimage,
                    grads: dict, stream=None):

@@ -25,6 +25,43 @@ def test_l2_loss_and_gradient():
     assert np.allclose(dL.cpu().numpy(), g, rtol=1e-6, atol=1e-12)
 
 
+@pytest.mark.parametrize("tile, depth", [((32, 16), 64), ((32, 32), 128), ((8, 8), 32)])
+def test_forward_with_fused_l2_loss(tile, depth):
+    """gv_render_batch_fwd_l2 on an uneven batch (three frames, own sets, ragged tiles; 32x32
+    tiles take the four-pixel forward): image, final T and last index equal the plain
+    forward's bit for bit, dL_dimage equals gv_l2_loss_grad's on that image bit for bit,
+    and the loss matches it (and the oracle's loss of that image) up to the order of the
+    float additions.  dL_dimage or loss may be left out."""
+    wu = synth.workload_uneven(F=3, n_lo=2e3, n_hi=2e4, resolutions=((131, 75), (200, 120), (96, 64)))
+    ctx = gv.Context(tile, depth)
+    run = CudaRun(ctx, wu["gaussians"], wu["frames"]).forward(grow=True)
+    n = 3 * run.total
+    rng = np.random.default_rng(5)
+    tgt_np = rng.uniform(size=n).astype(np.float32)
+    tgt = torch.from_numpy(tgt_np).cuda()
+    scale = 1.0 / n
+    dL_ref = torch.empty(n, device="cuda")
+    loss_ref = torch.zeros(1, device="cuda")
+    ctx.l2_loss_grad(run.image, tgt, scale, dL_ref, loss_ref)
+    image, T = torch.full_like(run.image, float("nan")), torch.full_like(run.T, float("nan"))
+    idx = torch.full_like(run.idx, -7)
+    dL = torch.full((n,), float("nan"), device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    ctx.render_fwd_l2(run.params, run.frames, run.ws, image, T, idx, tgt, scale, dL, loss)
+    torch.cuda.synchronize()
+    assert torch.equal(image, run.image) and torch.equal(T, run.T) and torch.equal(idx, run.idx)
+    assert torch.equal(dL, dL_ref)
+    L, _ = oracle.l2_loss_grad(run.image.cpu().numpy(), tgt_np, scale)
+    assert loss.item() == pytest.approx(loss_ref.item(), rel=1e-5)
+    assert loss.item() == pytest.approx(L, rel=1e-5)
+    loss2 = torch.zeros(1, device="cuda")
+    ctx.render_fwd_l2(run.params, run.frames, run.ws, image, T, idx, tgt, scale, None, loss2)
+    dL2 = torch.full((n,), float("nan"), device="cuda")
+    ctx.render_fwd_l2(run.params, run.frames, run.ws, image, T, idx, tgt, scale, dL2, None)
+    torch.cuda.synchronize()
+    assert loss2.item() == pytest.approx(loss_ref.item(), rel=1e-5) and torch.equal(dL2, dL_ref)
+
+
 @pytest.mark.parametrize("offset", [0, 1])
 def test_adam_matches_oracle_over_steps(offset):
     """n = 10007: float4 vectors and a ragged tail; offset 1: arrays not 16-byte aligned."""
