@@ -675,6 +675,10 @@ gv_status gv_render_bwd(gv_ctx *ctx, const gv_gaussians *g, const gv_camera *cam
     return gv_render_batch_bwd(ctx, g, &d, 1, workspace, ws_bytes, final_T, last_idx, dL_dimage, grad, stream);
 }
 
+// The forward for callers that cannot allocate device memory: a plug-in whose host
+// application owns every device allocation (it may not call cudaMalloc itself), or a
+// real-time loop that must not let cudaMalloc / cudaFree synchronise the device in the
+// middle of a frame.  Its workspace is g_noalloc_scratch; the kernels are gv_render_fwd's.
 gv_status gv_render_fwd_noalloc(gv_ctx *ctx, const gv_gaussians *g, const gv_camera *cam, float *image,
                                 float *final_T, int32_t *last_idx, gv_stream stream) {
     if (!ctx) return GV_ERR_INVALID_ARG;
