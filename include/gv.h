@@ -396,7 +396,8 @@ GV_API gv_status gv_debug_read_grad2d(gv_ctx *ctx, const gv_frame_desc *frames, 
  * image, final_T and last_idx are the caller's device buffers as for gv_render_fwd, and
  * the results are the same.
  *  - Each call looks up the array's device address in the current context (the current
- *    device's); the first call on a device also loads the library's module there.
+ *    device's); the first call on a device also loads the library's module there, so that
+ *    first call should come before any stream capture.
  *  - Every call on a device shares the one array and leaves the last call's contents in
  *    it; each call clears what must start at zero.  Calls that overlap on the GPU (two
  *    streams, two threads, two contexts of one process) race on the array: serialise them.
