@@ -436,13 +436,6 @@ gv_status check_grad(gv_ctx *ctx, const gv_gaussians_grad *grad, const gv_gaussi
     return GV_OK;
 }
 
-// Pixels covered by the frames' outputs (largest pixel_offset + W*H).
-long long total_pixels(const Plan &pl) {
-    long long t = 0;
-    for (const DevFrame &f : pl.frames) t = std::max<long long>(t, f.pixel_offset + (long long)f.W * f.H);
-    return t;
-}
-
 gv_frame_desc single_frame(const gv_camera *cam, long long N) {
     gv_frame_desc d;
     memset(&d, 0, sizeof(d));
