@@ -382,7 +382,7 @@ def run_gv(args):
     tile_passes = math.ceil(max(1, math.ceil(math.log2(tiles))) / 8)
     stages = stage_rates(stage_work(counters, tile_passes, "vel" in params, n_gauss), mean_stage, hbm_peak,
                          fp32_peak)
-    for s in ("setup", "ranges"):
+    for s in ("setup", "ranges"):  # (up to 2^22 keys of capacity the ranges have no launch: 0)
         stages[s] = {"ms": round(mean_stage[s], 4)}
     d = stages.get(dom, {"bound": "alu", "achieved": None, "unit": "Gop/s", "frac": None})
     # DRAM bytes per launch (read + write) of the dominant kernel in this launch configuration,

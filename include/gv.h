@@ -330,7 +330,9 @@ typedef enum {
     GV_STAGE_DEPTH_SORT = 2,    /* radix sort of the pairs by camera depth */
     GV_STAGE_EMIT = 3,          /* tile-count scan and key emission in depth order */
     GV_STAGE_TILE_SORT = 4,     /* stable radix sort of the keys by tile id */
-    GV_STAGE_RANGES = 5,        /* per-tile [start, end) of the sorted list */
+    GV_STAGE_RANGES = 5,        /* per-tile [start, end) of the sorted list (lists of up to
+                                   2^22 keys of capacity: recorded by the kernel that writes
+                                   the list, no launch of its own and no events) */
     GV_STAGE_COMPOSITE_FWD = 6, /* front-to-back alpha compositing */
     GV_STAGE_COMPOSITE_BWD = 7, /* back-to-front replay, screen-space gradients */
     GV_STAGE_PROJECT_BWD = 8,   /* chain rule to the raw parameters */

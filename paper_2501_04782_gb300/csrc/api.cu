@@ -334,7 +334,7 @@ cudaError_t tile_sort_rest(gv_ctx *ctx, const Work &w, cudaStream_t s, int *tres
         reinterpret_cast<const unsigned *>(reinterpret_cast<const char *>(w.hdr) + offsetof(DevHeader, keys_used));
     unsigned *tk[2] = {w.tkey[0], w.tkey[1]}, *tv[2] = {w.tval[0], w.tval[1]};
     return launch_radix_sort(w, tk, tv, n_keys, w.L.key_cap, w.L.tile_bits, false, true, 4, 4, ctx->num_sms, s, tres,
-                             1);
+                             1, nullptr, w.L.key_cap <= kFusedRangesKeys ? w.ranges : nullptr, w.L.tiles);
 }
 
 // loss: the L2 loss fused into the compositing forward (target == nullptr: none)
@@ -373,7 +373,7 @@ gv_status forward_stages(gv_ctx *ctx, const gv_gaussians *g, const Plan &pl, con
             StageTimer tm(ctx, GV_STAGE_TILE_SORT, s, sort_passes(w.L.tile_bits) - 1);
             GV_CUDA(tile_sort_rest(ctx, w, s, &tres));
         }
-        {
+        if (w.L.key_cap > kFusedRangesKeys) {  // else recorded by the kernel that wrote the list
             StageTimer tm(ctx, GV_STAGE_RANGES, s, 1);
             GV_CUDA(launch_ranges(w, tres, ctx->num_sms, s));
         }
@@ -1022,8 +1022,7 @@ gv_status gv_debug_read(gv_ctx *ctx, const gv_frame_desc *frames, int32_t F, con
         GV_CUDA(cudaMemcpyAsync(sorted_id, w.tval[tres], 4 * (size_t)h.keys_used, cudaMemcpyDeviceToDevice, s));
     if (sorted_tile && h.keys_used)
         GV_CUDA(cudaMemcpyAsync(sorted_tile, w.tkey[tres], 4 * (size_t)h.keys_used, cudaMemcpyDeviceToDevice, s));
-    if (ranges && pl.L.tiles)
-        GV_CUDA(cudaMemcpyAsync(ranges, w.ranges, 8 * (size_t)pl.L.tiles, cudaMemcpyDeviceToDevice, s));
+    if (ranges) GV_CUDA(launch_debug_ranges(w, reinterpret_cast<uint2 *>(ranges), s));
     GV_CUDA(cudaStreamSynchronize(s));
     if (P) *P = pl.L.P;
     if (K) *K = h.keys_used;

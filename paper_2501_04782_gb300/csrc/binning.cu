@@ -33,7 +33,9 @@ __global__ void setup_kernel(Work w, FrameChunk chunk, int first, int count, int
         *w.hdr = h;
     }
     for (int i = tid; i < 8 * kRadix; i += stride) w.hist[i] = 0u;
-    for (unsigned i = tid; i < w.L.tiles; i += stride) w.ranges[i] = make_uint2(0u, 0u);
+    // each tile's [start, end) is recorded by min / max over the runs of its id in the final
+    // list (start >= end: an empty tile)
+    for (unsigned i = tid; i < w.L.tiles; i += stride) w.ranges[i] = make_uint2(0xFFFFFFFFu, 0u);
     for (unsigned i = tid; i < w.L.emit_blocks; i += stride) w.scan_look[i] = 0ull;
     // look-back buffer 0 of the depth sort (its digits are counted by the projection)
     const unsigned nlook = sort_tiles(w.L.P, w.L.P) * kRadix;
@@ -193,9 +195,12 @@ struct EmitSortArgs {
     const unsigned *hist;   // low-digit counts of all kept keys
     unsigned *ctr;          // chunk counter
     unsigned *look_next;    // look-back buffer of the next tile-sort pass (cleared here)
+    uint2 *ranges;          // tile ids of one digit: this pass is the whole sort, so it also
+                            // records each tile's [start, end) (RANGES)
     int lw, lh;
 };
 
+template <bool RANGES>
 __global__ void __launch_bounds__(kEmitThreads, 4) emit_sort_kernel(Work w, EmitSortArgs a) {
     pdl_prologue();
     __shared__ int s_owner[kEmitBlock];          // later: the chunk's keys, reordered by digit
@@ -396,6 +401,10 @@ __global__ void __launch_bounds__(kEmitThreads, 4) emit_sort_kernel(Work w, Emit
                 if (gpos < w.L.key_cap) {
                     a.keys_out[gpos] = k;
                     a.vals_out[gpos] = s_vals[pos];
+                    if (RANGES) {  // runs of equal tile ids are contiguous in the chunk's order
+                        if (pos == 0 || s_keys[pos - 1] != k) atomicMin(&a.ranges[k].x, gpos);
+                        if (pos + 1 == nkeys || s_keys[pos + 1] != k) atomicMax(&a.ranges[k].y, gpos + 1u);
+                    }
                 }
             }
         }
@@ -403,7 +412,8 @@ __global__ void __launch_bounds__(kEmitThreads, 4) emit_sort_kernel(Work w, Emit
     }
 }
 
-// Per-tile [start, end) of the sorted keys.  A warp takes 32 * kRangeItems consecutive keys
+// Per-tile [start, end) of the sorted keys, for lists of more than kFusedRangesKeys keys of
+// capacity (the kernel that writes a smaller final list records them itself).  A warp takes 32 * kRangeItems consecutive keys
 // per round (lane l holds keys l, l + 32, ...: independent coalesced loads in flight) and
 // gets each key's neighbours by shuffles; only the round's two outer neighbours are loaded.
 constexpr int kRangeItems = 8;
@@ -438,6 +448,15 @@ __global__ void __launch_bounds__(256) ranges_kernel(Work w, const unsigned *key
             if (i == 0 || prev != t) w.ranges[t].x = i;
             if (i == n - 1 || next != t) w.ranges[t].y = i + 1;
         }
+    }
+}
+
+// The tile ranges for the debug read: an empty tile (start >= end) reads as (0, 0).
+__global__ void debug_ranges_kernel(Work w, uint2 *out) {
+    pdl_prologue();
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < w.L.tiles; t += gridDim.x * blockDim.x) {
+        const uint2 r = w.ranges[t];
+        out[t] = r.x < r.y ? r : make_uint2(0u, 0u);
     }
 }
 
@@ -488,15 +507,23 @@ cudaError_t launch_emit(const Work &w, int depth_buf, int tile_w, int tile_h, in
     a.hist = w.hist + 4 * kRadix;
     a.ctr = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(w.hdr) + offsetof(DevHeader, sort_ctr)) + 4;
     a.look_next = w.look + (size_t)w.L.look_tiles * kRadix;
+    a.ranges = w.ranges;
     a.lw = __builtin_ctz(tile_w);
     a.lh = __builtin_ctz(tile_h);
     const unsigned grid = std::max(1u, std::min(w.L.chunk_cap, (unsigned)num_sms * 4u));
-    launch_pdl(emit_sort_kernel, grid, kEmitThreads, 0, s, w, a);
+    if (sort_passes(w.L.tile_bits) <= 1 && w.L.key_cap <= kFusedRangesKeys)
+        launch_pdl(emit_sort_kernel<true>, grid, kEmitThreads, 0, s, w, a);
+    else launch_pdl(emit_sort_kernel<false>, grid, kEmitThreads, 0, s, w, a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ranges(const Work &w, int tile_buf, int num_sms, cudaStream_t s) {
     launch_pdl(ranges_kernel, num_sms * 8, 256, 0, s, w, w.tkey[tile_buf]);
+    return cudaGetLastError();
+}
+cudaError_t launch_debug_ranges(const Work &w, uint2 *out, cudaStream_t s) {
+    if (w.L.tiles == 0) return cudaSuccess;
+    launch_pdl(debug_ranges_kernel, (w.L.tiles + 255) / 256, 256, 0, s, w, out);
     return cudaGetLastError();
 }
 

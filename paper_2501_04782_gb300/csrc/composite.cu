@@ -205,7 +205,8 @@ __global__ void __launch_bounds__(TW *TH / 2) composite_fwd_kernel(Work w, const
         const bool in0 = x < W && y0 < H, in1 = x < W && y1 < H;
         const float px = (float)x + 0.5f;
         const float2 npy = make_float2(-((float)y0 + 0.5f), -((float)y1 + 0.5f));
-        const uint2 rg = failed ? make_uint2(0u, 0u) : w.ranges[tile];
+        uint2 rg = failed ? make_uint2(0u, 0u) : w.ranges[tile];
+        if (rg.x >= rg.y) rg = make_uint2(0u, 0u);  // an empty tile (no key recorded a range)
         float2 T = make_float2(1.f, 1.f), cr = make_float2(0.f, 0.f), cg = cr, cb = cr;
         int last0 = -1, last1 = -1;
         // per-pixel alpha threshold: 1/255, or 2 (above any alpha) once the pixel is done
@@ -318,7 +319,8 @@ __global__ void __launch_bounds__(TW *TH / PX) composite_fwd4_kernel(Work w, con
         const int x = (int)(lt % fr.tiles_x) * TW + lx;
         const int ybase = (int)(lt / fr.tiles_x) * TH + ly;
         const float px = (float)x + 0.5f;
-        const uint2 rg = failed ? make_uint2(0u, 0u) : w.ranges[tile];
+        uint2 rg = failed ? make_uint2(0u, 0u) : w.ranges[tile];
+        if (rg.x >= rg.y) rg = make_uint2(0u, 0u);  // an empty tile (no key recorded a range)
         // pixel 2k + h of the thread is row ybase + RS (2k + h); packed over pixel pairs
         float2 npy[NP], T[NP], cr[NP], cg[NP], cb[NP], thr[NP];
         int last[PX];
@@ -471,7 +473,8 @@ __global__ void __launch_bounds__(TW *TH / PX) composite_bwd_kernel(Work w, cons
         const int x = (int)(lt % fr.tiles_x) * TW + lx;
         const int ybase = (int)(lt / fr.tiles_x) * TH + ly;
         const float px = (float)x + 0.5f;
-        const uint2 rg = failed ? make_uint2(0u, 0u) : w.ranges[tile];
+        uint2 rg = failed ? make_uint2(0u, 0u) : w.ranges[tile];
+        if (rg.x >= rg.y) rg = make_uint2(0u, 0u);  // an empty tile (no key recorded a range)
         const size_t plane = (size_t)W * H;
         // per-pixel replay state, packed over pixel pairs: pixel 2k + h is row ybase + RS (2k + h)
         float2 npy[NP], T[NP], g0[NP], g1[NP], g2[NP], gS[NP];

@@ -225,7 +225,8 @@ int sort_passes(int bits);
 cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2], const unsigned *n_dev,
                               unsigned n_cap, int bits, bool vals_identity, bool prepared, int hist_slot,
                               int ctr_slot, int num_sms, cudaStream_t s, int *result_buf, int first_pass = 0,
-                              const unsigned *n_dev_later = nullptr);
+                              const unsigned *n_dev_later = nullptr, uint2 *final_ranges = nullptr,
+                              unsigned n_tiles = 0);
 // Warp-aggregated count of one 8-bit digit per lane into a shared histogram row.
 __device__ __forceinline__ void count_digit(unsigned *row, unsigned d, unsigned active) {
     const unsigned peers = __match_any_sync(active, d);
@@ -235,7 +236,16 @@ __device__ __forceinline__ void count_digit(unsigned *row, unsigned d, unsigned 
 // Cell offsets, then key emission fused with the first tile-sort pass: the kept keys land
 // in tkey[1] / tval[1] sorted by their low tile digit.
 cudaError_t launch_emit(const Work &w, int depth_buf, int tile_w, int tile_h, int num_sms, cudaStream_t s);
+// Each tile's [start, end) of the final list.  setup starts every tile empty (start >= end
+// reads as empty).  Lists of up to kFusedRangesKeys keys of capacity get them from the kernel
+// that writes the list (the last tile-sort pass, or the emission when the tile ids fit one
+// digit): one atomic min / max per run of equal ids it writes, which saves a launch.  Larger
+// lists -- where those atomics cost more than a separate pass (8 x 1920x1080 / 1M: 46M keys,
+// 64 runs per sort tile) -- from ranges_kernel (launch_ranges).  launch_debug_ranges copies
+// them out with empty tiles as (0, 0).
+constexpr unsigned kFusedRangesKeys = 1u << 22;
 cudaError_t launch_ranges(const Work &w, int tile_buf, int num_sms, cudaStream_t s);
+cudaError_t launch_debug_ranges(const Work &w, uint2 *out, cudaStream_t s);
 // composite.cu
 // The L2 loss fused into the compositing forward (Sec. 4.1); target == nullptr: none.
 // dL (if not null) = 2 scale (image - target), loss (if not null) += scale sum (image -

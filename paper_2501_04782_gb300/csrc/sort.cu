@@ -59,9 +59,12 @@ struct PassArgs {
     unsigned *look_next;    // cleared for the next pass
     unsigned *ctr;          // tile counter of this pass
     DevHeader *hdr;
+    uint2 *ranges;          // the last pass of the tile sort: each tile's [start, end) of the
+    unsigned n_tiles;       // final list, from the runs of equal keys it writes (else null)
 };
 
-template <int ITEMS, bool BALLOT>
+// RANGES: the last pass of a tile sort whose final list also gets each tile's range.
+template <int ITEMS, bool BALLOT, bool RANGES>
 __global__ void __launch_bounds__(kSortThreads, 4) sort_pass_kernel(PassArgs a) {
     pdl_prologue();
     constexpr int TILE = kSortThreads * ITEMS;
@@ -176,6 +179,13 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_pass_kernel(PassArgs a) 
                 if (gpos < n) {
                     a.keys_out[gpos] = key;
                     a.vals_out[gpos] = s_vals[pos];
+                    // the output is the final list: equal keys are contiguous here (stable, and
+                    // sorted by the lower bits before this pass), so each run's ends bound the
+                    // tile's range; other blocks' runs of the same key combine by min / max
+                    if (RANGES && key < a.n_tiles) {
+                        if (pos == 0 || s_keys[pos - 1] != key) atomicMin(&a.ranges[key].x, gpos);
+                        if (pos + 1 == (int)nlive || s_keys[pos + 1] != key) atomicMax(&a.ranges[key].y, gpos + 1u);
+                    }
                 }
             }
         }
@@ -202,7 +212,7 @@ constexpr unsigned kSortBallotN = 1u << 22;
 cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2], const unsigned *n_dev,
                               unsigned n_cap, int bits, bool vals_identity, bool prepared, int hist_slot,
                               int ctr_slot, int num_sms, cudaStream_t s, int *result_buf, int first_pass,
-                              const unsigned *n_dev_later) {
+                              const unsigned *n_dev_later, uint2 *final_ranges, unsigned n_tiles) {
     int passes = sort_passes(bits);
     *result_buf = first_pass & 1;
     if (passes <= first_pass || n_cap == 0) return cudaSuccess;
@@ -236,10 +246,19 @@ cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2
         a.ctr = reinterpret_cast<unsigned *>(reinterpret_cast<char *>(w.hdr) + offsetof(DevHeader, sort_ctr)) +
                 ctr_slot + ps;
         a.hdr = w.hdr;
-        if (items == 8) launch_pdl(sort_pass_kernel<8, false>, grid, kSortThreads, 0, s, a);
-        else if (items == 4) launch_pdl(sort_pass_kernel<4, false>, grid, kSortThreads, 0, s, a);
-        else if (n_cap < kSortBallotN) launch_pdl(sort_pass_kernel<12, false>, grid, kSortThreads, 0, s, a);
-        else launch_pdl(sort_pass_kernel<12, true>, grid, kSortThreads, 0, s, a);
+        a.ranges = ps == passes - 1 ? final_ranges : nullptr;
+        a.n_tiles = n_tiles;
+        if (a.ranges) {
+            if (items == 8) launch_pdl(sort_pass_kernel<8, false, true>, grid, kSortThreads, 0, s, a);
+            else if (items == 4) launch_pdl(sort_pass_kernel<4, false, true>, grid, kSortThreads, 0, s, a);
+            else if (n_cap < kSortBallotN) launch_pdl(sort_pass_kernel<12, false, true>, grid, kSortThreads, 0, s, a);
+            else launch_pdl(sort_pass_kernel<12, true, true>, grid, kSortThreads, 0, s, a);
+        } else {
+            if (items == 8) launch_pdl(sort_pass_kernel<8, false, false>, grid, kSortThreads, 0, s, a);
+            else if (items == 4) launch_pdl(sort_pass_kernel<4, false, false>, grid, kSortThreads, 0, s, a);
+            else if (n_cap < kSortBallotN) launch_pdl(sort_pass_kernel<12, false, false>, grid, kSortThreads, 0, s, a);
+            else launch_pdl(sort_pass_kernel<12, true, false>, grid, kSortThreads, 0, s, a);
+        }
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         cur ^= 1;

@@ -144,3 +144,35 @@ def test_projection_matches_fp64(wl):
     assert np.all(dd[same_tile] >= 0)
     ties = same_tile & (dd == 0)
     assert np.all(np.diff(s_id)[ties] > 0)
+
+
+@pytest.mark.parametrize("tile, wl, cap", [((32, 32), "single_128", 0), ((16, 16), "single_540p", 0),
+                                           ((8, 8), "clip_uhd", 0), ((16, 16), "single_540p", 5_000_000)])
+def test_tile_ranges_bound_each_tile_run(tile, wl, cap):
+    """Each tile's [start, end) equals the first and one-past-last position of the tile's id
+    in the sorted list, and (0, 0) for a tile with no key.  Up to 2^22 keys of capacity the
+    kernel that writes the final list records them: the emission when the tile ids fit one
+    digit (128x128 in 32x32 tiles: 16 tiles), else the last tile-sort pass (960x540 in 16x16
+    tiles: 11 bits, two passes; four 1920x1080 frames in 8x8 tiles: 17 bits, three passes).
+    With a capacity of 5M keys a separate kernel does."""
+    if wl == "single_128":
+        w = synth.workload_single_128()
+    elif wl == "single_540p":
+        w = synth.workload_single_540p(N=50000)
+    else:
+        w = synth.workload_clip_shared(F=4, N=20000, W=1920, H=1080)
+    ctx = gv.Context(tile, 64)
+    run = CudaRun(ctx, w["gaussians"], w["frames"], key_capacity=cap).forward()
+    dbg = run.debug()
+    st = dbg["sorted_tile"].cpu().numpy().astype(np.int64)
+    rg = dbg["ranges"].cpu().numpy().astype(np.int64)
+    n_tiles = dbg["tiles"]
+    assert len(st) == run.K > 0 and np.all(np.diff(st) >= 0)
+    lo = np.searchsorted(st, np.arange(n_tiles), side="left")
+    hi = np.searchsorted(st, np.arange(n_tiles), side="right")
+    expected = np.where((hi > lo)[:, None], np.stack([lo, hi], 1), 0)
+    assert np.array_equal(rg, expected)
+    if wl == "clip_uhd":
+        assert n_tiles > 1 << 16
+    if wl == "single_128":
+        assert n_tiles <= 256
