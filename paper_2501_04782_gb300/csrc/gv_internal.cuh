@@ -450,6 +450,77 @@ __device__ __forceinline__ unsigned lookback_digit(unsigned *look, unsigned tile
     return excl;
 }
 
+// Decoupled look-back of digit d by a group of G consecutive lanes of one warp (G a power of
+// two up to 32; member m = lane % G, gmask the group's lanes): the same protocol as
+// lookback_digit, but member m reads predecessors j - 4m .. j - 4m - 3, so one poll covers
+// 4G predecessors.  The group takes the nearest member whose window ends the walk (an
+// inclusive prefix, or an unpublished status) and sums the counts up to it; every member
+// returns the same sum.  Member 0 publishes.  Used by passes whose digit has fewer than 8
+// live bits, where the block has 256 / 2^bits threads per digit.
+__device__ __forceinline__ unsigned lookback_digit_group(unsigned *look, unsigned tile, unsigned d, unsigned mine,
+                                                         int G, int m, unsigned gmask, DevHeader *hdr,
+                                                         long long limit, bool drop, bool &gave_up) {
+    const int base = (int)(threadIdx.x & 31u) - m;  // the group's first lane
+    gave_up = false;
+    if (tile == 0) {
+        if (m == 0 && !drop) atomicExch(look + d, kFlagInc | mine);
+        return 0u;
+    }
+    if (m == 0) atomicExch(look + (size_t)tile * kRadix + d, kFlagAgg | mine);
+    unsigned excl = 0;
+    long long spins = 0;
+    int j = (int)tile - 1;
+    for (;;) {
+        unsigned st[kLookWindow];
+#pragma unroll
+        for (int k = 0; k < kLookWindow; k++) {
+            const int idx = j - kLookWindow * m - k;
+            const unsigned past = kFlagInc;  // before tile 0: an empty inclusive prefix
+            st[k] = idx >= 0 ? *((volatile unsigned *)(look + (size_t)idx * kRadix + d)) : past;
+        }
+        // this member's window, nearest first: 0 all aggregates, 1 an inclusive prefix ends it,
+        // 2 an unpublished status stops it (len: the entries taken)
+        unsigned sum = 0;
+        int term = 0, len = kLookWindow;
+#pragma unroll
+        for (int k = 0; k < kLookWindow; k++) {
+            if (term) continue;
+            const unsigned fl = st[k] & ~kValMask;
+            if (fl == kFlagInc) { sum += st[k] & kValMask; term = 1; len = k + 1; }
+            else if (fl == kFlagAgg) sum += st[k] & kValMask;
+            else { term = 2; len = k; }
+        }
+        const unsigned ended = (__ballot_sync(gmask, term != 0) >> base) & (G == 32 ? 0xffffffffu : (1u << G) - 1u);
+        const int ms = ended ? __ffs(ended) - 1 : G;  // nearest member whose window ends the walk
+        unsigned c = m <= ms ? sum : 0u;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+            if (o < G) c += __shfl_xor_sync(gmask, c, o, G);
+        excl += c;
+        const int ts = __shfl_sync(gmask, term, ms < G ? ms : 0, G);
+        const int ls = __shfl_sync(gmask, len, ms < G ? ms : 0, G);
+        if (ms < G && ts == 1) break;
+        const int taken = ms < G ? kLookWindow * ms + ls : kLookWindow * G;
+        j -= taken;
+        if (taken > 0) {
+            spins = 0;
+            continue;
+        }
+        bool quit = ++spins > limit || (*((volatile unsigned *)&hdr->err) & ERR_TIMEOUT);
+        quit = __shfl_sync(gmask, quit, 0, G);
+        if (quit) {
+            gave_up = true;
+            break;
+        }
+        __nanosleep(32);
+    }
+    if (m == 0) {
+        if (gave_up) atomicOr(&hdr->err, ERR_TIMEOUT);
+        atomicExch(look + (size_t)tile * kRadix + d, kFlagInc | ((excl + mine) & kValMask));
+    }
+    return excl;
+}
+
 // ---- culled tile binning (integer decisions, every FP32 operation explicitly rounded) --
 //
 // A pair is binned from the extent box of its alpha >= 1/255 ellipse d^T Sigma2^-1 d <= tau

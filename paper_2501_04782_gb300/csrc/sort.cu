@@ -11,6 +11,7 @@
 // ERR_TIMEOUT and publishes anyway; a block that gave up writes nothing (its output is
 // undefined but every write stays in bounds).
 #include <algorithm>
+#include <type_traits>
 #include <cstddef>
 
 #include "gv_internal.cuh"
@@ -64,7 +65,8 @@ struct PassArgs {
 };
 
 // RANGES: the last pass of a tile sort whose final list also gets each tile's range.
-template <int ITEMS, bool BALLOT, bool RANGES>
+// GROUPED: a digit of at most 4 live bits, its look-back walked by a group of threads.
+template <int ITEMS, bool BALLOT, bool RANGES, bool GROUPED>
 __global__ void __launch_bounds__(kSortThreads, 4) sort_pass_kernel(PassArgs a) {
     pdl_prologue();
     constexpr int TILE = kSortThreads * ITEMS;
@@ -151,10 +153,29 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_pass_kernel(PassArgs a) 
             s_whist[q][t] = total;
             total += c;
         }
-        // decoupled look-back for digit t (digits above the pass's live bits hold no key)
+        // decoupled look-back for digit t (digits above the pass's live bits hold no key);
+        // with at most 4 live bits, a group of G = 256 / 2^bits threads (16, or a warp) walks
+        // each digit's chain, G times as many predecessors per poll (960x540 tile pass, 2 bits:
+        // 22 -> 20 us; with 6 bits, groups of 4 were slower than one thread per digit)
         bool gave_up = false;
-        const unsigned excl =
-            t < (1 << a.dbits) ? lookback_digit(a.look_cur, tile, total, a.hdr, limit, drop, gave_up) : 0u;
+        unsigned excl = 0;
+        const unsigned ndig = 1u << a.dbits;
+        if (!GROUPED) {
+            if ((unsigned)t < ndig) excl = lookback_digit(a.look_cur, tile, total, a.hdr, limit, drop, gave_up);
+        } else {
+            s_gbase[t] = total;  // this tile's count of digit t, for its group
+            __syncthreads();
+            const int G = min(32, kRadix >> a.dbits), m = t % G;
+            const unsigned dg = (unsigned)(t / G);
+            const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << ((t & 31) - m);
+            unsigned ex = 0;
+            if (dg < ndig)
+                ex = lookback_digit_group(a.look_cur, tile, dg, s_gbase[dg], G, m, gmask, a.hdr, limit, drop, gave_up);
+            __syncthreads();  // every group has read its count
+            if (m == 0 && dg < ndig) s_gbase[dg] = ex;
+            __syncthreads();
+            excl = (unsigned)t < ndig ? s_gbase[t] : 0u;
+        }
         if (gave_up) s_abort = 1;
         unsigned dex;
         const unsigned nlive = block_excl_scan_256(total, s_scan, dex);
@@ -248,17 +269,20 @@ cudaError_t launch_radix_sort(const Work &w, unsigned *keys[2], unsigned *vals[2
         a.hdr = w.hdr;
         a.ranges = ps == passes - 1 ? final_ranges : nullptr;
         a.n_tiles = n_tiles;
-        if (a.ranges) {
-            if (items == 8) launch_pdl(sort_pass_kernel<8, false, true>, grid, kSortThreads, 0, s, a);
-            else if (items == 4) launch_pdl(sort_pass_kernel<4, false, true>, grid, kSortThreads, 0, s, a);
-            else if (n_cap < kSortBallotN) launch_pdl(sort_pass_kernel<12, false, true>, grid, kSortThreads, 0, s, a);
-            else launch_pdl(sort_pass_kernel<12, true, true>, grid, kSortThreads, 0, s, a);
-        } else {
-            if (items == 8) launch_pdl(sort_pass_kernel<8, false, false>, grid, kSortThreads, 0, s, a);
-            else if (items == 4) launch_pdl(sort_pass_kernel<4, false, false>, grid, kSortThreads, 0, s, a);
-            else if (n_cap < kSortBallotN) launch_pdl(sort_pass_kernel<12, false, false>, grid, kSortThreads, 0, s, a);
-            else launch_pdl(sort_pass_kernel<12, true, false>, grid, kSortThreads, 0, s, a);
-        }
+        // the kernel for this pass: keys per thread, ranking, range recording, grouped look-back
+        auto pick = [&](auto R, auto Gp) -> void (*)(PassArgs) {
+            constexpr bool RR = decltype(R)::value, GG = decltype(Gp)::value;
+            if (items == 8) return sort_pass_kernel<8, false, RR, GG>;
+            if (items == 4) return sort_pass_kernel<4, false, RR, GG>;
+            if (n_cap < kSortBallotN) return sort_pass_kernel<12, false, RR, GG>;
+            return sort_pass_kernel<12, true, RR, GG>;
+        };
+        const bool grouped = a.dbits <= 4;
+        void (*kern)(PassArgs) = a.ranges ? (grouped ? pick(std::true_type{}, std::true_type{})
+                                                     : pick(std::true_type{}, std::false_type{}))
+                                          : (grouped ? pick(std::false_type{}, std::true_type{})
+                                                     : pick(std::false_type{}, std::false_type{}));
+        launch_pdl(kern, grid, kSortThreads, 0, s, a);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
         cur ^= 1;
