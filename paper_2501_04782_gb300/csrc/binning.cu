@@ -48,7 +48,8 @@ __global__ void setup_kernel(Work w, FrameChunk chunk, int first, int count, int
 // (flag in the top two bits), and writes every pair's exclusive offset: off[i] for
 // i < n_drawn, off[n_drawn] = cells.  Each pair records the emission chunks whose first cell
 // it owns, and each block clears the emission's look-back words of the chunks that start in
-// its cells.  The block holding the last run checks the capacities: the kept keys (counted
+// its cells (warp 0 walks the look-back, 32 predecessors per poll).  The block holding the
+// last run checks the capacities: the kept keys (counted
 // by the projection) against the key capacity, the cells against the chunk table; on
 // overflow keys_total reports the key capacity the call needs.  Every wait is bounded: a
 // look-back that gives up sets ERR_TIMEOUT (the offsets are then wrong but every write
@@ -114,33 +115,58 @@ __global__ void __launch_bounds__(kEmitThreads) cell_offsets_kernel(Work w, cons
         }
         if (lane == 31) s_w[wid] = inc;
         __syncthreads();
-        if (t == 0) {
+        if (wid == 0) {  // warp 0 publishes this run's cells and finds the cells before it
             unsigned long long total = 0;
             for (int q = 0; q < kEmitThreads / 32; q++) total += s_w[q];
             unsigned long long excl = 0;
             if (b == 0) {
-                atomicExch(&w.scan_look[0], kScanInc | (total & kScanVal));
+                if (lane == 0) atomicExch(&w.scan_look[0], kScanInc | (total & kScanVal));
             } else {
-                atomicExch(&w.scan_look[b], kScanAgg | (total & kScanVal));
+                if (lane == 0) atomicExch(&w.scan_look[b], kScanAgg | (total & kScanVal));
+                // lane l reads predecessor j - l: one poll covers 32 runs; the walk ends at the
+                // nearest inclusive prefix, and waits at the nearest unpublished status
                 long long spins = 0;
                 int j = (int)b - 1;
                 for (;;) {
-                    const unsigned long long st = *((volatile unsigned long long *)&w.scan_look[j]);
+                    const int idx = j - lane;
+                    const unsigned long long past = kScanInc;  // before run 0: an empty prefix
+                    const unsigned long long st =
+                        idx >= 0 ? *((volatile unsigned long long *)&w.scan_look[idx]) : past;
                     const unsigned long long fl = st & ~kScanVal;
-                    if (fl == kScanInc) { excl += st & kScanVal; break; }
-                    if (fl == kScanAgg) { excl += st & kScanVal; j--; spins = 0; continue; }
-                    if (++spins > limit || (*((volatile unsigned *)&w.hdr->err) & ERR_TIMEOUT)) {
-                        atomicOr(&w.hdr->err, ERR_TIMEOUT);
+                    const unsigned stop = __ballot_sync(0xffffffffu, fl != kScanAgg);
+                    const int first = stop ? __ffs(stop) - 1 : 32;
+                    unsigned long long v = (lane < first || (lane == first && fl == kScanInc)) ? (st & kScanVal) : 0ull;
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    excl += v;
+                    if (first == 32) {
+                        j -= 32;
+                        spins = 0;
+                        continue;
+                    }
+                    const bool inc = __shfl_sync(0xffffffffu, fl == kScanInc, first);
+                    if (inc) break;
+                    j -= first;  // the aggregates before the unpublished status are taken
+                    if (first > 0) {
+                        spins = 0;
+                        continue;
+                    }
+                    bool quit = ++spins > limit || (*((volatile unsigned *)&w.hdr->err) & ERR_TIMEOUT);
+                    quit = __shfl_sync(0xffffffffu, quit, 0);
+                    if (quit) {
+                        if (lane == 0) atomicOr(&w.hdr->err, ERR_TIMEOUT);
                         break;
                     }
                     __nanosleep(32);
                 }
-                atomicExch(&w.scan_look[b], kScanInc | ((excl + total) & kScanVal));
+                if (lane == 0) atomicExch(&w.scan_look[b], kScanInc | ((excl + total) & kScanVal));
             }
-            s_excl = excl;
-            if (b == nblk - 1) {
-                w.offsets[nd] = (unsigned)min(excl + total, 0xFFFFFFFFull);
-                finish_cells(w, excl + total);
+            if (lane == 0) {
+                s_excl = excl;
+                if (b == nblk - 1) {
+                    w.offsets[nd] = (unsigned)min(excl + total, 0xFFFFFFFFull);
+                    finish_cells(w, excl + total);
+                }
             }
         }
         __syncthreads();
