@@ -571,7 +571,7 @@ __global__ void __launch_bounds__(TW *TH / PX) composite_bwd_kernel(Work w, cons
                 // S0 = sum dL/de, S1 = sum dL/de dy, S2 = sum dL/de dy^2 and the colour terms;
                 // the screen-space gradients follow by the chain rule of e: du = (2a'dx) S0 +
                 // b' S1, dv = (b'dx) S0 + 2c' S1, da' = dx^2 S0, db' = dx S1, dc' = S2, and
-                // dlog2o = S0 (alpha = 2^e, so dL/de carries the factor ln 2, applied to the sums).
+                // dlog2o = S0 (alpha = 2^e, so dL/de carries the factor ln 2, applied per term).
                 float2 A0, A1, A2, Cr, Cg, Cb;
 #pragma unroll
                 for (int k = 0; k < NP; k++) {
@@ -581,7 +581,8 @@ __global__ void __launch_bounds__(TW *TH / PX) composite_bwd_kernel(Work w, cons
                     const float2 al = make_float2(a0, a1);
                     // a pixel that does not composite this Gaussian has alpha 0: 1 / (1 - 0) is
                     // exactly 1 (the hardware reciprocal is exact on powers of two), so T stays
-                    const float2 ra = make_float2(rcp_approx(1.f - a0), rcp_approx(1.f - a1));
+                    const float2 om = __fadd2_rn(make_float2(1.f, 1.f), make_float2(-a0, -a1));
+                    const float2 ra = make_float2(rcp_approx(om.x), rcp_approx(om.y));
                     const float2 Tin = __fmul2_rn(T[k], ra);
                     const float2 wg = __fmul2_rn(al, Tin);
                     // dL/dalpha = sum_ch g_ch (c_ch Tin - S_ch / (1 - alpha)) = gc Tin + gS / (1 - alpha)
@@ -589,21 +590,23 @@ __global__ void __launch_bounds__(TW *TH / PX) composite_bwd_kernel(Work w, cons
                     const float2 dal = __ffma2_rn(gS[k], ra, __fmul2_rn(gc, Tin));
                     gS[k] = __ffma2_rn(make_float2(-gc.x, -gc.y), wg, gS[k]);
                     T[k] = Tin;
-                    // dL/de / ln 2 for the exponent e (alpha = 2^e unless clamped at 0.99)
-                    // (a < 0.99 ? a : 0) is r where composited below the clamp, else 0
-                    const float2 kk = make_float2(a0 < kAlphaMax ? a0 : 0.f, a1 < kAlphaMax ? a1 : 0.f);
+                    // dL/de for the exponent e: alpha = 2^e unless clamped at 0.99, so dalpha/de
+                    // is alpha ln 2 where composited below the clamp, else 0
+                    const float2 kk = __fmul2_rn(make_float2(a0 < kAlphaMax ? a0 : 0.f, a1 < kAlphaMax ? a1 : 0.f),
+                                                 dup2(kLn2));
                     const float2 de = __fmul2_rn(dal, kk);
                     const float2 ddy = __fmul2_rn(de, dy[k]);
-                    const float2 ddy2 = __fmul2_rn(ddy, dy[k]);
-                    const float2 dr = __fmul2_rn(wg, g0[k]), dg = __fmul2_rn(wg, g1[k]), db = __fmul2_rn(wg, g2[k]);
+                    // the moments and colour sums accumulate over the thread's pixels by fused
+                    // multiply-adds (one rounding per term)
                     if (k == 0) {
-                        A0 = de; A1 = ddy; A2 = ddy2; Cr = dr; Cg = dg; Cb = db;
+                        A0 = de; A1 = ddy; A2 = __fmul2_rn(ddy, dy[k]);
+                        Cr = __fmul2_rn(wg, g0[k]); Cg = __fmul2_rn(wg, g1[k]); Cb = __fmul2_rn(wg, g2[k]);
                     } else {
-                        A0 = __fadd2_rn(A0, de); A1 = __fadd2_rn(A1, ddy); A2 = __fadd2_rn(A2, ddy2);
-                        Cr = __fadd2_rn(Cr, dr); Cg = __fadd2_rn(Cg, dg); Cb = __fadd2_rn(Cb, db);
+                        A0 = __fadd2_rn(A0, de); A1 = __fadd2_rn(A1, ddy); A2 = __ffma2_rn(ddy, dy[k], A2);
+                        Cr = __ffma2_rn(wg, g0[k], Cr); Cg = __ffma2_rn(wg, g1[k], Cg); Cb = __ffma2_rn(wg, g2[k], Cb);
                     }
                 }
-                const float S0 = (A0.x + A0.y) * kLn2, S1 = (A1.x + A1.y) * kLn2, S2 = (A2.x + A2.y) * kLn2;
+                const float S0 = A0.x + A0.y, S1 = A1.x + A1.y, S2 = A2.x + A2.y;
                 const float vs[9] = {fmaf(f0.w, S1, 2.f * f0.z * dx * S0), fmaf(2.f * f1.x, S1, f0.w * dx * S0),
                                      dx * dx * S0, dx * S1, S2, S0, Cr.x + Cr.y, Cg.x + Cg.y, Cb.x + Cb.y};
                 if (__popc(act) <= kSparseLanes) {
