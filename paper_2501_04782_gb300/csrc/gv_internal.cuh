@@ -392,37 +392,45 @@ constexpr unsigned kFlagAgg = 1u << 30;
 constexpr unsigned kFlagInc = 2u << 30;
 constexpr unsigned kValMask = (1u << 30) - 1u;
 
-// Decoupled look-back of digit t = threadIdx.x for `tile` of a pass over look[tile][256]:
-// publishes the tile's own count (aggregate, then inclusive prefix) and returns the sum
-// of the counts of all earlier tiles.  The predecessors are read kLookWindow at a time
-// (independent loads in flight), their aggregates summed until an inclusive prefix is
-// found; an unpublished predecessor is polled again.  Every wait is bounded by `limit`
-// polls without progress; a wait that gives up (or finds ERR_TIMEOUT already set) sets
-// ERR_TIMEOUT and gave_up, publishes anyway and returns a partial sum: the caller then
-// writes nothing.  drop (test hook): tile 0 never publishes.
+// Decoupled look-back of one digit d of `tile` in a pass over look[tile][256], in two
+// steps so that a block can publish its counts as soon as it has them and walk its
+// predecessors only when it needs their sum (after its own shared-memory work, which gives
+// the predecessors that much longer to publish their inclusive prefixes):
+// - lookback_publish: the tile's own count of d (tile 0: directly as its inclusive prefix;
+//   others: as an aggregate).  drop (test hook): tile 0 never publishes.
+// - lookback_walk<WIN>: the sum of the counts of all earlier tiles.  The predecessors are
+//   read WIN at a time (independent loads in flight), their aggregates summed until an
+//   inclusive prefix is found; an unpublished predecessor is polled again.  Then the
+//   tile's inclusive prefix is published.  Every wait is bounded by `limit` polls without
+//   progress; a wait that gives up (or finds ERR_TIMEOUT already set) sets ERR_TIMEOUT and
+//   gave_up, publishes anyway and returns a partial sum: the caller then writes nothing.
 constexpr int kLookWindow = 4;
 
-__device__ __forceinline__ unsigned lookback_digit(unsigned *look, unsigned tile, unsigned mine, DevHeader *hdr,
-                                                   long long limit, bool drop, bool &gave_up) {
-    const unsigned t = threadIdx.x;
+__device__ __forceinline__ void lookback_publish(unsigned *look, unsigned tile, unsigned d, unsigned mine, bool drop) {
+    if (tile == 0) {
+        if (!drop) atomicExch(look + d, kFlagInc | mine);
+    } else {
+        atomicExch(look + (size_t)tile * kRadix + d, kFlagAgg | mine);
+    }
+}
+
+template <int WIN>
+__device__ __forceinline__ unsigned lookback_walk(unsigned *look, unsigned tile, unsigned d, unsigned mine,
+                                                  DevHeader *hdr, long long limit, bool &gave_up) {
     unsigned excl = 0;
     gave_up = false;
-    if (tile == 0) {
-        if (!drop) atomicExch(look + t, kFlagInc | mine);
-        return 0u;
-    }
-    atomicExch(look + (size_t)tile * kRadix + t, kFlagAgg | mine);
+    if (tile == 0) return 0u;
     long long spins = 0;
     int j = (int)tile - 1;
     bool found = false;
     while (!found) {
-        unsigned st[kLookWindow];
+        unsigned st[WIN];
 #pragma unroll
-        for (int k = 0; k < kLookWindow; k++)
-            st[k] = j - k >= 0 ? *((volatile unsigned *)(look + (size_t)(j - k) * kRadix + t)) : 0u;
+        for (int k = 0; k < WIN; k++)
+            st[k] = j - k >= 0 ? *((volatile unsigned *)(look + (size_t)(j - k) * kRadix + d)) : 0u;
         int adv = 0;
 #pragma unroll
-        for (int k = 0; k < kLookWindow; k++) {
+        for (int k = 0; k < WIN; k++) {
             if (found || adv < k || j - k < 0) continue;  // stop at the first unpublished status
             const unsigned fl = st[k] & ~kValMask;
             if (fl == kFlagInc) {
@@ -446,27 +454,23 @@ __device__ __forceinline__ unsigned lookback_digit(unsigned *look, unsigned tile
         __nanosleep(32);
     }
     if (gave_up) atomicOr(&hdr->err, ERR_TIMEOUT);
-    atomicExch(look + (size_t)tile * kRadix + t, kFlagInc | ((excl + mine) & kValMask));
+    atomicExch(look + (size_t)tile * kRadix + d, kFlagInc | ((excl + mine) & kValMask));
     return excl;
 }
 
-// Decoupled look-back of digit d by a group of G consecutive lanes of one warp (G a power of
-// two up to 32; member m = lane % G, gmask the group's lanes): the same protocol as
-// lookback_digit, but member m reads predecessors j - 4m .. j - 4m - 3, so one poll covers
-// 4G predecessors.  The group takes the nearest member whose window ends the walk (an
-// inclusive prefix, or an unpublished status) and sums the counts up to it; every member
-// returns the same sum.  Member 0 publishes.  Used by passes whose digit has fewer than 8
-// live bits, where the block has 256 / 2^bits threads per digit.
-__device__ __forceinline__ unsigned lookback_digit_group(unsigned *look, unsigned tile, unsigned d, unsigned mine,
-                                                         int G, int m, unsigned gmask, DevHeader *hdr,
-                                                         long long limit, bool drop, bool &gave_up) {
+// lookback_walk of digit d by a group of G consecutive lanes of one warp (G a power of two
+// up to 32; member m = lane % G, gmask the group's lanes), after lookback_publish: member m
+// reads predecessors j - 4m .. j - 4m - 3, so one poll covers 4G predecessors.  The group
+// takes the nearest member whose window ends the walk (an inclusive prefix, or an
+// unpublished status) and sums the counts up to it; every member returns the same sum.
+// Member 0 publishes the inclusive prefix.  Used by passes whose digit has fewer than 8 live
+// bits, where the block has 256 / 2^bits threads per digit.
+__device__ __forceinline__ unsigned lookback_walk_group(unsigned *look, unsigned tile, unsigned d, unsigned mine,
+                                                        int G, int m, unsigned gmask, DevHeader *hdr,
+                                                        long long limit, bool &gave_up) {
     const int base = (int)(threadIdx.x & 31u) - m;  // the group's first lane
     gave_up = false;
-    if (tile == 0) {
-        if (m == 0 && !drop) atomicExch(look + d, kFlagInc | mine);
-        return 0u;
-    }
-    if (m == 0) atomicExch(look + (size_t)tile * kRadix + d, kFlagAgg | mine);
+    if (tile == 0) return 0u;
     unsigned excl = 0;
     long long spins = 0;
     int j = (int)tile - 1;

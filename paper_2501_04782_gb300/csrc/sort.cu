@@ -2,9 +2,11 @@
 //
 // One pass is a single "onesweep" kernel: each block takes the next tile (256 x 4, 8 or 12
 // keys by the key count) from an atomic counter, ranks its keys stably per digit (warp
-// match or bit ballots + per-warp histograms), publishes its per-digit counts, obtains the
-// exclusive prefix of all earlier tiles by decoupled look-back, and scatters.  The per-digit global offsets come from one
-// histogram kernel that counts every pass's digits up front.  Keys and values are read
+// match or bit ballots + per-warp histograms), publishes its per-digit counts, stages its
+// keys in shared memory in digit order, obtains the exclusive prefix of all earlier tiles
+// by decoupled look-back (for a full 8-bit digit only after the staging), and scatters.
+// The per-digit global offsets come from one histogram kernel that counts every pass's
+// digits up front.  Keys and values are read
 // once and written once per pass (the HBM roofline of the sort).
 //
 // Bounded waits: a look-back spin gives up after DevHeader::spin_limit polls, sets
@@ -153,34 +155,26 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_pass_kernel(PassArgs a) 
             s_whist[q][t] = total;
             total += c;
         }
-        // decoupled look-back for digit t (digits above the pass's live bits hold no key);
-        // with at most 4 live bits, a group of G = 256 / 2^bits threads (16, or a warp) walks
-        // each digit's chain, G times as many predecessors per poll (960x540 tile pass, 2 bits:
-        // 22 -> 20 us; with 6 bits, groups of 4 were slower than one thread per digit)
+        // this tile's counts are published at once (digits above the pass's live bits hold no
+        // key).  With a full 8-bit digit the tile's keys go to shared memory in digit order
+        // before it walks its predecessors, which have that much longer to publish their
+        // inclusive prefixes (8 x 1080p depth sort 0.238 -> 0.220 ms); a digit of 5-7 bits walks
+        // at once, as its later inclusive prefix would lengthen its successors' walks more
+        // (tile pass 0.379 -> 0.389 ms when late).  With at most 4 live bits, a group of
+        // G = 256 / 2^bits threads (16, or a warp) walks each digit's chain, G times as many
+        // predecessors per poll (960x540 tile pass, 2 bits: 22 -> 20 us; with 6 bits, groups of
+        // 4 were slower than one thread per digit).
+        const unsigned ndig = 1u << a.dbits;
+        if ((unsigned)t < ndig) lookback_publish(a.look_cur, tile, (unsigned)t, total, drop);
+        if (GROUPED) s_gbase[t] = total;  // this tile's count of digit t, for its group
+        const bool early = !GROUPED && a.dbits < 8;
         bool gave_up = false;
         unsigned excl = 0;
-        const unsigned ndig = 1u << a.dbits;
-        if (!GROUPED) {
-            if ((unsigned)t < ndig) excl = lookback_digit(a.look_cur, tile, total, a.hdr, limit, drop, gave_up);
-        } else {
-            s_gbase[t] = total;  // this tile's count of digit t, for its group
-            __syncthreads();
-            const int G = min(32, kRadix >> a.dbits), m = t % G;
-            const unsigned dg = (unsigned)(t / G);
-            const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << ((t & 31) - m);
-            unsigned ex = 0;
-            if (dg < ndig)
-                ex = lookback_digit_group(a.look_cur, tile, dg, s_gbase[dg], G, m, gmask, a.hdr, limit, drop, gave_up);
-            __syncthreads();  // every group has read its count
-            if (m == 0 && dg < ndig) s_gbase[dg] = ex;
-            __syncthreads();
-            excl = (unsigned)t < ndig ? s_gbase[t] : 0u;
-        }
-        if (gave_up) s_abort = 1;
+        if (early && (unsigned)t < ndig)
+            excl = lookback_walk<kLookWindow>(a.look_cur, tile, (unsigned)t, total, a.hdr, limit, gave_up);
         unsigned dex;
         const unsigned nlive = block_excl_scan_256(total, s_scan, dex);
         s_dstart[t] = dex;
-        s_gbase[t] = s_gexcl[t] + excl;
         a.look_next[(size_t)tile * kRadix + t] = 0u;
         __syncthreads();
 #pragma unroll
@@ -191,6 +185,23 @@ __global__ void __launch_bounds__(kSortThreads, 4) sort_pass_kernel(PassArgs a) 
             s_keys[pos] = k[i];
             s_vals[pos] = v[i];
         }
+        if (!GROUPED) {
+            if (!early && (unsigned)t < ndig)
+                excl = lookback_walk<kLookWindow>(a.look_cur, tile, (unsigned)t, total, a.hdr, limit, gave_up);
+        } else {
+            const int G = min(32, kRadix >> a.dbits), m = t % G;
+            const unsigned dg = (unsigned)(t / G);
+            const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u) << ((t & 31) - m);
+            unsigned ex = 0;
+            if (dg < ndig)
+                ex = lookback_walk_group(a.look_cur, tile, dg, s_gbase[dg], G, m, gmask, a.hdr, limit, gave_up);
+            __syncthreads();  // every group has read its count
+            if (m == 0 && dg < ndig) s_gbase[dg] = ex;
+            __syncthreads();
+            excl = (unsigned)t < ndig ? s_gbase[t] : 0u;
+        }
+        if (gave_up) s_abort = 1;
+        s_gbase[t] = s_gexcl[t] + excl;
         __syncthreads();
         if (!s_abort) {
             for (int pos = t; pos < (int)nlive; pos += kSortThreads) {
