@@ -390,8 +390,8 @@ def run_gv(args):
     # workload); unknown (null) for other kernels or configurations
     o = ctx.options
     cfg_key = (dom, f"{o.tile_w}x{o.tile_h}", o.stage_depth)
-    ncu_traffic = {("composite_bwd", "32x16", 64): 15.057664e6, ("composite_bwd", "32x16", 128): 15.06688e6,
-                   ("composite_bwd", "32x16", 256): 15.07072e6}
+    ncu_traffic = {("composite_bwd", "32x16", 64): 15.063552e6, ("composite_bwd", "32x16", 128): 15.064064e6,
+                   ("composite_bwd", "32x16", 256): 15.061504e6}
     roofline = {"kernel": dom, "bound": d.get("bound"), "achieved": d.get("achieved"),
                 "peak": round(fp32_peak, 1) if d.get("bound") == "alu" else hbm_peak, "unit": d.get("unit"),
                 "frac": d.get("frac"), "traffic": ncu_traffic.get(cfg_key),
