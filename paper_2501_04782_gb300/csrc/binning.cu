@@ -215,7 +215,9 @@ __global__ void __launch_bounds__(kEmitThreads) cell_offsets_kernel(Work w, cons
 // compacted and sorted by the low tile digit, in depth order within a digit.  The global
 // digit offsets come from the projection's counts of the kept keys.
 constexpr int kEmitSmemFrames = 64;
-constexpr int kEmitStage = 256;  // pairs of a chunk whose records are staged in shared memory (8 x 1080p: 1.060 ms at 128, 1.034 at 256)
+// pairs of a chunk whose records are staged in shared memory (8 x 1920x1080 / 1M: emission
+// 1.060 ms with 128, 1.034 ms with 256)
+constexpr int kEmitStage = 256;
 constexpr int kEmitLookWindow = 4;  // predecessors read per poll of the emission's look-back
 
 struct EmitSortArgs {
