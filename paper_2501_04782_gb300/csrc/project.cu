@@ -904,48 +904,74 @@ __device__ __forceinline__ void sh_accumulate(const float *Y, int K, float4 g1, 
 
 // mode 0: one thread per pair, each Gaussian in at most one frame (plain +=)
 // mode 2: one thread per pair, overlapping sets (atomicAdd)
-// Grid-stride over the pairs; CAM: also the camera gradients of the frames; SPLINE: the
-// time-parameterised form.
+// A pair that binned nothing (no cell: culled, or its extent box off the frame) has a zero
+// screen-space gradient and adds exactly zero, so it is skipped: each warp takes a window
+// of 64 consecutive pairs, lists the ones that binned cells (in order, in shared memory)
+// and maps them 32 at a time, so its lanes stay busy when half the pairs are culled
+// (960x540 / 200k: 107k of 200k).  Grid-stride over the windows; CAM: also the camera
+// gradients of the frames; SPLINE: the time-parameterised form.
+constexpr int kBwdPairThreads = 128, kBwdPairWindow = 64;
+
 template <bool CAM, bool SPLINE, bool SH>
-__global__ void __launch_bounds__(128) project_bwd_pairs_kernel(Work w, GaussPtrs g, GradPtrs gr, int atomic) {
+__global__ void __launch_bounds__(kBwdPairThreads) project_bwd_pairs_kernel(Work w, GaussPtrs g, GradPtrs gr,
+                                                                            int atomic) {
     pdl_prologue();
     __shared__ float s_cam[CAM ? kCamSmemFrames : 1][kCamGrad];
+    __shared__ unsigned s_live[kBwdPairThreads / 32][kBwdPairWindow];
     const int F = (int)w.L.F;
     if (CAM) cam_block_init(s_cam, F);
-    for (unsigned base = blockIdx.x * blockDim.x; base < w.L.P; base += gridDim.x * blockDim.x) {
-        const unsigned p = base + threadIdx.x;
-        float cam[kCamGrad];
+    const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
+    const unsigned P = w.L.P, nwin = (P + kBwdPairWindow - 1) / kBwdPairWindow;
+    const unsigned nwarps = gridDim.x * (kBwdPairThreads / 32);
+    for (unsigned win = blockIdx.x * (kBwdPairThreads / 32) + wq; win < nwin; win += nwarps) {
+        const unsigned pa = win * kBwdPairWindow + lane, pb = pa + 32u;
+        const bool la = pa < P && w.rect[pa].z != 0u, lb = pb < P && w.rect[pb].z != 0u;
+        const unsigned ma = __ballot_sync(0xffffffffu, la), mb = __ballot_sync(0xffffffffu, lb);
+        const unsigned lt = lanemask_lt();
+        if (la) s_live[wq][__popc(ma & lt)] = pa;
+        if (lb) s_live[wq][__popc(ma) + __popc(mb & lt)] = pb;
+        __syncwarp();
+        const int n = __popc(ma) + __popc(mb);
+        for (int r = 0; r < n; r += 32) {
+            const bool live = r + lane < n;
+            float cam[kCamGrad];
 #pragma unroll
-        for (int k = 0; k < kCamGrad; k++) cam[k] = 0.f;
-        int f = F - 1;
-        if (p < w.L.P) {
-            f = find_frame_by_pair(w.frames, F, p);
-            const DevFrame &fr = w.frames[f];
-            long long gi = fr.gauss_offset + (long long)(p - fr.pair_offset);
-            PairState<float> st;
-            load_and_project<float, SPLINE>(g, gi, fr, st);
-            float acc[17];
+            for (int k = 0; k < kCamGrad; k++) cam[k] = 0.f;
+            int f = F - 1;
+            if (live) {
+                const unsigned p = s_live[wq][r + lane];
+                f = find_frame_by_pair(w.frames, F, p);
+                const DevFrame &fr = w.frames[f];
+                long long gi = fr.gauss_offset + (long long)(p - fr.pair_offset);
+                PairState<float> st;
+                load_and_project<float, SPLINE>(g, gi, fr, st);
+                float acc[17];
 #pragma unroll
-            for (int k = 0; k < 17; k++) acc[k] = 0.f;
-            const bool deferred = (w.rect[p].w & kRectFp64) != 0u;
-            float shY[SH ? kShMax : 1];
-            const float4 g1 = w.g1[p];
-            const float g2 = w.g2[p];
-            const bool live = pair_backward<SH>(st, deferred, fr, w.g0[p], g1, g2, acc, CAM ? cam : nullptr, &g, gi,
-                                                shY);
-            if (SH) {
-                // a deferred pair's mean rows hold the direction term only; the FP64 kernel
-                // adds the geometric part to the same planes concurrently
-                store_grad(gr, g.N, gi, acc, atomic != 0, deferred, false, SPLINE);
-                if (SPLINE) store_grad_time(gr, g, fr, gi, acc, atomic != 0 || deferred);
-                const float dc[3] = {g1.z, g1.w, g2};
-                if (live) store_grad_sh(gr, g, gi, shY, dc, nullptr, atomic != 0);
-            } else {
-                store_grad(gr, g.N, gi, acc, atomic != 0, false, deferred, SPLINE);
-                if (SPLINE && !deferred) store_grad_time(gr, g, fr, gi, acc, atomic != 0);
+                for (int k = 0; k < 17; k++) acc[k] = 0.f;
+                const bool deferred = (w.rect[p].w & kRectFp64) != 0u;
+                float shY[SH ? kShMax : 1];
+                const float4 g1 = w.g1[p];
+                const float g2 = w.g2[p];
+                const bool sh_live = pair_backward<SH>(st, deferred, fr, w.g0[p], g1, g2, acc, CAM ? cam : nullptr, &g,
+                                                       gi, shY);
+                if (SH) {
+                    // a deferred pair's mean rows hold the direction term only; the FP64 kernel
+                    // adds the geometric part to the same planes concurrently
+                    store_grad(gr, g.N, gi, acc, atomic != 0, deferred, false, SPLINE);
+                    if (SPLINE) store_grad_time(gr, g, fr, gi, acc, atomic != 0 || deferred);
+                    const float dc[3] = {g1.z, g1.w, g2};
+                    if (sh_live) store_grad_sh(gr, g, gi, shY, dc, nullptr, atomic != 0);
+                } else {
+                    store_grad(gr, g.N, gi, acc, atomic != 0, false, deferred, SPLINE);
+                    if (SPLINE && !deferred) store_grad_time(gr, g, fr, gi, acc, atomic != 0);
+                }
+            }
+            if (CAM) {  // an idle lane (zero gradient) takes lane 0's frame
+                const int fl = __shfl_sync(0xffffffffu, f, 0);
+                cam_add(cam, live ? f : fl, s_cam, gr.cam);
             }
         }
-        if (CAM) cam_add(cam, f, s_cam, gr.cam);
+        __syncwarp();  // the window's list is read before the next one overwrites it
     }
     if (CAM) cam_block_flush(s_cam, F, gr.cam);
 }
@@ -1154,11 +1180,12 @@ cudaError_t launch_project_bwd(const Work &w, const GaussPtrs &g, const GradPtrs
                        128, 0, s, w, g, gr);
         });
     } else {
-        unsigned blocks = std::min((w.L.P + 127) / 128, (unsigned)num_sms * 16u);
+        const unsigned per_block = kBwdPairThreads / 32 * kBwdPairWindow;  // one window per warp
+        unsigned blocks = std::min((w.L.P + per_block - 1) / per_block, (unsigned)num_sms * 16u);
         const int at = mode == 2 ? 1 : 0;
         dispatch_bwd(gr.cam != nullptr, g.n_ctrl > 0, g.sh_degree > 0, [&](auto C, auto S, auto H) {
             launch_pdl(project_bwd_pairs_kernel<decltype(C)::value, decltype(S)::value, decltype(H)::value>, blocks,
-                       128, 0, s, w, g, gr, at);
+                       kBwdPairThreads, 0, s, w, g, gr, at);
         });
     }
     return cudaGetLastError();
