@@ -906,26 +906,32 @@ __device__ __forceinline__ void sh_accumulate(const float *Y, int K, float4 g1, 
 // mode 2: one thread per pair, overlapping sets (atomicAdd)
 // A pair that binned nothing (no cell: culled, or its extent box off the frame) has a zero
 // screen-space gradient and adds exactly zero, so it is skipped: each warp takes a window
-// of 64 consecutive pairs, lists the ones that binned cells (in order, in shared memory)
-// and maps them 32 at a time, so its lanes stay busy when half the pairs are culled
-// (960x540 / 200k: 107k of 200k).  Grid-stride over the windows; CAM: also the camera
-// gradients of the frames; SPLINE: the time-parameterised form.
+// of consecutive pairs, lists the ones that binned cells (in order, in shared memory) and
+// maps them 32 at a time.  When at most half the pairs binned cells (960x540 / 200k: 93k
+// of 200k) a window is 64 pairs, whose live ones mostly fill one round of the warp's lanes;
+// otherwise 32, one round per window as with a thread per pair.  Grid-stride over the
+// windows; CAM: also the camera gradients of the frames; SPLINE: the time-parameterised form.
+// Without SH or CAM the kernel keeps six blocks per SM (80 registers; uncapped, the
+// time-parameterised form took 94 and ran 0.051 -> 0.071 ms at 960x540 / 200k).
 constexpr int kBwdPairThreads = 128, kBwdPairWindow = 64;
 
 template <bool CAM, bool SPLINE, bool SH>
-__global__ void __launch_bounds__(kBwdPairThreads) project_bwd_pairs_kernel(Work w, GaussPtrs g, GradPtrs gr,
-                                                                            int atomic) {
+__global__ void __launch_bounds__(kBwdPairThreads, (SH || CAM) ? 0 : 6)
+    project_bwd_pairs_kernel(Work w, GaussPtrs g, GradPtrs gr, int atomic) {
     pdl_prologue();
     __shared__ float s_cam[CAM ? kCamSmemFrames : 1][kCamGrad];
     __shared__ unsigned s_live[kBwdPairThreads / 32][kBwdPairWindow];
     const int F = (int)w.L.F;
     if (CAM) cam_block_init(s_cam, F);
     const int lane = threadIdx.x & 31, wq = threadIdx.x >> 5;
-    const unsigned P = w.L.P, nwin = (P + kBwdPairWindow - 1) / kBwdPairWindow;
+    const unsigned P = w.L.P;
+    const unsigned win_pairs = 2u * min(w.hdr->n_drawn, P) <= P ? (unsigned)kBwdPairWindow : 32u;
+    const unsigned nwin = (P + win_pairs - 1) / win_pairs;
     const unsigned nwarps = gridDim.x * (kBwdPairThreads / 32);
     for (unsigned win = blockIdx.x * (kBwdPairThreads / 32) + wq; win < nwin; win += nwarps) {
-        const unsigned pa = win * kBwdPairWindow + lane, pb = pa + 32u;
-        const bool la = pa < P && w.rect[pa].z != 0u, lb = pb < P && w.rect[pb].z != 0u;
+        const unsigned pa = win * win_pairs + lane, pb = pa + 32u;
+        const bool la = pa < P && w.rect[pa].z != 0u;
+        const bool lb = win_pairs > 32u && pb < P && w.rect[pb].z != 0u;
         const unsigned ma = __ballot_sync(0xffffffffu, la), mb = __ballot_sync(0xffffffffu, lb);
         const unsigned lt = lanemask_lt();
         if (la) s_live[wq][__popc(ma & lt)] = pa;
@@ -1180,8 +1186,8 @@ cudaError_t launch_project_bwd(const Work &w, const GaussPtrs &g, const GradPtrs
                        128, 0, s, w, g, gr);
         });
     } else {
-        const unsigned per_block = kBwdPairThreads / 32 * kBwdPairWindow;  // one window per warp
-        unsigned blocks = std::min((w.L.P + per_block - 1) / per_block, (unsigned)num_sms * 16u);
+        // one 32-pair window per warp (the 64-pair windows leave half the warps without one)
+        unsigned blocks = std::min((w.L.P + kBwdPairThreads - 1) / kBwdPairThreads, (unsigned)num_sms * 16u);
         const int at = mode == 2 ? 1 : 0;
         dispatch_bwd(gr.cam != nullptr, g.n_ctrl > 0, g.sh_degree > 0, [&](auto C, auto S, auto H) {
             launch_pdl(project_bwd_pairs_kernel<decltype(C)::value, decltype(S)::value, decltype(H)::value>, blocks,
